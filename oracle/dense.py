@@ -1,0 +1,199 @@
+"""Dense FP64 oracle for the Whittaker-Henderson smoother (test infrastructure).
+
+This is the plain, slow, obviously correct CPU statement of what the GPU path
+computes. Only the test-suite, the smoke check and the CPU-baseline leg of the
+benchmark may import it; the product path never does. It shares no code with the
+CUDA path: it builds the full T x T matrices and calls LAPACK.
+
+Notation (Section 2 of the paper): x in R^T observations, W = diag(w) observation
+weights, D in R^{(T-d) x T} the order-d difference operator (the paper's order
+k+1, written d here), Lambda = diag(lam_0 .. lam_{T-d-1}) per-row smoothing
+weights, Omega = W + D^T Lambda D (Section 3).
+
+Readings of the paper used here (each one also appears in the design notes):
+  * Lambda has one entry per row of D; the per-day input array has length T and
+    its last d entries are ignored (their gradient is 0).
+  * D is the unscaled binomial forward difference on a regular daily grid.
+  * Eq. 5 prints W Omega^{-1}; the vector-Jacobian product is dL/dx = W Omega^{-1} g.
+  * GCV (not defined in the paper) is the Craven-Wahba score
+    V = n_eff * RSS / (n_eff - tr H)^2 with H = Omega^{-1} W, summed over bands.
+"""
+from __future__ import annotations
+
+from math import comb
+
+import numpy as np
+import scipy.linalg as sla
+
+
+def diff_coeffs(d: int) -> np.ndarray:
+    """c_i = (-1)^(d-i) C(d, i), i = 0..d: row k of D is c at columns k..k+d (Section 2)."""
+    return np.array([(-1) ** (d - i) * comb(d, i) for i in range(d + 1)], dtype=np.float64)
+
+
+def difference_matrix(T: int, d: int) -> np.ndarray:
+    """The order-d discrete difference operator D in R^{(T-d) x T} (Section 2)."""
+    c = diff_coeffs(d)
+    D = np.zeros((max(T - d, 0), T), dtype=np.float64)
+    for k in range(T - d):
+        D[k, k:k + d + 1] = c
+    return D
+
+
+def lam_rows(lam, T: int, d: int) -> np.ndarray:
+    """Diagonal of Lambda (length T-d) from a scalar (Eq. 2) or a length-T per-day array (Eq. 3)."""
+    lam = np.asarray(lam, dtype=np.float64)
+    if lam.ndim == 0:
+        return np.full(max(T - d, 0), float(lam))
+    return lam[: max(T - d, 0)].copy()
+
+
+def omega(w, lam, d: int) -> np.ndarray:
+    """Omega = W + D^T Lambda D (Eq. 3; Eq. 2 when lam is a scalar)."""
+    w = np.asarray(w, dtype=np.float64)
+    T = w.shape[0]
+    D = difference_matrix(T, d)
+    return np.diag(w) + D.T @ (lam_rows(lam, T, d)[:, None] * D)
+
+
+def smooth_one(x, w, lam, d: int) -> np.ndarray:
+    """z = Omega^{-1} W x for one series; x may be [T] or [T, B] (bands as right-hand sides).
+
+    Dense Cholesky Omega = L L^T, then L y = W x and L^T z = y (Section 3.1).
+    Raises numpy.linalg.LinAlgError when Omega is not positive definite."""
+    x = np.asarray(x, dtype=np.float64)
+    w = np.asarray(w, dtype=np.float64)
+    O = omega(w, lam, d)
+    L = np.linalg.cholesky(O)
+    wx = np.where(w[:, None] > 0, w[:, None] * np.nan_to_num(x.reshape(len(w), -1)), 0.0)
+    y = sla.solve_triangular(L, wx, lower=True)
+    z = sla.solve_triangular(L.T, y, lower=False)
+    return z.reshape(x.shape)
+
+
+def solve_one(w, lam, d: int, rhs) -> np.ndarray:
+    """g = Omega^{-1} rhs (rhs [T] or [T, B])."""
+    O = omega(w, lam, d)
+    L = np.linalg.cholesky(O)
+    r = np.asarray(rhs, dtype=np.float64).reshape(O.shape[0], -1)
+    y = sla.solve_triangular(L, r, lower=True)
+    return sla.solve_triangular(L.T, y, lower=False).reshape(np.shape(rhs))
+
+
+def vjp_one(w, lam, d: int, z, gz, per_day: bool = True):
+    """Reverse-mode derivatives of L(z) through z = Omega^{-1} W x (Section 2.3).
+
+    g = Omega^{-1} dL/dz (Omega is symmetric), then
+      dL/dx_b     = W g_b                                  (Eq. 5, transposed)
+      dL/dlam_k   = - sum_b (d_k^T g_b)(d_k^T z_b)          (Eq. 4, k < T-d)
+    Per-day lambda: returns an array of length T with zeros in the last d entries.
+    Scalar lambda: returns the sum over k (lambda multiplies every row of D)."""
+    w = np.asarray(w, dtype=np.float64)
+    T = w.shape[0]
+    z2 = np.asarray(z, dtype=np.float64).reshape(T, -1)
+    g2 = solve_one(w, lam, d, np.asarray(gz, dtype=np.float64).reshape(T, -1))
+    gx = w[:, None] * g2
+    D = difference_matrix(T, d)
+    glam_rows = -np.sum((D @ g2) * (D @ z2), axis=1)
+    if per_day:
+        glam = np.zeros(T)
+        glam[: T - d] = glam_rows
+    else:
+        glam = np.array(glam_rows.sum())
+    return gx.reshape(np.shape(z)), glam
+
+
+def smooth_tile(x, w, lam, d: int):
+    """Batch over pixels in the tile layout x[t, b, p], w[t, p], lam[t, p] or lam[p].
+
+    Returns (z[t, b, p], ok[p]); series whose Omega is not positive definite get
+    ok = False and z = 0."""
+    x = np.asarray(x, dtype=np.float64)
+    w = np.asarray(w, dtype=np.float64)
+    lam = np.asarray(lam, dtype=np.float64)
+    T, B, P = x.shape
+    z = np.zeros_like(x)
+    ok = np.ones(P, dtype=bool)
+    for p in range(P):
+        lp = lam[p] if lam.ndim == 1 else lam[:, p]
+        try:
+            z[:, :, p] = smooth_one(x[:, :, p], w[:, p], lp, d)
+        except np.linalg.LinAlgError:
+            ok[p] = False
+    return z, ok
+
+
+def vjp_tile(w, lam, d: int, z, gz, log_lambda: bool = False):
+    """Tile-layout VJP: returns (gx[t,b,p], glam[t,p]); with log_lambda, dL/dlog(lam) = lam * dL/dlam."""
+    w = np.asarray(w, dtype=np.float64)
+    lam = np.asarray(lam, dtype=np.float64)
+    z = np.asarray(z, dtype=np.float64)
+    gz = np.asarray(gz, dtype=np.float64)
+    T, B, P = z.shape
+    gx = np.zeros_like(z)
+    glam = np.zeros((T, P)) if lam.ndim == 2 else np.zeros(P)
+    for p in range(P):
+        lp = lam[p] if lam.ndim == 1 else lam[:, p]
+        a, b = vjp_one(w[:, p], lp, d, z[:, :, p], gz[:, :, p], per_day=(lam.ndim == 2))
+        gx[:, :, p] = a
+        if lam.ndim == 2:
+            glam[:, p] = b * lp if log_lambda else b
+        else:
+            glam[p] = b * lp if log_lambda else b
+    return gx, glam
+
+
+def hat_trace(w, lam, d: int) -> float:
+    """tr H with H = Omega^{-1} W: sum_t w_t (Omega^{-1})_tt, from the dense inverse."""
+    w = np.asarray(w, dtype=np.float64)
+    Oi = np.linalg.inv(omega(w, lam, d))
+    return float(np.sum(w * np.diag(Oi)))
+
+
+def inverse_diag(w, lam, d: int) -> np.ndarray:
+    """diag(Omega^{-1}) from the dense inverse."""
+    return np.diag(np.linalg.inv(omega(np.asarray(w, dtype=np.float64), lam, d))).copy()
+
+
+def gcv_one(x, w, lam_grid, d: int):
+    """Grid search of a scalar lambda by generalized cross-validation.
+
+    For each grid value: z = Omega^{-1} W x (bands as right-hand sides),
+    RSS = sum_b sum_t w_t (x_tb - z_tb)^2, tr H = sum_t w_t (Omega^{-1})_tt,
+    n = sum_t w_t, and V = (n B) RSS / (n B - B tr H)^2. The smallest V wins;
+    ties go to the smaller lambda. Returns (best index, scores, z at the best)."""
+    x = np.asarray(x, dtype=np.float64)
+    w = np.asarray(w, dtype=np.float64)
+    T = w.shape[0]
+    x2 = x.reshape(T, -1)
+    B = x2.shape[1]
+    n = float(np.sum(w))
+    scores = []
+    for lam in lam_grid:
+        z = smooth_one(x2, w, float(lam), d)
+        rss = float(np.sum(w[:, None] * (np.where(w[:, None] > 0, x2, 0.0) - z) ** 2))
+        tr = hat_trace(w, float(lam), d)
+        scores.append(n * B * rss / (n * B - B * tr) ** 2)
+    scores = np.array(scores)
+    best = int(np.argmin(scores))          # argmin returns the first (smallest lambda) on ties
+    zb = smooth_one(x2, w, float(lam_grid[best]), d).reshape(x.shape)
+    return best, scores, zb
+
+
+def mse_maxe(z, x, w):
+    """Reconstruction metrics of Section 4.4: MSE = T^-1 sum_t W_tt (z_t - x_t)^2 and
+    MaxE = max_t W_tt |z_t - x_t|."""
+    z = np.asarray(z, dtype=np.float64)
+    x = np.asarray(x, dtype=np.float64)
+    w = np.asarray(w, dtype=np.float64)
+    r = w * np.abs(z - np.where(w > 0, x, 0.0))
+    return float(np.sum(w * (z - np.where(w > 0, x, 0.0)) ** 2) / z.shape[0]), float(np.max(r))
+
+
+def rel_err(a, b, axis_t: int = 0) -> float:
+    """Max over series/bands of ||a - b||_inf / max(||b||_inf, 1e-6), the inf-norm taken over time."""
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    num = np.max(np.abs(a - b), axis=axis_t)
+    den = np.maximum(np.max(np.abs(b), axis=axis_t), 1e-6)
+    return float(np.max(num / den)) if num.size else 0.0
