@@ -1,0 +1,383 @@
+#!/usr/bin/env python
+"""Throughput of the Whittaker-Henderson hot path on one 512x512-pixel tile.
+
+Workload (synthetic, seeded, generated on the device): 262,144 pixel series, T = 3288
+daily steps (2016-01-01 .. 2024-12-31), d = 2, 10 spectral bands sharing the weights
+and a per-day lambda = 10^U[1,5] smoothed over 15 days, FP32. One step is the smooth
+(Eq. 3, forward and backward sweeps) plus the adjoint (Eqs. 4-5: gradients with
+respect to x and log lambda) over the whole tile. Inputs (34.5 GB of x alone) are far
+larger than the 126 MB L2, so no flush is needed between steps.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line (rank 0). Under torchrun every rank processes its own tile
+(different series ids, no collective on the data path): weak scaling, value = the
+series of all ranks / the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "series/s fwd and fwd+bwd at T=3288,d=2; HBM roofline %; learned-λ vs GCV time"
+FALLBACK_HBM_GBS = 6400.0
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--pixels", type=int, default=262144, help="series per rank (262144 = the full tile)")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU work of the oracle baseline")
+    return ap.parse_args()
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            j = json.load(f)
+        return float(j["hbm_gbs"]), "measured"
+    return FALLBACK_HBM_GBS, "fallback"
+
+
+def kernel_sources_sha():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2604_00048_b300", "csrc")
+    for name in sorted(os.listdir(csrc)):
+        with open(os.path.join(csrc, name), "rb") as f:
+            h.update(name.encode())
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def traffic_from_profile(kernel: str):
+    """DRAM bytes per launch recorded by an ncu capture summary under profiles/, or None
+    when the summary is missing or was taken on different kernel sources."""
+    pdir = os.path.join(ROOT, "profiles")
+    if not os.path.isdir(pdir):
+        return None
+    want = kernel_sources_sha()
+    for name in sorted(os.listdir(pdir)):
+        if not name.endswith(".md") or not name.startswith(kernel):
+            continue
+        txt = open(os.path.join(pdir, name)).read()
+        m = re.search(r"traffic_bytes_per_full_launch:\s*([0-9.eE+]+)", txt)
+        s = re.search(r"source_sha256:\s*([0-9a-f]+)", txt)
+        if m and s and s.group(1) == want:
+            return float(m.group(1))
+    return None
+
+
+class ClockSampler:
+    """nvidia-smi samples (200 ms) of SM clock and throttle reasons during the timed region."""
+
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id: str):
+        self.gpu_id = gpu_id
+        self.rows = []
+        self.proc = None
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", self.gpu_id, f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([c.strip() for c in line.split(",")])
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=5)
+        sm = [float(r[0]) for r in self.rows if len(r) >= 8 and r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in self.rows if len(r) >= 8 and r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in self.rows if len(r) >= 8 for i in range(4) if r[4 + i] == "Active"})
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": reasons, "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(sm)}
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def cpu_oracle_rate(x, w, lam, gz, d, target_s, with_bwd=True):
+    """Banded FP64 oracle (Algorithm 1, OpenMP over pixels) on a bounded pixel sample:
+    returns (series/s, cores, sample description)."""
+    import numpy as np
+
+    from oracle import banded
+
+    cores = banded.max_threads()
+    P = x.shape[2]
+    n = min(P, 64)
+    t0 = time.perf_counter()
+    z, _ = banded.smooth_tile(x[:, :, :n], w[:, :n], lam[:, :n], d)
+    if with_bwd:
+        banded.vjp_tile(w[:, :n], lam[:, :n], d, z, gz[:, :, :n], log_lambda=True)
+    dt = time.perf_counter() - t0
+    n2 = int(min(P, max(n, n * target_s / max(dt, 1e-3))))
+    if n2 > n:
+        t0 = time.perf_counter()
+        z, _ = banded.smooth_tile(x[:, :, :n2], w[:, :n2], lam[:, :n2], d)
+        if with_bwd:
+            banded.vjp_tile(w[:, :n2], lam[:, :n2], d, z, gz[:, :, :n2], log_lambda=True)
+        dt = time.perf_counter() - t0
+        n = n2
+    return n / dt, cores, f"{n} of the tile's series (all {x.shape[0]} days, {x.shape[1]} bands), FP64"
+
+
+def run_reference(args):
+    """Reference arm: the CPU oracle as it stands, timed on this host's cores."""
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    import numpy as np
+    import torch
+
+    from paper_2604_00048_b300 import synth
+
+    rc = synth.RECIPES["hetero_tile"]
+    n = 512
+    inp = synth.generate_tile(rc, n, device="cpu", dtype=torch.float32)
+    x, w, lam = (inp[k].double().numpy() for k in ("x", "w", "lam"))
+    gz = np.random.default_rng(7).normal(size=x.shape)
+    from oracle import banded
+
+    times = []
+    for i in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        z, _ = banded.smooth_tile(x, w, lam, rc.d)
+        banded.vjp_tile(w, lam, rc.d, z, gz, log_lambda=True)
+        if i >= args.warmup:
+            times.append(time.perf_counter() - t0)
+    dt = sum(times)
+    val = n * len(times) / dt
+    cores = banded.max_threads()
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": "series/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / len(times),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "hetero_tile: 262144 px x 3288 d x 10 bands, d=2, fwd+bwd",
+                       "sample_series_per_step": n, "parallelism": "cpu"},
+            "cpu_baseline": {"value": val, "unit": "series/s", "cores": cores, "kind": "oracle",
+                             "sample": f"{n} series per step of the tile (3288 days, 10 bands), FP64 banded oracle"},
+            "e2e": {"value": val, "unit": "series/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local)
+
+    from paper_2604_00048_b300 import synth, ws
+
+    rc = synth.RECIPES["hetero_tile"]
+    P, T, B, d = args.pixels, rc.T, rc.n_bands, rc.d
+    series0 = rank * P
+    inp = synth.generate_tile(rc, P, series0=series0, device=dev, dtype=torch.float32)
+    x, w, lam = inp["x"], inp["w"], inp["lam"]
+    del inp
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(20260102 + rank)
+    z = torch.empty_like(x)
+    status = torch.empty(P, dtype=torch.uint8, device=dev)
+    has_bwd = hasattr(ws, "smooth_adjoint")
+    if has_bwd:
+        gz = torch.randn(x.shape, generator=gen, device=dev, dtype=torch.float32)
+        gx = torch.empty_like(x)
+        glam = torch.empty_like(lam)
+    stream = torch.cuda.Stream(device=dev)
+    ev = []
+
+    def step(record):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e2 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        ws.smooth(x, w, lam, d, z=z, status=status, stream=stream)
+        e1.record(stream)
+        if has_bwd:
+            ws.smooth_adjoint(w, lam, z, gz, d, gx=gx, glam=glam, log_lambda=True, stream=stream)
+        e2.record(stream)
+        if record:
+            ev.append((e0, e1, e2))
+
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            step(False)
+    torch.cuda.synchronize()
+    ws.sync_status(dev, stream)
+    bad = int((status != 0).sum().item())
+
+    gpu_uuid = str(torch.cuda.get_device_properties(dev).uuid)
+    clocks = ClockSampler(gpu_uuid if gpu_uuid.startswith("GPU-") else f"GPU-{gpu_uuid}")
+    clocks.start()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    t_start.record(stream)
+    with torch.cuda.stream(stream):
+        for _ in range(args.steps):
+            step(True)
+    t_end.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    ck = clocks.stop()
+    ms = t_start.elapsed_time(t_end)
+    ws.sync_status(dev, stream)
+    if world > 1:
+        tt = torch.tensor([ms], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms = float(tt.item())
+    fwd_ms = statistics.median([a.elapsed_time(b) for a, b, _ in ev])
+    bwd_ms = statistics.median([b.elapsed_time(c) for _, b, c in ev]) if has_bwd else 0.0
+    ms_step = ms / args.steps
+    value = P * world * args.steps / (ms / 1e3)
+
+    # roofline of the dominant kernel: algorithmic bytes per pixel-day, FP32
+    pd = float(P) * T
+    fwd_bytes = 4.0 * (2 * B + 2) * pd          # read x (B), w, lambda; write z (B)
+    bwd_bytes = 4.0 * (3 * B + 3) * pd          # read gz, z (2B), w, lambda; write gx (B), glam
+    hbm, peak_kind = peaks()
+    if has_bwd and bwd_ms > fwd_ms:
+        kname, kms, kbytes = "adjoint_tile", bwd_ms, bwd_bytes
+    else:
+        kname, kms, kbytes = "smooth_tile", fwd_ms, fwd_bytes
+    achieved = kbytes / (kms / 1e3) / 1e9
+    traffic = traffic_from_profile(kname)
+    roof = {"bound": "hbm", "kernel": kname, "achieved": achieved, "peak": hbm, "unit": "GB/s",
+            "frac": achieved / hbm, "peak_kind": f"{peak_kind} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)"
+            if peak_kind == "measured" else "fallback", "traffic": traffic,
+            "algorithmic_bytes_per_launch": kbytes, "kernel_ms": kms}
+
+    # end to end through the C-ABI with host buffers (pinned), on a block of the tile
+    e2e = None
+    if not args.no_e2e:
+        Pe = min(P, 32768)
+        hx = x[:, :, :Pe].contiguous().cpu().pin_memory()
+        hw = w[:, :Pe].contiguous().cpu().pin_memory()
+        hl = lam[:, :Pe].contiguous().cpu().pin_memory()
+        hz = torch.empty_like(hx).pin_memory()
+        dx, dw, dl, dz = (torch.empty_like(t, device=dev) for t in (hx, hw, hl, hx))
+        st_e = torch.empty(Pe, dtype=torch.uint8, device=dev)
+        if has_bwd:
+            hg = gz[:, :, :Pe].contiguous().cpu().pin_memory()
+            hgx = torch.empty_like(hx).pin_memory()
+            hgl = torch.empty_like(hl).pin_memory()
+            dg, dgx, dgl = torch.empty_like(hg, device=dev), torch.empty_like(hx, device=dev), torch.empty_like(hl, device=dev)
+
+        def e2e_step():
+            with torch.cuda.stream(stream):
+                dx.copy_(hx, non_blocking=True)
+                dw.copy_(hw, non_blocking=True)
+                dl.copy_(hl, non_blocking=True)
+                ws.smooth(dx, dw, dl, d, z=dz, status=st_e, stream=stream)
+                if has_bwd:
+                    dg.copy_(hg, non_blocking=True)
+                    ws.smooth_adjoint(dw, dl, dz, dg, d, gx=dgx, glam=dgl, log_lambda=True, stream=stream)
+                    hgx.copy_(dgx, non_blocking=True)
+                    hgl.copy_(dgl, non_blocking=True)
+                hz.copy_(dz, non_blocking=True)
+            stream.synchronize()
+
+        e2e_step()
+        ke = max(2, min(args.steps, 5))
+        t0 = time.perf_counter()
+        for _ in range(ke):
+            e2e_step()
+        dt = time.perf_counter() - t0
+        h2d = hx.numel() * 4 + hw.numel() * 4 + hl.numel() * 4 + (hg.numel() * 4 if has_bwd else 0)
+        d2h = hz.numel() * 4 + ((hgx.numel() + hgl.numel()) * 4 if has_bwd else 0)
+        e2e = {"value": Pe * world * ke / dt, "unit": "series/s", "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": d2h, "series_per_step": Pe,
+               "note": "pinned host buffers, copies + C-ABI calls + sync inside the timed region, "
+                       f"{Pe}-series block of the tile"}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        ns = 2048
+        xs = x[:, :, :ns].double().cpu().numpy()
+        wsn = w[:, :ns].double().cpu().numpy()
+        ls = lam[:, :ns].double().cpu().numpy()
+        gs = gz[:, :, :ns].double().cpu().numpy() if has_bwd else np.zeros_like(xs)
+        rate, cores, sample = cpu_oracle_rate(xs, wsn, ls, gs, d, args.cpu_seconds, with_bwd=has_bwd)
+        cpu = {"value": rate, "unit": "series/s", "cores": cores, "kind": "oracle", "sample": sample}
+
+    launches_per_step = 1 + (1 if has_bwd else 0)
+    line = {"metric": METRIC, "value": value, "unit": "series/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"hetero_tile: {P} px x {T} d x {B} bands, d={d}, per-day lambda, "
+                                   + ("fwd+bwd" if has_bwd else "fwd only"),
+                       "pixels_per_rank": P, "T": T, "bands": B, "d": d,
+                       "parallelism": f"replicas x{world} (pixel shards, no collective)",
+                       "l2": "inputs larger than L2 (34.5 GB of x per rank), no flush"},
+            "fwd_series_per_s": P * world / (fwd_ms / 1e3),
+            "fwd_ms": fwd_ms, "bwd_ms": bwd_ms,
+            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
+            "gpu_launches": launches_per_step * args.steps, "clocks": ck,
+            "series_with_status": bad}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,155 @@
+/*
+ * ws.h - C-ABI of the B300 Whittaker-Henderson smoother library (libws_b300.so).
+ *
+ * For every pixel time series (x, w, lambda) on a regular daily grid the library
+ * solves the banded symmetric positive-definite system
+ *
+ *     (W + D^T Lambda D) z = W x                                    (Eq. 3)
+ *
+ * where W = diag(w) holds observation weights (0 for cloudy or missing days),
+ * D in R^{(T-d) x T} is the order-d difference operator (the paper's order k+1)
+ * with rows c_0..c_d = (-1)^(d-i) C(d, i) at columns k..k+d (Section 2), and
+ * Lambda = diag(lambda_0 .. lambda_{T-d-1}) weights the rows of D (Section 2.2).
+ * A scalar lambda gives the homoscedastic smoother of Eq. 2. Several spectral
+ * bands share w and lambda and are solved as right-hand sides against one factor
+ * (Section 2, "batched multivariate"). The reverse-mode derivatives of Eqs. 4-5
+ * (Section 2.3) make the solve a differentiable layer.
+ *
+ * Conventions shared by every entry point
+ *   - Pointers named x, w, lam, z, factor, gz, gx, glam, status, workspace are
+ *     DEVICE pointers owned by the caller. The library never allocates memory on
+ *     a call path; callers size `workspace` with ws_workspace_size().
+ *   - `stream` is a cudaStream_t passed as void*. Every call only enqueues work
+ *     on that stream and never synchronises it (except ws_sync_status).
+ *   - Return value: WS_OK (0) or a negative WS_E* code; ws_last_error() gives the
+ *     text of the last error on the calling thread.
+ *   - Numerical failures are reported per series in the optional `status` array
+ *     (uint8, one per series) and do not make the call fail:
+ *       WS_SERIES_OK        0
+ *       WS_SERIES_NOT_PD    1  Omega singular: fewer than min(d, T) positive
+ *                              weights; outputs of the series are zero-filled
+ *       WS_SERIES_NONFINITE 2  a non-finite value (e.g. NaN x on a weighted day)
+ *                              reached the output
+ *       WS_SERIES_BADARG    3  some lambda_k (k < T-d) not > 0 and finite, or
+ *                              some w_t not >= 0 and finite; outputs zero-filled
+ *   - Where w_t == 0 the observation x_t is never read into the arithmetic (a NaN
+ *     in a gap is harmless).
+ *
+ * Tile layout (WS_LAYOUT_TILE): time-major, pixel-interleaved, pixel fastest:
+ *     x[(t*B + b)*P + p], z likewise, w[t*P + p],
+ *     lam[t*P + p] (WS_LAM_PER_DAY: entry k weights difference row k, which spans
+ *     days k..k+d; entries T-d..T-1 are ignored) or lam[p] (WS_LAM_SCALAR),
+ *     factor[(t*(d+1) + j)*P + p] (see ws_factor).
+ * Element type: float (WS_F32) or double (WS_F64) for every floating array of a call.
+ */
+#ifndef WS_B300_H
+#define WS_B300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* return codes */
+#define WS_OK 0
+#define WS_EINVAL (-1)        /* invalid argument (null pointer, size, alignment, enum) */
+#define WS_ENOMEM_WS (-2)     /* workspace smaller than ws_workspace_size() */
+#define WS_ECUDA (-3)         /* a CUDA runtime call failed (launch, attribute, ...) */
+#define WS_ETIMEOUT (-4)      /* a device-side wait gave up (reported by ws_sync_status) */
+#define WS_EUNSUPPORTED (-5)  /* valid request this build does not implement */
+
+/* per-series status codes */
+#define WS_SERIES_OK 0
+#define WS_SERIES_NOT_PD 1
+#define WS_SERIES_NONFINITE 2
+#define WS_SERIES_BADARG 3
+
+/* enums */
+#define WS_LAYOUT_TILE 0
+#define WS_F32 0
+#define WS_F64 1
+#define WS_LAM_PER_DAY 0
+#define WS_LAM_SCALAR 1
+
+/* flags */
+#define WS_GRAD_LOGLAM 0x1u   /* ws_solve_adjoint: glam = lambda * dL/dlambda (d/dlog lambda) */
+
+typedef struct ws_problem {
+  int64_t n_series; /* P >= 0: number of series (pixels) */
+  int32_t T;        /* days per series, >= 0 */
+  int32_t d;        /* difference order, 1..4 */
+  int32_t n_bands;  /* B >= 1: right-hand sides sharing w and lambda */
+  int32_t layout;   /* WS_LAYOUT_TILE */
+  int32_t dtype;    /* WS_F32 | WS_F64 */
+  int32_t lam_mode; /* WS_LAM_PER_DAY | WS_LAM_SCALAR */
+} ws_problem;
+
+/* Bytes of device scratch the calls below need for `pb` (checkpoints of the
+ * forward sweep plus a 256-byte header holding the device error word). The first
+ * 256 bytes must be zero before the first call that uses the workspace (e.g.
+ * cudaMemset once after allocation); ws_sync_status() clears the word again.
+ * Returns 0 for an invalid problem. */
+size_t ws_workspace_size(const ws_problem* pb, uint32_t flags);
+
+/* Smoothing, Eq. 3 (Eq. 2 with WS_LAM_SCALAR): z = (W + D^T Lambda D)^{-1} W x for
+ * every series and band. x, w, lam: inputs in the tile layout; z: output (may not
+ * alias x). factor_out: optional (NULL or the ws_factor layout) receives the
+ * factor of Omega. status: optional per-series codes. flags: 0. The factor is the
+ * Cholesky factor of Omega (Section 3.1) computed by plane rotations on the
+ * stacked square-root system [sqrt(W); sqrt(Lambda) D]; two sweeps over time
+ * (forward elimination, backward substitution). */
+int ws_smooth_batch(const ws_problem* pb, const void* x, const void* w, const void* lam, void* z,
+                    void* factor_out, uint8_t* status, uint32_t flags, void* workspace,
+                    size_t ws_bytes, void* stream);
+
+/* Factor only (Section 3.1): writes, per day t, factor[(t*(d+1) + 0)*P + p] = 1/D_t and
+ * factor[(t*(d+1) + j)*P + p] = L[t+j][t] (j = 1..d) of Omega = L diag(D) L^T with L
+ * unit lower triangular banded (entries that would fall past T are 0). One forward
+ * sweep; no workspace beyond the header. */
+int ws_factor(const ws_problem* pb, const void* w, const void* lam, void* factor, uint8_t* status,
+              void* workspace, size_t ws_bytes, void* stream);
+
+/* Solve with a stored factor: z = Omega^{-1} W x, Omega given by `factor` (ws_factor
+ * layout) and w. flags: 0. */
+int ws_solve(const ws_problem* pb, const void* factor, const void* w, const void* x, void* z,
+             uint32_t flags, void* workspace, size_t ws_bytes, void* stream);
+
+/* Reverse-mode derivatives through z = Omega^{-1} W x (Section 2.3, Eqs. 4-5).
+ * Given z (the forward output) and gz = dL/dz (tile layout, B bands):
+ *     g_b = Omega^{-1} gz_b                 (Omega symmetric)
+ *     gx_b = W g_b                          (Eq. 5; the vector-Jacobian product)
+ *     glam_k = -sum_b (D g_b)_k (D z_b)_k   (Eq. 4), k < T-d; glam_k = 0 for k >= T-d
+ * With WS_LAM_SCALAR, glam[p] is the sum over k. With WS_GRAD_LOGLAM, glam is
+ * multiplied by lambda (the derivative with respect to log lambda).
+ * factor_or_null: a stored factor (ws_factor layout), or NULL to recompute it from
+ * (w, lam) inside the sweeps (less memory). gx and glam are each optional (NULL). */
+int ws_solve_adjoint(const ws_problem* pb, const void* factor_or_null, const void* w,
+                     const void* lam, const void* z, const void* gz, void* gx, void* glam,
+                     uint32_t flags, uint8_t* status, void* workspace, size_t ws_bytes,
+                     void* stream);
+
+/* Tuning knobs of the tile kernels, process-wide (0 = automatic): pixels (threads)
+ * per CTA, a multiple of 32 in 32..256, and days per staged chunk, 1..(256-d). The
+ * chunk is clamped so that two stages fit in shared memory. ws_workspace_size()
+ * reflects the current setting. Returns WS_EINVAL for out-of-range values. */
+int ws_tune_set(int32_t pixels_per_cta, int32_t chunk_days);
+
+/* Synchronises `stream`, reads and clears the device error word in `workspace`.
+ * Returns WS_OK, WS_ETIMEOUT (a device-side wait gave up: its outputs are invalid)
+ * or WS_ECUDA. */
+int ws_sync_status(void* workspace, size_t ws_bytes, void* stream);
+
+/* Copies the text of the last error on the calling thread into buf (NUL-terminated,
+ * truncated to n bytes). Returns the code of that error (WS_OK if none). */
+int ws_last_error(char* buf, size_t n);
+
+/* Library version string, e.g. "ws_b300 0.1 sm_103a". */
+const char* ws_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* WS_B300_H */

@@ -20,8 +20,8 @@
  * Layout: the tile layout of the GPU library, x[(t*B + b)*P + p], w[t*P + p],
  * lam[t*P + p] (per day; entry k weights difference row k, the last d entries
  * are ignored) or lam[p] (scalar). Status per series: 0 ok, 1 Omega not positive
- * definite (fewer than d positive weights, or a non-positive pivot), 3 invalid
- * lambda or weight.
+ * definite (fewer than min(d, T) positive weights, or a non-positive pivot),
+ * 3 invalid lambda (not > 0 and finite) or weight (not >= 0 and finite).
  */
 #include <math.h>
 #include <stdint.h>
@@ -92,7 +92,10 @@ static int check_inputs(int T, int d, const double* w, const double* lamk) {
   }
   for (int k = 0; k < T - d; ++k)
     if (!(lamk[k] > 0.0) || !isfinite(lamk[k])) return 3;
-  if (npos < d || T <= d) return 1;
+  /* Omega is positive definite iff no nonzero polynomial of degree < d vanishes on the
+   * positive-weight days: at least min(d, T) positive weights (for T < d, D is empty and
+   * Omega = W). */
+  if (npos < (d < T ? d : T)) return 1;
   return 0;
 }
 

@@ -1,0 +1,287 @@
+// C-ABI entry points of libws_b300.so (declared in include/ws.h): argument
+// validation, workspace sizing, tensor-map encoding, band groups and launch.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cuda_runtime.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <mutex>
+
+#include "ws_internal.h"
+
+namespace ws {
+
+static thread_local int g_err_code = WS_OK;
+static thread_local char g_err_msg[512] = "";
+
+int set_error(int code, const char* fmt, ...) {
+  g_err_code = code;
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err_msg, sizeof(g_err_msg), fmt, ap);
+  va_end(ap);
+  return code;
+}
+
+static void clear_error() {
+  g_err_code = WS_OK;
+  g_err_msg[0] = '\0';
+}
+
+int device_info(DeviceInfo& info) {
+  static DeviceInfo cache[64];
+  static std::once_flag once[64];
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess || dev < 0 || dev >= 64) return set_error(WS_ECUDA, "cudaGetDevice: %s", cudaGetErrorString(e));
+  std::call_once(once[dev], [dev]() {
+    cudaDeviceGetAttribute(&cache[dev].sm_count, cudaDevAttrMultiProcessorCount, dev);
+    cudaDeviceGetAttribute(&cache[dev].smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  });
+  info = cache[dev];
+  if (info.sm_count <= 0 || info.smem_optin <= 0) return set_error(WS_ECUDA, "device attributes unavailable");
+  return WS_OK;
+}
+
+static PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, []() {
+    cudaDriverEntryPointQueryResult q;
+    void* p = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  });
+  return fn;
+}
+
+int make_tmap(CUtensorMap* map, int dtype, int rank, const void* base, const uint64_t* dims,
+              const uint64_t* strides_bytes, const uint32_t* box) {
+  auto fn = encode_fn();
+  if (fn == nullptr) return WS_EUNSUPPORTED;
+  cuuint64_t gd[3];
+  cuuint64_t gs[2];
+  cuuint32_t bx[3], es[3] = {1, 1, 1};
+  for (int i = 0; i < rank; ++i) {
+    gd[i] = dims[i];
+    bx[i] = box[i];
+  }
+  for (int i = 0; i + 1 < rank; ++i) gs[i] = strides_bytes[i];
+  CUresult r = fn(map, dtype == WS_F64 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32,
+                  (cuuint32_t)rank, const_cast<void*>(base), gd, gs, bx, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                  CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? WS_OK : WS_EUNSUPPORTED;
+}
+
+static int validate_problem(const ws_problem* pb) {
+  if (pb == nullptr) return set_error(WS_EINVAL, "problem is NULL");
+  if (pb->n_series < 0 || pb->n_series > 0x7fffffffLL) return set_error(WS_EINVAL, "n_series out of range");
+  if (pb->T < 0) return set_error(WS_EINVAL, "T < 0");
+  if (pb->d < 1 || pb->d > 4) return set_error(WS_EINVAL, "d must be 1..4 (got %d)", pb->d);
+  if (pb->n_bands < 1) return set_error(WS_EINVAL, "n_bands must be >= 1");
+  if (pb->layout != WS_LAYOUT_TILE) return set_error(WS_EINVAL, "layout must be WS_LAYOUT_TILE");
+  if (pb->dtype != WS_F32 && pb->dtype != WS_F64) return set_error(WS_EINVAL, "dtype must be WS_F32 or WS_F64");
+  if (pb->lam_mode != WS_LAM_PER_DAY && pb->lam_mode != WS_LAM_SCALAR)
+    return set_error(WS_EINVAL, "lam_mode must be WS_LAM_PER_DAY or WS_LAM_SCALAR");
+  return WS_OK;
+}
+
+static int elem_size(const ws_problem& pb) { return pb.dtype == WS_F64 ? 8 : 4; }
+
+// Largest supported band-group size <= want for this dtype/order.
+static int group_size(const ws_problem& pb, int want) {
+  if (pb.dtype == WS_F64) return (pb.d == 2 && want >= 2) ? 2 : 1;
+#ifdef WS_FAST_BUILD
+  return want >= 4 ? 4 : (want >= 2 ? 2 : 1);
+#else
+  return want > kNbMax ? kNbMax : want;
+#endif
+}
+
+static int extra_planes(int d) { return d > 2 ? d - 2 : 0; }
+
+static bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+static bool overlaps(const void* a, size_t na, const void* b, size_t nb) {
+  const char* pa = static_cast<const char*>(a);
+  const char* pb = static_cast<const char*>(b);
+  return pa < pb + nb && pb < pa + na;
+}
+
+// Checkpoint bytes needed by the tile path over all band groups.
+static int tile_ckpt_bytes(const ws_problem& pb, size_t& bytes) {
+  bytes = 0;
+  for (int b0 = 0; b0 < pb.n_bands;) {
+    const int nb = group_size(pb, pb.n_bands - b0);
+    TileCfg cfg;
+    int rc = plan_tile(pb, nb, pb.d, extra_planes(pb.d), cfg);
+    if (rc != WS_OK) return rc;
+    const size_t need = (size_t)cfg.grid * cfg.nch * cfg.fields * cfg.NP * elem_size(pb);
+    if (need > bytes) bytes = need;
+    b0 += nb;
+  }
+  return WS_OK;
+}
+
+static int check_workspace(const ws_problem& pb, void* workspace, size_t ws_bytes, size_t& ck_bytes) {
+  int rc = tile_ckpt_bytes(pb, ck_bytes);
+  if (rc != WS_OK) return rc;
+  if (workspace == nullptr) return set_error(WS_EINVAL, "workspace is NULL");
+  if ((reinterpret_cast<uintptr_t>(workspace) & 255u) != 0)
+    return set_error(WS_EINVAL, "workspace must be 256-byte aligned");
+  if (ws_bytes < kHeaderBytes + ck_bytes)
+    return set_error(WS_ENOMEM_WS, "workspace too small: %zu < %zu", ws_bytes, kHeaderBytes + ck_bytes);
+  return WS_OK;
+}
+
+}  // namespace ws
+
+using namespace ws;
+
+extern "C" size_t ws_workspace_size(const ws_problem* pb, uint32_t flags) {
+  (void)flags;
+  clear_error();
+  if (validate_problem(pb) != WS_OK) return 0;
+  size_t ck = 0;
+  if (pb->n_series == 0 || pb->T == 0) return kHeaderBytes;
+  if (tile_ckpt_bytes(*pb, ck) != WS_OK) return 0;
+  return kHeaderBytes + ck;
+}
+
+extern "C" int ws_smooth_batch(const ws_problem* pb, const void* x, const void* w, const void* lam, void* z,
+                               void* factor_out, uint8_t* status, uint32_t flags, void* workspace,
+                               size_t ws_bytes, void* stream) {
+  clear_error();
+  int rc = validate_problem(pb);
+  if (rc != WS_OK) return rc;
+  if (flags != 0) return set_error(WS_EINVAL, "unknown flags 0x%x", flags);
+  const ws_problem& P = *pb;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (P.n_series == 0) return WS_OK;
+  if (P.T == 0) {
+    if (status != nullptr && cudaMemsetAsync(status, 0, (size_t)P.n_series, st) != cudaSuccess)
+      return set_error(WS_ECUDA, "status memset failed");
+    return WS_OK;
+  }
+  if (!x || !w || !lam || !z) return set_error(WS_EINVAL, "x, w, lam and z must be non-NULL");
+  const int es = elem_size(P);
+  const size_t nx = (size_t)P.T * P.n_bands * P.n_series * es;
+  if (overlaps(x, nx, z, nx)) return set_error(WS_EINVAL, "z must not overlap x");
+  size_t ck_bytes = 0;
+  rc = check_workspace(P, workspace, ws_bytes, ck_bytes);
+  if (rc != WS_OK) return rc;
+  const bool per_day = P.lam_mode == WS_LAM_PER_DAY;
+  bool tma_ok = ((size_t)P.n_series * es) % 16 == 0 && aligned16(x) && aligned16(w) && aligned16(z) &&
+                (!per_day || aligned16(lam));
+
+  for (int b0 = 0; b0 < P.n_bands;) {
+    const int nb = group_size(P, P.n_bands - b0);
+    TileCfg cfg;
+    rc = plan_tile(P, nb, P.d, extra_planes(P.d), cfg);
+    if (rc != WS_OK) return rc;
+    CUtensorMap maps[4];
+    memset(maps, 0, sizeof(maps));
+    bool tma = tma_ok;
+    if (tma) {
+      const uint64_t Pn = (uint64_t)P.n_series, B = (uint64_t)P.n_bands, T = (uint64_t)P.T;
+      const uint64_t dx[3] = {Pn, B, T}, sx[2] = {Pn * es, B * Pn * es};
+      const uint32_t bx[3] = {(uint32_t)cfg.NP, (uint32_t)nb, (uint32_t)cfg.C};
+      const uint64_t d2[2] = {Pn, T}, s2[1] = {Pn * es};
+      const uint32_t bw[2] = {(uint32_t)cfg.NP, (uint32_t)(cfg.C + P.d)};
+      const uint32_t bl[2] = {(uint32_t)cfg.NP, (uint32_t)cfg.C};
+      tma = make_tmap(&maps[0], P.dtype, 3, x, dx, sx, bx) == WS_OK &&
+            make_tmap(&maps[1], P.dtype, 2, w, d2, s2, bw) == WS_OK &&
+            (!per_day || make_tmap(&maps[2], P.dtype, 2, lam, d2, s2, bl) == WS_OK) &&
+            make_tmap(&maps[3], P.dtype, 3, z, dx, sx, bx) == WS_OK;
+    }
+    TileArgs a;
+    memset(&a, 0, sizeof(a));
+    a.T = P.T;
+    a.P = (int)P.n_series;
+    a.B = P.n_bands;
+    a.b0 = b0;
+    a.C = cfg.C;
+    a.NP = cfg.NP;
+    a.nch = cfg.nch;
+    a.n_tiles = cfg.n_tiles;
+    a.lam_scalar = per_day ? 0 : 1;
+    a.tma = tma ? 1 : 0;
+    a.write_status = b0 == 0;
+    a.x = x;
+    a.w = w;
+    a.lam = lam;
+    a.out = z;
+    a.factor = factor_out;
+    a.status = status;
+    a.ckpt = static_cast<char*>(workspace) + kHeaderBytes;
+    a.err = static_cast<unsigned*>(workspace);
+    a.stage_elems = cfg.stage_elems;
+    rc = launch_smooth_tile(P, nb, cfg, a, maps, st);
+    if (rc != WS_OK) return rc;
+    b0 += nb;
+  }
+  return WS_OK;
+}
+
+extern "C" int ws_factor(const ws_problem* pb, const void* w, const void* lam, void* factor, uint8_t* status,
+                         void* workspace, size_t ws_bytes, void* stream) {
+  (void)pb, (void)w, (void)lam, (void)factor, (void)status, (void)workspace, (void)ws_bytes, (void)stream;
+  clear_error();
+  return set_error(WS_EUNSUPPORTED, "ws_factor: not built yet");
+}
+
+extern "C" int ws_solve(const ws_problem* pb, const void* factor, const void* w, const void* x, void* z,
+                        uint32_t flags, void* workspace, size_t ws_bytes, void* stream) {
+  (void)pb, (void)factor, (void)w, (void)x, (void)z, (void)flags, (void)workspace, (void)ws_bytes, (void)stream;
+  clear_error();
+  return set_error(WS_EUNSUPPORTED, "ws_solve: not built yet");
+}
+
+extern "C" int ws_solve_adjoint(const ws_problem* pb, const void* factor_or_null, const void* w, const void* lam,
+                                const void* z, const void* gz, void* gx, void* glam, uint32_t flags,
+                                uint8_t* status, void* workspace, size_t ws_bytes, void* stream) {
+  (void)pb, (void)factor_or_null, (void)w, (void)lam, (void)z, (void)gz, (void)gx, (void)glam, (void)flags;
+  (void)status, (void)workspace, (void)ws_bytes, (void)stream;
+  clear_error();
+  return set_error(WS_EUNSUPPORTED, "ws_solve_adjoint: not built yet");
+}
+
+extern "C" int ws_tune_set(int32_t pixels_per_cta, int32_t chunk_days) {
+  clear_error();
+  if (pixels_per_cta != 0 && (pixels_per_cta < 32 || pixels_per_cta > 256 || pixels_per_cta % 32 != 0))
+    return set_error(WS_EINVAL, "pixels_per_cta must be 0 or a multiple of 32 in 32..256");
+  if (chunk_days < 0 || chunk_days > 255) return set_error(WS_EINVAL, "chunk_days must be 0..255");
+  g_tune_np = pixels_per_cta;
+  g_tune_chunk = chunk_days;
+  return WS_OK;
+}
+
+extern "C" int ws_sync_status(void* workspace, size_t ws_bytes, void* stream) {
+  clear_error();
+  if (workspace == nullptr || ws_bytes < kHeaderBytes) return set_error(WS_EINVAL, "workspace too small or NULL");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  cudaError_t e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return set_error(WS_ECUDA, "cudaStreamSynchronize: %s", cudaGetErrorString(e));
+  unsigned word = 0;
+  e = cudaMemcpy(&word, workspace, sizeof(word), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return set_error(WS_ECUDA, "reading the device error word: %s", cudaGetErrorString(e));
+  if (word != 0) {
+    cudaMemset(workspace, 0, sizeof(word));
+    return set_error(WS_ETIMEOUT, "a device-side wait gave up (error word 0x%x)", word);
+  }
+  return WS_OK;
+}
+
+extern "C" int ws_last_error(char* buf, size_t n) {
+  if (buf != nullptr && n > 0) {
+    strncpy(buf, g_err_msg, n - 1);
+    buf[n - 1] = '\0';
+  }
+  return g_err_code;
+}
+
+extern "C" const char* ws_version(void) { return "ws_b300 0.1 sm_103a"; }

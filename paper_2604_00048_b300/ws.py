@@ -1,0 +1,189 @@
+"""Thin Python binding of libws_b300.so (C-ABI in include/ws.h).
+
+Argument marshalling only: shapes, dtypes and device pointers of torch tensors are
+checked and passed to the CUDA library, which does every step of the computation.
+There is no CPU fallback; if the shared library is missing, importing this module
+raises (build it with `python -m paper_2604_00048_b300.build`).
+
+Tensors use the tile layout of the C-ABI:
+    x, z   [T, B, P]   (pixel fastest)
+    w      [T, P]
+    lam    [T, P] per day (entry k weights difference row k) or [P] scalar
+    factor [T, d+1, P] (ws_factor layout)
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+from typing import Optional
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "libws_b300.so")
+HEADER = os.path.join(os.path.dirname(_HERE), "include", "ws.h")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"CUDA library not built: {LIB_PATH} (run python -m paper_2604_00048_b300.build)")
+_lib = ctypes.CDLL(LIB_PATH)
+
+WS_OK, WS_EINVAL, WS_ENOMEM_WS, WS_ECUDA, WS_ETIMEOUT, WS_EUNSUPPORTED = 0, -1, -2, -3, -4, -5
+SERIES_OK, SERIES_NOT_PD, SERIES_NONFINITE, SERIES_BADARG = 0, 1, 2, 3
+LAYOUT_TILE = 0
+F32, F64 = 0, 1
+LAM_PER_DAY, LAM_SCALAR = 0, 1
+GRAD_LOGLAM = 0x1
+
+
+class Problem(ctypes.Structure):
+    _fields_ = [("n_series", ctypes.c_int64), ("T", ctypes.c_int32), ("d", ctypes.c_int32),
+                ("n_bands", ctypes.c_int32), ("layout", ctypes.c_int32), ("dtype", ctypes.c_int32),
+                ("lam_mode", ctypes.c_int32)]
+
+
+_vp, _sz, _u32 = ctypes.c_void_p, ctypes.c_size_t, ctypes.c_uint32
+_PP = ctypes.POINTER(Problem)
+_lib.ws_workspace_size.restype = _sz
+_lib.ws_workspace_size.argtypes = [_PP, _u32]
+_lib.ws_smooth_batch.restype = ctypes.c_int
+_lib.ws_smooth_batch.argtypes = [_PP, _vp, _vp, _vp, _vp, _vp, _vp, _u32, _vp, _sz, _vp]
+_lib.ws_factor.restype = ctypes.c_int
+_lib.ws_factor.argtypes = [_PP, _vp, _vp, _vp, _vp, _vp, _sz, _vp]
+_lib.ws_solve.restype = ctypes.c_int
+_lib.ws_solve.argtypes = [_PP, _vp, _vp, _vp, _vp, _u32, _vp, _sz, _vp]
+_lib.ws_solve_adjoint.restype = ctypes.c_int
+_lib.ws_solve_adjoint.argtypes = [_PP, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _u32, _vp, _vp, _sz, _vp]
+_lib.ws_tune_set.restype = ctypes.c_int
+_lib.ws_tune_set.argtypes = [ctypes.c_int32, ctypes.c_int32]
+_lib.ws_sync_status.restype = ctypes.c_int
+_lib.ws_sync_status.argtypes = [_vp, _sz, _vp]
+_lib.ws_last_error.restype = ctypes.c_int
+_lib.ws_last_error.argtypes = [ctypes.c_char_p, _sz]
+_lib.ws_version.restype = ctypes.c_char_p
+_lib.ws_version.argtypes = []
+
+
+class WSError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"ws error {code}: {msg}")
+        self.code = code
+
+
+def lib():
+    return _lib
+
+
+def declared_symbols(header: str = HEADER):
+    """Function names declared in include/ws.h."""
+    txt = open(header).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(ws_[a-z0-9_]+)\s*\(", txt)))
+
+
+def last_error() -> str:
+    buf = ctypes.create_string_buffer(512)
+    _lib.ws_last_error(buf, 512)
+    return buf.value.decode()
+
+
+def _check(rc: int):
+    if rc != WS_OK:
+        raise WSError(rc, last_error())
+
+
+def version() -> str:
+    return _lib.ws_version().decode()
+
+
+def _dtype_code(t: torch.Tensor) -> int:
+    if t.dtype == torch.float32:
+        return F32
+    if t.dtype == torch.float64:
+        return F64
+    raise TypeError(f"unsupported dtype {t.dtype} (float32 or float64)")
+
+
+def _ptr(t: Optional[torch.Tensor]):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _stream_ptr(stream) -> ctypes.c_void_p:
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def make_problem(T: int, B: int, P: int, d: int, dtype: int, lam_mode: int) -> Problem:
+    return Problem(n_series=P, T=T, d=d, n_bands=B, layout=LAYOUT_TILE, dtype=dtype, lam_mode=lam_mode)
+
+
+def workspace_size(pb: Problem, flags: int = 0) -> int:
+    return int(_lib.ws_workspace_size(ctypes.byref(pb), flags))
+
+
+_ws_cache = {}
+
+
+def workspace(pb: Problem, device, flags: int = 0) -> torch.Tensor:
+    """Device scratch for `pb` (cached per device and grown on demand; header zeroed once)."""
+    need = workspace_size(pb, flags)
+    if need == 0:
+        raise WSError(WS_EINVAL, last_error() or "invalid problem")
+    dev = torch.device(device)
+    key = dev.index if dev.index is not None else torch.cuda.current_device()
+    buf = _ws_cache.get(key)
+    if buf is None or buf.numel() < need:
+        buf = torch.zeros(need, dtype=torch.uint8, device=dev)
+        _ws_cache[key] = buf
+    return buf
+
+
+def _check_tile(x, w, lam, d):
+    if x.dim() != 3:
+        raise ValueError("x must be [T, B, P]")
+    T, B, P = x.shape
+    if tuple(w.shape) != (T, P):
+        raise ValueError("w must be [T, P]")
+    if lam.dim() == 2 and tuple(lam.shape) != (T, P):
+        raise ValueError("per-day lam must be [T, P]")
+    if lam.dim() == 1 and lam.shape[0] != P:
+        raise ValueError("scalar lam must be [P]")
+    for t in (x, w, lam):
+        if not t.is_cuda or not t.is_contiguous() or t.dtype != x.dtype:
+            raise ValueError("x, w, lam must be contiguous CUDA tensors of one dtype")
+    return T, B, P, (LAM_SCALAR if lam.dim() == 1 else LAM_PER_DAY)
+
+
+def smooth(x: torch.Tensor, w: torch.Tensor, lam: torch.Tensor, d: int = 2, *, z=None, status=None,
+           factor=None, stream=None):
+    """z = (W + D^T Lambda D)^{-1} W x per series and band (Eq. 3; Eq. 2 for scalar lam).
+
+    Returns (z, status). `factor` (optional [T, d+1, P]) receives the factor."""
+    T, B, P, lm = _check_tile(x, w, lam, d)
+    pb = make_problem(T, B, P, d, _dtype_code(x), lm)
+    if z is None:
+        z = torch.empty_like(x)
+    if status is None:
+        status = torch.empty(P, dtype=torch.uint8, device=x.device)
+    ws = workspace(pb, x.device)
+    rc = _lib.ws_smooth_batch(ctypes.byref(pb), _ptr(x), _ptr(w), _ptr(lam), _ptr(z), _ptr(factor),
+                              _ptr(status), 0, _ptr(ws), ws.numel(), _stream_ptr(stream))
+    _check(rc)
+    return z, status
+
+
+def tune_set(pixels_per_cta: int = 0, chunk_days: int = 0):
+    """Process-wide tile tuning knobs (0 = automatic)."""
+    _check(_lib.ws_tune_set(int(pixels_per_cta), int(chunk_days)))
+
+
+def sync_status(device=None, stream=None):
+    """Synchronise and read/clear the device error word of the cached workspace."""
+    dev = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+    key = dev.index if dev.index is not None else torch.cuda.current_device()
+    buf = _ws_cache.get(key)
+    if buf is None:
+        torch.cuda.synchronize(dev)
+        return
+    _check(_lib.ws_sync_status(_ptr(buf), buf.numel(), _stream_ptr(stream)))

@@ -1,0 +1,124 @@
+"""GPU smoothing path against the FP64 oracle (parity tests proper, through the C-ABI).
+
+Tolerances: max relative error per series and band (inf-norm over time, normalised by
+the oracle's inf-norm, floor 1e-6) <= 1e-4 for FP32, <= 1e-9 for FP64."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import banded, dense
+from tests.gpu_util import rel_err_per_series, tile_inputs
+
+pytestmark = pytest.mark.gpu
+
+TOL = {torch.float32: 1e-4, torch.float64: 1e-9}
+
+
+@pytest.fixture(scope="module")
+def ws():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA device")
+    from paper_2604_00048_b300 import ws as mod
+    yield mod
+    mod.tune_set(0, 0)
+
+
+@pytest.mark.parametrize("dtype", [torch.float32, torch.float64])
+@pytest.mark.parametrize("d", [1, 2, 3, 4])
+@pytest.mark.parametrize("P", [300, 301])           # 300: TMA staging; 301: row pitch not 16-byte aligned
+def test_smooth_matches_dense_oracle_many_chunks(ws, dtype, d, P):
+    """Several tiles of 128 pixels plus a ragged tile, T = 61 days in chunks of 8 (ragged last chunk)."""
+    ws.tune_set(128, 8)
+    B = 3 if dtype == torch.float32 else 2
+    rc, g, c = tile_inputs("layer", P, T=61, B=B, dtype=dtype)
+    z, st = ws.smooth(g["x"], g["w"], g["lam"], d)
+    ws.sync_status()
+    zr, ok = dense.smooth_tile(c["x"], c["w"], c["lam"], d)
+    st = st.cpu().numpy()
+    assert np.array_equal(st == 0, ok)
+    assert rel_err_per_series(z.cpu().numpy()[:, :, ok], zr[:, :, ok]) <= TOL[dtype]
+    assert np.all(z.cpu().numpy()[:, :, ~ok] == 0)
+
+
+@pytest.mark.parametrize("B", [1, 4, 10, 13])
+def test_smooth_band_counts_auto_config(ws, B):
+    """Automatic staging configuration; 13 bands run as two band groups."""
+    ws.tune_set(0, 0)
+    rc, g, c = tile_inputs("hetero_tile", 256, T=400, B=B)
+    z, st = ws.smooth(g["x"], g["w"], g["lam"], 2)
+    ws.sync_status()
+    zb, stb = banded.smooth_tile(c["x"], c["w"], c["lam"], 2)
+    assert np.array_equal(st.cpu().numpy(), stb)
+    assert rel_err_per_series(z.cpu().numpy(), zb) <= 1e-4
+
+
+def test_scalar_lambda_fp64_homoscedastic(ws):
+    """Eq. 2 (one lambda per series) in FP64 on the one-year workload."""
+    ws.tune_set(0, 0)
+    rc, g, c = tile_inputs("homo_fp64", 512, dtype=torch.float64)
+    z, st = ws.smooth(g["x"], g["w"], g["lam"], 2)
+    ws.sync_status()
+    zr, ok = dense.smooth_tile(c["x"], c["w"], c["lam"], 2)
+    assert np.array_equal(st.cpu().numpy() == 0, ok)
+    assert rel_err_per_series(z.cpu().numpy()[:, :, ok], zr[:, :, ok]) <= 1e-9
+
+
+def test_status_codes_and_zero_fill(ws):
+    ws.tune_set(0, 0)
+    T, B, P, d = 40, 2, 8, 2
+    rng = np.random.default_rng(3)
+    x = rng.normal(size=(T, B, P))
+    w = np.ones((T, P))
+    lam = np.full((T, P), 10.0)
+    w[:, 0] = 0.0                      # no weights: not PD
+    w[:, 1] = 0.0
+    w[5, 1] = 1.0                      # one weight < d: not PD
+    lam[3, 2] = -1.0                   # invalid lambda on a difference row
+    w[4, 3] = np.nan                   # invalid weight
+    x[6, 0, 4] = np.nan                # NaN observation on a weighted day
+    w[7, 5] = 0.0
+    x[7, 1, 5] = np.nan                # NaN in a gap: harmless
+    lam[T - 1, 6] = -5.0               # last d entries are ignored
+    dev = "cuda"
+    z, st = ws.smooth(torch.tensor(x, dtype=torch.float32, device=dev), torch.tensor(w, dtype=torch.float32, device=dev),
+                      torch.tensor(lam, dtype=torch.float32, device=dev), d)
+    ws.sync_status()
+    st = st.cpu().numpy().tolist()
+    assert st == [1, 1, 3, 3, 2, 0, 0, 0]
+    z = z.cpu().numpy()
+    assert np.all(z[:, :, [0, 1, 2, 3]] == 0)
+    assert np.all(np.isfinite(z[:, :, 5:]))
+    zr, _ = dense.smooth_tile(np.nan_to_num(x[:, :, 5:7]), np.nan_to_num(w[:, 5:7]), np.abs(lam[:, 5:7]), d)
+    assert rel_err_per_series(z[:, :, 5:7], zr) <= 1e-4
+
+
+@pytest.mark.parametrize("T", [1, 2, 3, 5])
+def test_short_series(ws, T):
+    ws.tune_set(0, 0)
+    d = 2
+    rc, g, c = tile_inputs("layer", 64, T=T, B=1)
+    w = torch.ones_like(g["w"])
+    z, st = ws.smooth(g["x"], w, g["lam"], d)
+    ws.sync_status()
+    zr, ok = dense.smooth_tile(c["x"], np.ones_like(c["w"]), c["lam"], d)
+    assert np.array_equal(st.cpu().numpy() == 0, ok)
+    assert rel_err_per_series(z.cpu().numpy(), zr) <= 1e-4
+
+
+def test_factor_output_matches_dense_ldlt(ws):
+    """factor_out holds 1/D_t and L[t+j][t] of Omega = L diag(D) L^T."""
+    ws.tune_set(128, 16)
+    T, P, d = 50, 130, 2
+    rc, g, c = tile_inputs("layer", P, T=T, B=1, dtype=torch.float64)
+    f = torch.empty((T, d + 1, P), dtype=torch.float64, device="cuda")
+    z, st = ws.smooth(g["x"], g["w"], g["lam"], d, factor=f)
+    ws.sync_status()
+    f = f.cpu().numpy()
+    for p in range(0, P, 13):
+        L = np.linalg.cholesky(dense.omega(c["w"][:, p], c["lam"][:, p], d))
+        dg = np.diag(L)
+        assert np.allclose(f[:, 0, p], 1.0 / dg ** 2, rtol=1e-9)
+        for j in range(1, d + 1):
+            ref = np.zeros(T)
+            ref[: T - j] = np.diagonal(L, -j) / dg[: T - j]
+            assert np.allclose(f[:, j, p], ref, rtol=1e-9, atol=1e-12)

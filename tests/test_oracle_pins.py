@@ -296,3 +296,19 @@ def test_mse_maxe_hand_example():
     mse, maxe = dense.mse_maxe(z, x, w)
     assert mse == pytest.approx((0.25 + 0.0 + 1.0 + 0.0) / 4)
     assert maxe == pytest.approx(1.0)
+
+
+@pytest.mark.parametrize("d", [1, 2, 3])
+def test_short_series_edge_cases(rng, d):
+    """T <= d: D has no rows, Omega = W; positive definite iff every weight is positive."""
+    for T in range(1, d + 2):
+        x = rng.normal(size=(T, 2, 3))
+        w = np.ones((T, 3))
+        w[0, 1] = 0.0
+        lam = np.ones((T, 3))
+        z, st = banded.smooth_tile(x, w, lam, d)
+        zd, ok = dense.smooth_tile(x, w, lam, d)
+        assert list(st == 0) == list(ok)
+        assert np.max(np.abs(z - zd)) <= 1e-12
+        if T <= d:
+            assert np.allclose(z[:, :, 0], x[:, :, 0])
