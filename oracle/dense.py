@@ -103,11 +103,25 @@ def vjp_one(w, lam, d: int, z, gz, per_day: bool = True):
     return gx.reshape(np.shape(z)), glam
 
 
+def is_pd(w, lam, d: int) -> bool:
+    """Omega = W + D^T Lambda D is positive definite iff every lambda row weight is > 0
+    (finite), every w >= 0 (finite), and at least min(d, T) weights are positive: the
+    null space of D^T Lambda D is the polynomials of degree < d, and a nonzero one has
+    fewer than d roots. (Deciding this by attempting a Cholesky factorisation is not
+    reliable: on an exactly singular Omega rounding can leave every pivot positive.)"""
+    w = np.asarray(w, dtype=np.float64)
+    T = w.shape[0]
+    lr = lam_rows(lam, T, d)
+    if not (np.all(np.isfinite(w)) and np.all(w >= 0) and np.all(np.isfinite(lr)) and np.all(lr > 0)):
+        return False
+    return int(np.sum(w > 0)) >= min(d, T)
+
+
 def smooth_tile(x, w, lam, d: int):
     """Batch over pixels in the tile layout x[t, b, p], w[t, p], lam[t, p] or lam[p].
 
-    Returns (z[t, b, p], ok[p]); series whose Omega is not positive definite get
-    ok = False and z = 0."""
+    Returns (z[t, b, p], ok[p]); series whose Omega is not positive definite (is_pd)
+    get ok = False and z = 0."""
     x = np.asarray(x, dtype=np.float64)
     w = np.asarray(w, dtype=np.float64)
     lam = np.asarray(lam, dtype=np.float64)
@@ -116,10 +130,10 @@ def smooth_tile(x, w, lam, d: int):
     ok = np.ones(P, dtype=bool)
     for p in range(P):
         lp = lam[p] if lam.ndim == 1 else lam[:, p]
-        try:
-            z[:, :, p] = smooth_one(x[:, :, p], w[:, p], lp, d)
-        except np.linalg.LinAlgError:
+        if not is_pd(w[:, p], lp, d):
             ok[p] = False
+            continue
+        z[:, :, p] = smooth_one(x[:, :, p], w[:, p], lp, d)
     return z, ok
 
 

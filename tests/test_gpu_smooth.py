@@ -35,8 +35,11 @@ def test_smooth_matches_dense_oracle_many_chunks(ws, dtype, d, P):
     ws.sync_status()
     zr, ok = dense.smooth_tile(c["x"], c["w"], c["lam"], d)
     st = st.cpu().numpy()
-    assert np.array_equal(st == 0, ok)
-    assert rel_err_per_series(z.cpu().numpy()[:, :, ok], zr[:, :, ok]) <= TOL[dtype]
+    bad = np.flatnonzero((st == 0) != ok)
+    assert bad.size == 0, f"status mismatch at {bad[:10]}: gpu {st[bad[:10]]} oracle ok {ok[bad[:10]]} " \
+                          f"npos {(c['w'][:, bad[:10]] > 0).sum(0)}"
+    err = rel_err_per_series(z.cpu().numpy()[:, :, ok], zr[:, :, ok])
+    assert err <= TOL[dtype], f"max rel err {err:.3e}"
     assert np.all(z.cpu().numpy()[:, :, ~ok] == 0)
 
 

@@ -312,3 +312,18 @@ def test_short_series_edge_cases(rng, d):
         assert np.max(np.abs(z - zd)) <= 1e-12
         if T <= d:
             assert np.allclose(z[:, :, 0], x[:, :, 0])
+
+
+@pytest.mark.parametrize("d", [1, 2, 3, 4])
+def test_pd_rule_matches_spectrum(rng, d):
+    """is_pd (counting rule) agrees with the smallest eigenvalue of Omega."""
+    T = 18
+    for trial in range(40):
+        w = np.zeros(T)
+        k = int(rng.integers(0, d + 2))
+        w[rng.choice(T, size=k, replace=False)] = rng.uniform(0.5, 2.0, size=k)
+        lam = 10 ** rng.uniform(-1, 2, T)
+        ev = np.linalg.eigvalsh(dense.omega(w, lam, d))
+        scale = np.max(np.abs(ev))
+        assert dense.is_pd(w, lam, d) == (ev[0] > 1e-10 * scale)
+    assert not dense.is_pd(np.ones(T), np.concatenate([[-1.0], np.ones(T - 1)]), d)
