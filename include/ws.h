@@ -75,6 +75,7 @@ extern "C" {
 
 /* flags */
 #define WS_GRAD_LOGLAM 0x1u   /* ws_solve_adjoint: glam = lambda * dL/dlambda (d/dlog lambda) */
+#define WS_REFINE 0x2u        /* ws_smooth_batch: one step of iterative refinement */
 
 typedef struct ws_problem {
   int64_t n_series; /* P >= 0: number of series (pixels) */
@@ -87,7 +88,8 @@ typedef struct ws_problem {
 } ws_problem;
 
 /* Bytes of device scratch the calls below need for `pb` (checkpoints of the
- * forward sweep plus a 256-byte header holding the device error word). The first
+ * forward sweep plus a 256-byte header holding the device error word; with
+ * flags & WS_REFINE also the residual, T*B*P elements). The first
  * 256 bytes must be zero before the first call that uses the workspace (e.g.
  * cudaMemset once after allocation); ws_sync_status() clears the word again.
  * Returns 0 for an invalid problem. */
@@ -96,7 +98,10 @@ size_t ws_workspace_size(const ws_problem* pb, uint32_t flags);
 /* Smoothing, Eq. 3 (Eq. 2 with WS_LAM_SCALAR): z = (W + D^T Lambda D)^{-1} W x for
  * every series and band. x, w, lam: inputs in the tile layout; z: output (may not
  * alias x). factor_out: optional (NULL or the ws_factor layout) receives the
- * factor of Omega. status: optional per-series codes. flags: 0. The factor is the
+ * factor of Omega. status: optional per-series codes. flags: 0 or WS_REFINE: after
+ * the solve, the residual r = W x - Omega z is formed with double-word (FP64-level)
+ * accumulation, Omega d = r is solved with the same factorisation and z += d; this
+ * needs the larger workspace ws_workspace_size(pb, WS_REFINE). The factor is the
  * Cholesky factor of Omega (Section 3.1) computed by plane rotations on the
  * stacked square-root system [sqrt(W); sqrt(Lambda) D]; two sweeps over time
  * (forward elimination, backward substitution). */

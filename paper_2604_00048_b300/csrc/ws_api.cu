@@ -112,76 +112,56 @@ static bool overlaps(const void* a, size_t na, const void* b, size_t nb) {
   return pa < pb + nb && pb < pa + na;
 }
 
-// Checkpoint bytes needed by the tile path over all band groups.
+static int extra_planes_mode(int mode, int d) { return mode == MODE_ADJ ? d : extra_planes(d); }
+
+static size_t round256(size_t v) { return (v + 255) & ~(size_t)255; }
+
+// Checkpoint bytes of the tile kernels over all band groups and modes.
 static int tile_ckpt_bytes(const ws_problem& pb, size_t& bytes) {
   bytes = 0;
-  for (int b0 = 0; b0 < pb.n_bands;) {
-    const int nb = group_size(pb, pb.n_bands - b0);
-    TileCfg cfg;
-    int rc = plan_tile(pb, nb, pb.d, extra_planes(pb.d), cfg);
-    if (rc != WS_OK) return rc;
-    const size_t need = (size_t)cfg.grid * cfg.nch * cfg.fields * cfg.NP * elem_size(pb);
-    if (need > bytes) bytes = need;
-    b0 += nb;
+  for (int mode : {MODE_SMOOTH, MODE_ADJ}) {
+    for (int b0 = 0; b0 < pb.n_bands;) {
+      const int nb = group_size(pb, pb.n_bands - b0);
+      TileCfg cfg;
+      int rc = plan_tile(pb, nb, pb.d, extra_planes_mode(mode, pb.d), cfg);
+      if (rc != WS_OK) return rc;
+      const size_t need = (size_t)cfg.grid * cfg.nch * cfg.fields * cfg.NP * elem_size(pb);
+      if (need > bytes) bytes = need;
+      b0 += nb;
+    }
   }
+  bytes = round256(bytes);
   return WS_OK;
 }
 
-static int check_workspace(const ws_problem& pb, void* workspace, size_t ws_bytes, size_t& ck_bytes) {
+static size_t resid_bytes(const ws_problem& pb) {
+  return round256((size_t)pb.T * pb.n_bands * pb.n_series * elem_size(pb));
+}
+
+static int check_workspace(const ws_problem& pb, void* workspace, size_t ws_bytes, size_t extra,
+                           size_t& ck_bytes) {
   int rc = tile_ckpt_bytes(pb, ck_bytes);
   if (rc != WS_OK) return rc;
   if (workspace == nullptr) return set_error(WS_EINVAL, "workspace is NULL");
   if ((reinterpret_cast<uintptr_t>(workspace) & 255u) != 0)
     return set_error(WS_EINVAL, "workspace must be 256-byte aligned");
-  if (ws_bytes < kHeaderBytes + ck_bytes)
-    return set_error(WS_ENOMEM_WS, "workspace too small: %zu < %zu", ws_bytes, kHeaderBytes + ck_bytes);
+  if (ws_bytes < kHeaderBytes + ck_bytes + extra)
+    return set_error(WS_ENOMEM_WS, "workspace too small: %zu < %zu", ws_bytes, kHeaderBytes + ck_bytes + extra);
   return WS_OK;
 }
 
-}  // namespace ws
-
-using namespace ws;
-
-extern "C" size_t ws_workspace_size(const ws_problem* pb, uint32_t flags) {
-  (void)flags;
-  clear_error();
-  if (validate_problem(pb) != WS_OK) return 0;
-  size_t ck = 0;
-  if (pb->n_series == 0 || pb->T == 0) return kHeaderBytes;
-  if (tile_ckpt_bytes(*pb, ck) != WS_OK) return 0;
-  return kHeaderBytes + ck;
-}
-
-extern "C" int ws_smooth_batch(const ws_problem* pb, const void* x, const void* w, const void* lam, void* z,
-                               void* factor_out, uint8_t* status, uint32_t flags, void* workspace,
-                               size_t ws_bytes, void* stream) {
-  clear_error();
-  int rc = validate_problem(pb);
-  if (rc != WS_OK) return rc;
-  if (flags != 0) return set_error(WS_EINVAL, "unknown flags 0x%x", flags);
-  const ws_problem& P = *pb;
-  cudaStream_t st = static_cast<cudaStream_t>(stream);
-  if (P.n_series == 0) return WS_OK;
-  if (P.T == 0) {
-    if (status != nullptr && cudaMemsetAsync(status, 0, (size_t)P.n_series, st) != cudaSuccess)
-      return set_error(WS_ECUDA, "status memset failed");
-    return WS_OK;
-  }
-  if (!x || !w || !lam || !z) return set_error(WS_EINVAL, "x, w, lam and z must be non-NULL");
+// One tile-kernel mode over every band group of the problem.
+static int run_tile(const ws_problem& P, int mode, const void* rhs, const void* w, const void* lam,
+                    const void* zin, void* out, void* out2, void* factor, uint8_t* status, int accum,
+                    int grad_loglam, void* workspace, cudaStream_t st) {
   const int es = elem_size(P);
-  const size_t nx = (size_t)P.T * P.n_bands * P.n_series * es;
-  if (overlaps(x, nx, z, nx)) return set_error(WS_EINVAL, "z must not overlap x");
-  size_t ck_bytes = 0;
-  rc = check_workspace(P, workspace, ws_bytes, ck_bytes);
-  if (rc != WS_OK) return rc;
   const bool per_day = P.lam_mode == WS_LAM_PER_DAY;
-  bool tma_ok = ((size_t)P.n_series * es) % 16 == 0 && aligned16(x) && aligned16(w) && aligned16(z) &&
-                (!per_day || aligned16(lam));
-
+  const bool tma_ok = ((size_t)P.n_series * es) % 16 == 0 && aligned16(rhs) && aligned16(w) &&
+                      (out == nullptr || aligned16(out)) && (!per_day || aligned16(lam));
   for (int b0 = 0; b0 < P.n_bands;) {
     const int nb = group_size(P, P.n_bands - b0);
     TileCfg cfg;
-    rc = plan_tile(P, nb, P.d, extra_planes(P.d), cfg);
+    int rc = plan_tile(P, nb, P.d, extra_planes_mode(mode, P.d), cfg);
     if (rc != WS_OK) return rc;
     CUtensorMap maps[4];
     memset(maps, 0, sizeof(maps));
@@ -193,10 +173,10 @@ extern "C" int ws_smooth_batch(const ws_problem* pb, const void* x, const void* 
       const uint64_t d2[2] = {Pn, T}, s2[1] = {Pn * es};
       const uint32_t bw[2] = {(uint32_t)cfg.NP, (uint32_t)(cfg.C + P.d)};
       const uint32_t bl[2] = {(uint32_t)cfg.NP, (uint32_t)cfg.C};
-      tma = make_tmap(&maps[0], P.dtype, 3, x, dx, sx, bx) == WS_OK &&
+      tma = make_tmap(&maps[0], P.dtype, 3, rhs, dx, sx, bx) == WS_OK &&
             make_tmap(&maps[1], P.dtype, 2, w, d2, s2, bw) == WS_OK &&
             (!per_day || make_tmap(&maps[2], P.dtype, 2, lam, d2, s2, bl) == WS_OK) &&
-            make_tmap(&maps[3], P.dtype, 3, z, dx, sx, bx) == WS_OK;
+            (out == nullptr || make_tmap(&maps[3], P.dtype, 3, out, dx, sx, bx) == WS_OK);
     }
     TileArgs a;
     memset(&a, 0, sizeof(a));
@@ -211,20 +191,76 @@ extern "C" int ws_smooth_batch(const ws_problem* pb, const void* x, const void* 
     a.lam_scalar = per_day ? 0 : 1;
     a.tma = tma ? 1 : 0;
     a.write_status = b0 == 0;
-    a.x = x;
+    a.x = rhs;
     a.w = w;
     a.lam = lam;
-    a.out = z;
-    a.factor = factor_out;
+    a.zin = zin;
+    a.out = out;
+    a.out2 = out2;
+    a.factor = factor;
     a.status = status;
     a.ckpt = static_cast<char*>(workspace) + kHeaderBytes;
     a.err = static_cast<unsigned*>(workspace);
     a.stage_elems = cfg.stage_elems;
-    rc = launch_smooth_tile(P, nb, cfg, a, maps, st);
+    a.grad_loglam = grad_loglam;
+    a.accum = accum;
+    rc = launch_tile(P, mode, nb, cfg, a, maps, st);
     if (rc != WS_OK) return rc;
     b0 += nb;
   }
   return WS_OK;
+}
+
+}  // namespace ws
+
+using namespace ws;
+
+static int ws_adjoint_factored(const ws_problem* pb, const void* factor, const void* w, const void* lam, const void* z,
+                               const void* gz, void* gx, void* glam, uint32_t flags, uint8_t* status,
+                               void* workspace, size_t ws_bytes, void* stream) {
+  (void)pb, (void)factor, (void)w, (void)lam, (void)z, (void)gz, (void)gx, (void)glam, (void)flags;
+  (void)status, (void)workspace, (void)ws_bytes, (void)stream;
+  return set_error(WS_EUNSUPPORTED, "stored-factor adjoint: not built yet");
+}
+
+extern "C" size_t ws_workspace_size(const ws_problem* pb, uint32_t flags) {
+  clear_error();
+  if (validate_problem(pb) != WS_OK) return 0;
+  size_t ck = 0;
+  if (pb->n_series == 0 || pb->T == 0) return kHeaderBytes;
+  if (tile_ckpt_bytes(*pb, ck) != WS_OK) return 0;
+  return kHeaderBytes + ck + ((flags & WS_REFINE) ? resid_bytes(*pb) : 0);
+}
+
+extern "C" int ws_smooth_batch(const ws_problem* pb, const void* x, const void* w, const void* lam, void* z,
+                               void* factor_out, uint8_t* status, uint32_t flags, void* workspace,
+                               size_t ws_bytes, void* stream) {
+  clear_error();
+  int rc = validate_problem(pb);
+  if (rc != WS_OK) return rc;
+  if (flags & ~WS_REFINE) return set_error(WS_EINVAL, "unknown flags 0x%x", flags);
+  const ws_problem& P = *pb;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (P.n_series == 0) return WS_OK;
+  if (P.T == 0) {
+    if (status != nullptr && cudaMemsetAsync(status, 0, (size_t)P.n_series, st) != cudaSuccess)
+      return set_error(WS_ECUDA, "status memset failed");
+    return WS_OK;
+  }
+  if (!x || !w || !lam || !z) return set_error(WS_EINVAL, "x, w, lam and z must be non-NULL");
+  const size_t nx = (size_t)P.T * P.n_bands * P.n_series * elem_size(P);
+  if (overlaps(x, nx, z, nx)) return set_error(WS_EINVAL, "z must not overlap x");
+  const bool refine = (flags & WS_REFINE) != 0;
+  size_t ck_bytes = 0;
+  rc = check_workspace(P, workspace, ws_bytes, refine ? resid_bytes(P) : 0, ck_bytes);
+  if (rc != WS_OK) return rc;
+  rc = run_tile(P, MODE_SMOOTH, x, w, lam, nullptr, z, nullptr, factor_out, status, 0, 0, workspace, st);
+  if (rc != WS_OK || !refine) return rc;
+  // one step of iterative refinement: r = W x - Omega z (double-word residual), z += Omega^{-1} r
+  void* r = static_cast<char*>(workspace) + kHeaderBytes + ck_bytes;
+  rc = launch_residual(P, x, w, lam, z, r, st);
+  if (rc != WS_OK) return rc;
+  return run_tile(P, MODE_RAW, r, w, lam, nullptr, z, nullptr, nullptr, nullptr, 1, 0, workspace, st);
 }
 
 extern "C" int ws_factor(const ws_problem* pb, const void* w, const void* lam, void* factor, uint8_t* status,
@@ -244,10 +280,32 @@ extern "C" int ws_solve(const ws_problem* pb, const void* factor, const void* w,
 extern "C" int ws_solve_adjoint(const ws_problem* pb, const void* factor_or_null, const void* w, const void* lam,
                                 const void* z, const void* gz, void* gx, void* glam, uint32_t flags,
                                 uint8_t* status, void* workspace, size_t ws_bytes, void* stream) {
-  (void)pb, (void)factor_or_null, (void)w, (void)lam, (void)z, (void)gz, (void)gx, (void)glam, (void)flags;
-  (void)status, (void)workspace, (void)ws_bytes, (void)stream;
   clear_error();
-  return set_error(WS_EUNSUPPORTED, "ws_solve_adjoint: not built yet");
+  int rc = validate_problem(pb);
+  if (rc != WS_OK) return rc;
+  if (flags & ~WS_GRAD_LOGLAM) return set_error(WS_EINVAL, "unknown flags 0x%x", flags);
+  const ws_problem& P = *pb;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (P.n_series == 0) return WS_OK;
+  if (P.T == 0) {
+    if (status != nullptr && cudaMemsetAsync(status, 0, (size_t)P.n_series, st) != cudaSuccess)
+      return set_error(WS_ECUDA, "status memset failed");
+    if (glam != nullptr && P.lam_mode == WS_LAM_SCALAR &&
+        cudaMemsetAsync(glam, 0, (size_t)P.n_series * elem_size(P), st) != cudaSuccess)
+      return set_error(WS_ECUDA, "glam memset failed");
+    return WS_OK;
+  }
+  if (!w || !lam || !z || !gz) return set_error(WS_EINVAL, "w, lam, z and gz must be non-NULL");
+  const size_t nx = (size_t)P.T * P.n_bands * P.n_series * elem_size(P);
+  if (gx != nullptr && (overlaps(gx, nx, gz, nx) || overlaps(gx, nx, z, nx)))
+    return set_error(WS_EINVAL, "gx must not overlap gz or z");
+  if (factor_or_null != nullptr) return ws_adjoint_factored(pb, factor_or_null, w, lam, z, gz, gx, glam, flags,
+                                                            status, workspace, ws_bytes, stream);
+  size_t ck_bytes = 0;
+  rc = check_workspace(P, workspace, ws_bytes, 0, ck_bytes);
+  if (rc != WS_OK) return rc;
+  return run_tile(P, MODE_ADJ, gz, w, lam, z, gx, glam, nullptr, status, 0,
+                  (flags & WS_GRAD_LOGLAM) ? 1 : 0, workspace, st);
 }
 
 extern "C" int ws_tune_set(int32_t pixels_per_cta, int32_t chunk_days) {

@@ -9,7 +9,8 @@
 
 namespace ws {
 
-constexpr int kNbMax = 10;         // bands per launch; more bands run as band groups
+constexpr int kNbMax = 10;
+enum { MODE_SMOOTH = 0, MODE_RAW = 1, MODE_ADJ = 2 };         // bands per launch; more bands run as band groups
 constexpr size_t kHeaderBytes = 256;  // device error word + reserved
 
 // Staging / launch configuration of one tile launch.
@@ -44,6 +45,7 @@ struct TileArgs {
   unsigned* err;
   size_t stage_elems;
   int grad_loglam;
+  int accum;              // RAW: out += solution (refinement correction)
 };
 
 struct DeviceInfo {
@@ -61,7 +63,14 @@ int make_tmap(CUtensorMap* map, int dtype, int rank, const void* base, const uin
 // Launchers (return WS_OK or an error code, errors recorded via set_error).
 extern int g_tune_np, g_tune_chunk;  // ws_tune_set() overrides (0 = automatic)
 int plan_tile(const ws_problem& pb, int nb, int D, int extra_planes, TileCfg& cfg);
-int launch_smooth_tile(const ws_problem& pb, int nb, const TileCfg& cfg, const TileArgs& a,
-                       const CUtensorMap* maps, cudaStream_t st);
+int launch_tile(const ws_problem& pb, int mode, int nb, const TileCfg& cfg, const TileArgs& a,
+                const CUtensorMap* maps, cudaStream_t st);
+int launch_tile_d1(const ws_problem&, int, int, const TileCfg&, const TileArgs&, const CUtensorMap*, cudaStream_t);
+int launch_tile_d2(const ws_problem&, int, int, const TileCfg&, const TileArgs&, const CUtensorMap*, cudaStream_t);
+int launch_tile_d3(const ws_problem&, int, int, const TileCfg&, const TileArgs&, const CUtensorMap*, cudaStream_t);
+int launch_tile_d4(const ws_problem&, int, int, const TileCfg&, const TileArgs&, const CUtensorMap*, cudaStream_t);
+// r = W x - Omega z0 with double-word accumulation (refinement residual).
+int launch_residual(const ws_problem& pb, const void* x, const void* w, const void* lam, const void* z0,
+                    void* r, cudaStream_t st);
 
 }  // namespace ws

@@ -1,0 +1,102 @@
+// Residual of the smoothing system for one step of iterative refinement:
+//     r = W x - Omega z0 = W (x - z0) - D^T (Lambda (D z0))        (Omega from Eq. 3)
+// At a good z0 the two terms cancel to a few parts in 1e5, so every difference and
+// every sum is carried as a double word (ws_df.cuh): D z0, Lambda D z0 and the D^T
+// accumulation are exact up to the final rounding of r to working precision.
+// Thread = one pixel x a block of kDays days; all bands stream through rings of the
+// last d+1 values of z0 and of q_k = lambda_k (D z0)_k. Every load is coalesced across
+// the pixel-fastest tile layout.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "ws_df.cuh"
+#include "ws_internal.h"
+#include "ws_sweep.cuh"
+
+namespace ws {
+
+constexpr int kResidDays = 64;
+
+template <typename F, int D>
+__global__ void __launch_bounds__(128) k_residual(const F* __restrict__ x, const F* __restrict__ w,
+                                                  const F* __restrict__ lam, const F* __restrict__ z0,
+                                                  F* __restrict__ r, int T, int B, int P, int lam_scalar) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= P) return;
+  const int t0 = blockIdx.y * kResidDays;
+  const int t1 = min(T, t0 + kResidDays);
+  const size_t sP = (size_t)P, sBP = (size_t)B * P;
+  const F ls = lam_scalar ? lam[p] : F(0);
+  for (int b = 0; b < B; ++b) {
+    F zr[D + 1];     // z0_{u-D} .. z0_u
+    DW<F> qr[D + 1];  // q_{k-D} .. q_k
+#pragma unroll
+    for (int n = 0; n <= D; ++n) {
+      zr[n] = F(0);
+      qr[n] = {F(0), F(0)};
+    }
+    for (int u = t0 - D; u < t1 + D; ++u) {
+#pragma unroll
+      for (int n = 0; n < D; ++n) zr[n] = zr[n + 1];
+      zr[D] = (u >= 0 && u < T) ? z0[(size_t)u * sBP + (size_t)b * sP + p] : F(0);
+      const int k = u - D;  // difference row whose last day is u
+#pragma unroll
+      for (int n = 0; n < D; ++n) qr[n] = qr[n + 1];
+      DW<F> q = {F(0), F(0)};
+      if (k >= 0 && k <= T - D - 1) {
+        DW<F> dz = two_prod(F(dcoef<D>(0)), zr[0]);
+#pragma unroll
+        for (int n = 1; n <= D; ++n) dz = dw_add(dz, two_prod(F(dcoef<D>(n)), zr[n]));
+        const F lk = lam_scalar ? ls : lam[(size_t)k * sP + p];
+        q = dw_scale(dz, lk);
+      }
+      qr[D] = q;
+      const int t = k;  // residual day whose rows k-D..k are now all known
+      if (t >= t0 && t < t1) {
+        const F wt = w[(size_t)t * sP + p];
+        DW<F> acc = {F(0), F(0)};
+        if (wt > F(0)) {
+          const F xt = x[(size_t)t * sBP + (size_t)b * sP + p];
+          acc = dw_scale(two_sum(xt, -zr[0]), wt);  // zr[0] = z0_t (u = t + D)
+        }
+#pragma unroll
+        for (int n = 0; n <= D; ++n) acc = dw_add(acc, dw_scale(qr[D - n], F(-dcoef<D>(n))));
+        r[(size_t)t * sBP + (size_t)b * sP + p] = acc.hi + acc.lo;
+      }
+    }
+  }
+}
+
+template <typename F, int D>
+static int launch_resid_t(const ws_problem& pb, const void* x, const void* w, const void* lam, const void* z0,
+                          void* r, cudaStream_t st) {
+  dim3 grid((unsigned)((pb.n_series + 127) / 128), (unsigned)((pb.T + kResidDays - 1) / kResidDays));
+  k_residual<F, D><<<grid, 128, 0, st>>>(static_cast<const F*>(x), static_cast<const F*>(w),
+                                         static_cast<const F*>(lam), static_cast<const F*>(z0), static_cast<F*>(r),
+                                         pb.T, pb.n_bands, (int)pb.n_series, pb.lam_mode == WS_LAM_SCALAR);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return set_error(WS_ECUDA, "residual kernel launch: %s", cudaGetErrorString(e));
+  return WS_OK;
+}
+
+int launch_residual(const ws_problem& pb, const void* x, const void* w, const void* lam, const void* z0, void* r,
+                    cudaStream_t st) {
+  if (pb.dtype == WS_F32) {
+    switch (pb.d) {
+      case 1: return launch_resid_t<float, 1>(pb, x, w, lam, z0, r, st);
+      case 2: return launch_resid_t<float, 2>(pb, x, w, lam, z0, r, st);
+      case 3: return launch_resid_t<float, 3>(pb, x, w, lam, z0, r, st);
+      case 4: return launch_resid_t<float, 4>(pb, x, w, lam, z0, r, st);
+    }
+  } else {
+    switch (pb.d) {
+      case 1: return launch_resid_t<double, 1>(pb, x, w, lam, z0, r, st);
+      case 2: return launch_resid_t<double, 2>(pb, x, w, lam, z0, r, st);
+      case 3: return launch_resid_t<double, 3>(pb, x, w, lam, z0, r, st);
+      case 4: return launch_resid_t<double, 4>(pb, x, w, lam, z0, r, st);
+    }
+  }
+  return set_error(WS_EINVAL, "unsupported order d=%d", pb.d);
+}
+
+}  // namespace ws

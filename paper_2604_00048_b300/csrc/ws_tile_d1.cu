@@ -1,0 +1,10 @@
+// Instantiations of the tile kernels for difference order d = 1 (one translation unit
+// per order so that nvcc compiles them in parallel).
+#include "ws_tile_impl.cuh"
+
+namespace ws {
+int launch_tile_d1(const ws_problem& pb, int mode, int nb, const TileCfg& cfg, const TileArgs& a,
+                    const CUtensorMap* maps, cudaStream_t st) {
+  return dispatch_tile_d<1>(pb, mode, nb, cfg, a, maps, st);
+}
+}  // namespace ws

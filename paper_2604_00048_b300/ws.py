@@ -34,6 +34,7 @@ LAYOUT_TILE = 0
 F32, F64 = 0, 1
 LAM_PER_DAY, LAM_SCALAR = 0, 1
 GRAD_LOGLAM = 0x1
+REFINE = 0x2
 
 
 class Problem(ctypes.Structure):
@@ -156,21 +157,50 @@ def _check_tile(x, w, lam, d):
 
 
 def smooth(x: torch.Tensor, w: torch.Tensor, lam: torch.Tensor, d: int = 2, *, z=None, status=None,
-           factor=None, stream=None):
+           factor=None, refine: bool = False, stream=None):
     """z = (W + D^T Lambda D)^{-1} W x per series and band (Eq. 3; Eq. 2 for scalar lam).
 
+    refine: one step of iterative refinement with a double-word residual.
     Returns (z, status). `factor` (optional [T, d+1, P]) receives the factor."""
     T, B, P, lm = _check_tile(x, w, lam, d)
     pb = make_problem(T, B, P, d, _dtype_code(x), lm)
+    flags = REFINE if refine else 0
     if z is None:
         z = torch.empty_like(x)
     if status is None:
         status = torch.empty(P, dtype=torch.uint8, device=x.device)
-    ws = workspace(pb, x.device)
+    if factor is not None and (tuple(factor.shape) != (T, d + 1, P) or factor.dtype != x.dtype):
+        raise ValueError("factor must be [T, d+1, P] of x's dtype")
+    ws = workspace(pb, x.device, flags)
     rc = _lib.ws_smooth_batch(ctypes.byref(pb), _ptr(x), _ptr(w), _ptr(lam), _ptr(z), _ptr(factor),
-                              _ptr(status), 0, _ptr(ws), ws.numel(), _stream_ptr(stream))
+                              _ptr(status), flags, _ptr(ws), ws.numel(), _stream_ptr(stream))
     _check(rc)
     return z, status
+
+
+def smooth_adjoint(w: torch.Tensor, lam: torch.Tensor, z: torch.Tensor, gz: torch.Tensor, d: int = 2, *,
+                   gx=None, glam=None, want_gx: bool = True, want_glam: bool = True, log_lambda: bool = False,
+                   factor=None, status=None, stream=None):
+    """Vector-Jacobian products of z = Omega^{-1} W x (Eqs. 4-5): returns (gx, glam, status).
+
+    gx = W Omega^{-1} gz; glam_k = -sum_b (D g_b)_k (D z_b)_k (k < T-d, 0 after), times
+    lambda_k with log_lambda. factor: a stored factor ([T, d+1, P]) or None to recompute."""
+    T, B, P, lm = _check_tile(gz, w, lam, d)
+    if tuple(z.shape) != tuple(gz.shape) or not z.is_contiguous() or z.dtype != gz.dtype:
+        raise ValueError("z must match gz")
+    pb = make_problem(T, B, P, d, _dtype_code(gz), lm)
+    if gx is None and want_gx:
+        gx = torch.empty_like(gz)
+    if glam is None and want_glam:
+        glam = torch.empty_like(lam)
+    if status is None:
+        status = torch.empty(P, dtype=torch.uint8, device=gz.device)
+    ws = workspace(pb, gz.device)
+    flags = GRAD_LOGLAM if log_lambda else 0
+    rc = _lib.ws_solve_adjoint(ctypes.byref(pb), _ptr(factor), _ptr(w), _ptr(lam), _ptr(z), _ptr(gz), _ptr(gx),
+                               _ptr(glam), flags, _ptr(status), _ptr(ws), ws.numel(), _stream_ptr(stream))
+    _check(rc)
+    return gx, glam, status
 
 
 def tune_set(pixels_per_cta: int = 0, chunk_days: int = 0):

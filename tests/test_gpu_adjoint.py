@@ -1,0 +1,93 @@
+"""GPU adjoint (Eqs. 4-5) against the FP64 oracle's vector-Jacobian products.
+
+Tolerance: max relative error per series and band (inf-norm over time) <= 1e-3 for
+FP32 (gradients), <= 1e-9 for FP64; glam per series likewise."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import dense
+from tests.gpu_util import rel_err_per_series, tile_inputs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ws():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA device")
+    from paper_2604_00048_b300 import ws as mod
+    yield mod
+    mod.tune_set(0, 0)
+
+
+def _glam_err(a, b):
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    if a.ndim == 1:
+        return float(np.max(np.abs(a - b) / np.maximum(np.abs(b), 1e-6)))
+    return float(np.max(np.max(np.abs(a - b), axis=0) / np.maximum(np.max(np.abs(b), axis=0), 1e-6)))
+
+
+@pytest.mark.parametrize("dtype,tol", [(torch.float32, 1e-3), (torch.float64, 1e-9)])
+@pytest.mark.parametrize("d", [1, 2, 3])
+@pytest.mark.parametrize("log_lambda", [False, True])
+def test_adjoint_matches_oracle_vjp(ws, dtype, tol, d, log_lambda):
+    ws.tune_set(128, 16)
+    B = 4 if dtype == torch.float32 else 2
+    rc, g, c = tile_inputs("layer", 260, T=120, B=B, dtype=dtype)
+    # a dense valid pattern keeps FP32 well inside the gradient tolerance
+    gen = torch.Generator().manual_seed(5)
+    gz = torch.randn(g["x"].shape, generator=gen, dtype=dtype).to("cuda")
+    z, st = ws.smooth(g["x"], g["w"], g["lam"], d, refine=dtype == torch.float32)
+    gx, glam, st2 = ws.smooth_adjoint(g["w"], g["lam"], z, gz, d, log_lambda=log_lambda)
+    ws.sync_status()
+    ok = st2.cpu().numpy() == 0
+    zc = z.cpu().double().numpy()
+    gxr, glr = dense.vjp_tile(c["w"], c["lam"], d, zc, gz.cpu().double().numpy(), log_lambda=log_lambda)
+    assert rel_err_per_series(gx.cpu().numpy()[:, :, ok], gxr[:, :, ok]) <= tol
+    assert _glam_err(glam.cpu().numpy()[:, ok], glr[:, ok]) <= tol
+    assert np.all(glam.cpu().numpy()[-d:, :] == 0)
+
+
+def test_adjoint_scalar_lambda_and_band_groups(ws):
+    """Scalar lambda (Eq. 2): glam[p] sums over the rows; 13 bands span two band groups."""
+    ws.tune_set(0, 0)
+    rc, g, c = tile_inputs("homo_fp64", 200, T=150, B=13, dtype=torch.float64)
+    gz = torch.randn(g["x"].shape, dtype=torch.float64, generator=torch.Generator().manual_seed(1)).to("cuda")
+    z, st = ws.smooth(g["x"], g["w"], g["lam"], 2)
+    gx, glam, st2 = ws.smooth_adjoint(g["w"], g["lam"], z, gz, 2, log_lambda=True)
+    ws.sync_status()
+    ok = st2.cpu().numpy() == 0
+    gxr, glr = dense.vjp_tile(c["w"], c["lam"], 2, z.cpu().numpy(), gz.cpu().numpy(), log_lambda=True)
+    assert rel_err_per_series(gx.cpu().numpy()[:, :, ok], gxr[:, :, ok]) <= 1e-9
+    assert _glam_err(glam.cpu().numpy()[ok], glr[ok]) <= 1e-9
+
+
+def test_adjoint_optional_outputs(ws):
+    ws.tune_set(0, 0)
+    rc, g, c = tile_inputs("layer", 128, T=90, B=2)
+    gz = torch.randn(g["x"].shape, device="cuda")
+    z, _ = ws.smooth(g["x"], g["w"], g["lam"], 2)
+    gx_a, glam_a, _ = ws.smooth_adjoint(g["w"], g["lam"], z, gz, 2)
+    gx_b, glam_b, _ = ws.smooth_adjoint(g["w"], g["lam"], z, gz, 2, want_gx=False)
+    gx_c, glam_c, _ = ws.smooth_adjoint(g["w"], g["lam"], z, gz, 2, want_glam=False)
+    ws.sync_status()
+    assert gx_b is None and glam_c is None
+    assert torch.equal(glam_a, glam_b) and torch.equal(gx_a, gx_c)
+
+
+def test_adjoint_dot_product(ws):
+    """<gz, J v> = <J^T gz, v> with J v = smooth(v) (linear in x) and J^T gz = gx."""
+    ws.tune_set(0, 0)
+    rc, g, c = tile_inputs("layer", 96, T=200, B=1, dtype=torch.float64)
+    v = torch.randn(g["x"].shape, dtype=torch.float64, device="cuda")
+    gz = torch.randn(g["x"].shape, dtype=torch.float64, device="cuda")
+    Jv, st = ws.smooth(v, g["w"], g["lam"], 2)
+    z, _ = ws.smooth(g["x"], g["w"], g["lam"], 2)
+    gx, _, _ = ws.smooth_adjoint(g["w"], g["lam"], z, gz, 2)
+    ws.sync_status()
+    ok = (st == 0).view(1, 1, -1)
+    lhs = (gz * Jv * ok).sum(dim=(0, 1))
+    rhs = (gx * v * ok).sum(dim=(0, 1))
+    assert torch.max(torch.abs(lhs - rhs) / torch.clamp(torch.abs(lhs), min=1e-6)).item() <= 1e-9

@@ -27,11 +27,13 @@ def ws():
 @pytest.mark.parametrize("d", [1, 2, 3, 4])
 @pytest.mark.parametrize("P", [300, 301])           # 300: TMA staging; 301: row pitch not 16-byte aligned
 def test_smooth_matches_dense_oracle_many_chunks(ws, dtype, d, P):
-    """Several tiles of 128 pixels plus a ragged tile, T = 61 days in chunks of 8 (ragged last chunk)."""
+    """Several tiles of 128 pixels plus a ragged tile, T = 61 days in chunks of 8 (ragged last chunk).
+    Sparse weights (2-5 valid days) make these systems ill-conditioned: FP32 runs with one
+    refinement step."""
     ws.tune_set(128, 8)
     B = 3 if dtype == torch.float32 else 2
     rc, g, c = tile_inputs("layer", P, T=61, B=B, dtype=dtype)
-    z, st = ws.smooth(g["x"], g["w"], g["lam"], d)
+    z, st = ws.smooth(g["x"], g["w"], g["lam"], d, refine=dtype == torch.float32)
     ws.sync_status()
     zr, ok = dense.smooth_tile(c["x"], c["w"], c["lam"], d)
     st = st.cpu().numpy()
@@ -43,12 +45,14 @@ def test_smooth_matches_dense_oracle_many_chunks(ws, dtype, d, P):
     assert np.all(z.cpu().numpy()[:, :, ~ok] == 0)
 
 
+@pytest.mark.parametrize("refine", [False, True])
 @pytest.mark.parametrize("B", [1, 4, 10, 13])
-def test_smooth_band_counts_auto_config(ws, B):
-    """Automatic staging configuration; 13 bands run as two band groups."""
+def test_smooth_band_counts_auto_config(ws, B, refine):
+    """Automatic staging configuration; 13 bands run as two band groups. On these inputs
+    (T = 400, 5-day revisit, p = 0.35) the unrefined FP32 path is already within 1e-4."""
     ws.tune_set(0, 0)
     rc, g, c = tile_inputs("hetero_tile", 256, T=400, B=B)
-    z, st = ws.smooth(g["x"], g["w"], g["lam"], 2)
+    z, st = ws.smooth(g["x"], g["w"], g["lam"], 2, refine=refine)
     ws.sync_status()
     zb, stb = banded.smooth_tile(c["x"], c["w"], c["lam"], 2)
     assert np.array_equal(st.cpu().numpy(), stb)
@@ -84,7 +88,7 @@ def test_status_codes_and_zero_fill(ws):
     lam[T - 1, 6] = -5.0               # last d entries are ignored
     dev = "cuda"
     z, st = ws.smooth(torch.tensor(x, dtype=torch.float32, device=dev), torch.tensor(w, dtype=torch.float32, device=dev),
-                      torch.tensor(lam, dtype=torch.float32, device=dev), d)
+                      torch.tensor(lam, dtype=torch.float32, device=dev), d, refine=True)
     ws.sync_status()
     st = st.cpu().numpy().tolist()
     assert st == [1, 1, 3, 3, 2, 0, 0, 0]
@@ -101,7 +105,7 @@ def test_short_series(ws, T):
     d = 2
     rc, g, c = tile_inputs("layer", 64, T=T, B=1)
     w = torch.ones_like(g["w"])
-    z, st = ws.smooth(g["x"], w, g["lam"], d)
+    z, st = ws.smooth(g["x"], w, g["lam"], d, refine=True)
     ws.sync_status()
     zr, ok = dense.smooth_tile(c["x"], np.ones_like(c["w"]), c["lam"], d)
     assert np.array_equal(st.cpu().numpy() == 0, ok)
