@@ -109,6 +109,16 @@ int ws_smooth_batch(const ws_problem* pb, const void* x, const void* w, const vo
                     void* factor_out, uint8_t* status, uint32_t flags, void* workspace,
                     size_t ws_bytes, void* stream);
 
+/* One step of iterative refinement of a smoothing result z, in place:
+ *     r = W x - Omega z        (double-word accumulation: FP64-level accuracy from
+ *                               error-free transformations of the working precision)
+ *     z <- z + Omega^{-1} r    (same rotation factorisation, recomputed)
+ * x, w, lam: the inputs z was computed from. Needs ws_workspace_size(pb, WS_REFINE).
+ * The paper (Section 3) solves in one pass; this step restores the accuracy FP32 loses
+ * on ill-conditioned series (large lambda, few valid days, d >= 3). */
+int ws_refine(const ws_problem* pb, const void* x, const void* w, const void* lam, void* z,
+              void* workspace, size_t ws_bytes, void* stream);
+
 /* Factor only (Section 3.1): writes, per day t, factor[(t*(d+1) + 0)*P + p] = 1/D_t and
  * factor[(t*(d+1) + j)*P + p] = L[t+j][t] (j = 1..d) of Omega = L diag(D) L^T with L
  * unit lower triangular banded (entries that would fall past T are 0). One forward

@@ -256,7 +256,26 @@ extern "C" int ws_smooth_batch(const ws_problem* pb, const void* x, const void* 
   if (rc != WS_OK) return rc;
   rc = run_tile(P, MODE_SMOOTH, x, w, lam, nullptr, z, nullptr, factor_out, status, 0, 0, workspace, st);
   if (rc != WS_OK || !refine) return rc;
-  // one step of iterative refinement: r = W x - Omega z (double-word residual), z += Omega^{-1} r
+  void* r = static_cast<char*>(workspace) + kHeaderBytes + ck_bytes;
+  rc = launch_residual(P, x, w, lam, z, r, st);
+  if (rc != WS_OK) return rc;
+  return run_tile(P, MODE_RAW, r, w, lam, nullptr, z, nullptr, nullptr, nullptr, 1, 0, workspace, st);
+}
+
+extern "C" int ws_refine(const ws_problem* pb, const void* x, const void* w, const void* lam, void* z,
+                         void* workspace, size_t ws_bytes, void* stream) {
+  clear_error();
+  int rc = validate_problem(pb);
+  if (rc != WS_OK) return rc;
+  const ws_problem& P = *pb;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (P.n_series == 0 || P.T == 0) return WS_OK;
+  if (!x || !w || !lam || !z) return set_error(WS_EINVAL, "x, w, lam and z must be non-NULL");
+  const size_t nx = (size_t)P.T * P.n_bands * P.n_series * elem_size(P);
+  if (overlaps(x, nx, z, nx)) return set_error(WS_EINVAL, "z must not overlap x");
+  size_t ck_bytes = 0;
+  rc = check_workspace(P, workspace, ws_bytes, resid_bytes(P), ck_bytes);
+  if (rc != WS_OK) return rc;
   void* r = static_cast<char*>(workspace) + kHeaderBytes + ck_bytes;
   rc = launch_residual(P, x, w, lam, z, r, st);
   if (rc != WS_OK) return rc;

@@ -55,6 +55,8 @@ _lib.ws_solve.restype = ctypes.c_int
 _lib.ws_solve.argtypes = [_PP, _vp, _vp, _vp, _vp, _u32, _vp, _sz, _vp]
 _lib.ws_solve_adjoint.restype = ctypes.c_int
 _lib.ws_solve_adjoint.argtypes = [_PP, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _u32, _vp, _vp, _sz, _vp]
+_lib.ws_refine.restype = ctypes.c_int
+_lib.ws_refine.argtypes = [_PP, _vp, _vp, _vp, _vp, _vp, _sz, _vp]
 _lib.ws_tune_set.restype = ctypes.c_int
 _lib.ws_tune_set.argtypes = [ctypes.c_int32, ctypes.c_int32]
 _lib.ws_sync_status.restype = ctypes.c_int
@@ -176,6 +178,16 @@ def smooth(x: torch.Tensor, w: torch.Tensor, lam: torch.Tensor, d: int = 2, *, z
                               _ptr(status), flags, _ptr(ws), ws.numel(), _stream_ptr(stream))
     _check(rc)
     return z, status
+
+
+def refine(x: torch.Tensor, w: torch.Tensor, lam: torch.Tensor, z: torch.Tensor, d: int = 2, *, stream=None):
+    """One step of iterative refinement of z (in place) with a double-word residual."""
+    T, B, P, lm = _check_tile(x, w, lam, d)
+    pb = make_problem(T, B, P, d, _dtype_code(x), lm)
+    ws = workspace(pb, x.device, REFINE)
+    _check(_lib.ws_refine(ctypes.byref(pb), _ptr(x), _ptr(w), _ptr(lam), _ptr(z), _ptr(ws), ws.numel(),
+                          _stream_ptr(stream)))
+    return z
 
 
 def smooth_adjoint(w: torch.Tensor, lam: torch.Tensor, z: torch.Tensor, gz: torch.Tensor, d: int = 2, *,
