@@ -138,7 +138,8 @@ def smooth_tile(x, w, lam, d: int):
 
 
 def vjp_tile(w, lam, d: int, z, gz, log_lambda: bool = False):
-    """Tile-layout VJP: returns (gx[t,b,p], glam[t,p]); with log_lambda, dL/dlog(lam) = lam * dL/dlam."""
+    """Tile-layout VJP: returns (gx[t,b,p], glam[t,p]); with log_lambda, dL/dlog(lam) = lam * dL/dlam.
+    Series whose Omega is not positive definite (is_pd) get zeros."""
     w = np.asarray(w, dtype=np.float64)
     lam = np.asarray(lam, dtype=np.float64)
     z = np.asarray(z, dtype=np.float64)
@@ -148,6 +149,8 @@ def vjp_tile(w, lam, d: int, z, gz, log_lambda: bool = False):
     glam = np.zeros((T, P)) if lam.ndim == 2 else np.zeros(P)
     for p in range(P):
         lp = lam[p] if lam.ndim == 1 else lam[:, p]
+        if not is_pd(w[:, p], lp, d):
+            continue                       # singular Omega: gradients zero-filled
         a, b = vjp_one(w[:, p], lp, d, z[:, :, p], gz[:, :, p], per_day=(lam.ndim == 2))
         gx[:, :, p] = a
         if lam.ndim == 2:
