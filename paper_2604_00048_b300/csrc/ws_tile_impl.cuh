@@ -206,15 +206,26 @@ __global__ void __launch_bounds__(256) k_tile(const __grid_constant__ CUtensorMa
     const int dmin = D < T ? D : T;
     const uint8_t code = bad ? WS_SERIES_BADARG : (npos < dmin ? WS_SERIES_NOT_PD : WS_SERIES_OK);
     const bool okser = code == WS_SERIES_OK;
-    F zc[NB][D];   // g (or z) of the next D days, per band
-    F zw[NB][D];   // ADJ: forward output z of the next D days, per band
+    // zc: solution of the next D days (back substitution), per band.
+    // ADJ: difference triangles of g and z at day t+1, for (D g)_t and (D z)_t taken as
+    //      nested first differences (the recursive definition of the order-D forward
+    //      difference): on smooth sequences each subtraction is exact (Sterbenz), where
+    //      the binomial form would cancel ~3 digits in FP32.
+    //      gt[b][j-1] = Delta^j g_{t+1} (j = 1..D-1); zt[b][0] = z_{t+1}, zt[b][j] = Delta^j z_{t+1}.
+    constexpr int DT = D > 1 ? D - 1 : 1;
+    F zc[NB][D];
+    F gt[NB][DT];
+    F zt[NB][D];
 #pragma unroll
-    for (int b = 0; b < NB; ++b)
+    for (int b = 0; b < NB; ++b) {
 #pragma unroll
       for (int j = 0; j < D; ++j) {
         zc[b][j] = F(0);
-        zw[b][j] = F(0);
+        zt[b][j] = F(0);
       }
+#pragma unroll
+      for (int j = 0; j < DT; ++j) gt[b][j] = F(0);
+    }
     F glam_sum = F(0);  // ADJ with scalar lambda
     bool nonfin = false;
     for (int c = a.nch - 1; c >= 0; --c) {
@@ -272,19 +283,23 @@ __global__ void __launch_bounds__(256) k_tile(const __grid_constant__ CUtensorMa
           nonfin |= !finite_(acc);
           F out = okser ? acc : F(0);
           if (MODE == MODE_ADJ) {
-            const F zt = act ? gzin[((size_t)i * a.B + a.b0 + b) * a.P + p] : F(0);
-            if (i < T - D) {
-              F dg = F(dcoef<D>(0)) * out, dz = F(dcoef<D>(0)) * zt;
+            const F zv = act ? gzin[((size_t)i * a.B + a.b0 + b) * a.P + p] : F(0);
+            F cg = out, cz = zv;                 // level j at day t
+            F pg = zc[b][0], pz = zt[b][0];      // level j-1 at day t+1 (j = 1: the values)
+            zt[b][0] = zv;
 #pragma unroll
-              for (int n = 1; n <= D; ++n) {
-                dg = fma(F(dcoef<D>(n)), okser ? zc[b][n - 1] : F(0), dg);
-                dz = fma(F(dcoef<D>(n)), zw[b][n - 1], dz);
+            for (int j = 1; j <= D; ++j) {
+              const F ng = pg - cg, nz = pz - cz;  // Delta^j at day t
+              if (j < D) {
+                pg = gt[b][j - 1];
+                pz = zt[b][j];
+                gt[b][j - 1] = ng;
+                zt[b][j] = nz;
               }
-              dl = fma(dg, dz, dl);
+              cg = ng;
+              cz = nz;
             }
-#pragma unroll
-            for (int j = D - 1; j > 0; --j) zw[b][j] = zw[b][j - 1];
-            zw[b][0] = zt;
+            if (i < T - D) dl = fma(cg, cz, dl);
           }
 #pragma unroll
           for (int j = D - 1; j > 0; --j) zc[b][j] = zc[b][j - 1];
