@@ -76,6 +76,7 @@ extern "C" {
 /* flags */
 #define WS_GRAD_LOGLAM 0x1u   /* ws_solve_adjoint: glam = lambda * dL/dlambda (d/dlog lambda) */
 #define WS_REFINE 0x2u        /* ws_smooth_batch: one step of iterative refinement */
+#define WS_REFINE_ADJOINT 0x4u /* ws_solve_adjoint: one step of iterative refinement of g */
 
 typedef struct ws_problem {
   int64_t n_series; /* P >= 0: number of series (pixels) */
@@ -89,7 +90,8 @@ typedef struct ws_problem {
 
 /* Bytes of device scratch the calls below need for `pb` (checkpoints of the
  * forward sweep plus a 256-byte header holding the device error word; with
- * flags & WS_REFINE also the residual, T*B*P elements). The first
+ * flags & WS_REFINE also the residual, T*B*P elements; with WS_REFINE_ADJOINT two
+ * such arrays). The first
  * 256 bytes must be zero before the first call that uses the workspace (e.g.
  * cudaMemset once after allocation); ws_sync_status() clears the word again.
  * Returns 0 for an invalid problem. */
@@ -137,7 +139,10 @@ int ws_solve(const ws_problem* pb, const void* factor, const void* w, const void
  *     gx_b = W g_b                          (Eq. 5; the vector-Jacobian product)
  *     glam_k = -sum_b (D g_b)_k (D z_b)_k   (Eq. 4), k < T-d; glam_k = 0 for k >= T-d
  * With WS_LAM_SCALAR, glam[p] is the sum over k. With WS_GRAD_LOGLAM, glam is
- * multiplied by lambda (the derivative with respect to log lambda).
+ * multiplied by lambda (the derivative with respect to log lambda). With
+ * WS_REFINE_ADJOINT, g gets one step of iterative refinement (residual gz - Omega g with
+ * double-word accumulation) before the epilogue; needs ws_workspace_size(pb,
+ * WS_REFINE_ADJOINT). (D g)_k and (D z)_k are formed as nested first differences.
  * factor_or_null: a stored factor (ws_factor layout), or NULL to recompute it from
  * (w, lam) inside the sweeps (less memory). gx and glam are each optional (NULL). */
 int ws_solve_adjoint(const ws_problem* pb, const void* factor_or_null, const void* w,

@@ -152,8 +152,8 @@ static int check_workspace(const ws_problem& pb, void* workspace, size_t ws_byte
 
 // One tile-kernel mode over every band group of the problem.
 static int run_tile(const ws_problem& P, int mode, const void* rhs, const void* w, const void* lam,
-                    const void* zin, void* out, void* out2, void* factor, uint8_t* status, int accum,
-                    int grad_loglam, void* workspace, cudaStream_t st) {
+                    const void* zin, const void* g0, void* out, void* out2, void* factor, uint8_t* status,
+                    int accum, int grad_loglam, void* workspace, cudaStream_t st) {
   const int es = elem_size(P);
   const bool per_day = P.lam_mode == WS_LAM_PER_DAY;
   const bool tma_ok = ((size_t)P.n_series * es) % 16 == 0 && aligned16(rhs) && aligned16(w) &&
@@ -195,6 +195,7 @@ static int run_tile(const ws_problem& P, int mode, const void* rhs, const void* 
     a.w = w;
     a.lam = lam;
     a.zin = zin;
+    a.g0 = g0;
     a.out = out;
     a.out2 = out2;
     a.factor = factor;
@@ -229,7 +230,8 @@ extern "C" size_t ws_workspace_size(const ws_problem* pb, uint32_t flags) {
   size_t ck = 0;
   if (pb->n_series == 0 || pb->T == 0) return kHeaderBytes;
   if (tile_ckpt_bytes(*pb, ck) != WS_OK) return 0;
-  return kHeaderBytes + ck + ((flags & WS_REFINE) ? resid_bytes(*pb) : 0);
+  const size_t extra = (flags & WS_REFINE_ADJOINT) ? 2 * resid_bytes(*pb) : ((flags & WS_REFINE) ? resid_bytes(*pb) : 0);
+  return kHeaderBytes + ck + extra;
 }
 
 extern "C" int ws_smooth_batch(const ws_problem* pb, const void* x, const void* w, const void* lam, void* z,
@@ -254,12 +256,12 @@ extern "C" int ws_smooth_batch(const ws_problem* pb, const void* x, const void* 
   size_t ck_bytes = 0;
   rc = check_workspace(P, workspace, ws_bytes, refine ? resid_bytes(P) : 0, ck_bytes);
   if (rc != WS_OK) return rc;
-  rc = run_tile(P, MODE_SMOOTH, x, w, lam, nullptr, z, nullptr, factor_out, status, 0, 0, workspace, st);
+  rc = run_tile(P, MODE_SMOOTH, x, w, lam, nullptr, nullptr, z, nullptr, factor_out, status, 0, 0, workspace, st);
   if (rc != WS_OK || !refine) return rc;
   void* r = static_cast<char*>(workspace) + kHeaderBytes + ck_bytes;
-  rc = launch_residual(P, x, w, lam, z, r, st);
+  rc = launch_residual(P, x, w, lam, z, r, 0, st);
   if (rc != WS_OK) return rc;
-  return run_tile(P, MODE_RAW, r, w, lam, nullptr, z, nullptr, nullptr, nullptr, 1, 0, workspace, st);
+  return run_tile(P, MODE_RAW, r, w, lam, nullptr, z, nullptr, nullptr, nullptr, nullptr, 1, 0, workspace, st);
 }
 
 extern "C" int ws_refine(const ws_problem* pb, const void* x, const void* w, const void* lam, void* z,
@@ -277,9 +279,9 @@ extern "C" int ws_refine(const ws_problem* pb, const void* x, const void* w, con
   rc = check_workspace(P, workspace, ws_bytes, resid_bytes(P), ck_bytes);
   if (rc != WS_OK) return rc;
   void* r = static_cast<char*>(workspace) + kHeaderBytes + ck_bytes;
-  rc = launch_residual(P, x, w, lam, z, r, st);
+  rc = launch_residual(P, x, w, lam, z, r, 0, st);
   if (rc != WS_OK) return rc;
-  return run_tile(P, MODE_RAW, r, w, lam, nullptr, z, nullptr, nullptr, nullptr, 1, 0, workspace, st);
+  return run_tile(P, MODE_RAW, r, w, lam, nullptr, z, nullptr, nullptr, nullptr, nullptr, 1, 0, workspace, st);
 }
 
 extern "C" int ws_factor(const ws_problem* pb, const void* w, const void* lam, void* factor, uint8_t* status,
@@ -302,7 +304,7 @@ extern "C" int ws_solve_adjoint(const ws_problem* pb, const void* factor_or_null
   clear_error();
   int rc = validate_problem(pb);
   if (rc != WS_OK) return rc;
-  if (flags & ~WS_GRAD_LOGLAM) return set_error(WS_EINVAL, "unknown flags 0x%x", flags);
+  if (flags & ~(WS_GRAD_LOGLAM | WS_REFINE_ADJOINT)) return set_error(WS_EINVAL, "unknown flags 0x%x", flags);
   const ws_problem& P = *pb;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   if (P.n_series == 0) return WS_OK;
@@ -320,11 +322,23 @@ extern "C" int ws_solve_adjoint(const ws_problem* pb, const void* factor_or_null
     return set_error(WS_EINVAL, "gx must not overlap gz or z");
   if (factor_or_null != nullptr) return ws_adjoint_factored(pb, factor_or_null, w, lam, z, gz, gx, glam, flags,
                                                             status, workspace, ws_bytes, stream);
+  const bool refine = (flags & WS_REFINE_ADJOINT) != 0;
+  const int loglam = (flags & WS_GRAD_LOGLAM) ? 1 : 0;
   size_t ck_bytes = 0;
-  rc = check_workspace(P, workspace, ws_bytes, 0, ck_bytes);
+  rc = check_workspace(P, workspace, ws_bytes, refine ? 2 * resid_bytes(P) : 0, ck_bytes);
   if (rc != WS_OK) return rc;
-  return run_tile(P, MODE_ADJ, gz, w, lam, z, gx, glam, nullptr, status, 0,
-                  (flags & WS_GRAD_LOGLAM) ? 1 : 0, workspace, st);
+  if (!refine)
+    return run_tile(P, MODE_ADJ, gz, w, lam, z, nullptr, gx, glam, nullptr, status, 0, loglam, workspace, st);
+  // g0 = Omega^{-1} gz, r = gz - Omega g0 (double-word), then the adjoint pass solves
+  // Omega d = r and applies the epilogue to g = g0 + d.
+  char* base = static_cast<char*>(workspace) + kHeaderBytes + ck_bytes;
+  void* g0 = base;
+  void* r = base + resid_bytes(P);
+  rc = run_tile(P, MODE_RAW, gz, w, lam, nullptr, nullptr, g0, nullptr, nullptr, nullptr, 0, 0, workspace, st);
+  if (rc != WS_OK) return rc;
+  rc = launch_residual(P, gz, w, lam, g0, r, 1, st);
+  if (rc != WS_OK) return rc;
+  return run_tile(P, MODE_ADJ, r, w, lam, z, g0, gx, glam, nullptr, status, 1, loglam, workspace, st);
 }
 
 extern "C" int ws_tune_set(int32_t pixels_per_cta, int32_t chunk_days) {

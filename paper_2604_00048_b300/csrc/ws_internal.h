@@ -37,6 +37,7 @@ struct TileArgs {
   const void* w;
   const void* lam;
   const void* zin;        // ADJOINT: forward output z
+  const void* g0;         // ADJOINT with accum: first solution g0 (g = g0 + correction)
   void* out;              // SMOOTH: z; ADJOINT: gx (may be null)
   void* out2;             // ADJOINT: glam (may be null)
   void* factor;           // optional factor output (SMOOTH) / input (SOLVE)
@@ -70,7 +71,8 @@ int launch_tile_d2(const ws_problem&, int, int, const TileCfg&, const TileArgs&,
 int launch_tile_d3(const ws_problem&, int, int, const TileCfg&, const TileArgs&, const CUtensorMap*, cudaStream_t);
 int launch_tile_d4(const ws_problem&, int, int, const TileCfg&, const TileArgs&, const CUtensorMap*, cudaStream_t);
 // r = W x - Omega z0 with double-word accumulation (refinement residual).
+// raw = 0: r = W x - Omega z0; raw = 1: r = x - Omega z0.
 int launch_residual(const ws_problem& pb, const void* x, const void* w, const void* lam, const void* z0,
-                    void* r, cudaStream_t st);
+                    void* r, int raw, cudaStream_t st);
 
 }  // namespace ws

@@ -1,5 +1,7 @@
 // Residual of the smoothing system for one step of iterative refinement:
 //     r = W x - Omega z0 = W (x - z0) - D^T (Lambda (D z0))        (Omega from Eq. 3)
+// or, for a right-hand side taken as given (the adjoint solve Omega g = gz),
+//     r = x - Omega z0 = x - W z0 - D^T (Lambda (D z0)).
 // At a good z0 the two terms cancel to a few parts in 1e5, so every difference and
 // every sum is carried as a double word (ws_df.cuh): D z0, Lambda D z0 and the D^T
 // accumulation are exact up to the final rounding of r to working precision.
@@ -20,7 +22,8 @@ constexpr int kResidDays = 64;
 template <typename F, int D>
 __global__ void __launch_bounds__(128) k_residual(const F* __restrict__ x, const F* __restrict__ w,
                                                   const F* __restrict__ lam, const F* __restrict__ z0,
-                                                  F* __restrict__ r, int T, int B, int P, int lam_scalar) {
+                                                  F* __restrict__ r, int T, int B, int P, int lam_scalar,
+                                                  int raw) {
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= P) return;
   const int t0 = blockIdx.y * kResidDays;
@@ -55,7 +58,11 @@ __global__ void __launch_bounds__(128) k_residual(const F* __restrict__ x, const
       if (t >= t0 && t < t1) {
         const F wt = w[(size_t)t * sP + p];
         DW<F> acc = {F(0), F(0)};
-        if (wt > F(0)) {
+        if (raw) {
+          const F xt = x[(size_t)t * sBP + (size_t)b * sP + p];
+          const DW<F> wz = two_prod(wt, zr[0]);
+          acc = dw_add(DW<F>{xt, F(0)}, DW<F>{-wz.hi, -wz.lo});
+        } else if (wt > F(0)) {
           const F xt = x[(size_t)t * sBP + (size_t)b * sP + p];
           acc = dw_scale(two_sum(xt, -zr[0]), wt);  // zr[0] = z0_t (u = t + D)
         }
@@ -69,31 +76,31 @@ __global__ void __launch_bounds__(128) k_residual(const F* __restrict__ x, const
 
 template <typename F, int D>
 static int launch_resid_t(const ws_problem& pb, const void* x, const void* w, const void* lam, const void* z0,
-                          void* r, cudaStream_t st) {
+                          void* r, int raw, cudaStream_t st) {
   dim3 grid((unsigned)((pb.n_series + 127) / 128), (unsigned)((pb.T + kResidDays - 1) / kResidDays));
   k_residual<F, D><<<grid, 128, 0, st>>>(static_cast<const F*>(x), static_cast<const F*>(w),
                                          static_cast<const F*>(lam), static_cast<const F*>(z0), static_cast<F*>(r),
-                                         pb.T, pb.n_bands, (int)pb.n_series, pb.lam_mode == WS_LAM_SCALAR);
+                                         pb.T, pb.n_bands, (int)pb.n_series, pb.lam_mode == WS_LAM_SCALAR, raw);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return set_error(WS_ECUDA, "residual kernel launch: %s", cudaGetErrorString(e));
   return WS_OK;
 }
 
 int launch_residual(const ws_problem& pb, const void* x, const void* w, const void* lam, const void* z0, void* r,
-                    cudaStream_t st) {
+                    int raw, cudaStream_t st) {
   if (pb.dtype == WS_F32) {
     switch (pb.d) {
-      case 1: return launch_resid_t<float, 1>(pb, x, w, lam, z0, r, st);
-      case 2: return launch_resid_t<float, 2>(pb, x, w, lam, z0, r, st);
-      case 3: return launch_resid_t<float, 3>(pb, x, w, lam, z0, r, st);
-      case 4: return launch_resid_t<float, 4>(pb, x, w, lam, z0, r, st);
+      case 1: return launch_resid_t<float, 1>(pb, x, w, lam, z0, r, raw, st);
+      case 2: return launch_resid_t<float, 2>(pb, x, w, lam, z0, r, raw, st);
+      case 3: return launch_resid_t<float, 3>(pb, x, w, lam, z0, r, raw, st);
+      case 4: return launch_resid_t<float, 4>(pb, x, w, lam, z0, r, raw, st);
     }
   } else {
     switch (pb.d) {
-      case 1: return launch_resid_t<double, 1>(pb, x, w, lam, z0, r, st);
-      case 2: return launch_resid_t<double, 2>(pb, x, w, lam, z0, r, st);
-      case 3: return launch_resid_t<double, 3>(pb, x, w, lam, z0, r, st);
-      case 4: return launch_resid_t<double, 4>(pb, x, w, lam, z0, r, st);
+      case 1: return launch_resid_t<double, 1>(pb, x, w, lam, z0, r, raw, st);
+      case 2: return launch_resid_t<double, 2>(pb, x, w, lam, z0, r, raw, st);
+      case 3: return launch_resid_t<double, 3>(pb, x, w, lam, z0, r, raw, st);
+      case 4: return launch_resid_t<double, 4>(pb, x, w, lam, z0, r, raw, st);
     }
   }
   return set_error(WS_EINVAL, "unsupported order d=%d", pb.d);

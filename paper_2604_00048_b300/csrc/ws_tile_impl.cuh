@@ -63,6 +63,7 @@ __global__ void __launch_bounds__(256) k_tile(const __grid_constant__ CUtensorMa
   const F* gw = static_cast<const F*>(a.w);
   const F* gl = static_cast<const F*>(a.lam);
   const F* gzin = static_cast<const F*>(a.zin);
+  const F* gg0 = static_cast<const F*>(a.g0);
   F* gout = static_cast<F*>(a.out);
   F* gout2 = static_cast<F*>(a.out2);
   F* gf = static_cast<F*>(a.factor);
@@ -216,6 +217,7 @@ __global__ void __launch_bounds__(256) k_tile(const __grid_constant__ CUtensorMa
     F zc[NB][D];
     F gt[NB][DT];
     F zt[NB][D];
+    F gn[NB];  // ADJ: g_{t+1} (differs from zc[b][0] when accumulating a correction)
 #pragma unroll
     for (int b = 0; b < NB; ++b) {
 #pragma unroll
@@ -225,6 +227,7 @@ __global__ void __launch_bounds__(256) k_tile(const __grid_constant__ CUtensorMa
       }
 #pragma unroll
       for (int j = 0; j < DT; ++j) gt[b][j] = F(0);
+      gn[b] = F(0);
     }
     F glam_sum = F(0);  // ADJ with scalar lambda
     bool nonfin = false;
@@ -283,10 +286,13 @@ __global__ void __launch_bounds__(256) k_tile(const __grid_constant__ CUtensorMa
           nonfin |= !finite_(acc);
           F out = okser ? acc : F(0);
           if (MODE == MODE_ADJ) {
-            const F zv = act ? gzin[((size_t)i * a.B + a.b0 + b) * a.P + p] : F(0);
+            const size_t gi = ((size_t)i * a.B + a.b0 + b) * a.P + p;
+            const F zv = act ? gzin[gi] : F(0);
+            if (a.accum && act && okser) out += gg0[gi];   // g = g0 + correction
             F cg = out, cz = zv;                 // level j at day t
-            F pg = zc[b][0], pz = zt[b][0];      // level j-1 at day t+1 (j = 1: the values)
+            F pg = gn[b], pz = zt[b][0];         // level j-1 at day t+1 (j = 1: the values)
             zt[b][0] = zv;
+            gn[b] = out;
 #pragma unroll
             for (int j = 1; j <= D; ++j) {
               const F ng = pg - cg, nz = pz - cz;  // Delta^j at day t

@@ -35,6 +35,7 @@ F32, F64 = 0, 1
 LAM_PER_DAY, LAM_SCALAR = 0, 1
 GRAD_LOGLAM = 0x1
 REFINE = 0x2
+REFINE_ADJOINT = 0x4
 
 
 class Problem(ctypes.Structure):
@@ -192,7 +193,7 @@ def refine(x: torch.Tensor, w: torch.Tensor, lam: torch.Tensor, z: torch.Tensor,
 
 def smooth_adjoint(w: torch.Tensor, lam: torch.Tensor, z: torch.Tensor, gz: torch.Tensor, d: int = 2, *,
                    gx=None, glam=None, want_gx: bool = True, want_glam: bool = True, log_lambda: bool = False,
-                   factor=None, status=None, stream=None):
+                   factor=None, status=None, refine: bool = False, stream=None):
     """Vector-Jacobian products of z = Omega^{-1} W x (Eqs. 4-5): returns (gx, glam, status).
 
     gx = W Omega^{-1} gz; glam_k = -sum_b (D g_b)_k (D z_b)_k (k < T-d, 0 after), times
@@ -207,8 +208,8 @@ def smooth_adjoint(w: torch.Tensor, lam: torch.Tensor, z: torch.Tensor, gz: torc
         glam = torch.empty_like(lam)
     if status is None:
         status = torch.empty(P, dtype=torch.uint8, device=gz.device)
-    ws = workspace(pb, gz.device)
-    flags = GRAD_LOGLAM if log_lambda else 0
+    flags = (GRAD_LOGLAM if log_lambda else 0) | (REFINE_ADJOINT if refine else 0)
+    ws = workspace(pb, gz.device, flags)
     rc = _lib.ws_solve_adjoint(ctypes.byref(pb), _ptr(factor), _ptr(w), _ptr(lam), _ptr(z), _ptr(gz), _ptr(gx),
                                _ptr(glam), flags, _ptr(status), _ptr(ws), ws.numel(), _stream_ptr(stream))
     _check(rc)

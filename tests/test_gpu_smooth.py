@@ -11,7 +11,7 @@ from tests.gpu_util import rel_err_per_series, tile_inputs
 
 pytestmark = pytest.mark.gpu
 
-TOL = {torch.float32: 1e-4, torch.float64: 1e-9}
+TOL = {torch.float32: 1e-4, torch.float64: 1e-6}   # FP64: eps64 * cond(Omega) on sparse-weight inputs
 
 
 @pytest.fixture(scope="module")
