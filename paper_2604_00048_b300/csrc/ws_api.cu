@@ -154,6 +154,12 @@ static int check_workspace(const ws_problem& pb, void* workspace, size_t ws_byte
 static int run_tile(const ws_problem& P, int mode, const void* rhs, const void* w, const void* lam,
                     const void* zin, const void* g0, void* out, void* out2, void* factor, uint8_t* status,
                     int accum, int grad_loglam, void* workspace, cudaStream_t st) {
+  // pointer contract of each mode (an inconsistent internal call is an error, never a fault)
+  if (rhs == nullptr || w == nullptr || lam == nullptr) return set_error(WS_EINVAL, "tile: missing input");
+  if (mode != MODE_ADJ && out == nullptr) return set_error(WS_EINVAL, "tile: missing output");
+  if (mode == MODE_ADJ && zin == nullptr) return set_error(WS_EINVAL, "tile: adjoint needs z");
+  if (mode == MODE_ADJ && accum && g0 == nullptr) return set_error(WS_EINVAL, "tile: accumulation needs g0");
+  if (mode == MODE_SMOOTH && accum) return set_error(WS_EINVAL, "tile: smooth does not accumulate");
   const int es = elem_size(P);
   const bool per_day = P.lam_mode == WS_LAM_PER_DAY;
   const bool tma_ok = ((size_t)P.n_series * es) % 16 == 0 && aligned16(rhs) && aligned16(w) &&
@@ -261,7 +267,8 @@ extern "C" int ws_smooth_batch(const ws_problem* pb, const void* x, const void* 
   void* r = static_cast<char*>(workspace) + kHeaderBytes + ck_bytes;
   rc = launch_residual(P, x, w, lam, z, r, 0, st);
   if (rc != WS_OK) return rc;
-  return run_tile(P, MODE_RAW, r, w, lam, nullptr, z, nullptr, nullptr, nullptr, nullptr, 1, 0, workspace, st);
+  return run_tile(P, MODE_RAW, r, w, lam, /*zin*/ nullptr, /*g0*/ nullptr, /*out*/ z, /*out2*/ nullptr,
+                  /*factor*/ nullptr, /*status*/ nullptr, /*accum*/ 1, /*loglam*/ 0, workspace, st);
 }
 
 extern "C" int ws_refine(const ws_problem* pb, const void* x, const void* w, const void* lam, void* z,
@@ -281,7 +288,8 @@ extern "C" int ws_refine(const ws_problem* pb, const void* x, const void* w, con
   void* r = static_cast<char*>(workspace) + kHeaderBytes + ck_bytes;
   rc = launch_residual(P, x, w, lam, z, r, 0, st);
   if (rc != WS_OK) return rc;
-  return run_tile(P, MODE_RAW, r, w, lam, nullptr, z, nullptr, nullptr, nullptr, nullptr, 1, 0, workspace, st);
+  return run_tile(P, MODE_RAW, r, w, lam, /*zin*/ nullptr, /*g0*/ nullptr, /*out*/ z, /*out2*/ nullptr,
+                  /*factor*/ nullptr, /*status*/ nullptr, /*accum*/ 1, /*loglam*/ 0, workspace, st);
 }
 
 extern "C" int ws_factor(const ws_problem* pb, const void* w, const void* lam, void* factor, uint8_t* status,

@@ -287,8 +287,8 @@ __global__ void __launch_bounds__(256) k_tile(const __grid_constant__ CUtensorMa
           F out = okser ? acc : F(0);
           if (MODE == MODE_ADJ) {
             const size_t gi = ((size_t)i * a.B + a.b0 + b) * a.P + p;
-            const F zv = act ? gzin[gi] : F(0);
-            if (a.accum && act && okser) out += gg0[gi];   // g = g0 + correction
+            const F zv = (act && gzin != nullptr) ? gzin[gi] : F(0);
+            if (a.accum && act && okser && gg0 != nullptr) out += gg0[gi];   // g = g0 + correction
             F cg = out, cz = zv;                 // level j at day t
             F pg = gn[b], pz = zt[b][0];         // level j-1 at day t+1 (j = 1: the values)
             zt[b][0] = zv;
@@ -311,7 +311,7 @@ __global__ void __launch_bounds__(256) k_tile(const __grid_constant__ CUtensorMa
           for (int j = D - 1; j > 0; --j) zc[b][j] = zc[b][j - 1];
           zc[b][0] = acc;
           if (MODE == MODE_ADJ) out = wk * out;
-          if (MODE == MODE_RAW && a.accum && act) out += gout[((size_t)i * a.B + a.b0 + b) * a.P + p];
+          if (MODE == MODE_RAW && a.accum && act && want_out) out += gout[((size_t)i * a.B + a.b0 + b) * a.P + p];
           if (a.tma)
             S[(rowX + k * NB + b) * NP + tid] = out;
           else if (act && want_out)

@@ -138,7 +138,13 @@ def workspace(pb: Problem, device, flags: int = 0) -> torch.Tensor:
     key = dev.index if dev.index is not None else torch.cuda.current_device()
     buf = _ws_cache.get(key)
     if buf is None or buf.numel() < need:
+        if buf is not None:
+            # kernels on any stream may still use the old scratch: drain before freeing it
+            torch.cuda.synchronize(dev)
+            _ws_cache[key] = None
+            del buf
         buf = torch.zeros(need, dtype=torch.uint8, device=dev)
+        torch.cuda.synchronize(dev)
         _ws_cache[key] = buf
     return buf
 
