@@ -150,11 +150,12 @@ int ws_solve_adjoint(const ws_problem* pb, const void* factor_or_null, const voi
                      uint32_t flags, uint8_t* status, void* workspace, size_t ws_bytes,
                      void* stream);
 
-/* Tuning knobs of the tile kernels, process-wide (0 = automatic): pixels (threads)
- * per CTA, a multiple of 32 in 32..256, and days per staged chunk, 1..(256-d). The
- * chunk is clamped so that two stages fit in shared memory. ws_workspace_size()
- * reflects the current setting. Returns WS_EINVAL for out-of-range values. */
-int ws_tune_set(int32_t pixels_per_cta, int32_t chunk_days);
+/* Tuning knobs of the tile kernels, process-wide (0 = automatic): the number of CTAs
+ * (128 pixels each) to fit on one SM, 1..8, which sets the shared memory per CTA, and
+ * an upper bound on the days per staged chunk, 1..255. The chunk is the largest that
+ * fits; registers may allow fewer CTAs than requested. ws_workspace_size() reflects the
+ * current setting. Returns WS_EINVAL for out-of-range values. */
+int ws_tune_set(int32_t ctas_per_sm, int32_t chunk_days);
 
 /* Synchronises `stream`, reads and clears the device error word in `workspace`.
  * Returns WS_OK, WS_ETIMEOUT (a device-side wait gave up: its outputs are invalid)

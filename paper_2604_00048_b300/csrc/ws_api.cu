@@ -39,9 +39,10 @@ int device_info(DeviceInfo& info) {
   std::call_once(once[dev], [dev]() {
     cudaDeviceGetAttribute(&cache[dev].sm_count, cudaDevAttrMultiProcessorCount, dev);
     cudaDeviceGetAttribute(&cache[dev].smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    cudaDeviceGetAttribute(&cache[dev].smem_per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
   });
   info = cache[dev];
-  if (info.sm_count <= 0 || info.smem_optin <= 0) return set_error(WS_ECUDA, "device attributes unavailable");
+  if (info.sm_count <= 0 || info.smem_optin <= 0 || info.smem_per_sm <= 0) return set_error(WS_ECUDA, "device attributes unavailable");
   return WS_OK;
 }
 
@@ -119,11 +120,11 @@ static size_t round256(size_t v) { return (v + 255) & ~(size_t)255; }
 // Checkpoint bytes of the tile kernels over all band groups and modes.
 static int tile_ckpt_bytes(const ws_problem& pb, size_t& bytes) {
   bytes = 0;
-  for (int mode : {MODE_SMOOTH, MODE_ADJ}) {
+  for (int mode : {MODE_SMOOTH, MODE_RAW, MODE_ADJ}) {
     for (int b0 = 0; b0 < pb.n_bands;) {
       const int nb = group_size(pb, pb.n_bands - b0);
       TileCfg cfg;
-      int rc = plan_tile(pb, nb, pb.d, extra_planes_mode(mode, pb.d), cfg);
+      int rc = plan_tile(pb, mode, nb, cfg);
       if (rc != WS_OK) return rc;
       const size_t need = (size_t)cfg.grid * cfg.nch * cfg.fields * cfg.NP * elem_size(pb);
       if (need > bytes) bytes = need;
@@ -162,27 +163,31 @@ static int run_tile(const ws_problem& P, int mode, const void* rhs, const void* 
   if (mode == MODE_SMOOTH && accum) return set_error(WS_EINVAL, "tile: smooth does not accumulate");
   const int es = elem_size(P);
   const bool per_day = P.lam_mode == WS_LAM_PER_DAY;
+  // the array staged into the Z region in pass 2: z (adjoint) or z0 = out (accumulating RAW)
+  const void* zin_stage = mode == MODE_ADJ ? zin : ((mode == MODE_RAW && accum) ? out : nullptr);
   const bool tma_ok = ((size_t)P.n_series * es) % 16 == 0 && aligned16(rhs) && aligned16(w) &&
-                      (out == nullptr || aligned16(out)) && (!per_day || aligned16(lam));
+                      (out == nullptr || aligned16(out)) && (!per_day || aligned16(lam)) &&
+                      (zin_stage == nullptr || aligned16(zin_stage));
   for (int b0 = 0; b0 < P.n_bands;) {
     const int nb = group_size(P, P.n_bands - b0);
     TileCfg cfg;
-    int rc = plan_tile(P, nb, P.d, extra_planes_mode(mode, P.d), cfg);
+    int rc = plan_tile(P, mode, nb, cfg);
     if (rc != WS_OK) return rc;
-    CUtensorMap maps[4];
+    CUtensorMap maps[5];
     memset(maps, 0, sizeof(maps));
     bool tma = tma_ok;
     if (tma) {
       const uint64_t Pn = (uint64_t)P.n_series, B = (uint64_t)P.n_bands, T = (uint64_t)P.T;
       const uint64_t dx[3] = {Pn, B, T}, sx[2] = {Pn * es, B * Pn * es};
-      const uint32_t bx[3] = {(uint32_t)cfg.NP, (uint32_t)nb, (uint32_t)cfg.C};
+      const uint32_t bx[3] = {(uint32_t)kNP, (uint32_t)nb, (uint32_t)cfg.C};
       const uint64_t d2[2] = {Pn, T}, s2[1] = {Pn * es};
-      const uint32_t bw[2] = {(uint32_t)cfg.NP, (uint32_t)(cfg.C + P.d)};
-      const uint32_t bl[2] = {(uint32_t)cfg.NP, (uint32_t)cfg.C};
+      const uint32_t bw[2] = {(uint32_t)kNP, (uint32_t)(cfg.C + P.d)};
+      const uint32_t bl[2] = {(uint32_t)kNP, (uint32_t)cfg.C};
       tma = make_tmap(&maps[0], P.dtype, 3, rhs, dx, sx, bx) == WS_OK &&
             make_tmap(&maps[1], P.dtype, 2, w, d2, s2, bw) == WS_OK &&
             (!per_day || make_tmap(&maps[2], P.dtype, 2, lam, d2, s2, bl) == WS_OK) &&
-            (out == nullptr || make_tmap(&maps[3], P.dtype, 3, out, dx, sx, bx) == WS_OK);
+            (out == nullptr || make_tmap(&maps[3], P.dtype, 3, out, dx, sx, bx) == WS_OK) &&
+            (zin_stage == nullptr || make_tmap(&maps[4], P.dtype, 3, zin_stage, dx, sx, bx) == WS_OK);
     }
     TileArgs a;
     memset(&a, 0, sizeof(a));
@@ -191,7 +196,7 @@ static int run_tile(const ws_problem& P, int mode, const void* rhs, const void* 
     a.B = P.n_bands;
     a.b0 = b0;
     a.C = cfg.C;
-    a.NP = cfg.NP;
+    a.NP = kNP;
     a.nch = cfg.nch;
     a.n_tiles = cfg.n_tiles;
     a.lam_scalar = per_day ? 0 : 1;
@@ -200,7 +205,7 @@ static int run_tile(const ws_problem& P, int mode, const void* rhs, const void* 
     a.x = rhs;
     a.w = w;
     a.lam = lam;
-    a.zin = zin;
+    a.zin = zin_stage;
     a.g0 = g0;
     a.out = out;
     a.out2 = out2;
@@ -349,12 +354,11 @@ extern "C" int ws_solve_adjoint(const ws_problem* pb, const void* factor_or_null
   return run_tile(P, MODE_ADJ, r, w, lam, z, g0, gx, glam, nullptr, status, 1, loglam, workspace, st);
 }
 
-extern "C" int ws_tune_set(int32_t pixels_per_cta, int32_t chunk_days) {
+extern "C" int ws_tune_set(int32_t ctas_per_sm, int32_t chunk_days) {
   clear_error();
-  if (pixels_per_cta != 0 && (pixels_per_cta < 32 || pixels_per_cta > 256 || pixels_per_cta % 32 != 0))
-    return set_error(WS_EINVAL, "pixels_per_cta must be 0 or a multiple of 32 in 32..256");
+  if (ctas_per_sm < 0 || ctas_per_sm > 8) return set_error(WS_EINVAL, "ctas_per_sm must be 0..8");
   if (chunk_days < 0 || chunk_days > 255) return set_error(WS_EINVAL, "chunk_days must be 0..255");
-  g_tune_np = pixels_per_cta;
+  g_tune_ctas = ctas_per_sm;
   g_tune_chunk = chunk_days;
   return WS_OK;
 }

@@ -10,12 +10,35 @@
 namespace ws {
 
 constexpr int kNbMax = 10;
-enum { MODE_SMOOTH = 0, MODE_RAW = 1, MODE_ADJ = 2 };         // bands per launch; more bands run as band groups
+enum { MODE_SMOOTH = 0, MODE_RAW = 1, MODE_ADJ = 2 };
+constexpr int kNP = 128;  // pixels per CTA of the tile kernels
+
+// Threads per pixel of a band group: two (each owning half the bands) for 6, 8, 10 bands.
+__host__ __device__ inline int band_split(int nb, bool fp64) { return (!fp64 && nb >= 6 && nb % 2 == 0) ? 2 : 1; }
+
+// Shared-memory layout of the tile kernels, in rows of kNP elements (ws_tile_impl.cuh).
+__host__ __device__ inline int tile_extra_planes(int mode, int D, int S) {
+  return (mode == MODE_ADJ || S > 1) ? D : (D > 2 ? D - 2 : 0);
+}
+__host__ __device__ inline size_t tile_stage_rows(int mode, int C, int NB, int D, int S) {
+  return (size_t)C * NB + C + D + C + (size_t)tile_extra_planes(mode, D, S) * C;
+}
+__host__ __device__ inline size_t tile_smem_rows(int mode, int C, int NB, int D, int S) {
+  size_t rows = 2 * tile_stage_rows(mode, C, NB, D, S);
+  if (mode == MODE_RAW || mode == MODE_ADJ) rows += (size_t)C * NB;
+  if (mode == MODE_ADJ) rows += (size_t)S * C;
+  return rows;
+}
+// rows + 3 mbarriers (64 bytes reserved) + kNP status words
+__host__ __device__ inline size_t tile_smem_bytes(int mode, int C, int NB, int D, int S, int es) {
+  return tile_smem_rows(mode, C, NB, D, S) * kNP * es + 64 + kNP * 4;
+}         // bands per launch; more bands run as band groups
 constexpr size_t kHeaderBytes = 256;  // device error word + reserved
 
 // Staging / launch configuration of one tile launch.
 struct TileCfg {
-  int NP = 128;        // pixels (threads) per CTA
+  int NP = kNP;        // pixels per CTA
+  int S = 1;           // threads per pixel (band split)
   int C = 16;          // days per chunk
   int nch = 0;         // chunks per series
   int n_tiles = 0;     // ceil(P / NP)
@@ -51,7 +74,8 @@ struct TileArgs {
 
 struct DeviceInfo {
   int sm_count = 0;
-  int smem_optin = 0;
+  int smem_optin = 0;   // max dynamic shared memory per block
+  int smem_per_sm = 0;  // shared memory per SM
 };
 int device_info(DeviceInfo& info);
 
@@ -62,10 +86,15 @@ int make_tmap(CUtensorMap* map, int dtype, int rank, const void* base, const uin
               const uint64_t* strides_bytes, const uint32_t* box);
 
 // Launchers (return WS_OK or an error code, errors recorded via set_error).
-extern int g_tune_np, g_tune_chunk;  // ws_tune_set() overrides (0 = automatic)
-int plan_tile(const ws_problem& pb, int nb, int D, int extra_planes, TileCfg& cfg);
+extern int g_tune_ctas, g_tune_chunk;  // ws_tune_set() overrides (0 = automatic)
+int plan_tile(const ws_problem& pb, int mode, int nb, TileCfg& cfg);
 int launch_tile(const ws_problem& pb, int mode, int nb, const TileCfg& cfg, const TileArgs& a,
                 const CUtensorMap* maps, cudaStream_t st);
+const void* tile_kernel_ptr(const ws_problem& pb, int mode, int nb);
+const void* tile_kernel_ptr_d1(const ws_problem& pb, int mode, int nb);
+const void* tile_kernel_ptr_d2(const ws_problem& pb, int mode, int nb);
+const void* tile_kernel_ptr_d3(const ws_problem& pb, int mode, int nb);
+const void* tile_kernel_ptr_d4(const ws_problem& pb, int mode, int nb);
 int launch_tile_d1(const ws_problem&, int, int, const TileCfg&, const TileArgs&, const CUtensorMap*, cudaStream_t);
 int launch_tile_d2(const ws_problem&, int, int, const TileCfg&, const TileArgs&, const CUtensorMap*, cudaStream_t);
 int launch_tile_d3(const ws_problem&, int, int, const TileCfg&, const TileArgs&, const CUtensorMap*, cudaStream_t);

@@ -71,10 +71,13 @@ struct Sweep {
       if (q == m) pr[q][q] = sqrt_(wm > F(0) ? wm : F(0));
   }
 
-  // Steps 1-2: rotations for day i; returns rho_{i,1..D} and 1/D_i.
+  // Steps 1-2: rotations for day i; returns rho_{i,1..D} and 1/D_i. Reciprocals and
+  // square roots come from the rotations' reciprocal square roots (one MUFU op each):
+  // row i's final diagonal is sqrt(h0) with h0 from its last rotation, so 1/R_ii = rsqrt(h0).
   __device__ __forceinline__ void factor_step(bool has_row, F lam, F w_ahead, F (&rho)[D], F& invD) {
     F v[D + 1];
     F nd = F(0);
+    F inv = F(0);
     if (has_row) {
       const F sl = sqrt_(lam);
 #pragma unroll
@@ -87,6 +90,7 @@ struct Sweep {
         const F cs = h > F(0) ? a * ir : F(1);
         const F sn = b * ir;
         pr[m][m] = h * ir;
+        if (m == 0) inv = ir;
 #pragma unroll
         for (int n = m + 1; n < D; ++n) {
           const F p = pr[m][n];
@@ -96,12 +100,14 @@ struct Sweep {
         pr[m][D] = sn * v[D];
         v[D] = cs * v[D];
       }
-      nd = sqrt_(fma(v[D], v[D], w_ahead > F(0) ? w_ahead : F(0)));
+      const F hn = fma(v[D], v[D], w_ahead > F(0) ? w_ahead : F(0));
+      nd = hn > F(0) ? hn * rsqrt_(hn) : F(0);
     } else {
 #pragma unroll
       for (int m = 0; m < D; ++m) pr[m][D] = F(0);
+      const F h0 = pr[0][0] * pr[0][0];
+      inv = h0 > F(0) ? rsqrt_(h0) : F(0);
     }
-    const F inv = F(1) / pr[0][0];
     invD = inv * inv;
 #pragma unroll
     for (int n = 1; n <= D; ++n) rho[n - 1] = pr[0][n] * inv;
@@ -135,6 +141,47 @@ struct Sweep {
       for (int n = j; n < D; ++n) rr[j][n] = rr[j - 1][n];
 #pragma unroll
     for (int n = 0; n < D; ++n) rr[0][n] = rho[n];
+  }
+
+  static constexpr int kFactorFields = D * (D + 1);
+
+  // Checkpoint in two parts: the factor state (identical for every thread of a pixel)
+  // and this thread's forward-substitution state.
+  __device__ __forceinline__ void save_factor(F* base, int stride) const {
+    int f = 0;
+#pragma unroll
+    for (int m = 0; m < D; ++m)
+#pragma unroll
+      for (int n = m; n < D; ++n) base[(f++) * stride] = pr[m][n];
+#pragma unroll
+    for (int j = 0; j < D; ++j)
+#pragma unroll
+      for (int n = j; n < D; ++n) base[(f++) * stride] = rr[j][n];
+  }
+  __device__ __forceinline__ void save_y(F* base, int stride) const {
+    int f = 0;
+#pragma unroll
+    for (int b = 0; b < NB; ++b)
+#pragma unroll
+      for (int j = 0; j < D; ++j) base[(f++) * stride] = y[b][j];
+  }
+  __device__ __forceinline__ void load_factor(const F* base, int stride) {
+    int f = 0;
+#pragma unroll
+    for (int m = 0; m < D; ++m)
+#pragma unroll
+      for (int n = m; n < D; ++n) pr[m][n] = base[(f++) * stride];
+#pragma unroll
+    for (int j = 0; j < D; ++j)
+#pragma unroll
+      for (int n = j; n < D; ++n) rr[j][n] = base[(f++) * stride];
+  }
+  __device__ __forceinline__ void load_y(const F* base, int stride) {
+    int f = 0;
+#pragma unroll
+    for (int b = 0; b < NB; ++b)
+#pragma unroll
+      for (int j = 0; j < D; ++j) y[b][j] = base[(f++) * stride];
   }
 
   // Checkpoint: field f of this thread at base[f * stride].

@@ -35,36 +35,82 @@ namespace ws {
 // ----------------------------------------------------------------------------------
 // host side
 
-int g_tune_np = 0, g_tune_chunk = 0;
+int g_tune_ctas = 0, g_tune_chunk = 0;
 
-int plan_tile(const ws_problem& pb, int nb, int D, int extra_planes, TileCfg& cfg) {
+// Largest chunk (days) whose shared memory fits `ctas` CTAs on one SM.
+static long chunk_for(const ws_problem& pb, int mode, int nb, int S, int ctas, const DeviceInfo& di) {
+  const int es = pb.dtype == WS_F64 ? 8 : 4;
+  const int D = pb.d;
+  long per_cta = (long)di.smem_per_sm / ctas - 1024;
+  if (per_cta > di.smem_optin) per_cta = di.smem_optin;
+  const long rows = (per_cta - 64 - kNP * 4) / ((long)kNP * es);
+  const long coef = (long)tile_smem_rows(mode, 1, nb, D, S) - 2 * D;  // rows per day of chunk
+  return (rows - 2 * D) / coef;
+}
+
+int plan_tile(const ws_problem& pb, int mode, int nb, TileCfg& cfg) {
   DeviceInfo di;
   int rc = device_info(di);
   if (rc != WS_OK) return rc;
   const int es = pb.dtype == WS_F64 ? 8 : 4;
-  cfg.NP = g_tune_np > 0 ? g_tune_np : 128;
+  const int D = pb.d, T = pb.T;
+  const int S = band_split(nb, pb.dtype == WS_F64);
+  cfg.NP = kNP;
+  cfg.S = S;
   cfg.stages = 2;
-  const int T = pb.T;
-  // rows per stage = C * (nb + 2 + extra_planes) + D; two stages in the opt-in shared memory
-  const long budget = (long)di.smem_optin - 1024;
-  const long rows_max = budget / (2L * cfg.NP * es);
-  long C = (rows_max - D) / (nb + 2 + extra_planes);
-  if (C > 256 - D) C = 256 - D;
-  if (g_tune_chunk > 0 && g_tune_chunk < C) C = g_tune_chunk;
-  if (C > T) C = T > 0 ? T : 1;
-  if (C < 1) C = 1;
+  // Aim at 16 resident warps per SM (latency of the sequential recurrence), but keep
+  // chunks of at least 8 days (checkpoint traffic grows as 1/C).
+  int ctas = g_tune_ctas > 0 ? g_tune_ctas : (S > 1 ? 2 : 4);
+  long C = 0;
+  for (; ctas >= 1; --ctas) {
+    C = chunk_for(pb, mode, nb, S, ctas, di);
+    if (C >= 8 || ctas == 1 || g_tune_ctas > 0) break;
+  }
+  // registers may allow fewer CTAs than shared memory: then give the chunk the room
+  const void* kern = tile_kernel_ptr(pb, mode, nb);
+  if (kern == nullptr) return set_error(WS_EUNSUPPORTED, "no tile kernel for %d bands", nb);
+  auto fit = [&](long Cc, int* occ) -> int {
+    const size_t smem = tile_smem_bytes(mode, (int)Cc, nb, D, S, es);
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return set_error(WS_ECUDA, "cudaFuncSetAttribute: %s", cudaGetErrorString(e));
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, kern, kNP * S, smem);
+    if (e != cudaSuccess) return set_error(WS_ECUDA, "occupancy query: %s", cudaGetErrorString(e));
+    return WS_OK;
+  };
+  auto clampC = [&](long Cc) {
+    if (Cc > 256 - D) Cc = 256 - D;
+    if (g_tune_chunk > 0 && g_tune_chunk < Cc) Cc = g_tune_chunk;
+    if (Cc > T) Cc = T > 0 ? T : 1;
+    if (Cc < 1) Cc = 1;
+    return Cc;
+  };
+  C = clampC(C);
+  int occ = 0;
+  if ((rc = fit(C, &occ)) != WS_OK) return rc;
+  if (occ >= 1 && occ < ctas && g_tune_chunk == 0) {
+    C = clampC(chunk_for(pb, mode, nb, S, occ, di));
+    if ((rc = fit(C, &occ)) != WS_OK) return rc;
+  }
+  if (occ < 1) return set_error(WS_EUNSUPPORTED, "tile kernel does not fit on an SM (chunk %ld)", C);
   cfg.C = (int)C;
   cfg.nch = T > 0 ? (T + cfg.C - 1) / cfg.C : 0;
-  cfg.n_tiles = (int)((pb.n_series + cfg.NP - 1) / cfg.NP);
-  const size_t rows = (size_t)cfg.C * (nb + 2 + extra_planes) + D;
-  cfg.stage_elems = rows * cfg.NP;
-  cfg.smem_bytes = 2 * cfg.stage_elems * es + 64;
-  int per_sm = (int)((long)(di.smem_optin + 1024) / (long)(cfg.smem_bytes + 1024));
-  if (per_sm < 1) per_sm = 1;
-  const long cap = (long)di.sm_count * per_sm;
+  cfg.n_tiles = (int)((pb.n_series + kNP - 1) / kNP);
+  cfg.stage_elems = tile_stage_rows(mode, cfg.C, nb, D, S) * kNP;
+  cfg.smem_bytes = tile_smem_bytes(mode, cfg.C, nb, D, S, es);
+  const long cap = (long)di.sm_count * occ;
   cfg.grid = (int)(cfg.n_tiles < cap ? cfg.n_tiles : cap);
   cfg.fields = D * (D + 1) + nb * D;
   return WS_OK;
+}
+
+const void* tile_kernel_ptr(const ws_problem& pb, int mode, int nb) {
+  switch (pb.d) {
+    case 1: return tile_kernel_ptr_d1(pb, mode, nb);
+    case 2: return tile_kernel_ptr_d2(pb, mode, nb);
+    case 3: return tile_kernel_ptr_d3(pb, mode, nb);
+    case 4: return tile_kernel_ptr_d4(pb, mode, nb);
+  }
+  return nullptr;
 }
 
 int launch_tile(const ws_problem& pb, int mode, int nb, const TileCfg& cfg, const TileArgs& a,

@@ -222,9 +222,9 @@ def smooth_adjoint(w: torch.Tensor, lam: torch.Tensor, z: torch.Tensor, gz: torc
     return gx, glam, status
 
 
-def tune_set(pixels_per_cta: int = 0, chunk_days: int = 0):
-    """Process-wide tile tuning knobs (0 = automatic)."""
-    _check(_lib.ws_tune_set(int(pixels_per_cta), int(chunk_days)))
+def tune_set(ctas_per_sm: int = 0, chunk_days: int = 0):
+    """Process-wide tile tuning knobs (0 = automatic): CTAs per SM and a chunk-size cap."""
+    _check(_lib.ws_tune_set(int(ctas_per_sm), int(chunk_days)))
 
 
 def sync_status(device=None, stream=None):

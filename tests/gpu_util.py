@@ -5,9 +5,10 @@ import torch
 from paper_2604_00048_b300 import synth
 
 
-def tile_inputs(recipe: str, P: int, T=None, B=None, dtype=torch.float32, series0=0, device="cuda"):
+def tile_inputs(recipe: str, P: int, T=None, B=None, dtype=torch.float32, series0=0, device="cuda", **over):
     rc = synth.RECIPES[recipe]
     kw = dict(rc.__dict__)
+    kw.update(over)
     if T is not None:
         kw["T"] = T
     if B is not None:
