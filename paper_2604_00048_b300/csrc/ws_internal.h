@@ -20,8 +20,10 @@ __host__ __device__ inline int band_split(int nb, bool fp64) { return (!fp64 && 
 __host__ __device__ inline int tile_extra_planes(int mode, int D, int S) {
   return (mode == MODE_ADJ || S > 1) ? D : (D > 2 ? D - 2 : 0);
 }
+// checkpoint words per pixel per chunk: factor state + forward-substitution state
+__host__ __device__ inline int tile_ckpt_fields(int NB, int D) { return D * (D + 1) + NB * D; }
 __host__ __device__ inline size_t tile_stage_rows(int mode, int C, int NB, int D, int S) {
-  return (size_t)C * NB + C + D + C + (size_t)tile_extra_planes(mode, D, S) * C;
+  return (size_t)C * NB + C + D + C + (size_t)tile_extra_planes(mode, D, S) * C + tile_ckpt_fields(NB, D);
 }
 __host__ __device__ inline size_t tile_smem_rows(int mode, int C, int NB, int D, int S) {
   size_t rows = 2 * tile_stage_rows(mode, C, NB, D, S);

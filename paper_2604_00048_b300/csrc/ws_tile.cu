@@ -44,8 +44,9 @@ static long chunk_for(const ws_problem& pb, int mode, int nb, int S, int ctas, c
   long per_cta = (long)di.smem_per_sm / ctas - 1024;
   if (per_cta > di.smem_optin) per_cta = di.smem_optin;
   const long rows = (per_cta - 64 - kNP * 4) / ((long)kNP * es);
-  const long coef = (long)tile_smem_rows(mode, 1, nb, D, S) - 2 * D;  // rows per day of chunk
-  return (rows - 2 * D) / coef;
+  const long fixed = (long)tile_smem_rows(mode, 0, nb, D, S);         // rows independent of C
+  const long coef = (long)tile_smem_rows(mode, 1, nb, D, S) - fixed;  // rows per day of chunk
+  return (rows - fixed) / coef;
 }
 
 int plan_tile(const ws_problem& pb, int mode, int nb, TileCfg& cfg) {

@@ -66,16 +66,19 @@ __global__ void __launch_bounds__(kNP* S, S > 1 ? 2 : 4) k_tile(const __grid_con
   const int pl = tid % kNP;  // pixel lane within the tile
   const int h = tid / kNP;   // band half (S = 2) or 0
   const int C = a.C, T = a.T;
-  const size_t stage_rows = (size_t)C * NB + C + D + C + (size_t)EXTRA * C;
+  constexpr int kFF = SW::kFactorFields;
+  constexpr int kFields = kFF + NB * D;
+  const size_t stage_rows = (size_t)C * NB + C + D + C + (size_t)EXTRA * C + kFields;
   F* const smem = reinterpret_cast<F*>(smem_raw);
   F* const zbuf = smem + 2 * stage_rows * kNP;                  // Z region
   F* const gbuf = zbuf + (HAS_Z ? (size_t)C * NB * kNP : 0);     // G region
   const size_t rows_total = tile_smem_rows(MODE, C, NB, D, S);
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem + rows_total * kNP);
   unsigned* nflag = reinterpret_cast<unsigned*>(bar + 4);
-  const int rowW = NB * C, rowL = rowW + C + D, rowE = rowL + C;
+  const int rowW = NB * C, rowL = rowW + C + D, rowE = rowL + C, rowK = rowE + EXTRA * C;
   const uint32_t tx_bytes = static_cast<uint32_t>((NB * C + C + D + (a.lam_scalar ? 0 : C)) * kNP * sizeof(F));
   const uint32_t tz_bytes = static_cast<uint32_t>(NB * C * kNP * sizeof(F));
+  const uint32_t tk_bytes = static_cast<uint32_t>(kFields * kNP * sizeof(F));
   const F* gx_in = static_cast<const F*>(a.x);
   const F* gw = static_cast<const F*>(a.w);
   const F* gl = static_cast<const F*>(a.lam);
@@ -110,12 +113,13 @@ __global__ void __launch_bounds__(kNP* S, S > 1 ? 2 : 4) k_tile(const __grid_con
   uint32_t pending = 0u;  // bit i: a load on barrier i has not been waited for
 
   // Stage load of chunk c: every thread calls it (TMA: thread 0 issues; LDGSTS: each
-  // thread copies its own columns).
-  auto issue = [&](int c, int st, int p0) {
+  // thread copies its own columns). ckg: the chunk's checkpoint to prefetch (pass 2, TMA).
+  auto issue = [&](int c, int st, int p0, const F* ckg) {
     F* Sg = stage(st);
     if (a.tma) {
       if (tid == 0) {
-        mbar_arrive_expect_tx(&bar[st], tx_bytes);
+        mbar_arrive_expect_tx(&bar[st], tx_bytes + (ckg != nullptr ? tk_bytes : 0u));
+        if (ckg != nullptr) bulk_load_1d(Sg + (size_t)rowK * kNP, ckg, tk_bytes, &bar[st]);
         tma_load_3d(Sg, &tm_x, &bar[st], p0, a.b0, c * C);
         tma_load_2d(Sg + (size_t)rowW * kNP, &tm_w, &bar[st], p0, c * C);
         if (!a.lam_scalar) tma_load_2d(Sg + (size_t)rowL * kNP, &tm_l, &bar[st], p0, c * C);
@@ -172,11 +176,13 @@ __global__ void __launch_bounds__(kNP* S, S > 1 ? 2 : 4) k_tile(const __grid_con
 
   // Wait for barrier i. LDGSTS path: `newer` groups were committed after the awaited one
   // (waiting for the Z group drains every group, which is correct and only costs overlap).
+  // TMA path: thread 0 alone polls the barrier (the others wait at the block barrier
+  // that always follows, which orders the copied data for them).
   auto wait_bar = [&](int i, int newer) -> bool {
     bool ok = true;
     if (a.tma) {
-      ok = mbar_wait_bounded(&bar[i], (phase >> i) & 1u);
-      if (ok) phase ^= 1u << i;
+      if (tid == 0) ok = mbar_wait_bounded(&bar[i], (phase >> i) & 1u);
+      if (ok) phase ^= 1u << i;  // thread 0 keeps the parity it gave up on, for abort_all
     } else {
       if (newer >= 1)
         cp_async_wait<1>();
@@ -201,17 +207,15 @@ __global__ void __launch_bounds__(kNP* S, S > 1 ? 2 : 4) k_tile(const __grid_con
     if (!a.tma) cp_async_wait<0>();
   };
 
-  constexpr int kFF = SW::kFactorFields;
-  constexpr int kFields = kFF + NB * D;
   for (int tile = blockIdx.x; tile < a.n_tiles; tile += gridDim.x) {
     const int p0 = tile * kNP;
     const int p = p0 + pl;
     const bool act = p < a.P;
-    F* ck = static_cast<F*>(a.ckpt) + (size_t)blockIdx.x * a.nch * kFields * kNP + pl;
+    F* ck = static_cast<F*>(a.ckpt) + (size_t)blockIdx.x * a.nch * kFields * kNP + pl;  // this thread's column
 
     // ---------------- pass 1: forward sweep, checkpoints ----------------
-    issue(0, 0, p0);
-    if (a.nch > 1) issue(1, 1, p0);
+    issue(0, 0, p0, nullptr);
+    if (a.nch > 1) issue(1, 1, p0, nullptr);
     SW s;
     s.reset();
     int npos = 0;
@@ -256,8 +260,9 @@ __global__ void __launch_bounds__(kNP* S, S > 1 ? 2 : 4) k_tile(const __grid_con
         s.factor_step(has_row, li, wa, rho, invD);
         s.subst_step(rho, invD, bv, yh);
       }
+      if (c + 2 >= a.nch) fence_proxy_async_global();  // checkpoints are read back by bulk copies
       __syncthreads();
-      if (c + 2 < a.nch) issue(c + 2, st, p0);
+      if (c + 2 < a.nch) issue(c + 2, st, p0, nullptr);
     }
 
     // ---------------- pass 2: backward sweep, chunk recompute ----------------
@@ -300,7 +305,9 @@ __global__ void __launch_bounds__(kNP* S, S > 1 ? 2 : 4) k_tile(const __grid_con
       }
       if (want_z) issue_z(c, p0);
       F* Sg = stage(st);
-      F* ckc = ck + (size_t)c * kFields * kNP;
+      // the chunk's checkpoint: prefetched into the stage by the bulk copy, except for the
+      // two chunks still resident from pass 1 (and on the LDGSTS path)
+      const F* ckc = (a.tma && c < a.nch - 2) ? Sg + (size_t)rowK * kNP + pl : ck + (size_t)c * kFields * kNP;
       s.load_factor(ckc, kNP);
       s.load_y(ckc + (size_t)(kFF + h * NBT * D) * kNP, kNP);
       const int nd = min(C, T - c * C);
@@ -427,11 +434,11 @@ __global__ void __launch_bounds__(kNP* S, S > 1 ? 2 : 4) k_tile(const __grid_con
           }
           if (c >= 2) {
             bulk_wait_read_all();
-            issue(c - 2, st, p0);
+            issue(c - 2, st, p0, static_cast<const F*>(a.ckpt) + ((size_t)blockIdx.x * a.nch + (c - 2)) * kFields * kNP);
           }
         }
       } else if (c >= 2) {
-        issue(c - 2, st, p0);
+        issue(c - 2, st, p0, nullptr);
       }
     }
     // per-series status; the band halves combine their non-finite flags
