@@ -79,7 +79,7 @@ struct Sweep {
     F nd = F(0);
     F inv = F(0);
     if (has_row) {
-      const F sl = sqrt_(lam);
+      const F sl = lam > F(0) ? lam * rsqrt_(lam) : F(0);  // sqrt(lambda) from one MUFU op
 #pragma unroll
       for (int n = 0; n <= D; ++n) v[n] = sl * F(dcoef<D>(n));
 #pragma unroll
