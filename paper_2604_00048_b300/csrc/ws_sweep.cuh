@@ -31,7 +31,14 @@ __host__ __device__ constexpr int dcoef(int n) {
   return ((D - n) % 2 ? -1 : 1) * binom(D, n);
 }
 
-__device__ __forceinline__ float rsqrt_(float v) { return rsqrtf(v); }
+// FP32: the hardware reciprocal square root (one MUFU op, relative error ~2^-22): the
+// rotations only need it to working precision, and the library rsqrtf is a longer
+// sequence with special-case branches. FP64 keeps the library routine.
+__device__ __forceinline__ float rsqrt_(float v) {
+  float r;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(v));
+  return r;
+}
 __device__ __forceinline__ double rsqrt_(double v) { return rsqrt(v); }
 __device__ __forceinline__ float sqrt_(float v) { return sqrtf(v); }
 __device__ __forceinline__ double sqrt_(double v) { return sqrt(v); }
