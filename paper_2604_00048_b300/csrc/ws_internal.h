@@ -5,7 +5,7 @@
 #include <stddef.h>
 #include <stdint.h>
 
-#include "../../include/ws.h"
+#include "ws.h"
 
 namespace ws {
 

@@ -23,7 +23,13 @@
 
 namespace ws {
 
-__host__ __device__ constexpr int binom(int n, int k) { return k == 0 ? 1 : binom(n, k - 1) * (n - k + 1) / k; }
+// Binomial coefficient, iterative: a recursive constexpr function is not inlined in
+// device code and would become a real call inside the day loop.
+__host__ __device__ constexpr int binom(int n, int k) {
+  int r = 1;
+  for (int i = 1; i <= k; ++i) r = r * (n - k + i) / i;
+  return r;
+}
 
 // c_n = (-1)^(D-n) C(D, n): row k of D holds c at columns k..k+D (Section 2).
 template <int D>
