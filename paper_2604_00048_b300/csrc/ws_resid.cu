@@ -2,9 +2,9 @@
 //     r = W x - Omega z0 = W (x - z0) - D^T (Lambda (D z0))        (Omega from Eq. 3)
 // or, for a right-hand side taken as given (the adjoint solve Omega g = gz),
 //     r = x - Omega z0 = x - W z0 - D^T (Lambda (D z0)).
-// At a good z0 the two terms cancel to a few parts in 1e5, so every difference and
-// every sum is carried as a double word (ws_df.cuh): D z0, Lambda D z0 and the D^T
-// accumulation are exact up to the final rounding of r to working precision.
+// At a good z0 the two terms cancel to a few parts in 1e5. D z0 and D^T q are taken
+// as nested first differences (exact on smooth sequences, where the binomial sums
+// would cancel digits), and the final combination is a double word (ws_df.cuh).
 // Thread = one pixel x a block of kDays days; all bands stream through rings of the
 // last d+1 values of z0 and of q_k = lambda_k (D z0)_k. Every load is coalesced across
 // the pixel-fastest tile layout.
@@ -31,12 +31,18 @@ __global__ void __launch_bounds__(128) k_residual(const F* __restrict__ x, const
   const size_t sP = (size_t)P, sBP = (size_t)B * P;
   const F ls = lam_scalar ? lam[p] : F(0);
   for (int b = 0; b < B; ++b) {
-    F zr[D + 1];     // z0_{u-D} .. z0_u
-    DW<F> qr[D + 1];  // q_{k-D} .. q_k
+    // Forward differences of z0 by nested first differences: fd[j] = Delta^j z0 at the
+    // current row k (j = 0..D). Backward differences of q_k = lambda_k (D z0)_k likewise:
+    // bq[j] = nabla^j q at the current residual day t, so (D^T q)_t = (-1)^D nabla^D q_t.
+    // On smooth sequences every subtraction is exact (Sterbenz), where the binomial form
+    // cancels digits; the two large terms W(x - z0) and D^T Lambda D z0 that cancel in r
+    // are combined as a double word.
+    F zr[D + 1];      // z0 at rows u-D .. u (only the differences are used)
+    F qb[D + 1];      // q at rows k-D .. k
 #pragma unroll
     for (int n = 0; n <= D; ++n) {
       zr[n] = F(0);
-      qr[n] = {F(0), F(0)};
+      qb[n] = F(0);
     }
     for (int u = t0 - D; u < t1 + D; ++u) {
 #pragma unroll
@@ -44,30 +50,41 @@ __global__ void __launch_bounds__(128) k_residual(const F* __restrict__ x, const
       zr[D] = (u >= 0 && u < T) ? z0[(size_t)u * sBP + (size_t)b * sP + p] : F(0);
       const int k = u - D;  // difference row whose last day is u
 #pragma unroll
-      for (int n = 0; n < D; ++n) qr[n] = qr[n + 1];
-      DW<F> q = {F(0), F(0)};
+      for (int n = 0; n < D; ++n) qb[n] = qb[n + 1];
+      F q = F(0);
       if (k >= 0 && k <= T - D - 1) {
-        DW<F> dz = two_prod(F(dcoef<D>(0)), zr[0]);
+        F lv[D + 1];
 #pragma unroll
-        for (int n = 1; n <= D; ++n) dz = dw_add(dz, two_prod(F(dcoef<D>(n)), zr[n]));
+        for (int n = 0; n <= D; ++n) lv[n] = zr[n];
+#pragma unroll
+        for (int j = 0; j < D; ++j)
+#pragma unroll
+          for (int n = 0; n < D - j; ++n) lv[n] = lv[n + 1] - lv[n];
         const F lk = lam_scalar ? ls : lam[(size_t)k * sP + p];
-        q = dw_scale(dz, lk);
+        q = lk * lv[0];
       }
-      qr[D] = q;
+      qb[D] = q;
       const int t = k;  // residual day whose rows k-D..k are now all known
       if (t >= t0 && t < t1) {
-        const F wt = w[(size_t)t * sP + p];
-        DW<F> acc = {F(0), F(0)};
-        if (raw) {
-          const F xt = x[(size_t)t * sBP + (size_t)b * sP + p];
-          const DW<F> wz = two_prod(wt, zr[0]);
-          acc = dw_add(DW<F>{xt, F(0)}, DW<F>{-wz.hi, -wz.lo});
-        } else if (wt > F(0)) {
-          const F xt = x[(size_t)t * sBP + (size_t)b * sP + p];
-          acc = dw_scale(two_sum(xt, -zr[0]), wt);  // zr[0] = z0_t (u = t + D)
-        }
+        // (D^T q)_t = sum_n c_n q_{t-n} = (-1)^D * (D-th backward difference of q at t)
+        F lv[D + 1];
 #pragma unroll
-        for (int n = 0; n <= D; ++n) acc = dw_add(acc, dw_scale(qr[D - n], F(-dcoef<D>(n))));
+        for (int n = 0; n <= D; ++n) lv[n] = qb[n];  // q_{t-D} .. q_t
+#pragma unroll
+        for (int j = 0; j < D; ++j)
+#pragma unroll
+          for (int n = D; n > j; --n) lv[n] = lv[n] - lv[n - 1];
+        const F dtq = (D % 2) ? -lv[D] : lv[D];
+        const F wt = w[(size_t)t * sP + p];
+        const F xt = x[(size_t)t * sBP + (size_t)b * sP + p];
+        DW<F> acc;
+        if (raw) {
+          const DW<F> wz = two_prod(wt, zr[0]);  // zr[0] = z0_t (u = t + D)
+          acc = dw_add(DW<F>{xt, F(0)}, DW<F>{-wz.hi, -wz.lo});
+        } else {
+          acc = wt > F(0) ? dw_scale(two_sum(xt, -zr[0]), wt) : DW<F>{F(0), F(0)};
+        }
+        acc = dw_add(acc, DW<F>{-dtq, F(0)});
         r[(size_t)t * sBP + (size_t)b * sP + p] = acc.hi + acc.lo;
       }
     }
