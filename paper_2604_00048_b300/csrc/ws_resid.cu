@@ -19,7 +19,7 @@ namespace ws {
 
 constexpr int kResidDays = 64;
 
-template <typename F, int D>
+template <typename F, int D, int NBR>
 __global__ void __launch_bounds__(128) k_residual(const F* __restrict__ x, const F* __restrict__ w,
                                                   const F* __restrict__ lam, const F* __restrict__ z0,
                                                   F* __restrict__ r, int T, int B, int P, int lam_scalar,
@@ -28,64 +28,72 @@ __global__ void __launch_bounds__(128) k_residual(const F* __restrict__ x, const
   if (p >= P) return;
   const int t0 = blockIdx.y * kResidDays;
   const int t1 = min(T, t0 + kResidDays);
+  const int b0 = blockIdx.z * NBR;
+  const int nb = min(NBR, B - b0);
   const size_t sP = (size_t)P, sBP = (size_t)B * P;
   const F ls = lam_scalar ? lam[p] : F(0);
-  for (int b = 0; b < B; ++b) {
-    // Forward differences of z0 by nested first differences: fd[j] = Delta^j z0 at the
-    // current row k (j = 0..D). Backward differences of q_k = lambda_k (D z0)_k likewise:
-    // bq[j] = nabla^j q at the current residual day t, so (D^T q)_t = (-1)^D nabla^D q_t.
-    // On smooth sequences every subtraction is exact (Sterbenz), where the binomial form
-    // cancels digits; the two large terms W(x - z0) and D^T Lambda D z0 that cancel in r
-    // are combined as a double word.
-    F zr[D + 1];      // z0 at rows u-D .. u (only the differences are used)
-    F qb[D + 1];      // q at rows k-D .. k
+  // Days outer, bands inner: w_t and lambda_k are read once per day for all bands.
+  // Per band: z0 at rows u-D..u and q = lambda (D z0) at rows k-D..k. D z0 and D^T q are
+  // nested first differences (exact on smooth sequences, where the binomial sums would
+  // cancel digits); the two large terms W(x - z0) and D^T Lambda D z0 that cancel in r
+  // are combined as a double word.
+  F zr[NBR][D + 1];
+  F qb[NBR][D + 1];
+#pragma unroll
+  for (int j = 0; j < NBR; ++j)
 #pragma unroll
     for (int n = 0; n <= D; ++n) {
-      zr[n] = F(0);
-      qb[n] = F(0);
+      zr[j][n] = F(0);
+      qb[j][n] = F(0);
     }
-    for (int u = t0 - D; u < t1 + D; ++u) {
+  for (int u = t0 - D; u < t1 + D; ++u) {
+    const int k = u - D;  // difference row whose last day is u
+    const bool row = k >= 0 && k <= T - D - 1;
+    const F lk = row ? (lam_scalar ? ls : lam[(size_t)k * sP + p]) : F(0);
+    const int t = k;      // residual day whose rows k-D..k are now all known
+    const bool emit = t >= t0 && t < t1;
+    const F wt = emit ? w[(size_t)t * sP + p] : F(0);
 #pragma unroll
-      for (int n = 0; n < D; ++n) zr[n] = zr[n + 1];
-      zr[D] = (u >= 0 && u < T) ? z0[(size_t)u * sBP + (size_t)b * sP + p] : F(0);
-      const int k = u - D;  // difference row whose last day is u
+    for (int j = 0; j < NBR; ++j) {
+      if (j >= nb) break;
+      const size_t col = (size_t)(b0 + j) * sP + p;
 #pragma unroll
-      for (int n = 0; n < D; ++n) qb[n] = qb[n + 1];
+      for (int n = 0; n < D; ++n) zr[j][n] = zr[j][n + 1];
+      zr[j][D] = (u >= 0 && u < T) ? z0[(size_t)u * sBP + col] : F(0);
+#pragma unroll
+      for (int n = 0; n < D; ++n) qb[j][n] = qb[j][n + 1];
       F q = F(0);
-      if (k >= 0 && k <= T - D - 1) {
+      if (row) {
         F lv[D + 1];
 #pragma unroll
-        for (int n = 0; n <= D; ++n) lv[n] = zr[n];
+        for (int n = 0; n <= D; ++n) lv[n] = zr[j][n];
 #pragma unroll
-        for (int j = 0; j < D; ++j)
+        for (int i = 0; i < D; ++i)
 #pragma unroll
-          for (int n = 0; n < D - j; ++n) lv[n] = lv[n + 1] - lv[n];
-        const F lk = lam_scalar ? ls : lam[(size_t)k * sP + p];
+          for (int n = 0; n < D - i; ++n) lv[n] = lv[n + 1] - lv[n];
         q = lk * lv[0];
       }
-      qb[D] = q;
-      const int t = k;  // residual day whose rows k-D..k are now all known
-      if (t >= t0 && t < t1) {
+      qb[j][D] = q;
+      if (emit) {
         // (D^T q)_t = sum_n c_n q_{t-n} = (-1)^D * (D-th backward difference of q at t)
         F lv[D + 1];
 #pragma unroll
-        for (int n = 0; n <= D; ++n) lv[n] = qb[n];  // q_{t-D} .. q_t
+        for (int n = 0; n <= D; ++n) lv[n] = qb[j][n];
 #pragma unroll
-        for (int j = 0; j < D; ++j)
+        for (int i = 0; i < D; ++i)
 #pragma unroll
-          for (int n = D; n > j; --n) lv[n] = lv[n] - lv[n - 1];
+          for (int n = D; n > i; --n) lv[n] = lv[n] - lv[n - 1];
         const F dtq = (D % 2) ? -lv[D] : lv[D];
-        const F wt = w[(size_t)t * sP + p];
-        const F xt = x[(size_t)t * sBP + (size_t)b * sP + p];
+        const F xt = x[(size_t)t * sBP + col];
         DW<F> acc;
         if (raw) {
-          const DW<F> wz = two_prod(wt, zr[0]);  // zr[0] = z0_t (u = t + D)
+          const DW<F> wz = two_prod(wt, zr[j][0]);  // zr[j][0] = z0_t (u = t + D)
           acc = dw_add(DW<F>{xt, F(0)}, DW<F>{-wz.hi, -wz.lo});
         } else {
-          acc = wt > F(0) ? dw_scale(two_sum(xt, -zr[0]), wt) : DW<F>{F(0), F(0)};
+          acc = wt > F(0) ? dw_scale(two_sum(xt, -zr[j][0]), wt) : DW<F>{F(0), F(0)};
         }
         acc = dw_add(acc, DW<F>{-dtq, F(0)});
-        r[(size_t)t * sBP + (size_t)b * sP + p] = acc.hi + acc.lo;
+        r[(size_t)t * sBP + col] = acc.hi + acc.lo;
       }
     }
   }
@@ -94,8 +102,10 @@ __global__ void __launch_bounds__(128) k_residual(const F* __restrict__ x, const
 template <typename F, int D>
 static int launch_resid_t(const ws_problem& pb, const void* x, const void* w, const void* lam, const void* z0,
                           void* r, int raw, cudaStream_t st) {
-  dim3 grid((unsigned)((pb.n_series + 127) / 128), (unsigned)((pb.T + kResidDays - 1) / kResidDays));
-  k_residual<F, D><<<grid, 128, 0, st>>>(static_cast<const F*>(x), static_cast<const F*>(w),
+  constexpr int NBR = 5;  // bands per thread
+  dim3 grid((unsigned)((pb.n_series + 127) / 128), (unsigned)((pb.T + kResidDays - 1) / kResidDays),
+            (unsigned)((pb.n_bands + NBR - 1) / NBR));
+  k_residual<F, D, NBR><<<grid, 128, 0, st>>>(static_cast<const F*>(x), static_cast<const F*>(w),
                                          static_cast<const F*>(lam), static_cast<const F*>(z0), static_cast<F*>(r),
                                          pb.T, pb.n_bands, (int)pb.n_series, pb.lam_mode == WS_LAM_SCALAR, raw);
   cudaError_t e = cudaGetLastError();
