@@ -124,12 +124,14 @@ int ws_refine(const ws_problem* pb, const void* x, const void* w, const void* la
 /* Factor only (Section 3.1): writes, per day t, factor[(t*(d+1) + 0)*P + p] = 1/D_t and
  * factor[(t*(d+1) + j)*P + p] = L[t+j][t] (j = 1..d) of Omega = L diag(D) L^T with L
  * unit lower triangular banded (entries that would fall past T are 0). One forward
- * sweep; no workspace beyond the header. */
+ * sweep (the same plane rotations as ws_smooth_batch); workspace unused (may be NULL).
+ * Series that fail (status != 0) get a zero factor. */
 int ws_factor(const ws_problem* pb, const void* w, const void* lam, void* factor, uint8_t* status,
               void* workspace, size_t ws_bytes, void* stream);
 
 /* Solve with a stored factor: z = Omega^{-1} W x, Omega given by `factor` (ws_factor
- * layout) and w. flags: 0. */
+ * layout) and w; z is used as scratch between the two sweeps. flags: 0; workspace
+ * unused (may be NULL). */
 int ws_solve(const ws_problem* pb, const void* factor, const void* w, const void* x, void* z,
              uint32_t flags, void* workspace, size_t ws_bytes, void* stream);
 
@@ -144,7 +146,9 @@ int ws_solve(const ws_problem* pb, const void* factor, const void* w, const void
  * double-word accumulation) before the epilogue; needs ws_workspace_size(pb,
  * WS_REFINE_ADJOINT). (D g)_k and (D z)_k are formed as nested first differences.
  * factor_or_null: a stored factor (ws_factor layout), or NULL to recompute it from
- * (w, lam) inside the sweeps (less memory). gx and glam are each optional (NULL). */
+ * (w, lam) inside the sweeps (less memory). With a stored factor the workspace must be
+ * ws_workspace_size(pb, WS_REFINE) bytes (g is held there) and `status` is not written.
+ * gx and glam are each optional (NULL). */
 int ws_solve_adjoint(const ws_problem* pb, const void* factor_or_null, const void* w,
                      const void* lam, const void* z, const void* gz, void* gx, void* glam,
                      uint32_t flags, uint8_t* status, void* workspace, size_t ws_bytes,

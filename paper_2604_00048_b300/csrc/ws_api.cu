@@ -227,12 +227,23 @@ static int run_tile(const ws_problem& P, int mode, const void* rhs, const void* 
 
 using namespace ws;
 
+// Adjoint with a stored factor: g = Omega^{-1} gz into the refinement region of the
+// workspace, then the gx / glam epilogue. (status is left untouched: ws_factor set it.)
 static int ws_adjoint_factored(const ws_problem* pb, const void* factor, const void* w, const void* lam, const void* z,
                                const void* gz, void* gx, void* glam, uint32_t flags, uint8_t* status,
                                void* workspace, size_t ws_bytes, void* stream) {
-  (void)pb, (void)factor, (void)w, (void)lam, (void)z, (void)gz, (void)gx, (void)glam, (void)flags;
-  (void)status, (void)workspace, (void)ws_bytes, (void)stream;
-  return set_error(WS_EUNSUPPORTED, "stored-factor adjoint: not built yet");
+  (void)status;
+  const ws_problem& P = *pb;
+  if (flags & WS_REFINE_ADJOINT) return set_error(WS_EINVAL, "refinement needs the recomputed factor (factor = NULL)");
+  size_t ck_bytes = 0;
+  int rc = check_workspace(P, workspace, ws_bytes, resid_bytes(P), ck_bytes);
+  if (rc != WS_OK) return rc;
+  void* gs = static_cast<char*>(workspace) + kHeaderBytes + ck_bytes;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  rc = launch_factored(1, P, factor, nullptr, w, lam, gz, gs, nullptr, nullptr, nullptr, nullptr, nullptr, 0, 0, st);
+  if (rc != WS_OK) return rc;
+  return launch_factored(2, P, factor, nullptr, w, lam, nullptr, nullptr, z, gs, gx, glam, nullptr, 0,
+                         (flags & WS_GRAD_LOGLAM) ? 1 : 0, st);
 }
 
 extern "C" size_t ws_workspace_size(const ws_problem* pb, uint32_t flags) {
@@ -299,16 +310,29 @@ extern "C" int ws_refine(const ws_problem* pb, const void* x, const void* w, con
 
 extern "C" int ws_factor(const ws_problem* pb, const void* w, const void* lam, void* factor, uint8_t* status,
                          void* workspace, size_t ws_bytes, void* stream) {
-  (void)pb, (void)w, (void)lam, (void)factor, (void)status, (void)workspace, (void)ws_bytes, (void)stream;
+  (void)workspace, (void)ws_bytes;
   clear_error();
-  return set_error(WS_EUNSUPPORTED, "ws_factor: not built yet");
+  int rc = validate_problem(pb);
+  if (rc != WS_OK) return rc;
+  if (pb->n_series == 0 || pb->T == 0) return WS_OK;
+  if (!w || !lam || !factor) return set_error(WS_EINVAL, "w, lam and factor must be non-NULL");
+  return launch_factored(0, *pb, nullptr, factor, w, lam, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr,
+                         status, 0, 0, static_cast<cudaStream_t>(stream));
 }
 
 extern "C" int ws_solve(const ws_problem* pb, const void* factor, const void* w, const void* x, void* z,
                         uint32_t flags, void* workspace, size_t ws_bytes, void* stream) {
-  (void)pb, (void)factor, (void)w, (void)x, (void)z, (void)flags, (void)workspace, (void)ws_bytes, (void)stream;
+  (void)workspace, (void)ws_bytes;
   clear_error();
-  return set_error(WS_EUNSUPPORTED, "ws_solve: not built yet");
+  int rc = validate_problem(pb);
+  if (rc != WS_OK) return rc;
+  if (flags != 0) return set_error(WS_EINVAL, "unknown flags 0x%x", flags);
+  if (pb->n_series == 0 || pb->T == 0) return WS_OK;
+  if (!factor || !w || !x || !z) return set_error(WS_EINVAL, "factor, w, x and z must be non-NULL");
+  const size_t nx = (size_t)pb->T * pb->n_bands * pb->n_series * elem_size(*pb);
+  if (overlaps(x, nx, z, nx)) return set_error(WS_EINVAL, "z must not overlap x");
+  return launch_factored(1, *pb, factor, nullptr, w, nullptr, x, z, nullptr, nullptr, nullptr, nullptr, nullptr, 1,
+                         0, static_cast<cudaStream_t>(stream));
 }
 
 extern "C" int ws_solve_adjoint(const ws_problem* pb, const void* factor_or_null, const void* w, const void* lam,

@@ -215,11 +215,37 @@ def smooth_adjoint(w: torch.Tensor, lam: torch.Tensor, z: torch.Tensor, gz: torc
     if status is None:
         status = torch.empty(P, dtype=torch.uint8, device=gz.device)
     flags = (GRAD_LOGLAM if log_lambda else 0) | (REFINE_ADJOINT if refine else 0)
-    ws = workspace(pb, gz.device, flags)
+    ws = workspace(pb, gz.device, flags | (REFINE if factor is not None else 0))
     rc = _lib.ws_solve_adjoint(ctypes.byref(pb), _ptr(factor), _ptr(w), _ptr(lam), _ptr(z), _ptr(gz), _ptr(gx),
                                _ptr(glam), flags, _ptr(status), _ptr(ws), ws.numel(), _stream_ptr(stream))
     _check(rc)
     return gx, glam, status
+
+
+def factor(w: torch.Tensor, lam: torch.Tensor, d: int = 2, *, out=None, status=None, stream=None):
+    """Factor of Omega (ws_factor layout [T, d+1, P]): 1/D_t and L[t+j][t]. Returns (factor, status)."""
+    if w.dim() != 2:
+        raise ValueError("w must be [T, P]")
+    T, P = w.shape
+    lm = LAM_SCALAR if lam.dim() == 1 else LAM_PER_DAY
+    pb = make_problem(T, 1, P, d, _dtype_code(w), lm)
+    if out is None:
+        out = torch.empty((T, d + 1, P), dtype=w.dtype, device=w.device)
+    if status is None:
+        status = torch.empty(P, dtype=torch.uint8, device=w.device)
+    _check(_lib.ws_factor(ctypes.byref(pb), _ptr(w), _ptr(lam), _ptr(out), _ptr(status), None, 0,
+                          _stream_ptr(stream)))
+    return out, status
+
+
+def solve(fac: torch.Tensor, w: torch.Tensor, x: torch.Tensor, d: int = 2, *, z=None, stream=None):
+    """z = Omega^{-1} W x with a stored factor."""
+    T, B, P = x.shape
+    pb = make_problem(T, B, P, d, _dtype_code(x), LAM_PER_DAY)
+    if z is None:
+        z = torch.empty_like(x)
+    _check(_lib.ws_solve(ctypes.byref(pb), _ptr(fac), _ptr(w), _ptr(x), _ptr(z), 0, None, 0, _stream_ptr(stream)))
+    return z
 
 
 def tune_set(ctas_per_sm: int = 0, chunk_days: int = 0):
