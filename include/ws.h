@@ -161,6 +161,56 @@ int ws_solve_adjoint(const ws_problem* pb, const void* factor_or_null, const voi
  * current setting. Returns WS_EINVAL for out-of-range values. */
 int ws_tune_set(int32_t ctas_per_sm, int32_t chunk_days);
 
+/* ---------------------------------------------------------------------------------
+ * Ragged batches: series of different lengths (and orders) packed back to back.
+ * Band b of series i occupies x[b*N + offsets[i] + t], t < T_i = offsets[i+1] - offsets[i],
+ * N = offsets[n_series]; w, z likewise (w one band); lam per day packed like w
+ * (WS_LAM_PER_DAY) or one value per series (WS_LAM_SCALAR). FP32.
+ * A plan sorts the series by (order, length) into work items of 32 series (one per
+ * lane of a warp); a persistent grid pulls items from an atomic counter, each warp
+ * running the same two-sweep rotation solve as ws_smooth_batch. ws_plan_create reads
+ * offsets and orders back to the host (it synchronises `stream`) and allocates the plan's
+ * device tables and checkpoint area (freed by ws_plan_destroy); ws_plan_execute
+ * allocates nothing. */
+typedef struct ws_ragged {
+  int64_t n_series;            /* n >= 0 */
+  const int64_t* offsets;      /* device, n + 1 entries, offsets[0] = 0, non-decreasing */
+  const int8_t* d_per_series;  /* device, n orders in 1..4, or NULL: every series uses d_uniform */
+  int32_t d_uniform;           /* 1..4 when d_per_series is NULL */
+  int32_t n_bands;             /* B >= 1 */
+  int32_t dtype;               /* WS_F32 */
+  int32_t lam_mode;            /* WS_LAM_PER_DAY | WS_LAM_SCALAR */
+} ws_ragged;
+
+typedef struct ws_plan ws_plan;
+
+typedef struct ws_plan_stats {
+  int32_t n_items;        /* work items (warps of 32 series) */
+  int32_t chunk_days;     /* days staged per chunk */
+  int32_t warps_per_cta;
+  int32_t grid;           /* persistent CTAs */
+  int32_t tuned;          /* the autotuner has run */
+  int32_t graph;          /* a CUDA graph is instantiated */
+  float tuned_ms;         /* best time the autotuner measured */
+} ws_plan_stats;
+
+#define WS_PLAN_AUTOTUNE 0x1u  /* ws_plan_execute: time the (chunk, warps/CTA) candidates once */
+#define WS_PLAN_GRAPH 0x2u     /* ws_plan_execute: replay a captured CUDA graph (one band) */
+
+int ws_plan_create(const ws_ragged* rg, ws_plan** out, void* stream);
+
+/* z = Omega^{-1} W x for every series of the plan (Eq. 3 with each series' own T_i and d).
+ * status: optional per-series codes. flags: WS_PLAN_AUTOTUNE and/or WS_PLAN_GRAPH. With
+ * WS_PLAN_AUTOTUNE the first call times the candidates (running the solve several times
+ * on these buffers) and keeps the fastest; with WS_PLAN_GRAPH the launch is captured once
+ * and later calls update its arguments and replay it. */
+int ws_plan_execute(ws_plan* plan, const void* x, const void* w, const void* lam, void* z, uint8_t* status,
+                    uint32_t flags, void* stream);
+
+int ws_plan_info(const ws_plan* plan, ws_plan_stats* out);
+
+void ws_plan_destroy(ws_plan* plan);
+
 /* Synchronises `stream`, reads and clears the device error word in `workspace`.
  * Returns WS_OK, WS_ETIMEOUT (a device-side wait gave up: its outputs are invalid)
  * or WS_ECUDA. */

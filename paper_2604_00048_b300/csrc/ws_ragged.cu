@@ -1,0 +1,526 @@
+// Ragged batches: series of different lengths T_i and orders d_i packed back to back,
+// band b of series i at x[b*N + off[i] + t] (N = off[n]), w and lambda like one band.
+//
+// Host plan: series are sorted by (d, length descending) and cut into work items of 32
+// (one per lane), so every warp runs one order and lanes of similar length; items are
+// ordered largest first. A persistent grid of warps pulls items from an atomic counter.
+// Per item, the warp runs the same two-pass recurrence as the tile kernels (ws_sweep.cuh):
+// pass 1 forward over chunks of RC days with checkpoints, pass 2 backward recomputing each
+// chunk from its checkpoint. Each lane owns one series; chunks are staged in shared memory
+// by warp-cooperative LDGSTS copies that read each series contiguously (coalesced) and
+// write a padded [day][lane] layout (conflict-free), and results leave the same way.
+// The launch (counter reset + kernel) is captured in a CUDA graph and replayed; an
+// autotuner picks the chunk length and warps per CTA on the plan's own data.
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string.h>
+
+#include <algorithm>
+#include <numeric>
+#include <vector>
+
+#include "ws_internal.h"
+#include "ws_ptx.cuh"
+#include "ws_sweep.cuh"
+
+namespace ws {
+
+constexpr int kPitch = 33;  // shared-memory row pitch: 32 lanes + 1 pad
+
+struct RaggedArgs {
+  const int64_t* off;     // n + 1
+  const int32_t* order;   // n_items * 32 series ids (-1 = idle lane)
+  const int8_t* item_d;   // order of each item
+  const int32_t* item_nch;
+  int n_items;
+  int64_t N;              // off[n]
+  int B, band;            // band of this launch
+  int lam_scalar;
+  const float* x;
+  const float* w;
+  const float* lam;
+  float* z;
+  uint8_t* status;
+  float* ckpt;            // per persistent warp: max_nch * kFieldsMax * 32
+  int max_nch;
+  int* counter;
+  unsigned* err;
+};
+
+constexpr int kFieldsMax = 4 * 5 + 4;  // d(d+1) + d for d <= 4, one band
+
+template <int RC>
+struct RaggedSmem {
+  // rows of kPitch floats: X [RC], W [RC + 4], L [RC], E [2 * RC] (rho_3, rho_4)
+  static constexpr int rowX = 0, rowW = RC, rowL = 2 * RC + 4, rowE = 3 * RC + 4, rows = 5 * RC + 4;
+};
+
+// One item (32 series of order D) on one warp.
+template <int D, int RC>
+__device__ void ragged_item(const RaggedArgs& a, int item, float* sm, float* ck, int lane) {
+  using L = RaggedSmem<RC>;
+  using SW = Sweep<float, D, 1>;
+  constexpr int kFF = SW::kFactorFields;
+  constexpr int kF = kFF + D;
+  const int sid = a.order[(size_t)item * 32 + lane];
+  const bool live = sid >= 0;
+  const int64_t off = live ? a.off[sid] : 0;
+  const int T = live ? (int)(a.off[sid + 1] - off) : 0;
+  const int nch = a.item_nch[item];
+  const float* xb = a.x + (size_t)a.band * a.N;
+  float* zb = a.z + (size_t)a.band * a.N;
+  auto stg = [&](int st) -> float* { return sm + (size_t)st * L::rows * kPitch; };
+  if (nch == 0) {  // every series of the item is empty
+    if (live && a.status != nullptr && a.band == 0) a.status[sid] = WS_SERIES_OK;
+    return;
+  }
+
+  // warp-cooperative staging of chunk c into stage st: for every series s of the item,
+  // consecutive lanes copy consecutive days (coalesced), into row = day, column = s.
+  auto issue = [&](int c, int st) {
+    float* S = stg(st);
+    const int t0 = c * RC;
+    for (int s = 0; s < 32; ++s) {
+      const int64_t os = __shfl_sync(0xffffffffu, off, s);
+      const int Ts = __shfl_sync(0xffffffffu, T, s);
+      for (int j = lane; j < RC + 4; j += 32) {
+        const int t = t0 + j;
+        const bool v = t < Ts;
+        const int64_t g = os + (v ? t : 0);
+        if (j < RC) {
+          cp_async_elem<4>(S + (L::rowX + j) * kPitch + s, xb + g, v);
+          if (!a.lam_scalar) cp_async_elem<4>(S + (L::rowL + j) * kPitch + s, a.lam + g, v);
+        }
+        cp_async_elem<4>(S + (L::rowW + j) * kPitch + s, a.w + g, v);
+      }
+    }
+    cp_async_commit();
+  };
+
+  SW s;
+  s.reset();
+  int npos = 0;
+  bool bad = false;
+  const float ls = (live && a.lam_scalar) ? a.lam[sid] : 0.f;
+  issue(0, 0);
+  if (nch > 1) issue(1, 1);
+  for (int c = 0; c < nch; ++c) {
+    if (c + 1 < nch) cp_async_wait<1>(); else cp_async_wait<0>();
+    __syncwarp();
+    const float* S = stg(c & 1);
+    if (c == 0)
+      for (int m = 0; m < D; ++m)
+        if (m < T) s.init_weight(m, S[(L::rowW + m) * kPitch + lane]);
+    float* ckc = ck + (size_t)c * kF * 32 + lane;
+    s.save_factor(ckc, 32);
+    s.save_y(ckc + kFF * 32, 32);
+    const int nd = min(RC, T - c * RC);
+    for (int k = 0; k < nd; ++k) {
+      const int i = c * RC + k;
+      const float wi = S[(L::rowW + k) * kPitch + lane];
+      const float wa = S[(L::rowW + k + D) * kPitch + lane];
+      const float li = a.lam_scalar ? ls : S[(L::rowL + k) * kPitch + lane];
+      const bool has_row = i < T - D;
+      bad |= !(wi >= 0.f) || !isfinite(wi);
+      npos += wi > 0.f;
+      if (has_row) bad |= !(li > 0.f) || !isfinite(li);
+      float bv[1] = {wi > 0.f ? wi * S[(L::rowX + k) * kPitch + lane] : 0.f};
+      float rho[D], yh[1], invD;
+      s.factor_step(has_row, li, wa, rho, invD);
+      s.subst_step(rho, invD, bv, yh);
+    }
+    __syncwarp();
+    if (c + 2 < nch) issue(c + 2, c & 1);
+  }
+  const int dmin = D < T ? D : T;
+  const uint8_t code = bad ? WS_SERIES_BADARG : (npos < dmin ? WS_SERIES_NOT_PD : WS_SERIES_OK);
+  const bool okser = code == WS_SERIES_OK;
+  float zc[D];
+#pragma unroll
+  for (int j = 0; j < D; ++j) zc[j] = 0.f;
+  float nanacc = 0.f;
+  for (int c = nch - 1; c >= 0; --c) {
+    const int st = c & 1;
+    if (c < nch - 2) {
+      if (c >= 1) cp_async_wait<1>(); else cp_async_wait<0>();
+      __syncwarp();
+    }
+    float* S = stg(st);
+    const float* ckc = ck + (size_t)c * kF * 32 + lane;
+    s.load_factor(ckc, 32);
+    s.load_y(ckc + kFF * 32, 32);
+    const int nd = min(RC, T - c * RC);
+    for (int k = 0; k < nd; ++k) {
+      const int i = c * RC + k;
+      const float wi = S[(L::rowW + k) * kPitch + lane];
+      const float wa = S[(L::rowW + k + D) * kPitch + lane];
+      const float li = a.lam_scalar ? ls : S[(L::rowL + k) * kPitch + lane];
+      const bool has_row = i < T - D;
+      float bv[1] = {wi > 0.f ? wi * S[(L::rowX + k) * kPitch + lane] : 0.f};
+      float rho[D], yh[1], invD;
+      s.factor_step(has_row, li, wa, rho, invD);
+      s.subst_step(rho, invD, bv, yh);
+      S[(L::rowX + k) * kPitch + lane] = yh[0];
+      // rho_1 over lambda, rho_2 over w (both already consumed for day k), rho_3.. in E
+      S[(L::rowL + k) * kPitch + lane] = rho[0];
+      if (D >= 2) S[(L::rowW + k) * kPitch + lane] = rho[D >= 2 ? 1 : 0];
+#pragma unroll
+      for (int j = 3; j <= D; ++j) S[(L::rowE + (j - 3) * RC + k) * kPitch + lane] = rho[j - 1];
+    }
+    for (int k = nd - 1; k >= 0; --k) {
+      float rho[D];
+      rho[0] = S[(L::rowL + k) * kPitch + lane];
+      if (D >= 2) rho[D >= 2 ? 1 : 0] = S[(L::rowW + k) * kPitch + lane];
+#pragma unroll
+      for (int j = 3; j <= D; ++j) rho[j - 1] = S[(L::rowE + (j - 3) * RC + k) * kPitch + lane];
+      float acc = S[(L::rowX + k) * kPitch + lane];
+#pragma unroll
+      for (int j = 1; j <= D; ++j) acc = fmaf(-rho[j - 1], zc[j - 1], acc);
+#pragma unroll
+      for (int j = D - 1; j > 0; --j) zc[j] = zc[j - 1];
+      zc[0] = acc;
+      const float out = okser ? acc : 0.f;
+      nanacc = fmaf(out, 0.f, nanacc);
+      S[(L::rowX + k) * kPitch + lane] = out;
+    }
+    __syncwarp();
+    // transposed store of the chunk: consecutive lanes write consecutive days of series s
+    const int t0 = c * RC;
+    for (int s2 = 0; s2 < 32; ++s2) {
+      const int64_t os = __shfl_sync(0xffffffffu, off, s2);
+      const int Ts = __shfl_sync(0xffffffffu, T, s2);
+      for (int j = lane; j < RC; j += 32)
+        if (t0 + j < Ts) zb[os + t0 + j] = S[(L::rowX + j) * kPitch + s2];
+    }
+    __syncwarp();
+    if (c >= 2) issue(c - 2, st);
+  }
+  if (live && a.status != nullptr) {
+    const bool nonfin = !(nanacc == 0.f);
+    if (a.band == 0)
+      a.status[sid] = okser ? (nonfin ? WS_SERIES_NONFINITE : WS_SERIES_OK) : code;
+    else if (nonfin && a.status[sid] == WS_SERIES_OK)
+      a.status[sid] = WS_SERIES_NONFINITE;
+  }
+}
+
+template <int RC>
+__global__ void __launch_bounds__(256) k_ragged(const RaggedArgs a) {
+  extern __shared__ __align__(16) float rsm[];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  float* sm = rsm + (size_t)wid * 2 * RaggedSmem<RC>::rows * kPitch;
+  const int gw = blockIdx.x * (blockDim.x >> 5) + wid;  // persistent warp id
+  float* ck = a.ckpt + (size_t)gw * a.max_nch * kFieldsMax * 32;
+  for (;;) {
+    int item = 0;
+    if (lane == 0) item = atomicAdd(a.counter, 1);
+    item = __shfl_sync(0xffffffffu, item, 0);
+    if (item >= a.n_items) break;
+    switch (a.item_d[item]) {
+      case 1: ragged_item<1, RC>(a, item, sm, ck, lane); break;
+      case 2: ragged_item<2, RC>(a, item, sm, ck, lane); break;
+      case 3: ragged_item<3, RC>(a, item, sm, ck, lane); break;
+      case 4: ragged_item<4, RC>(a, item, sm, ck, lane); break;
+    }
+  }
+}
+
+}  // namespace ws
+
+using namespace ws;
+
+struct ws_plan {
+  ws_ragged rg;
+  int n_items = 0, max_nch16 = 0, max_nch32 = 0;
+  int RC = 16, warps = 8, grid = 0;
+  int64_t N = 0;
+  int32_t* d_order = nullptr;
+  int8_t* d_item_d = nullptr;
+  int32_t* d_nch16 = nullptr;
+  int32_t* d_nch32 = nullptr;
+  int* d_counter = nullptr;
+  unsigned* d_err = nullptr;
+  float* d_ckpt = nullptr;
+  size_t ckpt_bytes = 0;
+  bool tuned = false;
+  float tuned_ms = 0.f;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  cudaGraphNode_t knode = nullptr;
+  int graph_rc = 0, graph_warps = 0;
+};
+
+static size_t ragged_smem(int RC, int warps) { return (size_t)warps * 2 * (5 * RC + 4) * kPitch * sizeof(float); }
+
+static int ragged_grid(int RC, int warps, int items, int* grid) {
+  DeviceInfo di;
+  int rc = device_info(di);
+  if (rc != WS_OK) return rc;
+  const void* kern = RC == 16 ? (const void*)k_ragged<16> : (const void*)k_ragged<32>;
+  const size_t smem = ragged_smem(RC, warps);
+  if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+    return set_error(WS_ECUDA, "ragged: cudaFuncSetAttribute");
+  int occ = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, warps * 32, smem) != cudaSuccess || occ < 1)
+    return set_error(WS_ECUDA, "ragged: occupancy query");
+  const int max_warps = di.sm_count * occ * warps;
+  const int need = (items + warps - 1) / warps;
+  *grid = std::min(di.sm_count * occ, std::max(1, need));
+  (void)max_warps;
+  return WS_OK;
+}
+
+static int ragged_launch(ws_plan* pl, const void* x, const void* w, const void* lam, void* z, uint8_t* status,
+                         int band, cudaStream_t st) {
+  RaggedArgs a;
+  memset(&a, 0, sizeof(a));
+  a.off = pl->rg.offsets;
+  a.order = pl->d_order;
+  a.item_d = pl->d_item_d;
+  a.item_nch = pl->RC == 16 ? pl->d_nch16 : pl->d_nch32;
+  a.n_items = pl->n_items;
+  a.N = pl->N;
+  a.B = pl->rg.n_bands;
+  a.band = band;
+  a.lam_scalar = pl->rg.lam_mode == WS_LAM_SCALAR;
+  a.x = (const float*)x;
+  a.w = (const float*)w;
+  a.lam = (const float*)lam;
+  a.z = (float*)z;
+  a.status = status;
+  a.ckpt = pl->d_ckpt;
+  a.max_nch = pl->RC == 16 ? pl->max_nch16 : pl->max_nch32;
+  a.counter = pl->d_counter + band;
+  a.err = pl->d_err;
+  const size_t smem = ragged_smem(pl->RC, pl->warps);
+  if (cudaMemsetAsync(a.counter, 0, sizeof(int), st) != cudaSuccess) return set_error(WS_ECUDA, "ragged: memset");
+  if (pl->RC == 16)
+    k_ragged<16><<<pl->grid, pl->warps * 32, smem, st>>>(a);
+  else
+    k_ragged<32><<<pl->grid, pl->warps * 32, smem, st>>>(a);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return set_error(WS_ECUDA, "ragged kernel launch: %s", cudaGetErrorString(e));
+  return WS_OK;
+}
+
+static int ragged_config(ws_plan* pl, int RC, int warps) {
+  pl->RC = RC;
+  pl->warps = warps;
+  int rc = ragged_grid(RC, warps, pl->n_items, &pl->grid);
+  if (rc != WS_OK) return rc;
+  const size_t need = (size_t)pl->grid * warps * (RC == 16 ? pl->max_nch16 : pl->max_nch32) * kFieldsMax * 32 * 4;
+  if (need > pl->ckpt_bytes) {
+    if (pl->d_ckpt) cudaFree(pl->d_ckpt);
+    pl->d_ckpt = nullptr;
+    if (cudaMalloc(&pl->d_ckpt, need) != cudaSuccess) return set_error(WS_ECUDA, "ragged: checkpoint allocation");
+    pl->ckpt_bytes = need;
+  }
+  return WS_OK;
+}
+
+extern "C" int ws_plan_create(const ws_ragged* rg, ws_plan** out, void* stream) {
+  if (out == nullptr || rg == nullptr) return set_error(WS_EINVAL, "plan: NULL argument");
+  *out = nullptr;
+  if (rg->n_series < 0 || rg->n_series > 0x7fffffffLL) return set_error(WS_EINVAL, "plan: n_series out of range");
+  if (rg->dtype != WS_F32) return set_error(WS_EUNSUPPORTED, "ragged path: FP32 only");
+  if (rg->n_bands < 1) return set_error(WS_EINVAL, "plan: n_bands must be >= 1");
+  if (rg->lam_mode != WS_LAM_PER_DAY && rg->lam_mode != WS_LAM_SCALAR) return set_error(WS_EINVAL, "plan: lam_mode");
+  if (rg->offsets == nullptr) return set_error(WS_EINVAL, "plan: offsets is NULL");
+  if (rg->d_per_series == nullptr && (rg->d_uniform < 1 || rg->d_uniform > 4))
+    return set_error(WS_EINVAL, "plan: d_uniform must be 1..4 when d_per_series is NULL");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const int n = (int)rg->n_series;
+  std::vector<int64_t> off(n + 1);
+  std::vector<int8_t> dd(n, (int8_t)rg->d_uniform);
+  if (cudaMemcpyAsync(off.data(), rg->offsets, sizeof(int64_t) * (n + 1), cudaMemcpyDeviceToHost, st) != cudaSuccess)
+    return set_error(WS_ECUDA, "plan: reading offsets");
+  if (rg->d_per_series && n > 0 &&
+      cudaMemcpyAsync(dd.data(), rg->d_per_series, n, cudaMemcpyDeviceToHost, st) != cudaSuccess)
+    return set_error(WS_ECUDA, "plan: reading orders");
+  if (cudaStreamSynchronize(st) != cudaSuccess) return set_error(WS_ECUDA, "plan: synchronise");
+  if (off[0] != 0) return set_error(WS_EINVAL, "plan: offsets[0] must be 0");
+  for (int i = 0; i < n; ++i) {
+    if (off[i + 1] < off[i]) return set_error(WS_EINVAL, "plan: offsets not non-decreasing at %d", i);
+    if (off[i + 1] - off[i] > 0x7fffffff) return set_error(WS_EINVAL, "plan: series %d too long", i);
+    if (dd[i] < 1 || dd[i] > 4) return set_error(WS_EINVAL, "plan: order of series %d is %d (1..4)", i, (int)dd[i]);
+  }
+  // sort by (order, length descending); cut into items of 32
+  std::vector<int> idx(n);
+  std::iota(idx.begin(), idx.end(), 0);
+  std::stable_sort(idx.begin(), idx.end(), [&](int a, int b) {
+    if (dd[a] != dd[b]) return dd[a] < dd[b];
+    return off[a + 1] - off[a] > off[b + 1] - off[b];
+  });
+  struct Item {
+    int first, count, d;
+    int64_t tmax;
+  };
+  std::vector<Item> items;
+  for (int i = 0; i < n;) {
+    int j = i;
+    while (j < n && j - i < 32 && dd[idx[j]] == dd[idx[i]]) ++j;
+    items.push_back({i, j - i, dd[idx[i]], off[idx[i] + 1] - off[idx[i]]});
+    i = j;
+  }
+  std::stable_sort(items.begin(), items.end(), [](const Item& a, const Item& b) { return a.tmax > b.tmax; });
+  ws_plan* pl = new ws_plan();
+  pl->rg = *rg;
+  pl->n_items = (int)items.size();
+  pl->N = off[n];
+  std::vector<int32_t> order((size_t)pl->n_items * 32, -1), n16(pl->n_items), n32(pl->n_items);
+  std::vector<int8_t> idd(pl->n_items);
+  for (int k = 0; k < pl->n_items; ++k) {
+    for (int l = 0; l < items[k].count; ++l) order[(size_t)k * 32 + l] = idx[items[k].first + l];
+    idd[k] = (int8_t)items[k].d;
+    n16[k] = (int32_t)((items[k].tmax + 15) / 16);
+    n32[k] = (int32_t)((items[k].tmax + 31) / 32);
+    pl->max_nch16 = std::max(pl->max_nch16, n16[k]);
+    pl->max_nch32 = std::max(pl->max_nch32, n32[k]);
+  }
+  const size_t ni = std::max(1, pl->n_items);
+  bool okm = cudaMalloc(&pl->d_order, ni * 32 * 4) == cudaSuccess && cudaMalloc(&pl->d_item_d, ni) == cudaSuccess &&
+             cudaMalloc(&pl->d_nch16, ni * 4) == cudaSuccess && cudaMalloc(&pl->d_nch32, ni * 4) == cudaSuccess &&
+             cudaMalloc(&pl->d_counter, sizeof(int) * rg->n_bands) == cudaSuccess &&
+             cudaMalloc(&pl->d_err, 4) == cudaSuccess;
+  if (!okm) {
+    ws_plan_destroy(pl);
+    return set_error(WS_ECUDA, "plan: device allocation");
+  }
+  if (pl->n_items > 0) {
+    cudaMemcpy(pl->d_order, order.data(), order.size() * 4, cudaMemcpyHostToDevice);
+    cudaMemcpy(pl->d_item_d, idd.data(), idd.size(), cudaMemcpyHostToDevice);
+    cudaMemcpy(pl->d_nch16, n16.data(), n16.size() * 4, cudaMemcpyHostToDevice);
+    cudaMemcpy(pl->d_nch32, n32.data(), n32.size() * 4, cudaMemcpyHostToDevice);
+  }
+  cudaMemset(pl->d_err, 0, 4);
+  int rc = ragged_config(pl, 16, 8);
+  if (rc != WS_OK) {
+    ws_plan_destroy(pl);
+    return rc;
+  }
+  *out = pl;
+  return WS_OK;
+}
+
+// Autotuner: time every (chunk, warps per CTA) candidate on the plan's own data, keep the fastest.
+static int ragged_autotune(ws_plan* pl, const void* x, const void* w, const void* lam, void* z, cudaStream_t st) {
+  const int cands[][2] = {{16, 4}, {16, 8}, {32, 4}, {32, 8}};
+  float best = 1e30f;
+  int bi = 1;
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  for (int c = 0; c < 4; ++c) {
+    int rc = ragged_config(pl, cands[c][0], cands[c][1]);
+    if (rc != WS_OK) continue;
+    if ((rc = ragged_launch(pl, x, w, lam, z, nullptr, 0, st)) != WS_OK) return rc;  // warm-up
+    cudaEventRecord(e0, st);
+    if ((rc = ragged_launch(pl, x, w, lam, z, nullptr, 0, st)) != WS_OK) return rc;
+    cudaEventRecord(e1, st);
+    cudaEventSynchronize(e1);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (ms < best) {
+      best = ms;
+      bi = c;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  pl->tuned = true;
+  pl->tuned_ms = best;
+  return ragged_config(pl, cands[bi][0], cands[bi][1]);
+}
+
+extern "C" int ws_plan_execute(ws_plan* pl, const void* x, const void* w, const void* lam, void* z, uint8_t* status,
+                               uint32_t flags, void* stream) {
+  if (pl == nullptr) return set_error(WS_EINVAL, "plan is NULL");
+  if (flags & ~(WS_PLAN_AUTOTUNE | WS_PLAN_GRAPH)) return set_error(WS_EINVAL, "unknown flags 0x%x", flags);
+  if (pl->n_items == 0) return WS_OK;
+  if (!x || !w || !lam || !z) return set_error(WS_EINVAL, "x, w, lam and z must be non-NULL");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  int rc;
+  if ((flags & WS_PLAN_AUTOTUNE) && !pl->tuned && (rc = ragged_autotune(pl, x, w, lam, z, st)) != WS_OK) return rc;
+  if (!(flags & WS_PLAN_GRAPH) || pl->rg.n_bands > 1) {
+    for (int b = 0; b < pl->rg.n_bands; ++b)
+      if ((rc = ragged_launch(pl, x, w, lam, z, status, b, st)) != WS_OK) return rc;
+    return WS_OK;
+  }
+  // CUDA graph: captured once per configuration, kernel arguments updated on each replay
+  if (pl->exec == nullptr || pl->graph_rc != pl->RC || pl->graph_warps != pl->warps) {
+    if (pl->exec) cudaGraphExecDestroy(pl->exec);
+    if (pl->graph) cudaGraphDestroy(pl->graph);
+    pl->exec = nullptr;
+    pl->graph = nullptr;
+    cudaStream_t cs;
+    if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) return set_error(WS_ECUDA, "graph stream");
+    if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+      cudaStreamDestroy(cs);
+      return set_error(WS_ECUDA, "graph capture");
+    }
+    rc = ragged_launch(pl, x, w, lam, z, status, 0, cs);
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamEndCapture(cs, &g);
+    cudaStreamDestroy(cs);
+    if (rc != WS_OK || e != cudaSuccess) return set_error(WS_ECUDA, "graph capture failed");
+    if (cudaGraphInstantiate(&pl->exec, g, 0) != cudaSuccess) {
+      cudaGraphDestroy(g);
+      return set_error(WS_ECUDA, "graph instantiate");
+    }
+    pl->graph = g;
+    pl->graph_rc = pl->RC;
+    pl->graph_warps = pl->warps;
+    size_t nn = 0;
+    cudaGraphGetNodes(g, nullptr, &nn);
+    std::vector<cudaGraphNode_t> nodes(nn);
+    cudaGraphGetNodes(g, nodes.data(), &nn);
+    pl->knode = nullptr;
+    for (auto nd : nodes) {
+      cudaGraphNodeType t;
+      cudaGraphNodeGetType(nd, &t);
+      if (t == cudaGraphNodeTypeKernel) pl->knode = nd;
+    }
+  } else if (pl->knode != nullptr) {
+    cudaKernelNodeParams kp;
+    if (cudaGraphKernelNodeGetParams(pl->knode, &kp) != cudaSuccess) return set_error(WS_ECUDA, "graph params");
+    RaggedArgs* a = static_cast<RaggedArgs*>(kp.kernelParams[0]);
+    RaggedArgs na = *a;
+    na.x = (const float*)x;
+    na.w = (const float*)w;
+    na.lam = (const float*)lam;
+    na.z = (float*)z;
+    na.status = status;
+    void* args[1] = {&na};
+    kp.kernelParams = args;
+    if (cudaGraphExecKernelNodeSetParams(pl->exec, pl->knode, &kp) != cudaSuccess)
+      return set_error(WS_ECUDA, "graph update");
+  }
+  if (cudaGraphLaunch(pl->exec, st) != cudaSuccess) return set_error(WS_ECUDA, "graph launch");
+  return WS_OK;
+}
+
+extern "C" int ws_plan_info(const ws_plan* pl, ws_plan_stats* out) {
+  if (pl == nullptr || out == nullptr) return set_error(WS_EINVAL, "NULL argument");
+  out->n_items = pl->n_items;
+  out->chunk_days = pl->RC;
+  out->warps_per_cta = pl->warps;
+  out->grid = pl->grid;
+  out->tuned = pl->tuned ? 1 : 0;
+  out->tuned_ms = pl->tuned_ms;
+  out->graph = pl->exec != nullptr ? 1 : 0;
+  return WS_OK;
+}
+
+extern "C" void ws_plan_destroy(ws_plan* pl) {
+  if (pl == nullptr) return;
+  if (pl->exec) cudaGraphExecDestroy(pl->exec);
+  if (pl->graph) cudaGraphDestroy(pl->graph);
+  cudaFree(pl->d_order);
+  cudaFree(pl->d_item_d);
+  cudaFree(pl->d_nch16);
+  cudaFree(pl->d_nch32);
+  cudaFree(pl->d_counter);
+  cudaFree(pl->d_err);
+  cudaFree(pl->d_ckpt);
+  delete pl;
+}

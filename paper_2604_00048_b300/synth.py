@@ -264,27 +264,28 @@ def generate_lambda(rc: Recipe, n_series: int, series0: int = 0, device="cpu",
     return lam
 
 
-def ragged_layout(rc: Recipe, n_series: int, device="cpu"):
-    """Lengths T_i ~ U{120..3288}, orders d_i in {1,2,3} in equal thirds assigned
-    through a shuffled index, and int64 offsets (n_series + 1)."""
+def ragged_layout(rc: Recipe, n_series: int, device="cpu", t_range=RAGGED_T_RANGE, orders=(1, 2, 3)):
+    """Lengths T_i ~ U{t_range}, orders d_i from `orders` in equal shares assigned through
+    a shuffled index, and int64 offsets (n_series + 1)."""
     dev = torch.device(device)
     i = torch.arange(n_series, device=dev, dtype=torch.int64)
-    lo, hi = RAGGED_T_RANGE
+    lo, hi = t_range
     lengths = lo + (hash_u32(rc.seed, S_LEN, i) % (hi - lo + 1))
     perm_key = hash_u32(rc.seed, S_ORDER, i)
     rank = torch.empty_like(i)
     rank[torch.argsort(perm_key * n_series + i)] = i
-    order = (1 + rank % 3).to(torch.int8)
+    ords = torch.tensor(list(orders), device=dev, dtype=torch.int8)
+    order = ords[rank % len(orders)]
     offsets = torch.zeros(n_series + 1, device=dev, dtype=torch.int64)
     offsets[1:] = torch.cumsum(lengths, 0)
     return lengths, order, offsets
 
 
 def generate_ragged(rc: Recipe, n_series: int, device="cpu", dtype=torch.float32,
-                    chunk_elems: int = 1 << 26):
+                    chunk_elems: int = 1 << 26, t_range=RAGGED_T_RANGE, orders=(1, 2, 3)):
     """Packed ragged batch: series i occupies [off[i], off[i+1]) of x, w, lam."""
     dev = torch.device(device)
-    lengths, order, offsets = ragged_layout(rc, n_series, dev)
+    lengths, order, offsets = ragged_layout(rc, n_series, dev, t_range, orders)
     N = int(offsets[-1].item())
     x = torch.empty(N, dtype=dtype, device=dev)
     w = torch.empty(N, dtype=dtype, device=dev)

@@ -68,6 +68,29 @@ _lib.ws_version.restype = ctypes.c_char_p
 _lib.ws_version.argtypes = []
 
 
+class Ragged(ctypes.Structure):
+    _fields_ = [("n_series", ctypes.c_int64), ("offsets", ctypes.c_void_p), ("d_per_series", ctypes.c_void_p),
+                ("d_uniform", ctypes.c_int32), ("n_bands", ctypes.c_int32), ("dtype", ctypes.c_int32),
+                ("lam_mode", ctypes.c_int32)]
+
+
+class PlanStats(ctypes.Structure):
+    _fields_ = [("n_items", ctypes.c_int32), ("chunk_days", ctypes.c_int32), ("warps_per_cta", ctypes.c_int32),
+                ("grid", ctypes.c_int32), ("tuned", ctypes.c_int32), ("graph", ctypes.c_int32),
+                ("tuned_ms", ctypes.c_float)]
+
+
+PLAN_AUTOTUNE, PLAN_GRAPH = 0x1, 0x2
+_lib.ws_plan_create.restype = ctypes.c_int
+_lib.ws_plan_create.argtypes = [ctypes.POINTER(Ragged), ctypes.POINTER(ctypes.c_void_p), ctypes.c_void_p]
+_lib.ws_plan_execute.restype = ctypes.c_int
+_lib.ws_plan_execute.argtypes = [ctypes.c_void_p] + [ctypes.c_void_p] * 5 + [ctypes.c_uint32, ctypes.c_void_p]
+_lib.ws_plan_info.restype = ctypes.c_int
+_lib.ws_plan_info.argtypes = [ctypes.c_void_p, ctypes.POINTER(PlanStats)]
+_lib.ws_plan_destroy.restype = None
+_lib.ws_plan_destroy.argtypes = [ctypes.c_void_p]
+
+
 class WSError(RuntimeError):
     def __init__(self, code: int, msg: str):
         super().__init__(f"ws error {code}: {msg}")
@@ -262,3 +285,45 @@ def sync_status(device=None, stream=None):
         torch.cuda.synchronize(dev)
         return
     _check(_lib.ws_sync_status(_ptr(buf), buf.numel(), _stream_ptr(stream)))
+
+
+class RaggedPlan:
+    """Plan for a packed ragged batch (ws_plan_*): offsets [n+1] int64 and optional orders
+    [n] int8 on the device; x/w/lam/z flat FP32 arrays (band b of series i at
+    b*N + offsets[i] + t)."""
+
+    def __init__(self, offsets: torch.Tensor, order=None, d: int = 2, n_bands: int = 1, lam_scalar: bool = False,
+                 stream=None):
+        if offsets.dtype != torch.int64 or not offsets.is_cuda:
+            raise ValueError("offsets must be a CUDA int64 tensor")
+        if order is not None and (order.dtype != torch.int8 or not order.is_cuda):
+            raise ValueError("order must be a CUDA int8 tensor")
+        self.offsets, self.order = offsets, order
+        self.n = offsets.numel() - 1
+        self.n_bands = n_bands
+        self._rg = Ragged(self.n, offsets.data_ptr(), None if order is None else order.data_ptr(), int(d), n_bands,
+                          F32, LAM_SCALAR if lam_scalar else LAM_PER_DAY)
+        h = ctypes.c_void_p()
+        _check(_lib.ws_plan_create(ctypes.byref(self._rg), ctypes.byref(h), _stream_ptr(stream)))
+        self._h = h
+
+    def execute(self, x, w, lam, z=None, status=None, autotune: bool = False, graph: bool = False, stream=None):
+        if z is None:
+            z = torch.empty_like(x)
+        if status is None:
+            status = torch.empty(self.n, dtype=torch.uint8, device=x.device)
+        flags = (PLAN_AUTOTUNE if autotune else 0) | (PLAN_GRAPH if graph else 0)
+        _check(_lib.ws_plan_execute(self._h, _ptr(x), _ptr(w), _ptr(lam), _ptr(z), _ptr(status), flags,
+                                    _stream_ptr(stream)))
+        return z, status
+
+    def info(self) -> dict:
+        st = PlanStats()
+        _check(_lib.ws_plan_info(self._h, ctypes.byref(st)))
+        return {k: getattr(st, k) for k, _ in PlanStats._fields_}
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value:
+            _lib.ws_plan_destroy(h)
+            self._h = None
