@@ -43,6 +43,7 @@ def parse_args():
     ap.add_argument("--pixels", type=int, default=262144, help="series per rank (262144 = the full tile)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-ragged", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU work of the oracle baseline")
     return ap.parse_args()
 
@@ -163,6 +164,45 @@ def cpu_oracle_rate(x, w, lam, gz, d, target_s, with_bwd=True):
         dt = time.perf_counter() - t0
         n = n2
     return n / dt, cores, f"{n} of the tile's series (all {x.shape[0]} days, {x.shape[1]} bands), FP64"
+
+
+def ragged_measure(dev, steps):
+    """The ragged batch: 1,048,576 series, T ~ U{120..3288}, d in {1,2,3}, one band, FP32,
+    one persistent launch replayed from a CUDA graph with the autotuned configuration."""
+    import torch
+
+    from paper_2604_00048_b300 import synth, ws
+
+    rc = synth.RECIPES["ragged"]
+    n = 1 << 20
+    out = synth.generate_ragged(rc, n, device=dev)
+    x, w, lam = out["x"], out["w"], out["lam"]
+    N = x.numel()
+    plan = ws.RaggedPlan(out["offsets"], out["order"])
+    z = torch.empty_like(x)
+    st = torch.empty(n, dtype=torch.uint8, device=dev)
+    plan.execute(x, w, lam, z=z, status=st, autotune=True, graph=True)
+    for _ in range(2):
+        plan.execute(x, w, lam, z=z, status=st, graph=True)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        plan.execute(x, w, lam, z=z, status=st, graph=True)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    hbm, _ = peaks()
+    alg = 16.0 * N  # read x, w, lambda; write z (FP32)
+    info = plan.info()
+    res = {"workload": "ragged: 1,048,576 series, T~U{120..3288}, d in {1,2,3}, 1 band, FP32",
+           "series_per_s": n / (ms / 1e3), "ms": ms, "pixel_days": N,
+           "achieved_alg_gbs": alg / (ms / 1e3) / 1e9, "frac_of_measured_hbm": alg / (ms / 1e3) / 1e9 / hbm,
+           "plan": {k: info[k] for k in ("n_items", "chunk_days", "warps_per_cta", "grid", "graph")},
+           "series_with_status": int((st != 0).sum().item())}
+    del out, x, w, lam, z, plan
+    torch.cuda.empty_cache()
+    return res
 
 
 def run_reference(args):
@@ -353,6 +393,14 @@ def run_ours(args):
         cpu = {"value": rate, "unit": "series/s", "cores": cores, "kind": "oracle", "sample": sample}
 
     launches_per_step = 3 + (1 if has_bwd else 0)
+    ragged = None
+    if not args.no_ragged:
+        del x, w, lam, z, status
+        if has_bwd:
+            del gz, gx, glam
+        ws._ws_cache.clear()
+        torch.cuda.empty_cache()
+        ragged = ragged_measure(dev, max(3, args.steps))
     line = {"metric": METRIC, "value": value, "unit": "series/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
@@ -364,7 +412,7 @@ def run_ours(args):
             "fwd_series_per_s": P * world / ((fwd_ms + ref_ms) / 1e3),
             "fwd_unrefined_series_per_s": P * world / (fwd_ms / 1e3),
             "smooth_ms": fwd_ms, "refine_ms": ref_ms, "adjoint_ms": bwd_ms,
-            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
+            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "ragged": ragged,
             "gpu_launches": launches_per_step * args.steps, "clocks": ck,
             "series_with_status": bad}
     if rank == 0:
