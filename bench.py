@@ -182,22 +182,30 @@ def ragged_measure(dev, steps):
     z = torch.empty_like(x)
     st = torch.empty(n, dtype=torch.uint8, device=dev)
     plan.execute(x, w, lam, z=z, status=st, autotune=True, graph=True)
-    for _ in range(2):
-        plan.execute(x, w, lam, z=z, status=st, graph=True)
-    torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record()
-    for _ in range(steps):
-        plan.execute(x, w, lam, z=z, status=st, graph=True)
-    e1.record()
-    torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1) / steps
+
+    def timed(refine):
+        for _ in range(2):
+            plan.execute(x, w, lam, z=z, status=st, graph=True, refine=refine)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(steps):
+            plan.execute(x, w, lam, z=z, status=st, graph=True, refine=refine)
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / steps
+
+    ms_solve = timed(False)
+    ms = timed(True)  # the accuracy-gated result: refinement + FP64 re-solve of unsettled series
     hbm, _ = peaks()
-    alg = 16.0 * N  # read x, w, lambda; write z (FP32)
+    alg = 16.0 * N  # read x, w, lambda; write z (FP32), once
     info = plan.info()
-    res = {"workload": "ragged: 1,048,576 series, T~U{120..3288}, d in {1,2,3}, 1 band, FP32",
+    res = {"workload": "ragged: 1,048,576 series, T~U{120..3288}, d in {1,2,3}, 1 band, FP32 + refinement",
            "series_per_s": n / (ms / 1e3), "ms": ms, "pixel_days": N,
-           "achieved_alg_gbs": alg / (ms / 1e3) / 1e9, "frac_of_measured_hbm": alg / (ms / 1e3) / 1e9 / hbm,
+           "solve_only_ms": ms_solve, "solve_only_series_per_s": n / (ms_solve / 1e3),
+           "solve_only_alg_gbs": alg / (ms_solve / 1e3) / 1e9,
+           "frac_of_measured_hbm_solve_only": alg / (ms_solve / 1e3) / 1e9 / hbm,
+           "hp_resolved_series": info["hp_series"],
            "plan": {k: info[k] for k in ("n_items", "chunk_days", "warps_per_cta", "grid", "graph")},
            "series_with_status": int((st != 0).sum().item())}
     del out, x, w, lam, z, plan

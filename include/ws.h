@@ -192,15 +192,25 @@ typedef struct ws_plan_stats {
   int32_t tuned;          /* the autotuner has run */
   int32_t graph;          /* a CUDA graph is instantiated */
   float tuned_ms;         /* best time the autotuner measured */
+  int32_t hp_series;      /* series of band 0 re-solved in double-float by the last refined
+                             execute (reading it synchronises the device) */
 } ws_plan_stats;
 
 #define WS_PLAN_AUTOTUNE 0x1u  /* ws_plan_execute: time the (chunk, warps/CTA) candidates once */
 #define WS_PLAN_GRAPH 0x2u     /* ws_plan_execute: replay a captured CUDA graph (one band) */
+#define WS_PLAN_REFINE 0x4u    /* ws_plan_execute: iterative refinement (the paper
+                                  fixes no precision): up to two FP32 steps, r = W x - Omega z with a
+                                  double-word combination, z += Omega^{-1} r, until the
+                                  correction of a series is <= 1e-5 max|z|; series still
+                                  unsettled are solved again in double-float arithmetic
+                                  (hi + lo FP32 pairs, about 48 bits). On first use the plan
+                                  allocates N floats, 10 bytes per series and about
+                                  0.76 GB of checkpoints at T = 3288. */
 
 int ws_plan_create(const ws_ragged* rg, ws_plan** out, void* stream);
 
 /* z = Omega^{-1} W x for every series of the plan (Eq. 3 with each series' own T_i and d).
- * status: optional per-series codes. flags: WS_PLAN_AUTOTUNE and/or WS_PLAN_GRAPH. With
+ * status: optional per-series codes. flags: WS_PLAN_AUTOTUNE, WS_PLAN_GRAPH, WS_PLAN_REFINE. With
  * WS_PLAN_AUTOTUNE the first call times the candidates (running the solve several times
  * on these buffers) and keeps the fastest; with WS_PLAN_GRAPH the launch is captured once
  * and later calls update its arguments and replay it. */

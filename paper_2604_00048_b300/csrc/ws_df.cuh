@@ -44,4 +44,59 @@ __device__ __forceinline__ DW<F> dw_scale(DW<F> a, F c) {
   return {h, p.lo - (h - p.hi)};
 }
 
+// Double-float number type for the ragged path's high-precision re-solve: normalised
+// hi + lo with |lo| <= ulp(hi)/2, about 48 significant bits, from FP32 operations only
+// (B300 issues FP64 at a small fraction of its FP32 rate). Addition is the accurate
+// two-TwoSum form and multiplication the FMA form analysed by Joldes, Muller and Popescu
+// (ACM TOMS 2017: relative errors about 3u^2 and 5u^2 with u = 2^-24); the reciprocal
+// square root is one Newton step in double-float from the rounded FP32 value.
+__device__ __forceinline__ DW<float> fast_two_sum(float a, float b) {
+  const float s = a + b;
+  return {s, b - (s - a)};
+}
+
+struct dwf {
+  float hi, lo;
+  __device__ __forceinline__ dwf() : hi(0.f), lo(0.f) {}
+  __device__ __forceinline__ dwf(float h, float l) : hi(h), lo(l) {}
+  __device__ __forceinline__ dwf(float v) : hi(v), lo(0.f) {}
+  __device__ __forceinline__ explicit dwf(int v) : hi((float)v), lo(0.f) {}
+  __device__ __forceinline__ float to_float() const { return hi + lo; }
+};
+
+__device__ __forceinline__ dwf operator-(dwf a) { return {-a.hi, -a.lo}; }
+
+__device__ __forceinline__ dwf operator+(dwf a, dwf b) {
+  const DW<float> s = two_sum(a.hi, b.hi);
+  const DW<float> t = two_sum(a.lo, b.lo);
+  DW<float> v = fast_two_sum(s.hi, s.lo + t.hi);
+  v = fast_two_sum(v.hi, v.lo + t.lo);
+  return {v.hi, v.lo};
+}
+
+__device__ __forceinline__ dwf operator-(dwf a, dwf b) { return a + (-b); }
+
+__device__ __forceinline__ dwf operator*(dwf a, dwf b) {
+  DW<float> p = two_prod(a.hi, b.hi);
+  const float t = fmaf(a.lo, b.hi, a.hi * b.lo);
+  p = fast_two_sum(p.hi, p.lo + t);
+  return {p.hi, p.lo};
+}
+
+__device__ __forceinline__ bool operator>(dwf a, dwf b) { return a.hi > b.hi || (a.hi == b.hi && a.lo > b.lo); }
+
+// fma overloads in this namespace (a declaration here hides the global ones)
+__device__ __forceinline__ dwf fma(dwf a, dwf b, dwf c) { return a * b + c; }
+__device__ __forceinline__ float fma(float a, float b, float c) { return fmaf(a, b, c); }
+__device__ __forceinline__ double fma(double a, double b, double c) { return ::fma(a, b, c); }
+
+// 1/sqrt(x) for x > 0: r0 = 1/sqrtf(x.hi) (IEEE-rounded FP32), then r = r0 + r0 (1 - x r0^2) / 2.
+__device__ __forceinline__ dwf rsqrt_(dwf x) {
+  const float r0 = 1.0f / sqrtf(x.hi);
+  const dwf e = dwf(1.0f) - x * dwf(two_prod(r0, r0).hi, two_prod(r0, r0).lo);
+  return dwf(r0) + dwf(0.5f * r0) * e;
+}
+
+__device__ __forceinline__ dwf sqrt_(dwf x) { return x.hi > 0.f ? x * rsqrt_(x) : dwf(0.f); }
+
 }  // namespace ws

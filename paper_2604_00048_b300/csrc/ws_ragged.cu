@@ -20,6 +20,7 @@
 #include <vector>
 
 #include "ws_internal.h"
+#include "ws_df.cuh"
 #include "ws_ptx.cuh"
 #include "ws_sweep.cuh"
 
@@ -45,6 +46,17 @@ struct RaggedArgs {
   int max_nch;
   int* counter;
   unsigned* err;
+  // refinement (plan-owned; NULL without WS_PLAN_REFINE)
+  float* resid;           // r = W x - Omega z, same packing as x
+  uint8_t* active;        // per item: 1 while some series of the item has not settled
+  uint8_t* conv;          // per series: 1 once the last correction was below tau * max|z|
+  float* zmax;            // per series: max |z| of the unrefined solution
+  int32_t* list64;        // series re-solved in double-float
+  int* count64;
+  double* ck64;           // double-float checkpoints (8 bytes each), kFieldsMax * max_nch64 per thread
+  const int8_t* d_of;     // per series order
+  int max_nch64;
+  float tau;
 };
 
 constexpr int kFieldsMax = 4 * 5 + 4;  // d(d+1) + d for d <= 4, one band
@@ -55,8 +67,9 @@ struct RaggedSmem {
   static constexpr int rowX = 0, rowW = RC, rowL = 2 * RC + 4, rowE = 3 * RC + 4, rows = 5 * RC + 4;
 };
 
-// One item (32 series of order D) on one warp.
-template <int D, int RC>
+// One item (32 series of order D) on one warp. RAW: the right-hand side is taken as given
+// (the refinement residual) and the solution is added to z (z0 + correction).
+template <int D, int RC, int MODE>
 __device__ void ragged_item(const RaggedArgs& a, int item, float* sm, float* ck, int lane) {
   using L = RaggedSmem<RC>;
   using SW = Sweep<float, D, 1>;
@@ -67,7 +80,8 @@ __device__ void ragged_item(const RaggedArgs& a, int item, float* sm, float* ck,
   const int64_t off = live ? a.off[sid] : 0;
   const int T = live ? (int)(a.off[sid + 1] - off) : 0;
   const int nch = a.item_nch[item];
-  const float* xb = a.x + (size_t)a.band * a.N;
+  if (MODE == MODE_RAW && !a.active[item]) return;  // every series of the item has settled
+  const float* xb = MODE == MODE_RAW ? a.resid : a.x + (size_t)a.band * a.N;
   float* zb = a.z + (size_t)a.band * a.N;
   auto stg = [&](int st) -> float* { return sm + (size_t)st * L::rows * kPitch; };
   if (nch == 0) {  // every series of the item is empty
@@ -124,7 +138,8 @@ __device__ void ragged_item(const RaggedArgs& a, int item, float* sm, float* ck,
       bad |= !(wi >= 0.f) || !isfinite(wi);
       npos += wi > 0.f;
       if (has_row) bad |= !(li > 0.f) || !isfinite(li);
-      float bv[1] = {wi > 0.f ? wi * S[(L::rowX + k) * kPitch + lane] : 0.f};
+      float bv[1] = {MODE == MODE_RAW ? S[(L::rowX + k) * kPitch + lane]
+                                      : (wi > 0.f ? wi * S[(L::rowX + k) * kPitch + lane] : 0.f)};
       float rho[D], yh[1], invD;
       s.factor_step(has_row, li, wa, rho, invD);
       s.subst_step(rho, invD, bv, yh);
@@ -138,7 +153,7 @@ __device__ void ragged_item(const RaggedArgs& a, int item, float* sm, float* ck,
   float zc[D];
 #pragma unroll
   for (int j = 0; j < D; ++j) zc[j] = 0.f;
-  float nanacc = 0.f;
+  float nanacc = 0.f, amax = 0.f;
   for (int c = nch - 1; c >= 0; --c) {
     const int st = c & 1;
     if (c < nch - 2) {
@@ -156,7 +171,8 @@ __device__ void ragged_item(const RaggedArgs& a, int item, float* sm, float* ck,
       const float wa = S[(L::rowW + k + D) * kPitch + lane];
       const float li = a.lam_scalar ? ls : S[(L::rowL + k) * kPitch + lane];
       const bool has_row = i < T - D;
-      float bv[1] = {wi > 0.f ? wi * S[(L::rowX + k) * kPitch + lane] : 0.f};
+      float bv[1] = {MODE == MODE_RAW ? S[(L::rowX + k) * kPitch + lane]
+                                      : (wi > 0.f ? wi * S[(L::rowX + k) * kPitch + lane] : 0.f)};
       float rho[D], yh[1], invD;
       s.factor_step(has_row, li, wa, rho, invD);
       s.subst_step(rho, invD, bv, yh);
@@ -181,6 +197,7 @@ __device__ void ragged_item(const RaggedArgs& a, int item, float* sm, float* ck,
       zc[0] = acc;
       const float out = okser ? acc : 0.f;
       nanacc = fmaf(out, 0.f, nanacc);
+      amax = fmaxf(amax, fabsf(out));
       S[(L::rowX + k) * kPitch + lane] = out;
     }
     __syncwarp();
@@ -190,12 +207,25 @@ __device__ void ragged_item(const RaggedArgs& a, int item, float* sm, float* ck,
       const int64_t os = __shfl_sync(0xffffffffu, off, s2);
       const int Ts = __shfl_sync(0xffffffffu, T, s2);
       for (int j = lane; j < RC; j += 32)
-        if (t0 + j < Ts) zb[os + t0 + j] = S[(L::rowX + j) * kPitch + s2];
+        if (t0 + j < Ts) {
+          const float v = S[(L::rowX + j) * kPitch + s2];
+          if (MODE == MODE_RAW)
+            zb[os + t0 + j] += v;  // z0 + correction
+          else
+            zb[os + t0 + j] = v;
+        }
     }
     __syncwarp();
     if (c >= 2) issue(c - 2, st);
   }
-  if (live && a.status != nullptr) {
+  if (MODE == MODE_SMOOTH && live && a.zmax != nullptr) a.zmax[sid] = amax;
+  if (MODE == MODE_RAW) {
+    // a series has settled when its correction is below tau * max|z| (NaN never settles)
+    const bool settled = !live || (amax <= a.tau * a.zmax[sid]);
+    if (live) a.conv[sid] = settled ? 1 : 0;
+    if (__all_sync(0xffffffffu, settled) && lane == 0) a.active[item] = 0;
+  }
+  if (MODE == MODE_SMOOTH && live && a.status != nullptr) {
     const bool nonfin = !(nanacc == 0.f);
     if (a.band == 0)
       a.status[sid] = okser ? (nonfin ? WS_SERIES_NONFINITE : WS_SERIES_OK) : code;
@@ -204,7 +234,7 @@ __device__ void ragged_item(const RaggedArgs& a, int item, float* sm, float* ck,
   }
 }
 
-template <int RC>
+template <int RC, int MODE>
 __global__ void __launch_bounds__(256) k_ragged(const RaggedArgs a) {
   extern __shared__ __align__(16) float rsm[];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -217,11 +247,173 @@ __global__ void __launch_bounds__(256) k_ragged(const RaggedArgs a) {
     item = __shfl_sync(0xffffffffu, item, 0);
     if (item >= a.n_items) break;
     switch (a.item_d[item]) {
-      case 1: ragged_item<1, RC>(a, item, sm, ck, lane); break;
-      case 2: ragged_item<2, RC>(a, item, sm, ck, lane); break;
-      case 3: ragged_item<3, RC>(a, item, sm, ck, lane); break;
-      case 4: ragged_item<4, RC>(a, item, sm, ck, lane); break;
+      case 1: ragged_item<1, RC, MODE>(a, item, sm, ck, lane); break;
+      case 2: ragged_item<2, RC, MODE>(a, item, sm, ck, lane); break;
+      case 3: ragged_item<3, RC, MODE>(a, item, sm, ck, lane); break;
+      case 4: ragged_item<4, RC, MODE>(a, item, sm, ck, lane); break;
     }
+  }
+}
+
+// Refinement residual of a ragged batch, r = W x - Omega z0, carried in double-word
+// arithmetic from the first difference on: the series of this path reach cond(Omega) ~ 1e13
+// (unsmoothed lambda up to 1e5, d = 3, sparse weights), where a working-precision residual
+// would stall the refinement at the FP32 solution's own error. One warp per item, the lanes
+// over consecutive days of one series at a time (coalesced, no recurrence).
+template <int D>
+__device__ void ragged_resid_item(const RaggedArgs& a, int item, int lane) {
+  using DWf = DW<float>;
+  const float* xb = a.x + (size_t)a.band * a.N;
+  const float* zb = a.z + (size_t)a.band * a.N;
+  float* rb = a.resid;  // one band at a time
+  for (int s = 0; s < 32; ++s) {
+    const int sid = a.order[(size_t)item * 32 + s];
+    if (sid < 0) continue;
+    const int64_t os = a.off[sid];
+    const int T = (int)(a.off[sid + 1] - os);
+    const float ls = a.lam_scalar ? a.lam[sid] : 0.f;
+    for (int t = lane; t < T; t += 32) {
+      // q_k = lambda_k (D z0)_k for the rows k = t-D..t that touch day t
+      DWf dtq[D + 1];
+#pragma unroll
+      for (int n = 0; n <= D; ++n) {
+        const int k = t - D + n;
+        DWf q = {0.f, 0.f};
+        if (k >= 0 && k <= T - D - 1) {
+          DWf lv[D];
+#pragma unroll
+          for (int m = 0; m < D; ++m) lv[m] = two_sum(zb[os + k + m + 1], -zb[os + k + m]);  // exact
+#pragma unroll
+          for (int i = 1; i < D; ++i)
+#pragma unroll
+            for (int m = 0; m < D - i; ++m) lv[m] = dw_add(lv[m + 1], DWf{-lv[m].hi, -lv[m].lo});
+          q = dw_scale(lv[0], a.lam_scalar ? ls : a.lam[os + k]);
+        }
+        dtq[n] = q;
+      }
+#pragma unroll
+      for (int i = 0; i < D; ++i)
+#pragma unroll
+        for (int n = D; n > i; --n) dtq[n] = dw_add(dtq[n], DWf{-dtq[n - 1].hi, -dtq[n - 1].lo});
+      const DWf v = (D % 2) ? DWf{-dtq[D].hi, -dtq[D].lo} : dtq[D];
+      const float wt = a.w[os + t], xt = xb[os + t], zt = zb[os + t];
+      DWf acc = wt > 0.f ? dw_scale(two_sum(xt, -zt), wt) : DWf{0.f, 0.f};
+      acc = dw_add(acc, DWf{-v.hi, -v.lo});
+      rb[os + t] = acc.hi + acc.lo;
+    }
+  }
+}
+
+__global__ void __launch_bounds__(256) k_ragged_resid(const RaggedArgs a) {
+  const int lane = threadIdx.x & 31;
+  const int item = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (item >= a.n_items || !a.active[item]) return;
+  switch (a.item_d[item]) {
+    case 1: ragged_resid_item<1>(a, item, lane); break;
+    case 2: ragged_resid_item<2>(a, item, lane); break;
+    case 3: ragged_resid_item<3>(a, item, lane); break;
+    case 4: ragged_resid_item<4>(a, item, lane); break;
+  }
+}
+
+// Series whose FP32 refinement has not settled are listed for a double-float re-solve: one warp
+// per item, one atomic per warp, so the list keeps the items' (order, length) grouping
+// within each item and roughly across items.
+__global__ void __launch_bounds__(256) k_ragged_collect(const RaggedArgs a) {
+  const int lane = threadIdx.x & 31;
+  const int item = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (item >= a.n_items || !a.active[item]) return;
+  const int sid = a.order[(size_t)item * 32 + lane];
+  const bool need = sid >= 0 && !a.conv[sid];
+  const unsigned m = __ballot_sync(0xffffffffu, need);
+  if (m == 0) return;
+  int base = 0;
+  if (lane == 0) base = atomicAdd(a.count64, __popc(m));
+  base = __shfl_sync(0xffffffffu, base, 0);
+  if (need) a.list64[base + __popc(m & ((1u << lane) - 1u))] = sid;
+}
+
+// High-precision re-solve of one listed series by one thread: the same two-pass recurrence
+// in double-float (HP = dwf, about 48 bits) instead of FP32, inputs read directly from
+// global memory (a small share of the batch goes this way), checkpoints every kRC64 days in
+// the thread's global slot, the chunk's recomputed (yhat, rho) in local arrays. Overwrites
+// z of the series.
+constexpr int kRC64 = 64;
+using HP = dwf;
+static_assert(sizeof(HP) == sizeof(double), "checkpoint slots hold 8-byte values");
+
+template <int D>
+__device__ void ragged64_series(const RaggedArgs& a, int sid, HP* ck) {
+  using SW = Sweep<HP, D, 1>;
+  constexpr int kFF = SW::kFactorFields;
+  constexpr int kF = kFF + D;
+  const int64_t os = a.off[sid];
+  const int T = (int)(a.off[sid + 1] - os);
+  const float* xs = a.x + (size_t)a.band * a.N + os;
+  const float* ws = a.w + os;
+  const float* lsr = a.lam + (a.lam_scalar ? (int64_t)sid : os);
+  float* zs = a.z + (size_t)a.band * a.N + os;
+  auto lam_at = [&](int i) -> HP { return HP(a.lam_scalar ? lsr[0] : lsr[i]); };
+  auto w_at = [&](int i) -> HP { return HP(i < T ? ws[i] : 0.f); };
+  const HP zero(0.f);
+  SW s;
+  s.reset();
+  for (int m = 0; m < D && m < T; ++m) s.init_weight(m, w_at(m));
+  const int nch = (T + kRC64 - 1) / kRC64;
+  for (int c = 0; c < nch; ++c) {
+    s.save_factor(ck + (size_t)c * kF, 1);
+    s.save_y(ck + (size_t)c * kF + kFF, 1);
+    const int i1 = min(T, (c + 1) * kRC64);
+    for (int i = c * kRC64; i < i1; ++i) {
+      const HP wi = w_at(i);
+      HP bv[1] = {wi > zero ? wi * HP(xs[i]) : zero};
+      HP rho[D], yh[1], invD;
+      s.factor_step(i < T - D, i < T - D ? lam_at(i) : zero, w_at(i + D), rho, invD);
+      s.subst_step(rho, invD, bv, yh);
+    }
+  }
+  HP zc[D];
+#pragma unroll
+  for (int j = 0; j < D; ++j) zc[j] = zero;
+  HP yk[kRC64], rk[kRC64][D];
+  for (int c = nch - 1; c >= 0; --c) {
+    s.load_factor(ck + (size_t)c * kF, 1);
+    s.load_y(ck + (size_t)c * kF + kFF, 1);
+    const int i0 = c * kRC64, nd = min(kRC64, T - i0);
+    for (int k = 0; k < nd; ++k) {
+      const int i = i0 + k;
+      const HP wi = w_at(i);
+      HP bv[1] = {wi > zero ? wi * HP(xs[i]) : zero};
+      HP rho[D], yh[1], invD;
+      s.factor_step(i < T - D, i < T - D ? lam_at(i) : zero, w_at(i + D), rho, invD);
+      s.subst_step(rho, invD, bv, yh);
+      yk[k] = yh[0];
+#pragma unroll
+      for (int j = 0; j < D; ++j) rk[k][j] = rho[j];
+    }
+    for (int k = nd - 1; k >= 0; --k) {
+      HP acc = yk[k];
+#pragma unroll
+      for (int j = 1; j <= D; ++j) acc = fma(-rk[k][j - 1], zc[j - 1], acc);
+#pragma unroll
+      for (int j = D - 1; j > 0; --j) zc[j] = zc[j - 1];
+      zc[0] = acc;
+      zs[i0 + k] = acc.to_float();
+    }
+  }
+}
+
+__global__ void __launch_bounds__(128) k_ragged64(const RaggedArgs a) {
+  const int gt = blockIdx.x * blockDim.x + threadIdx.x;
+  HP* ck = reinterpret_cast<HP*>(a.ck64) + (size_t)gt * a.max_nch64 * kFieldsMax;
+  const int n = *a.count64;
+  for (int j = gt; j < n; j += gridDim.x * blockDim.x) {
+    const int sid = a.list64[j];
+    const int d = a.d_of[sid];
+    if (d == 1) ragged64_series<1>(a, sid, ck);
+    else if (d == 2) ragged64_series<2>(a, sid, ck);
+    else if (d == 3) ragged64_series<3>(a, sid, ck);
+    else ragged64_series<4>(a, sid, ck);
   }
 }
 
@@ -242,24 +434,41 @@ struct ws_plan {
   unsigned* d_err = nullptr;
   float* d_ckpt = nullptr;
   size_t ckpt_bytes = 0;
+  // refinement state, allocated on the first execute with WS_PLAN_REFINE
+  float* d_resid = nullptr;    // N floats (one band at a time)
+  uint8_t* d_active = nullptr; // n_items
+  uint8_t* d_conv = nullptr;   // n_series
+  float* d_zmax = nullptr;     // n_series
+  int32_t* d_list64 = nullptr; // n_series
+  int* d_count64 = nullptr;    // n_bands
+  double* d_ck64 = nullptr;
+  int8_t* d_dof = nullptr;     // n_series
+  int max_nch64 = 0, grid64 = 0;
   bool tuned = false;
   float tuned_ms = 0.f;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
-  cudaGraphNode_t knode = nullptr;
+  std::vector<cudaGraphNode_t> knodes;
   int graph_rc = 0, graph_warps = 0;
+  bool graph_refine = false;
 };
 
 static size_t ragged_smem(int RC, int warps) { return (size_t)warps * 2 * (5 * RC + 4) * kPitch * sizeof(float); }
+
+static const void* ragged_kernel(int RC, int mode) {
+  if (RC == 16) return mode == MODE_RAW ? (const void*)k_ragged<16, MODE_RAW> : (const void*)k_ragged<16, MODE_SMOOTH>;
+  return mode == MODE_RAW ? (const void*)k_ragged<32, MODE_RAW> : (const void*)k_ragged<32, MODE_SMOOTH>;
+}
 
 static int ragged_grid(int RC, int warps, int items, int* grid) {
   DeviceInfo di;
   int rc = device_info(di);
   if (rc != WS_OK) return rc;
-  const void* kern = RC == 16 ? (const void*)k_ragged<16> : (const void*)k_ragged<32>;
+  const void* kern = ragged_kernel(RC, MODE_SMOOTH);
   const size_t smem = ragged_smem(RC, warps);
-  if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
-    return set_error(WS_ECUDA, "ragged: cudaFuncSetAttribute");
+  for (int m : {MODE_SMOOTH, MODE_RAW})
+    if (cudaFuncSetAttribute(ragged_kernel(RC, m), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+      return set_error(WS_ECUDA, "ragged: cudaFuncSetAttribute");
   int occ = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, warps * 32, smem) != cudaSuccess || occ < 1)
     return set_error(WS_ECUDA, "ragged: occupancy query");
@@ -270,8 +479,25 @@ static int ragged_grid(int RC, int warps, int items, int* grid) {
   return WS_OK;
 }
 
+constexpr int kRefineSteps = 2;     // FP32 refinement steps before the double-float re-solve
+constexpr float kRefineTau = 1e-5f;  // settled: correction <= tau * max|z|
+constexpr int kHPBlocksPerSM = 4;    // double-float re-solve: 4 x 128 threads per SM (128 registers each)
+
+static void fill_refine_args(const ws_plan* pl, RaggedArgs& a) {
+  a.resid = pl->d_resid;
+  a.active = pl->d_active;
+  a.conv = pl->d_conv;
+  a.zmax = pl->d_zmax;
+  a.list64 = pl->d_list64;
+  a.count64 = pl->d_count64 + a.band;
+  a.ck64 = pl->d_ck64;
+  a.d_of = pl->d_dof;
+  a.max_nch64 = pl->max_nch64;
+  a.tau = kRefineTau;
+}
+
 static int ragged_launch(ws_plan* pl, const void* x, const void* w, const void* lam, void* z, uint8_t* status,
-                         int band, cudaStream_t st) {
+                         int band, cudaStream_t st, int mode = MODE_SMOOTH, bool refine = false) {
   RaggedArgs a;
   memset(&a, 0, sizeof(a));
   a.off = pl->rg.offsets;
@@ -292,14 +518,75 @@ static int ragged_launch(ws_plan* pl, const void* x, const void* w, const void* 
   a.max_nch = pl->RC == 16 ? pl->max_nch16 : pl->max_nch32;
   a.counter = pl->d_counter + band;
   a.err = pl->d_err;
+  if (refine) fill_refine_args(pl, a);
   const size_t smem = ragged_smem(pl->RC, pl->warps);
   if (cudaMemsetAsync(a.counter, 0, sizeof(int), st) != cudaSuccess) return set_error(WS_ECUDA, "ragged: memset");
-  if (pl->RC == 16)
-    k_ragged<16><<<pl->grid, pl->warps * 32, smem, st>>>(a);
+  if (pl->RC == 16 && mode == MODE_RAW)
+    k_ragged<16, MODE_RAW><<<pl->grid, pl->warps * 32, smem, st>>>(a);
+  else if (pl->RC == 16)
+    k_ragged<16, MODE_SMOOTH><<<pl->grid, pl->warps * 32, smem, st>>>(a);
+  else if (mode == MODE_RAW)
+    k_ragged<32, MODE_RAW><<<pl->grid, pl->warps * 32, smem, st>>>(a);
   else
-    k_ragged<32><<<pl->grid, pl->warps * 32, smem, st>>>(a);
+    k_ragged<32, MODE_SMOOTH><<<pl->grid, pl->warps * 32, smem, st>>>(a);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return set_error(WS_ECUDA, "ragged kernel launch: %s", cudaGetErrorString(e));
+  return WS_OK;
+}
+
+// Refinement of a ragged solution z in place. Up to kRefineSteps FP32 steps
+// (r = W x - Omega z with a double-word combination, z += Omega^{-1} r); an item drops out
+// once all its series have settled. Series still unsettled after the last step are listed
+// and solved again from scratch in double-float arithmetic.
+static int ragged_refine(ws_plan* pl, const void* x, const void* w, const void* lam, void* z, int band,
+                         cudaStream_t st) {
+  RaggedArgs a;
+  memset(&a, 0, sizeof(a));
+  a.off = pl->rg.offsets;
+  a.order = pl->d_order;
+  a.item_d = pl->d_item_d;
+  a.n_items = pl->n_items;
+  a.N = pl->N;
+  a.B = pl->rg.n_bands;
+  a.band = band;
+  a.lam_scalar = pl->rg.lam_mode == WS_LAM_SCALAR;
+  a.x = (const float*)x;
+  a.w = (const float*)w;
+  a.lam = (const float*)lam;
+  a.z = (float*)z;
+  fill_refine_args(pl, a);
+  if (cudaMemsetAsync(pl->d_active, 1, pl->n_items, st) != cudaSuccess) return set_error(WS_ECUDA, "ragged: memset");
+  const int gi = (pl->n_items + 7) / 8;
+  for (int k = 0; k < kRefineSteps; ++k) {
+    k_ragged_resid<<<gi, 256, 0, st>>>(a);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return set_error(WS_ECUDA, "ragged residual launch: %s", cudaGetErrorString(e));
+    int rc = ragged_launch(pl, x, w, lam, z, nullptr, band, st, MODE_RAW, true);
+    if (rc != WS_OK) return rc;
+  }
+  if (cudaMemsetAsync(a.count64, 0, sizeof(int), st) != cudaSuccess) return set_error(WS_ECUDA, "ragged: memset");
+  k_ragged_collect<<<gi, 256, 0, st>>>(a);
+  k_ragged64<<<pl->grid64, 128, 0, st>>>(a);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return set_error(WS_ECUDA, "ragged double-float re-solve launch: %s", cudaGetErrorString(e));
+  return WS_OK;
+}
+
+static int refine_alloc(ws_plan* pl) {
+  if (pl->d_resid != nullptr) return WS_OK;
+  const size_t n = (size_t)std::max<int64_t>(1, pl->rg.n_series), ni = (size_t)std::max(1, pl->n_items);
+  DeviceInfo di;
+  int rc = device_info(di);
+  if (rc != WS_OK) return rc;
+  pl->grid64 = di.sm_count * kHPBlocksPerSM;
+  const size_t ck = (size_t)pl->grid64 * 128 * std::max(1, pl->max_nch64) * kFieldsMax * sizeof(double);
+  const bool ok = cudaMalloc(&pl->d_resid, sizeof(float) * (size_t)std::max<int64_t>(1, pl->N)) == cudaSuccess &&
+                  cudaMalloc(&pl->d_active, ni) == cudaSuccess && cudaMalloc(&pl->d_conv, n) == cudaSuccess &&
+                  cudaMalloc(&pl->d_zmax, 4 * n) == cudaSuccess && cudaMalloc(&pl->d_list64, 4 * n) == cudaSuccess &&
+                  cudaMalloc(&pl->d_count64, sizeof(int) * pl->rg.n_bands) == cudaSuccess &&
+                  cudaMalloc(&pl->d_ck64, ck) == cudaSuccess;
+  if (!ok) return set_error(WS_ECUDA, "plan: refinement allocation");
+  cudaMemset(pl->d_count64, 0, sizeof(int) * pl->rg.n_bands);
   return WS_OK;
 }
 
@@ -381,7 +668,7 @@ extern "C" int ws_plan_create(const ws_ragged* rg, ws_plan** out, void* stream) 
   bool okm = cudaMalloc(&pl->d_order, ni * 32 * 4) == cudaSuccess && cudaMalloc(&pl->d_item_d, ni) == cudaSuccess &&
              cudaMalloc(&pl->d_nch16, ni * 4) == cudaSuccess && cudaMalloc(&pl->d_nch32, ni * 4) == cudaSuccess &&
              cudaMalloc(&pl->d_counter, sizeof(int) * rg->n_bands) == cudaSuccess &&
-             cudaMalloc(&pl->d_err, 4) == cudaSuccess;
+             cudaMalloc(&pl->d_err, 4) == cudaSuccess && cudaMalloc(&pl->d_dof, std::max(1, n)) == cudaSuccess;
   if (!okm) {
     ws_plan_destroy(pl);
     return set_error(WS_ECUDA, "plan: device allocation");
@@ -391,7 +678,9 @@ extern "C" int ws_plan_create(const ws_ragged* rg, ws_plan** out, void* stream) 
     cudaMemcpy(pl->d_item_d, idd.data(), idd.size(), cudaMemcpyHostToDevice);
     cudaMemcpy(pl->d_nch16, n16.data(), n16.size() * 4, cudaMemcpyHostToDevice);
     cudaMemcpy(pl->d_nch32, n32.data(), n32.size() * 4, cudaMemcpyHostToDevice);
+    cudaMemcpy(pl->d_dof, dd.data(), n, cudaMemcpyHostToDevice);
   }
+  for (const Item& it : items) pl->max_nch64 = std::max(pl->max_nch64, (int)((it.tmax + kRC64 - 1) / kRC64));
   cudaMemset(pl->d_err, 0, 4);
   int rc = ragged_config(pl, 16, 8);
   if (rc != WS_OK) {
@@ -435,19 +724,23 @@ static int ragged_autotune(ws_plan* pl, const void* x, const void* w, const void
 extern "C" int ws_plan_execute(ws_plan* pl, const void* x, const void* w, const void* lam, void* z, uint8_t* status,
                                uint32_t flags, void* stream) {
   if (pl == nullptr) return set_error(WS_EINVAL, "plan is NULL");
-  if (flags & ~(WS_PLAN_AUTOTUNE | WS_PLAN_GRAPH)) return set_error(WS_EINVAL, "unknown flags 0x%x", flags);
+  if (flags & ~(WS_PLAN_AUTOTUNE | WS_PLAN_GRAPH | WS_PLAN_REFINE)) return set_error(WS_EINVAL, "unknown flags 0x%x", flags);
+  const bool refine = (flags & WS_PLAN_REFINE) != 0;
   if (pl->n_items == 0) return WS_OK;
+  int rc;
+  if (refine && (rc = refine_alloc(pl)) != WS_OK) return rc;
   if (!x || !w || !lam || !z) return set_error(WS_EINVAL, "x, w, lam and z must be non-NULL");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  int rc;
   if ((flags & WS_PLAN_AUTOTUNE) && !pl->tuned && (rc = ragged_autotune(pl, x, w, lam, z, st)) != WS_OK) return rc;
   if (!(flags & WS_PLAN_GRAPH) || pl->rg.n_bands > 1) {
-    for (int b = 0; b < pl->rg.n_bands; ++b)
-      if ((rc = ragged_launch(pl, x, w, lam, z, status, b, st)) != WS_OK) return rc;
+    for (int b = 0; b < pl->rg.n_bands; ++b) {
+      if ((rc = ragged_launch(pl, x, w, lam, z, status, b, st, MODE_SMOOTH, refine)) != WS_OK) return rc;
+      if (refine && (rc = ragged_refine(pl, x, w, lam, z, b, st)) != WS_OK) return rc;
+    }
     return WS_OK;
   }
   // CUDA graph: captured once per configuration, kernel arguments updated on each replay
-  if (pl->exec == nullptr || pl->graph_rc != pl->RC || pl->graph_warps != pl->warps) {
+  if (pl->exec == nullptr || pl->graph_rc != pl->RC || pl->graph_warps != pl->warps || pl->graph_refine != refine) {
     if (pl->exec) cudaGraphExecDestroy(pl->exec);
     if (pl->graph) cudaGraphDestroy(pl->graph);
     pl->exec = nullptr;
@@ -458,7 +751,8 @@ extern "C" int ws_plan_execute(ws_plan* pl, const void* x, const void* w, const 
       cudaStreamDestroy(cs);
       return set_error(WS_ECUDA, "graph capture");
     }
-    rc = ragged_launch(pl, x, w, lam, z, status, 0, cs);
+    rc = ragged_launch(pl, x, w, lam, z, status, 0, cs, MODE_SMOOTH, refine);
+    if (rc == WS_OK && refine) rc = ragged_refine(pl, x, w, lam, z, 0, cs);
     cudaGraph_t g = nullptr;
     cudaError_t e = cudaStreamEndCapture(cs, &g);
     cudaStreamDestroy(cs);
@@ -470,30 +764,33 @@ extern "C" int ws_plan_execute(ws_plan* pl, const void* x, const void* w, const 
     pl->graph = g;
     pl->graph_rc = pl->RC;
     pl->graph_warps = pl->warps;
+    pl->graph_refine = refine;
     size_t nn = 0;
     cudaGraphGetNodes(g, nullptr, &nn);
     std::vector<cudaGraphNode_t> nodes(nn);
     cudaGraphGetNodes(g, nodes.data(), &nn);
-    pl->knode = nullptr;
+    pl->knodes.clear();
     for (auto nd : nodes) {
       cudaGraphNodeType t;
       cudaGraphNodeGetType(nd, &t);
-      if (t == cudaGraphNodeTypeKernel) pl->knode = nd;
+      if (t == cudaGraphNodeTypeKernel) pl->knodes.push_back(nd);
     }
-  } else if (pl->knode != nullptr) {
-    cudaKernelNodeParams kp;
-    if (cudaGraphKernelNodeGetParams(pl->knode, &kp) != cudaSuccess) return set_error(WS_ECUDA, "graph params");
-    RaggedArgs* a = static_cast<RaggedArgs*>(kp.kernelParams[0]);
-    RaggedArgs na = *a;
-    na.x = (const float*)x;
-    na.w = (const float*)w;
-    na.lam = (const float*)lam;
-    na.z = (float*)z;
-    na.status = status;
-    void* args[1] = {&na};
-    kp.kernelParams = args;
-    if (cudaGraphExecKernelNodeSetParams(pl->exec, pl->knode, &kp) != cudaSuccess)
-      return set_error(WS_ECUDA, "graph update");
+  } else {
+    // new buffers: every kernel node takes one RaggedArgs; only the user buffers change
+    for (auto nd : pl->knodes) {
+      cudaKernelNodeParams kp;
+      if (cudaGraphKernelNodeGetParams(nd, &kp) != cudaSuccess) return set_error(WS_ECUDA, "graph params");
+      RaggedArgs na = *static_cast<RaggedArgs*>(kp.kernelParams[0]);
+      na.x = (const float*)x;
+      na.w = (const float*)w;
+      na.lam = (const float*)lam;
+      na.z = (float*)z;
+      na.status = status;  // read by the smoothing launch only
+      void* args1[1] = {&na};
+      kp.kernelParams = args1;
+      if (cudaGraphExecKernelNodeSetParams(pl->exec, nd, &kp) != cudaSuccess)
+        return set_error(WS_ECUDA, "graph update");
+    }
   }
   if (cudaGraphLaunch(pl->exec, st) != cudaSuccess) return set_error(WS_ECUDA, "graph launch");
   return WS_OK;
@@ -508,6 +805,9 @@ extern "C" int ws_plan_info(const ws_plan* pl, ws_plan_stats* out) {
   out->tuned = pl->tuned ? 1 : 0;
   out->tuned_ms = pl->tuned_ms;
   out->graph = pl->exec != nullptr ? 1 : 0;
+  out->hp_series = 0;
+  if (pl->d_count64 != nullptr && cudaMemcpy(&out->hp_series, pl->d_count64, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
+    return set_error(WS_ECUDA, "plan info: reading the re-solve count");
   return WS_OK;
 }
 
@@ -522,5 +822,13 @@ extern "C" void ws_plan_destroy(ws_plan* pl) {
   cudaFree(pl->d_counter);
   cudaFree(pl->d_err);
   cudaFree(pl->d_ckpt);
+  cudaFree(pl->d_resid);
+  cudaFree(pl->d_active);
+  cudaFree(pl->d_conv);
+  cudaFree(pl->d_zmax);
+  cudaFree(pl->d_list64);
+  cudaFree(pl->d_count64);
+  cudaFree(pl->d_ck64);
+  cudaFree(pl->d_dof);
   delete pl;
 }

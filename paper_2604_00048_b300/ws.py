@@ -77,10 +77,10 @@ class Ragged(ctypes.Structure):
 class PlanStats(ctypes.Structure):
     _fields_ = [("n_items", ctypes.c_int32), ("chunk_days", ctypes.c_int32), ("warps_per_cta", ctypes.c_int32),
                 ("grid", ctypes.c_int32), ("tuned", ctypes.c_int32), ("graph", ctypes.c_int32),
-                ("tuned_ms", ctypes.c_float)]
+                ("tuned_ms", ctypes.c_float), ("hp_series", ctypes.c_int32)]
 
 
-PLAN_AUTOTUNE, PLAN_GRAPH = 0x1, 0x2
+PLAN_AUTOTUNE, PLAN_GRAPH, PLAN_REFINE = 0x1, 0x2, 0x4
 _lib.ws_plan_create.restype = ctypes.c_int
 _lib.ws_plan_create.argtypes = [ctypes.POINTER(Ragged), ctypes.POINTER(ctypes.c_void_p), ctypes.c_void_p]
 _lib.ws_plan_execute.restype = ctypes.c_int
@@ -307,12 +307,13 @@ class RaggedPlan:
         _check(_lib.ws_plan_create(ctypes.byref(self._rg), ctypes.byref(h), _stream_ptr(stream)))
         self._h = h
 
-    def execute(self, x, w, lam, z=None, status=None, autotune: bool = False, graph: bool = False, stream=None):
+    def execute(self, x, w, lam, z=None, status=None, autotune: bool = False, graph: bool = False,
+                refine: bool = False, stream=None):
         if z is None:
             z = torch.empty_like(x)
         if status is None:
             status = torch.empty(self.n, dtype=torch.uint8, device=x.device)
-        flags = (PLAN_AUTOTUNE if autotune else 0) | (PLAN_GRAPH if graph else 0)
+        flags = (PLAN_AUTOTUNE if autotune else 0) | (PLAN_GRAPH if graph else 0) | (PLAN_REFINE if refine else 0)
         _check(_lib.ws_plan_execute(self._h, _ptr(x), _ptr(w), _ptr(lam), _ptr(z), _ptr(status), flags,
                                     _stream_ptr(stream)))
         return z, status
