@@ -111,6 +111,29 @@ int ws_smooth_batch(const ws_problem* pb, const void* x, const void* w, const vo
                     void* factor_out, uint8_t* status, uint32_t flags, void* workspace,
                     size_t ws_bytes, void* stream);
 
+/* ws_smooth_batch without a caller-provided workspace (the paper has no counterpart:
+ * this is an interface for callers that cannot allocate device memory where they
+ * smooth, e.g. under a framework's caching allocator that already holds the memory, or
+ * where the device-wide synchronisation of cudaFree must be avoided). Same arguments,
+ * results and per-series status as ws_smooth_batch, whose kernels it runs; the scratch
+ * is a file-scope device array of WS_NOALLOC_MAX_BYTES per device.
+ *   - Problems with ws_workspace_size(pb, flags) > WS_NOALLOC_MAX_BYTES (32 MiB)
+ *     return WS_ENOMEM_WS before anything is launched. That size is the checkpoints of
+ *     the persistent grid (up to grid x ceil(T/C) x (d(d+1) + B d) x 128 elements, C the
+ *     planned chunk) plus, with WS_REFINE, a T x B x P residual: 4096 FP64 series of
+ *     T = 365, d = 2, one band, with WS_REFINE fit (about 18 MiB).
+ *   - No cudaMalloc, cudaFree or allocating library routine is called.
+ *   - The first call on each device does the set-up with that device current
+ *     (cudaGetSymbolAddress, then a synchronous cudaMemset clearing the error word):
+ *     make that first call before any stream capture.
+ *   - Calls on the same device share the array: calls that overlap in time (host
+ *     threads, or streams without ordering between them) race on it.
+ *   - A device-side wait that gives up sets the array's error word, which this entry
+ *     point does not report; use ws_smooth_batch and ws_sync_status for that report. */
+#define WS_NOALLOC_MAX_BYTES (32u << 20)
+int ws_smooth_batch_noalloc(const ws_problem* pb, const void* x, const void* w, const void* lam, void* z,
+                            void* factor_out, uint8_t* status, uint32_t flags, void* stream);
+
 /* One step of iterative refinement of a smoothing result z, in place:
  *     r = W x - Omega z        (double-word accumulation: FP64-level accuracy from
  *                               error-free transformations of the working precision)

@@ -58,6 +58,9 @@ _lib.ws_solve_adjoint.restype = ctypes.c_int
 _lib.ws_solve_adjoint.argtypes = [_PP, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _u32, _vp, _vp, _sz, _vp]
 _lib.ws_refine.restype = ctypes.c_int
 _lib.ws_refine.argtypes = [_PP, _vp, _vp, _vp, _vp, _vp, _sz, _vp]
+_lib.ws_smooth_batch_noalloc.restype = ctypes.c_int
+_lib.ws_smooth_batch_noalloc.argtypes = [_PP, _vp, _vp, _vp, _vp, _vp, _vp, _u32, _vp]
+NOALLOC_MAX_BYTES = 32 << 20
 _lib.ws_tune_set.restype = ctypes.c_int
 _lib.ws_tune_set.argtypes = [ctypes.c_int32, ctypes.c_int32]
 _lib.ws_sync_status.restype = ctypes.c_int
@@ -207,6 +210,22 @@ def smooth(x: torch.Tensor, w: torch.Tensor, lam: torch.Tensor, d: int = 2, *, z
     rc = _lib.ws_smooth_batch(ctypes.byref(pb), _ptr(x), _ptr(w), _ptr(lam), _ptr(z), _ptr(factor),
                               _ptr(status), flags, _ptr(ws), ws.numel(), _stream_ptr(stream))
     _check(rc)
+    return z, status
+
+
+def smooth_noalloc(x: torch.Tensor, w: torch.Tensor, lam: torch.Tensor, d: int = 2, *, z, status,
+                   refine: bool = False, stream=None):
+    """smooth() through ws_smooth_batch_noalloc: the scratch is the library's static device
+    array (NOALLOC_MAX_BYTES), so nothing is allocated; z and status must be given.
+    Raises WSError (code ENOMEM_WS) when the problem's workspace exceeds the array."""
+    T, B, P, lm = _check_tile(x, w, lam, d)
+    pb = make_problem(T, B, P, d, _dtype_code(x), lm)
+    if tuple(z.shape) != tuple(x.shape) or z.dtype != x.dtype or not z.is_contiguous():
+        raise ValueError("z must be a contiguous tensor shaped and typed like x")
+    if status.numel() != P or status.dtype != torch.uint8:
+        raise ValueError("status must hold P uint8 codes")
+    _check(_lib.ws_smooth_batch_noalloc(ctypes.byref(pb), _ptr(x), _ptr(w), _ptr(lam), _ptr(z), None,
+                                        _ptr(status), REFINE if refine else 0, _stream_ptr(stream)))
     return z, status
 
 
