@@ -44,6 +44,7 @@ def parse_args():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-ragged", action="store_true")
+    ap.add_argument("--no-gcv", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU work of the oracle baseline")
     return ap.parse_args()
 
@@ -209,6 +210,36 @@ def ragged_measure(dev, steps):
            "plan": {k: info[k] for k in ("n_items", "chunk_days", "warps_per_cta", "grid", "graph")},
            "series_with_status": int((st != 0).sum().item())}
     del out, x, w, lam, z, plan
+    torch.cuda.empty_cache()
+    return res
+
+
+def gcv_measure(dev, steps):
+    """GCV grid search (16 lambda values, log10 in {0, 1/3, ..., 5}) then the smoothing at the
+    chosen lambda, on the learned-lambda evaluation set: 262,144 series x 730 days, d = 2,
+    one band, FP32."""
+    import torch
+
+    from paper_2604_00048_b300 import synth, ws
+
+    P, T = 262144, 730
+    out = synth.generate_tile(synth.RECIPES["learned"], P, device=dev)
+    x, w = out["x"], out["w"]
+    ws.gcv_smooth(x, w, None, 2, want_scores=False)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        z, lam_best, _, st = ws.gcv_smooth(x, w, None, 2, want_scores=False)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    hbm, _ = peaks()
+    res = {"workload": f"gcv: {P} series x {T} days, d=2, 1 band, FP32, 16-value grid, then the smooth",
+           "series_per_s": P / (ms / 1e3), "ms": ms,
+           "lambda_evals_per_s": 16 * P / (ms / 1e3),
+           "series_with_status": int((st != 0).sum().item())}
+    del out, x, w, z, lam_best, st
     torch.cuda.empty_cache()
     return res
 
@@ -409,6 +440,7 @@ def run_ours(args):
         ws._ws_cache.clear()
         torch.cuda.empty_cache()
         ragged = ragged_measure(dev, max(3, args.steps))
+    gcv = None if args.no_gcv else gcv_measure(dev, max(3, args.steps))
     line = {"metric": METRIC, "value": value, "unit": "series/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
@@ -420,7 +452,7 @@ def run_ours(args):
             "fwd_series_per_s": P * world / ((fwd_ms + ref_ms) / 1e3),
             "fwd_unrefined_series_per_s": P * world / (fwd_ms / 1e3),
             "smooth_ms": fwd_ms, "refine_ms": ref_ms, "adjoint_ms": bwd_ms,
-            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "ragged": ragged,
+            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "ragged": ragged, "gcv": gcv,
             "gpu_launches": launches_per_step * args.steps, "clocks": ck,
             "series_with_status": bad}
     if rank == 0:

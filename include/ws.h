@@ -76,6 +76,7 @@ extern "C" {
 /* flags */
 #define WS_GRAD_LOGLAM 0x1u   /* ws_solve_adjoint: glam = lambda * dL/dlambda (d/dlog lambda) */
 #define WS_REFINE 0x2u        /* ws_smooth_batch: one step of iterative refinement */
+#define WS_GCV 0x8u           /* ws_workspace_size: size for ws_gcv_smooth */
 #define WS_REFINE_ADJOINT 0x4u /* ws_solve_adjoint: one step of iterative refinement of g */
 
 typedef struct ws_problem {
@@ -110,6 +111,24 @@ size_t ws_workspace_size(const ws_problem* pb, uint32_t flags);
 int ws_smooth_batch(const ws_problem* pb, const void* x, const void* w, const void* lam, void* z,
                     void* factor_out, uint8_t* status, uint32_t flags, void* workspace,
                     size_t ws_bytes, void* stream);
+
+/* Smoothing with lambda chosen per series by generalized cross-validation over a grid.
+ * The paper names the selection problem but defines no criterion; this is the
+ * Craven-Wahba score: for each grid value lam_g, z = Omega^{-1} W x (Eq. 2, scalar lambda),
+ * RSS = sum_t w_t (x_t - z_t)^2, tr H = sum_t w_t (Omega^{-1})_tt with H = Omega^{-1} W
+ * (diagonal of the inverse by the banded selected-inverse recursion on the same factor),
+ * n = sum_t w_t, V_g = n RSS / (n - tr H)^2. The smallest V wins, ties to the smaller
+ * lambda; z is then the smoothing at that lambda (ws_smooth_batch, WS_REFINE allowed).
+ * pb: FP32, one band, tile layout; pb->lam_mode is ignored (the final smooth uses one
+ * lambda per series). lam_grid: HOST array of n_grid (1..16) finite positive values.
+ * x, w, z: device, [T][P]. lam_best: device, P floats (output). scores: optional device
+ * [n_grid][P] (V per grid value; NaN where the series is not positive definite or has
+ * invalid weights). status: optional per-series codes of the final smooth.
+ * Workspace: ws_workspace_size(pb, WS_GCV | flags). Errors as ws_smooth_batch;
+ * WS_EUNSUPPORTED for FP64 or several bands. */
+int ws_gcv_smooth(const ws_problem* pb, const void* x, const void* w, const float* lam_grid, int n_grid,
+                  void* z, float* lam_best, float* scores, uint8_t* status, uint32_t flags,
+                  void* workspace, size_t ws_bytes, void* stream);
 
 /* ws_smooth_batch without a caller-provided workspace (the paper has no counterpart:
  * this is an interface for callers that cannot allocate device memory where they

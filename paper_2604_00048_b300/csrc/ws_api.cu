@@ -9,6 +9,9 @@
 
 #include <mutex>
 
+#include <algorithm>
+#include <cmath>
+
 #include "ws_internal.h"
 
 namespace ws {
@@ -253,7 +256,43 @@ extern "C" size_t ws_workspace_size(const ws_problem* pb, uint32_t flags) {
   if (pb->n_series == 0 || pb->T == 0) return kHeaderBytes;
   if (tile_ckpt_bytes(*pb, ck) != WS_OK) return 0;
   const size_t extra = (flags & WS_REFINE_ADJOINT) ? 2 * resid_bytes(*pb) : ((flags & WS_REFINE) ? resid_bytes(*pb) : 0);
-  return kHeaderBytes + ck + extra;
+  size_t need = kHeaderBytes + ck + extra;
+  if (flags & WS_GCV) {  // the grid search's checkpoints, then the final smooth, reuse one region
+    int grid = 0, nch = 0;
+    size_t gck = 0;
+    if (gcv_plan(*pb, grid, nch, gck) != WS_OK) return 0;
+    need = std::max(need, kHeaderBytes + round256(gck));
+  }
+  return need;
+}
+
+extern "C" int ws_gcv_smooth(const ws_problem* pb, const void* x, const void* w, const float* lam_grid, int n_grid,
+                             void* z, float* lam_best, float* scores, uint8_t* status, uint32_t flags,
+                             void* workspace, size_t ws_bytes, void* stream) {
+  clear_error();
+  int rc = validate_problem(pb);
+  if (rc != WS_OK) return rc;
+  if (flags & ~WS_REFINE) return set_error(WS_EINVAL, "unknown flags 0x%x", flags);
+  if (pb->dtype != WS_F32) return set_error(WS_EUNSUPPORTED, "GCV grid search: FP32 only");
+  if (pb->n_bands != 1) return set_error(WS_EUNSUPPORTED, "GCV grid search: one band");
+  if (lam_grid == nullptr || n_grid < 1 || n_grid > 16) return set_error(WS_EINVAL, "n_grid must be 1..16");
+  for (int g = 0; g < n_grid; ++g)
+    if (!(lam_grid[g] > 0.f) || !std::isfinite(lam_grid[g]))
+      return set_error(WS_EINVAL, "lam_grid[%d] must be finite and > 0", g);
+  ws_problem P = *pb;
+  P.lam_mode = WS_LAM_SCALAR;  // the final smooth takes lam_best per series
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (P.n_series == 0) return WS_OK;
+  if (!x || !w || !z || !lam_best) return set_error(WS_EINVAL, "x, w, z and lam_best must be non-NULL");
+  if (P.T == 0) return ws_smooth_batch(&P, x, w, lam_best, z, nullptr, status, 0, workspace, ws_bytes, stream);
+  const size_t need = ws_workspace_size(&P, WS_GCV | (flags & WS_REFINE));
+  if (need == 0) return WS_ECUDA;
+  if (workspace == nullptr || (reinterpret_cast<uintptr_t>(workspace) & 255u) != 0)
+    return set_error(WS_EINVAL, "workspace must be non-NULL and 256-byte aligned");
+  if (ws_bytes < need) return set_error(WS_ENOMEM_WS, "workspace too small: %zu < %zu", ws_bytes, need);
+  rc = launch_gcv(P, x, w, lam_grid, n_grid, lam_best, scores, static_cast<char*>(workspace) + kHeaderBytes, st);
+  if (rc != WS_OK) return rc;
+  return ws_smooth_batch(&P, x, w, lam_best, z, nullptr, status, flags & WS_REFINE, workspace, ws_bytes, stream);
 }
 
 extern "C" int ws_smooth_batch(const ws_problem* pb, const void* x, const void* w, const void* lam, void* z,

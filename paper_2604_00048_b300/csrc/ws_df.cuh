@@ -44,6 +44,19 @@ __device__ __forceinline__ DW<F> dw_scale(DW<F> a, F c) {
   return {h, p.lo - (h - p.hi)};
 }
 
+// acc + r * s with r a working-precision scalar: error ~ u^2 (|acc| + |r s|) (the
+// sloppy double-word sum; enough where the terms' magnitudes, not the result's, set the
+// scale, as in a linear recursion).
+template <typename F>
+__device__ __forceinline__ DW<F> dw_fma(DW<F> acc, F r, DW<F> s) {
+  DW<F> p = two_prod(r, s.hi);
+  p.lo = fma(r, s.lo, p.lo);
+  DW<F> t = two_sum(acc.hi, p.hi);
+  t.lo += acc.lo + p.lo;
+  const F h = t.hi + t.lo;
+  return {h, t.lo - (h - t.hi)};
+}
+
 // Double-float number type for the ragged path's high-precision re-solve: normalised
 // hi + lo with |lo| <= ulp(hi)/2, about 48 significant bits, from FP32 operations only
 // (B300 issues FP64 at a small fraction of its FP32 rate). Addition is the accurate

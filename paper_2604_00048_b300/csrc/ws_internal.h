@@ -87,6 +87,11 @@ int set_error(int code, const char* fmt, ...);
 int make_tmap(CUtensorMap* map, int dtype, int rank, const void* base, const uint64_t* dims,
               const uint64_t* strides_bytes, const uint32_t* box);
 
+// GCV grid search (ws_gcv.cu): persistent grid, chunks and checkpoint bytes; launch.
+int gcv_plan(const ws_problem& pb, int& grid, int& nch, size_t& ck_bytes);
+int launch_gcv(const ws_problem& pb, const void* x, const void* w, const float* grid_vals, int n_grid,
+               float* lam_best, float* scores, void* ckpt, cudaStream_t st);
+
 // Launchers (return WS_OK or an error code, errors recorded via set_error).
 extern int g_tune_ctas, g_tune_chunk;  // ws_tune_set() overrides (0 = automatic)
 int plan_tile(const ws_problem& pb, int mode, int nb, TileCfg& cfg);

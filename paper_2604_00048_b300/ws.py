@@ -58,6 +58,9 @@ _lib.ws_solve_adjoint.restype = ctypes.c_int
 _lib.ws_solve_adjoint.argtypes = [_PP, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _u32, _vp, _vp, _sz, _vp]
 _lib.ws_refine.restype = ctypes.c_int
 _lib.ws_refine.argtypes = [_PP, _vp, _vp, _vp, _vp, _vp, _sz, _vp]
+_lib.ws_gcv_smooth.restype = ctypes.c_int
+_lib.ws_gcv_smooth.argtypes = [_PP, _vp, _vp, ctypes.POINTER(ctypes.c_float), ctypes.c_int, _vp, _vp, _vp, _vp,
+                               _u32, _vp, _sz, _vp]
 _lib.ws_smooth_batch_noalloc.restype = ctypes.c_int
 _lib.ws_smooth_batch_noalloc.argtypes = [_PP, _vp, _vp, _vp, _vp, _vp, _vp, _u32, _vp]
 NOALLOC_MAX_BYTES = 32 << 20
@@ -211,6 +214,32 @@ def smooth(x: torch.Tensor, w: torch.Tensor, lam: torch.Tensor, d: int = 2, *, z
                               _ptr(status), flags, _ptr(ws), ws.numel(), _stream_ptr(stream))
     _check(rc)
     return z, status
+
+
+GCV = 0x8
+GCV_GRID = [10.0 ** (i / 3.0) for i in range(16)]  # log10 lambda in {0, 1/3, ..., 5}
+
+
+def gcv_smooth(x: torch.Tensor, w: torch.Tensor, lam_grid=None, d: int = 2, *, refine: bool = False,
+               want_scores: bool = True, stream=None):
+    """Per-series lambda by GCV over a grid of scalar values, then the smoothing at it.
+
+    x: [T, 1, P] FP32, w: [T, P]. lam_grid: up to 16 positive values (default GCV_GRID).
+    Returns (z, lam_best [P], scores [n_grid, P] or None, status [P])."""
+    grid = [float(v) for v in (GCV_GRID if lam_grid is None else lam_grid)]
+    lam_dummy = torch.empty(x.shape[2], dtype=x.dtype, device=x.device)
+    T, B, P, _ = _check_tile(x, w, lam_dummy, d)
+    pb = make_problem(T, B, P, d, _dtype_code(x), LAM_SCALAR)
+    flags = REFINE if refine else 0
+    z = torch.empty_like(x)
+    lam_best = torch.empty(P, dtype=torch.float32, device=x.device)
+    scores = torch.empty(len(grid), P, dtype=torch.float32, device=x.device) if want_scores else None
+    status = torch.empty(P, dtype=torch.uint8, device=x.device)
+    ws = workspace(pb, x.device, GCV | flags)
+    arr = (ctypes.c_float * len(grid))(*grid)
+    _check(_lib.ws_gcv_smooth(ctypes.byref(pb), _ptr(x), _ptr(w), arr, len(grid), _ptr(z), _ptr(lam_best),
+                              _ptr(scores), _ptr(status), flags, _ptr(ws), ws.numel(), _stream_ptr(stream)))
+    return z, lam_best, scores, status
 
 
 def smooth_noalloc(x: torch.Tensor, w: torch.Tensor, lam: torch.Tensor, d: int = 2, *, z, status,
