@@ -130,6 +130,51 @@ int ws_gcv_smooth(const ws_problem* pb, const void* x, const void* w, const floa
                   void* z, float* lam_best, float* scores, uint8_t* status, uint32_t flags,
                   void* workspace, size_t ws_bytes, void* stream);
 
+/* ---- Learned lambda: temporal convolution network g_theta (Section 4.2 names a network
+ * with a sigmoid output range; this one is a 4-layer 1-D convolution net) ----
+ * Per series, per day: (x_t [w_t > 0], w_t) -> conv(2->64, k=9) -> ReLU -> conv(64->64) ->
+ * ReLU -> conv(64->64) -> ReLU -> conv(64->1) = o_t; log lambda_t = Lmin + sigmoid(o_t)
+ * (Lmax - Lmin). "Same" zero padding per series. BF16 weights and activations, FP32
+ * accumulation; the two 64->64 layers and their data gradients run on the tensor cores
+ * (tcgen05), the 2->64 and 64->1 layers and the weight gradients on CUDA cores.
+ * Parameters: an FP32 master vector of WS_TCN_PARAMS values, PyTorch conv1d layouts
+ * concatenated: W1 [64][2][9], b1 [64], W2 [64][64][9], b2, W3 [64][64][9], b3, W4 [1][64][9],
+ * b4 [1]. ws_tcn_pack writes the BF16 copy (WS_TCN_PACKED_BYTES) the kernels read; biases are
+ * read from the master. All pointers are device pointers. */
+#define WS_TCN_PARAMS 75649
+#define WS_TCN_PACKED_BYTES 298368
+typedef struct ws_tcn_batch {
+  int32_t T;            /* days per series */
+  int32_t n_series;     /* P: series of the [T][P] inputs */
+  float log_lam_min;    /* Lmin, natural log */
+  float log_lam_max;    /* Lmax > Lmin */
+} ws_tcn_batch;
+
+/* Scratch bytes for ws_tcn_forward (training = 0: inference; 1: keeps the activations the
+ * backward pass needs) and ws_tcn_backward (training = 1). 0 on invalid input. */
+size_t ws_tcn_scratch_size(const ws_tcn_batch* b, int training);
+int ws_tcn_pack(const float* master, void* packed, void* stream);
+/* lam, loglam (optional): [T][P] FP32 outputs. x, w: [T][P] FP32 inputs. */
+int ws_tcn_forward(const ws_tcn_batch* b, const void* packed, const float* master, const float* x, const float* w,
+                   float* lam, float* loglam, void* scratch, size_t scratch_bytes, int training, void* stream);
+/* grad (FP32, WS_TCN_PARAMS) += dL/dtheta given g_loglam = dL/dlog lambda ([T][P]), using the
+ * activations the last training forward left in scratch. */
+int ws_tcn_backward(const ws_tcn_batch* b, const void* packed, const float* g_loglam, float* grad, void* scratch,
+                    size_t scratch_bytes, void* stream);
+/* One 64 -> 64 layer over `rows` stream rows (series of T days each followed by 4 gap rows):
+ * out[r][co] = relu(bias[co] + sum_{k,ci} W[k][ci][co] in[r + k - 4][ci]) with zeros on gap
+ * rows (mode 0), or the data gradient form out[r][co] = [mask[r][co] > 0] sum_{k,ci} ... (mode
+ * 1). in, mask, out: BF16 [rows][64]; wplanes: BF16 [9 taps][8 ci chunks][64 co][8 ci] (73,728
+ * bytes, the layout ws_tcn_pack writes); err_word: a device word set if a wait gives up. */
+int ws_tcn_conv64(const void* in, const void* wplanes, const float* bias, const void* mask, void* out, int64_t rows,
+                  int32_t T, int32_t mode, void* err_word, void* stream);
+/* Adam with bias correction (step >= 1); grad is cleared after the update. */
+int ws_adam_step(float* params, float* m, float* v, float* grad, int64_t n, int32_t step, float lr, float beta1,
+                 float beta2, float eps, void* stream);
+/* gz = scale (z - target); *loss_sum += scale/2 sum (z - target)^2 (loss_sum may be NULL). */
+int ws_mse_grad(const float* z, const float* target, float* gz, float* loss_sum, int64_t n, float scale,
+                void* stream);
+
 /* ws_smooth_batch without a caller-provided workspace (the paper has no counterpart:
  * this is an interface for callers that cannot allocate device memory where they
  * smooth, e.g. under a framework's caching allocator that already holds the memory, or

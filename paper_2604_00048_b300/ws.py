@@ -18,6 +18,7 @@ import os
 import re
 from typing import Optional
 
+import numpy as np
 import torch
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -376,3 +377,123 @@ class RaggedPlan:
         if h is not None and h.value:
             _lib.ws_plan_destroy(h)
             self._h = None
+
+
+# ---- learned lambda: temporal convolution network ----------------------------------------
+class TcnBatch(ctypes.Structure):
+    _fields_ = [("T", ctypes.c_int32), ("n_series", ctypes.c_int32), ("log_lam_min", ctypes.c_float),
+                ("log_lam_max", ctypes.c_float)]
+
+
+TCN_PARAMS, TCN_PACKED_BYTES, TCN_GAP = 75649, 298368, 4
+TCN_LOG_LAM = (float(np.log(1e-1)), float(np.log(1e6)))
+_TB = ctypes.POINTER(TcnBatch)
+_lib.ws_tcn_scratch_size.restype = _sz
+_lib.ws_tcn_scratch_size.argtypes = [_TB, ctypes.c_int]
+_lib.ws_tcn_pack.restype = ctypes.c_int
+_lib.ws_tcn_pack.argtypes = [_vp, _vp, _vp]
+_lib.ws_tcn_forward.restype = ctypes.c_int
+_lib.ws_tcn_forward.argtypes = [_TB, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _sz, ctypes.c_int, _vp]
+_lib.ws_tcn_backward.restype = ctypes.c_int
+_lib.ws_tcn_backward.argtypes = [_TB, _vp, _vp, _vp, _vp, _sz, _vp]
+_lib.ws_tcn_conv64.restype = ctypes.c_int
+_lib.ws_tcn_conv64.argtypes = [_vp, _vp, _vp, _vp, _vp, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, _vp, _vp]
+_lib.ws_adam_step.restype = ctypes.c_int
+_lib.ws_adam_step.argtypes = [_vp, _vp, _vp, _vp, ctypes.c_int64, ctypes.c_int32, ctypes.c_float, ctypes.c_float,
+                              ctypes.c_float, ctypes.c_float, _vp]
+_lib.ws_mse_grad.restype = ctypes.c_int
+_lib.ws_mse_grad.argtypes = [_vp, _vp, _vp, _vp, ctypes.c_int64, ctypes.c_float, _vp]
+
+TCN_OFFSETS = {"W1": (0, (64, 2, 9)), "b1": (1152, (64,)), "W2": (1216, (64, 64, 9)), "b2": (38080, (64,)),
+               "W3": (38144, (64, 64, 9)), "b3": (75008, (64,)), "W4": (75072, (1, 64, 9)), "b4": (75648, (1,))}
+
+
+def tcn_init(seed: int = 0, device="cuda") -> torch.Tensor:
+    """He-normal conv weights (std sqrt(2 / fan_in)), zero biases, last layer std 1e-2."""
+    g = torch.Generator().manual_seed(seed)
+    theta = torch.zeros(TCN_PARAMS, dtype=torch.float32)
+    for name, (off, shape) in TCN_OFFSETS.items():
+        if name.startswith("W"):
+            fan_in = shape[1] * shape[2]
+            std = 1e-2 if name == "W4" else (2.0 / fan_in) ** 0.5
+            n = int(np.prod(shape))
+            theta[off:off + n] = torch.randn(n, generator=g) * std
+    return theta.to(device)
+
+
+def tcn_pack(theta: torch.Tensor, packed: Optional[torch.Tensor] = None, stream=None) -> torch.Tensor:
+    if packed is None:
+        packed = torch.empty(TCN_PACKED_BYTES // 2, dtype=torch.bfloat16, device=theta.device)
+    _check(_lib.ws_tcn_pack(_ptr(theta), _ptr(packed), _stream_ptr(stream)))
+    return packed
+
+
+class Tcn:
+    """The lambda network's parameters (FP32 master, Adam moments, gradient, BF16 copy) and
+    its forward / backward / update calls."""
+
+    def __init__(self, theta: torch.Tensor, log_lam=TCN_LOG_LAM):
+        self.theta = theta.contiguous()
+        self.m = torch.zeros_like(self.theta)
+        self.v = torch.zeros_like(self.theta)
+        self.grad = torch.zeros_like(self.theta)
+        self.packed = tcn_pack(self.theta)
+        self.log_lam = log_lam
+        self.step_count = 0
+        self._scratch = None
+
+    def _batch(self, T, P):
+        return TcnBatch(T, P, self.log_lam[0], self.log_lam[1])
+
+    def _scratch_for(self, b, training, device):
+        need = int(_lib.ws_tcn_scratch_size(ctypes.byref(b), int(training)))
+        if need == 0:
+            raise WSError(WS_EINVAL, last_error())
+        if self._scratch is None or self._scratch.numel() < need:
+            self._scratch = None
+            self._scratch = torch.zeros(need, dtype=torch.uint8, device=device)
+        return self._scratch
+
+    def forward(self, x: torch.Tensor, w: torch.Tensor, training: bool = False, stream=None):
+        """x, w: [T, P] FP32 (one band). Returns (lam, loglam), both [T, P]."""
+        T, P = w.shape
+        x2 = x.reshape(T, P)
+        b = self._batch(T, P)
+        sc = self._scratch_for(b, training, x.device)
+        lam = torch.empty(T, P, dtype=torch.float32, device=x.device)
+        loglam = torch.empty_like(lam)
+        _check(_lib.ws_tcn_forward(ctypes.byref(b), _ptr(self.packed), _ptr(self.theta), _ptr(x2), _ptr(w),
+                                   _ptr(lam), _ptr(loglam), _ptr(sc), sc.numel(), int(training),
+                                   _stream_ptr(stream)))
+        return lam, loglam
+
+    def backward(self, g_loglam: torch.Tensor, stream=None):
+        """grad += dL/dtheta for dL/dlog lambda (after a training forward on the same batch)."""
+        T, P = g_loglam.shape
+        b = self._batch(T, P)
+        sc = self._scratch_for(b, True, g_loglam.device)
+        _check(_lib.ws_tcn_backward(ctypes.byref(b), _ptr(self.packed), _ptr(g_loglam.contiguous()), _ptr(self.grad),
+                                    _ptr(sc), sc.numel(), _stream_ptr(stream)))
+
+    def step(self, lr: float, betas=(0.9, 0.999), eps: float = 1e-8, stream=None):
+        self.step_count += 1
+        _check(_lib.ws_adam_step(_ptr(self.theta), _ptr(self.m), _ptr(self.v), _ptr(self.grad), TCN_PARAMS,
+                                 self.step_count, lr, betas[0], betas[1], eps, _stream_ptr(stream)))
+        tcn_pack(self.theta, self.packed, stream)
+
+
+def mse_grad(z: torch.Tensor, target: torch.Tensor, scale: float, loss: Optional[torch.Tensor] = None, stream=None):
+    """gz = scale (z - target); loss (1 FP32 element) += scale/2 sum (z - target)^2."""
+    gz = torch.empty_like(z)
+    _check(_lib.ws_mse_grad(_ptr(z), _ptr(target), _ptr(gz), _ptr(loss), z.numel(), scale, _stream_ptr(stream)))
+    return gz
+
+
+def tcn_conv64(inp: torch.Tensor, wplanes: torch.Tensor, T: int, mode: int, bias=None, mask=None, stream=None):
+    """One 64 -> 64 layer (mode 0: ReLU(conv + bias), zero gaps; 1: data gradient with mask)."""
+    rows = inp.shape[0]
+    out = torch.empty_like(inp)
+    err = torch.zeros(64, dtype=torch.int32, device=inp.device)
+    _check(_lib.ws_tcn_conv64(_ptr(inp), _ptr(wplanes), _ptr(bias), _ptr(mask), _ptr(out), rows, T, mode, _ptr(err),
+                              _stream_ptr(stream)))
+    return out, err
