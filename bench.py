@@ -45,6 +45,8 @@ def parse_args():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-ragged", action="store_true")
     ap.add_argument("--no-gcv", action="store_true")
+    ap.add_argument("--no-learned", action="store_true")
+    ap.add_argument("--tcn-ckpt", default=None, help="trained lambda network (else one epoch is trained first)")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU work of the oracle baseline")
     return ap.parse_args()
 
@@ -240,6 +242,59 @@ def gcv_measure(dev, steps):
            "lambda_evals_per_s": 16 * P / (ms / 1e3),
            "series_with_status": int((st != 0).sum().item())}
     del out, x, w, z, lam_best, st
+    torch.cuda.empty_cache()
+    return res
+
+
+def learned_measure(dev, steps, ckpt=None, train_epochs=1.0):
+    """Learned lambda vs the GCV grid on the evaluation set (262,144 new series x 730 days,
+    d = 2, one band): the lambda network is trained first on the project's kernels (one
+    epoch of 2,097,152 series in batches of 4096) unless a checkpoint is given. Timed: the
+    network's forward plus the smoothing at its per-day lambda, against ws_gcv_smooth."""
+    import math
+
+    import torch
+
+    from paper_2604_00048_b300 import synth, train, ws
+
+    t0 = time.time()
+    if ckpt:
+        net, _ = train.load_checkpoint(ckpt, device=dev)
+        trained = {"checkpoint": os.path.basename(ckpt)}
+    else:
+        net, nb, hist = train.train(2097152, 4096, train_epochs, 2e-3, seed=0, log_every=10 ** 9, device=dev)
+        torch.cuda.synchronize()
+        trained = {"batches": nb, "batch": 4096, "epochs": train_epochs, "train_s": time.time() - t0}
+    P, T = 262144, 730
+    base = synth.RECIPES["learned"]
+    rc = synth.Recipe(**{**base.__dict__, "seed": base.seed + 1000, "T": T})
+    out = synth.generate_tile(rc, P, device=dev, want_clean=True)
+    x, w, clean = out["x"], out["w"], out["clean"][:, 0, :].contiguous()
+    del out
+
+    def timed(fn):
+        fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(steps):
+            r = fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / steps, r
+
+    ms_l, (zl, lam, _) = timed(lambda: train.learned_smooth(net, x, w))
+    ms_tcn, _ = timed(lambda: net.forward(x[:, 0, :], w))
+    ms_g, (zg, _, _, _) = timed(lambda: ws.gcv_smooth(x, w, None, 2, want_scores=False))
+    rl, rg = train.rmse(zl, clean), train.rmse(zg, clean)
+    flop = 150912.0 * P * T  # network multiply-adds x 2 per position
+    res = {"workload": f"learned lambda vs GCV: {P} new series x {T} days, d=2, 1 band",
+           "learned_ms": ms_l, "tcn_forward_ms": ms_tcn, "gcv_ms": ms_g,
+           "learned_series_per_s": P / (ms_l / 1e3), "gcv_series_per_s": P / (ms_g / 1e3),
+           "learned_faster_than_gcv": ms_l < ms_g,
+           "tcn_tflops": flop / (ms_tcn / 1e3) / 1e12,
+           "rmse_learned": rl, "rmse_gcv": rg, "rmse_ratio": rl / rg, "training": trained}
+    del x, w, clean, zl, zg, lam
     torch.cuda.empty_cache()
     return res
 
@@ -441,6 +496,7 @@ def run_ours(args):
         torch.cuda.empty_cache()
         ragged = ragged_measure(dev, max(3, args.steps))
     gcv = None if args.no_gcv else gcv_measure(dev, max(3, args.steps))
+    learned = None if args.no_learned else learned_measure(dev, max(3, args.steps), args.tcn_ckpt)
     line = {"metric": METRIC, "value": value, "unit": "series/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
@@ -452,7 +508,7 @@ def run_ours(args):
             "fwd_series_per_s": P * world / ((fwd_ms + ref_ms) / 1e3),
             "fwd_unrefined_series_per_s": P * world / (fwd_ms / 1e3),
             "smooth_ms": fwd_ms, "refine_ms": ref_ms, "adjoint_ms": bwd_ms,
-            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "ragged": ragged, "gcv": gcv,
+            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "ragged": ragged, "gcv": gcv, "learned": learned,
             "gpu_launches": launches_per_step * args.steps, "clocks": ck,
             "series_with_status": bad}
     if rank == 0:

@@ -142,7 +142,7 @@ int ws_gcv_smooth(const ws_problem* pb, const void* x, const void* w, const floa
  * b4 [1]. ws_tcn_pack writes the BF16 copy (WS_TCN_PACKED_BYTES) the kernels read; biases are
  * read from the master. All pointers are device pointers. */
 #define WS_TCN_PARAMS 75649
-#define WS_TCN_PACKED_BYTES 298368
+#define WS_TCN_PACKED_BYTES 304512
 typedef struct ws_tcn_batch {
   int32_t T;            /* days per series */
   int32_t n_series;     /* P: series of the [T][P] inputs */

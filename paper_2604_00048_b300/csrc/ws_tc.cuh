@@ -26,6 +26,20 @@ __device__ __forceinline__ uint64_t umma_desc(uint32_t saddr, uint32_t lbo, uint
   return d;
 }
 
+// The same for the 128-byte swizzled K-major layout (layout type 2): rows of 128 bytes
+// (64 BF16 along K), 8-row atoms of 1024 bytes in which the 16-byte chunk c of row r sits at
+// chunk position c ^ (r % 8); SBO = 1024 between 8-row groups, LBO unused (16). A K-slice
+// of 16 elements starts 32 bytes further along the row.
+__device__ __forceinline__ uint64_t umma_desc_sw128(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
+  d |= (uint64_t)1u << 16;
+  d |= (uint64_t)(1024u >> 4) << 32;
+  d |= (uint64_t)1u << 46;
+  d |= (uint64_t)2u << 61;
+  return d;
+}
+
 // Instruction descriptor of kind::f16 with BF16 A and B, FP32 accumulation, both operands
 // K-major: D format (bits 4-5) = F32, A format (7-9) = BF16, B format (10-12) = BF16,
 // N >> 3 in bits 17-22, M >> 4 in bits 24-28.

@@ -13,10 +13,10 @@
 //
 // Kernels:
 //   k_tcn_in      (x, w) in the [T][P] tile layout -> in0[R][2] (BF16), zero on gaps
-//   k_tcn_l1      layer 1 (2 -> 64) on CUDA cores, + bias, ReLU            (2.3 kFLOP / row)
-//   k_conv64      layers 2, 3 (64 -> 64): tcgen05 MMAs, BF16 x BF16 -> FP32 in TMEM (147 kFLOP /
-//                 row for both); also the data gradient of those layers (flipped weights)
-//   k_tcn_l4      layer 4 (64 -> 1) + sigmoid range -> lambda, log lambda in [T][P]
+//   k_tcn_fused   the forward: all four layers per tile on the tensor cores (tcgen05, BF16 x
+//                 BF16 -> FP32 in TMEM, ~151 kFLOP / row), sigmoid range -> lambda in [T][P]
+//   k_conv64      one 64 -> 64 layer on the tensor cores; the backward uses it for the data
+//                 gradients of layers 3 and 2 (flipped, transposed weights)
 //   backward      d o, layer-4 data gradient, weight gradients (CUDA cores), Adam
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
@@ -47,9 +47,12 @@ constexpr int kOW1 = 0, kOB1 = kOW1 + kCh * 2 * kTaps, kOW2 = kOB1 + kCh, kOB2 =
               kNParams = kOB4 + 1;
 static_assert(kNParams == WS_TCN_PARAMS, "parameter count");
 // packed BF16 buffer (elements): W1 [co][c][k], W2 fwd, W2 bwd, W3 fwd, W3 bwd ([tap][chunk][row][8]), W4 [ci][k]
+// + tensor-core copies of W1 (K = 2 x 9 -> 32: [4 chunks][64 co][8]) and W4 as taps x channels
+// ([16 rows: tap 0..8, zero beyond][64 ci])
 constexpr int kPW1 = 0, kPW2F = kPW1 + kCh * 2 * kTaps, kPW2B = kPW2F + kCh * kCh * kTaps,
               kPW3F = kPW2B + kCh * kCh * kTaps, kPW3B = kPW3F + kCh * kCh * kTaps,
-              kPW4 = kPW3B + kCh * kCh * kTaps, kPackedElems = kPW4 + kCh * kTaps;
+              kPW4 = kPW3B + kCh * kCh * kTaps, kPW1T = kPW4 + kCh * kTaps, kPW4T = kPW1T + 4 * kCh * 8,
+              kPackedElems = kPW4T + 16 * kCh;
 static_assert(WS_TCN_PACKED_BYTES == kPackedElems * 2, "packed size");
 
 __device__ __forceinline__ bool is_gap(int64_t r, int T) { return (int)(r % (T + kGap)) >= T; }
@@ -74,48 +77,6 @@ __global__ void k_tcn_in(const float* __restrict__ x, const float* __restrict__ 
     xv = wv > 0.f ? x[(size_t)t * P + s] : 0.f;
   }
   in0[r] = pack_bf16x2(xv, wv);
-}
-
-// Layer 1 (2 -> 64): one thread per row, ReLU, zero on gaps. W1 BF16 [co][c][k], b1 FP32.
-__global__ void __launch_bounds__(128) k_tcn_l1(const uint32_t* __restrict__ in0, const __nv_bfloat16* __restrict__ w1,
-                                                const float* __restrict__ b1, uint4* __restrict__ a1, int T, int64_t R) {
-  __shared__ float sw[kCh * 2 * kTaps];
-  __shared__ float sb[kCh];
-  for (int i = threadIdx.x; i < kCh * 2 * kTaps; i += blockDim.x) sw[i] = __bfloat162float(w1[i]);
-  for (int i = threadIdx.x; i < kCh; i += blockDim.x) sb[i] = b1[i];
-  __syncthreads();
-  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (r >= R) return;
-  uint4* out = a1 + r * 8;
-  if (is_gap(r, T)) {
-    for (int j = 0; j < 8; ++j) out[j] = make_uint4(0, 0, 0, 0);
-    return;
-  }
-  float in[kTaps][2];
-#pragma unroll
-  for (int k = 0; k < kTaps; ++k) {
-    const int64_t rr = r + k - kHalf;
-    const uint32_t u = (rr >= 0 && rr < R) ? in0[rr] : 0u;
-    in[k][0] = bf16_lo(u);
-    in[k][1] = bf16_hi(u);
-  }
-#pragma unroll
-  for (int j = 0; j < 8; ++j) {
-    float v[8];
-#pragma unroll
-    for (int e = 0; e < 8; ++e) {
-      const int co = 8 * j + e;
-      float acc = sb[co];
-#pragma unroll
-      for (int k = 0; k < kTaps; ++k) {
-        acc = fmaf(sw[(co * 2 + 0) * kTaps + k], in[k][0], acc);
-        acc = fmaf(sw[(co * 2 + 1) * kTaps + k], in[k][1], acc);
-      }
-      v[e] = fmaxf(acc, 0.f);
-    }
-    out[j] = make_uint4(pack_bf16x2(v[0], v[1]), pack_bf16x2(v[2], v[3]), pack_bf16x2(v[4], v[5]),
-                        pack_bf16x2(v[6], v[7]));
-  }
 }
 
 // ---------------------------------------------------------------------------------------
@@ -160,8 +121,12 @@ __global__ void __launch_bounds__(kConvThreads, 1) k_conv64(const ConvArgs a) {
     tmem_alloc(tslot, kTmemCols);
     tmem_relinquish();
   }
-  // weights once per CTA
-  for (int i = tid; i < kWBytes / 16; i += kConvThreads) cp_async16(wts + 16 * i, a.wp + i, true);
+  // weights once per CTA: plane layout in global ([tap][chunk][row][8]) -> 128-byte swizzled
+  // rows in shared memory ([tap][row][chunk ^ (row % 8)])
+  for (int i = tid; i < kWBytes / 16; i += kConvThreads) {
+    const int row = i & 63, chunk = (i >> 6) & 7, tap = i >> 9;
+    cp_async16(wts + tap * 8192 + row * 128 + ((chunk ^ (row & 7)) << 4), a.wp + i, true);
+  }
   cp_async_commit();
   tc_fence_before();
   __syncthreads();
@@ -173,12 +138,13 @@ __global__ void __launch_bounds__(kConvThreads, 1) k_conv64(const ConvArgs a) {
 
   for (int tile = blockIdx.x; tile < a.n_tiles; tile += gridDim.x) {
     const int64_t r0 = (int64_t)tile * kTileRows;
-    // stage input rows r0 - 4 .. r0 + 387 as planes: chunk j of row i -> act + j * kPlaneBytes + 16 i
+    // stage input rows r0 - 4 .. r0 + 387, 128-byte swizzled: chunk j of row i at
+    // act + 128 i + 16 (j ^ (i % 8))
     for (int e = tid; e < kInRows * 8; e += kConvThreads) {
       const int i = e >> 3, j = e & 7;
       const int64_t r = r0 - kHalf + i;
       const bool v = r >= 0 && r < a.R;
-      cp_async16(act + j * kPlaneBytes + 16 * i, a.in + (v ? r * 8 + j : 0), v);
+      cp_async16(act + 128 * i + ((j ^ (i & 7)) << 4), a.in + (v ? r * 8 + j : 0), v);
     }
     cp_async_commit();
     cp_async_wait<0>();
@@ -191,9 +157,8 @@ __global__ void __launch_bounds__(kConvThreads, 1) k_conv64(const ConvArgs a) {
         for (int tap = 0; tap < kTaps; ++tap) {
 #pragma unroll
           for (int s = 0; s < 4; ++s) {
-            const uint64_t ad = umma_desc(act_s + (uint32_t)(2 * s * kPlaneBytes) + (uint32_t)((b * 128 + tap) * 16),
-                                          kPlaneBytes, 128);
-            const uint64_t bd = umma_desc(wts_s + (uint32_t)((tap * 8 + 2 * s) * kCh * 16), kCh * 16, 128);
+            const uint64_t ad = umma_desc_sw128(act_s + (uint32_t)((b * 128 + tap) * 128 + 32 * s));
+            const uint64_t bd = umma_desc_sw128(wts_s + (uint32_t)(tap * 8192 + 32 * s));
             umma_bf16(d, ad, bd, idesc, (tap | s) != 0);
           }
         }
@@ -260,41 +225,269 @@ __global__ void __launch_bounds__(kConvThreads, 1) k_conv64(const ConvArgs a) {
 }
 
 // ---------------------------------------------------------------------------------------
-// Layer 4 (64 -> 1) and the sigmoid range: one thread per row.
-__global__ void __launch_bounds__(128) k_tcn_l4(const uint4* __restrict__ a3, const __nv_bfloat16* __restrict__ w4,
-                                                const float* __restrict__ b4, float* __restrict__ lam,
-                                                float* __restrict__ loglam, float* __restrict__ o_out, int T, int P,
-                                                int64_t R, float lmin, float lmax) {
-  __shared__ float sw[kCh * kTaps];
-  for (int i = threadIdx.x; i < kCh * kTaps; i += blockDim.x) sw[i] = __bfloat162float(w4[i]);
-  __syncthreads();
-  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (r >= R) return;
-  const int s = (int)(r / (T + kGap)), t = (int)(r % (T + kGap));
-  if (t >= T) {
-    if (o_out) o_out[r] = 0.f;
-    return;
+// Fused forward: the four layers of one tile of 384 computed rows, activations kept in
+// shared memory, all weights resident (one CTA per SM).
+//   layer 1: tensor cores, im2col of the 2 input channels x 9 taps (K = 18 padded to 32)
+//   layers 2, 3: tensor cores, 9 taps x 4 K-steps of M128 x N64 x K16, operands read in place
+//   layer 4 (64 -> 1): the per-tap products P[r][tap] = sum_ci a3[r][ci] W4[ci][tap] as one
+//     unshifted M128 x N16 GEMM (4 K-steps per M-block, taps along N), then the shift on the
+//     output side, o[r] = b4 + sum_tap P[r + tap - 4][tap], through shared memory. (Shifting
+//     the input instead takes 36 N = 16 MMAs per M-block, each reading the 4 KB A operand.)
+// Activations live in the 128-byte swizzled K-major layout (row r's 64 channels in 128 bytes,
+// 16-byte chunk c at position c ^ (r % 8)): a tap shift is a start address 128 bytes further.
+// Each layer's epilogue (TMEM -> registers -> bias, ReLU -> BF16) writes over the layer's
+// input after its MMAs have completed. A layer is exact 4 rows less deep at each end of the
+// tile, so of the 384 computed rows the middle 352 (rows 16 .. 367) are final.
+constexpr int kFuseUseful = kTileRows - 32;
+constexpr int kFuseThreads = 512;                  // 16 warps: four per TMEM lane quarter
+constexpr int kActSw = kInRows * 128;              // 50,176: swizzled activation rows
+constexpr int kImPlane = kTileRows * 16;           // 6144: one 8-wide K chunk of the im2col
+constexpr int kW1TBytes = 4 * kCh * 16;            // 4096
+constexpr int kWSwBytes = kTaps * kCh * 128;       // 73,728: [tap][row][128 B swizzled]
+constexpr int kFW2 = kActSw, kFW3 = kFW2 + kWSwBytes, kFW4 = kFW3 + kWSwBytes, kFW1 = kFW4 + 16 * 128,
+              kFP = kFW1 + kW1TBytes, kFIn = kFP + kTileRows * kTaps * 4, kFBar = kFIn + kInRows * 4,
+              kFBias = kFBar + 16, kFSmem = kFBias + (3 * kCh + 4) * 4;
+
+struct FusedArgs {
+  const uint32_t* in0;
+  const uint4 *w1t, *w2, *w3;
+  const __nv_bfloat16* w4t;  // [16 tap rows][64 ci]
+  const float* master;
+  float* lam;
+  float* loglam;
+  float* o_out;
+  uint4 *a1, *a2, *a3;  // training: activations of the final rows
+  int64_t R;
+  int T, P, n_tiles;
+  float lmin, lmax;
+  unsigned* err;
+};
+
+__global__ void __launch_bounds__(kFuseThreads, 1) k_tcn_fused(const FusedArgs a) {
+  extern __shared__ __align__(1024) unsigned char smem[];
+  unsigned char* act = smem;
+  float* sP = reinterpret_cast<float*>(smem + kFP);    // [384][9] layer-4 per-tap products
+  uint32_t* sin0 = reinterpret_cast<uint32_t*>(smem + kFIn);
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem + kFBar);
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(smem + kFBar + 8);
+  int* sflag = reinterpret_cast<int*>(smem + kFBar + 12);
+  float* sb = reinterpret_cast<float*>(smem + kFBias);  // b1 | b2 | b3 | b4
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, quarter = warp & 3, part = warp >> 2;
+
+  if (tid == 0) {
+    mbar_init(bar, 1);
+    fence_mbar_init();
+    *sflag = 0;
   }
-  float acc = b4[0];
-  for (int k = 0; k < kTaps; ++k) {
-    const int64_t rr = r + k - kHalf;
-    if (rr < 0 || rr >= R) continue;
+  if (warp == 0) {
+    tmem_alloc(tslot, kTmemCols);
+    tmem_relinquish();
+  }
+  // W2, W3: plane layout in global ([tap][chunk][row][8]) -> swizzled rows
+  for (int i = tid; i < kWBytes / 16; i += kFuseThreads) {
+    const int row = i & 63, chunk = (i >> 6) & 7, tap = i >> 9;
+    const int dst = tap * 8192 + row * 128 + ((chunk ^ (row & 7)) << 4);
+    cp_async16(smem + kFW2 + dst, a.w2 + i, true);
+    cp_async16(smem + kFW3 + dst, a.w3 + i, true);
+  }
+  for (int i = tid; i < kW1TBytes / 16; i += kFuseThreads) cp_async16(smem + kFW1 + 16 * i, a.w1t + i, true);
+  for (int i = tid; i < 16 * 8; i += kFuseThreads) {  // W4T rows (taps) of 8 chunks, swizzled
+    const int row = i >> 3, chunk = i & 7;
+    cp_async16(smem + kFW4 + row * 128 + ((chunk ^ (row & 7)) << 4), reinterpret_cast<const uint4*>(a.w4t) + i, true);
+  }
+  cp_async_commit();
+  for (int i = tid; i < kActSw / 16; i += kFuseThreads) reinterpret_cast<uint4*>(act)[i] = make_uint4(0, 0, 0, 0);
+  for (int i = tid; i < 3 * kCh; i += kFuseThreads)
+    sb[i] = a.master[(i >> 6) == 0 ? kOB1 + i : (i >> 6) == 1 ? kOB2 + i - 64 : kOB3 + i - 128];
+  if (tid == 0) sb[3 * kCh] = a.master[kOB4];
+  cp_async_wait<0>();
+  fence_proxy_async_smem();
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tslot;
+  const uint32_t id64 = umma_idesc_bf16(128, 64);
+  const uint32_t act_s = smem_u32(act);
+  const uint64_t im_desc = umma_desc(act_s, kImPlane, 128);  // layer 1's im2col planes (no swizzle)
+  const uint64_t w1d = umma_desc(smem_u32(smem + kFW1), kCh * 16, 128);
+  const uint64_t act_d = umma_desc_sw128(act_s);
+  const uint64_t w2d = umma_desc_sw128(smem_u32(smem + kFW2)), w3d = umma_desc_sw128(smem_u32(smem + kFW3));
+  const uint64_t w4d = umma_desc_sw128(smem_u32(smem + kFW4));
+  const uint32_t id16 = umma_idesc_bf16(128, 16);
+  uint32_t phase = 0;
+
+  auto wait_mma = [&]() -> bool {
+    if (tid == 0 && !mbar_wait_bounded(bar, phase)) {
+      atomicOr(a.err, kDevErrTimeout);
+      *sflag = 1;
+    }
+    __syncthreads();
+    phase ^= 1u;
+    tc_fence_after();
+    return *sflag == 0;
+  };
+  // 64 -> 64 layer: 3 M-blocks x 9 taps x 4 K-steps (descriptor = base + start >> 4)
+  auto issue_conv = [&](uint64_t wd) {
+    if (tid == 0) {
+      tc_fence_after();
+#pragma unroll 1
+      for (int b = 0; b < 3; ++b)
 #pragma unroll
-    for (int j = 0; j < 8; ++j) {
-      const uint4 u = a3[rr * 8 + j];
-      const uint32_t uu[4] = {u.x, u.y, u.z, u.w};
+        for (int tap = 0; tap < kTaps; ++tap)
 #pragma unroll
-      for (int e = 0; e < 4; ++e) {
-        acc = fmaf(sw[(8 * j + 2 * e) * kTaps + k], bf16_lo(uu[e]), acc);
-        acc = fmaf(sw[(8 * j + 2 * e + 1) * kTaps + k], bf16_hi(uu[e]), acc);
+          for (int s = 0; s < 4; ++s)
+            umma_bf16(tmem + (uint32_t)(b * 64), act_d + (uint64_t)(((b * 128 + tap) * 128 + 32 * s) >> 4),
+                      wd + (uint64_t)((tap * 8192 + 32 * s) >> 4), id64, (tap | s) != 0);
+      umma_commit(bar);
+    }
+  };
+
+  const int period = a.T + kGap;
+  bool rowok[3];
+  int rs[3], rt[3];
+  // epilogue of a 64-channel layer: bias, ReLU, zero off-series; in place at buffer row + 4.
+  // With l4, also the layer-4 partial sums of this row's 16 channels.
+  auto epi64 = [&](int64_t r0, const float* bias_s, uint4* store) {
+    float bias[16];
+#pragma unroll
+    for (int c = 0; c < 16; ++c) bias[c] = bias_s[part * 16 + c];
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+      const int row = b * 128 + quarter * 32 + lane;
+      const int64_t r = r0 + row;
+      uint32_t v[16];
+      tmem_ld16(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(b * 64 + part * 16), v);
+      tmem_ld_wait();
+      const bool zero = !rowok[b];
+      uint4 q[2];
+#pragma unroll
+      for (int j = 0; j < 2; ++j) {
+        float f[8];
+#pragma unroll
+        for (int e = 0; e < 8; ++e) f[e] = zero ? 0.f : fmaxf(__uint_as_float(v[8 * j + e]) + bias[8 * j + e], 0.f);
+        q[j] = make_uint4(pack_bf16x2(f[0], f[1]), pack_bf16x2(f[2], f[3]), pack_bf16x2(f[4], f[5]),
+                          pack_bf16x2(f[6], f[7]));
+        const int srow = row + kHalf, chunk = part * 2 + j;
+        *reinterpret_cast<uint4*>(act + srow * 128 + ((chunk ^ (srow & 7)) << 4)) = q[j];
+      }
+      if (store != nullptr && row >= 16 && row < 16 + kFuseUseful && r >= 0 && r < a.R)
+#pragma unroll
+        for (int j = 0; j < 2; ++j) store[r * 8 + part * 2 + j] = q[j];
+    }
+    fence_proxy_async_smem();
+    tc_fence_before();
+    __syncthreads();
+  };
+
+  for (int tile = blockIdx.x; tile < a.n_tiles; tile += gridDim.x) {
+    const int64_t r0 = (int64_t)tile * kFuseUseful - 16;  // first computed row
+    {
+      const int64_t rb = r0 < 0 ? 0 : r0;
+      const int64_t sb0 = rb / period;  // one 64-bit division per tile, 32-bit math after
+      const int tb0 = (int)(rb - sb0 * period);
+#pragma unroll
+      for (int b = 0; b < 3; ++b) {
+        const int64_t r = r0 + b * 128 + quarter * 32 + lane;
+        const int off = tb0 + (int)(r - rb);
+        const int q = off / period;
+        rs[b] = (int)(sb0 + q);
+        rt[b] = off - q * period;
+        rowok[b] = r >= 0 && r < a.R && rt[b] < a.T;
       }
     }
+    for (int i = tid; i < kInRows; i += kFuseThreads) {
+      const int64_t r = r0 - kHalf + i;
+      sin0[i] = (r >= 0 && r < a.R) ? a.in0[r] : 0u;
+    }
+    __syncthreads();
+    // im2col of layer 1: row i, K index kk = 2 tap + c (c = 0: x, 1: w), 4 chunks of 8
+    for (int e = tid; e < kTileRows * 4; e += kFuseThreads) {
+      const int i = e >> 2, j = e & 3;
+      uint32_t u[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        float f[2];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const int kk = 8 * j + 2 * q + h;
+          const uint32_t src = kk < 2 * kTaps ? sin0[i + (kk >> 1)] : 0u;
+          f[h] = (kk & 1) ? bf16_hi(src) : bf16_lo(src);
+        }
+        u[q] = pack_bf16x2(f[0], f[1]);
+      }
+      *reinterpret_cast<uint4*>(act + j * kImPlane + i * 16) = make_uint4(u[0], u[1], u[2], u[3]);
+    }
+    fence_proxy_async_smem();
+    __syncthreads();
+    if (tid == 0) {
+      tc_fence_after();
+      for (int b = 0; b < 3; ++b)
+#pragma unroll
+        for (int s = 0; s < 2; ++s)
+          umma_bf16(tmem + (uint32_t)(b * 64), im_desc + (uint64_t)((2 * s * kImPlane + b * 128 * 16) >> 4),
+                    w1d + (uint64_t)((2 * s * kCh * 16) >> 4), id64, s != 0);
+      umma_commit(bar);
+    }
+    if (!wait_mma()) break;
+    epi64(r0, sb, a.a1);
+    issue_conv(w2d);
+    if (!wait_mma()) break;
+    epi64(r0, sb + kCh, a.a2);
+    issue_conv(w3d);
+    if (!wait_mma()) break;
+    epi64(r0, sb + 2 * kCh, a.a3);
+    // layer 4: P[row][tap] on the tensor cores (A = a3 rows, unshifted: buffer row + 4)
+    if (tid == 0) {
+      tc_fence_after();
+      for (int b = 0; b < 3; ++b)
+#pragma unroll
+        for (int s = 0; s < 4; ++s)
+          umma_bf16(tmem + (uint32_t)(b * 64), act_d + (uint64_t)(((b * 128 + kHalf) * 128 + 32 * s) >> 4),
+                    w4d + (uint64_t)((32 * s) >> 4), id16, s != 0);
+      umma_commit(bar);
+    }
+    if (!wait_mma()) break;
+    if (part == 0) {
+#pragma unroll
+      for (int b = 0; b < 3; ++b) {
+        const int row = b * 128 + quarter * 32 + lane;
+        uint32_t v[16];
+        tmem_ld16(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(b * 64), v);
+        tmem_ld_wait();
+#pragma unroll
+        for (int tap = 0; tap < kTaps; ++tap) sP[row * kTaps + tap] = __uint_as_float(v[tap]);
+      }
+    }
+    tc_fence_before();
+    __syncthreads();
+    // o[row] = b4 + sum_tap P[row + tap - 4][tap] for the final rows
+    if (part == 0) {
+#pragma unroll
+      for (int b = 0; b < 3; ++b) {
+        const int row = b * 128 + quarter * 32 + lane;
+        const int64_t r = r0 + row;
+        if (row < 16 || row >= 16 + kFuseUseful || r < 0 || r >= a.R) continue;
+        if (!rowok[b]) {
+          if (a.o_out) a.o_out[r] = 0.f;
+          continue;
+        }
+        float o = sb[3 * kCh];
+#pragma unroll
+        for (int tap = 0; tap < kTaps; ++tap) o += sP[(row + tap - kHalf) * kTaps + tap];
+        const float sg = 1.f / (1.f + expf(-o));
+        const float ll = a.lmin + sg * (a.lmax - a.lmin);
+        a.lam[(size_t)rt[b] * a.P + rs[b]] = expf(ll);
+        if (a.loglam) a.loglam[(size_t)rt[b] * a.P + rs[b]] = ll;
+        if (a.o_out) a.o_out[r] = o;
+      }
+    }
+    __syncthreads();
   }
-  const float sg = 1.f / (1.f + expf(-acc));
-  const float ll = lmin + sg * (lmax - lmin);
-  lam[(size_t)t * P + s] = expf(ll);
-  if (loglam) loglam[(size_t)t * P + s] = ll;
-  if (o_out) o_out[r] = acc;
+  __syncthreads();
+  if (*sflag && tid == 0) mbar_wait_bounded(bar, phase);  // let MMAs in flight drain before freeing TMEM
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 0) tmem_dealloc(tmem, kTmemCols);
 }
 
 // ---------------------------------------------------------------------------------------
@@ -509,6 +702,14 @@ __global__ void k_tcn_pack(const float* __restrict__ m, __nv_bfloat16* __restric
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < kCh * 2 * kTaps) p[kPW1 + i] = __float2bfloat16_rn(m[kOW1 + i]);
   if (i < kCh * kTaps) p[kPW4 + i] = __float2bfloat16_rn(m[kOW4 + i]);
+  if (i < 4 * kCh * 8) {  // W1 for the tensor cores: K index kk = 2 tap + c, zero beyond 18
+    const int e = i & 7, co = (i >> 3) & 63, chunk = i >> 9, kk = 8 * chunk + e;
+    p[kPW1T + i] = __float2bfloat16_rn(kk < 2 * kTaps ? m[kOW1 + (co * 2 + (kk & 1)) * kTaps + (kk >> 1)] : 0.f);
+  }
+  if (i < 16 * kCh) {  // W4 for the tensor cores: row = tap (zero beyond 8), column = ci
+    const int ci = i & 63, tap = i >> 6;
+    p[kPW4T + i] = __float2bfloat16_rn(tap < kTaps ? m[kOW4 + ci * kTaps + tap] : 0.f);
+  }
   if (i < kCh * kCh * kTaps) {
     // plane index i = ((tap * 8 + chunk) * 64 + row) * 8 + e
     const int e = i & 7, row = (i >> 3) & 63, chunk = (i >> 9) & 7, tap = i >> 12;
@@ -592,11 +793,12 @@ size_t tcn_scratch_bytes(const ws_tcn_batch* b, int training, TcnScratch* s, voi
   TcnScratch t;
   t.err = p ? reinterpret_cast<unsigned*>(p) : nullptr;
   t.in0 = static_cast<uint32_t*>(take((size_t)R * 4));
-  t.a1 = static_cast<uint4*>(take((size_t)R * 128));
-  t.a2 = static_cast<uint4*>(take((size_t)R * 128));
-  t.a3 = training ? static_cast<uint4*>(take((size_t)R * 128)) : t.a1;  // inference reuses a1 for layer 3
   t.o = static_cast<float*>(take((size_t)R * 4));
-  if (training) {
+  t.a1 = t.a2 = t.a3 = nullptr;
+  if (training) {  // activations of every layer for the backward pass
+    t.a1 = static_cast<uint4*>(take((size_t)R * 128));
+    t.a2 = static_cast<uint4*>(take((size_t)R * 128));
+    t.a3 = static_cast<uint4*>(take((size_t)R * 128));
     t.dha = static_cast<uint4*>(take((size_t)R * 128));
     t.dhb = static_cast<uint4*>(take((size_t)R * 128));
     t.dout = static_cast<float*>(take((size_t)R * 4));
@@ -681,13 +883,31 @@ extern "C" int ws_tcn_forward(const ws_tcn_batch* b, const void* packed, const f
   const int64_t R = tcn_rows(b);
   const __nv_bfloat16* pk = static_cast<const __nv_bfloat16*>(packed);
   k_tcn_in<<<grid_for(R, 256), 256, 0, st>>>(x, w, s.in0, b->T, b->n_series, R);
-  k_tcn_l1<<<grid_for(R, 128), 128, 0, st>>>(s.in0, pk + kPW1, master + kOB1, s.a1, b->T, R);
-  if ((rc = conv_launch(CONV_FWD, s.a1, pk + kPW2F, master + kOB2, nullptr, s.a2, R, b->T, s.err, st)) != WS_OK)
-    return rc;
-  if ((rc = conv_launch(CONV_FWD, s.a2, pk + kPW3F, master + kOB3, nullptr, s.a3, R, b->T, s.err, st)) != WS_OK)
-    return rc;
-  k_tcn_l4<<<grid_for(R, 128), 128, 0, st>>>(s.a3, pk + kPW4, master + kOB4, lam, loglam, s.o, b->T, b->n_series,
-                                             R, b->log_lam_min, b->log_lam_max);
+  DeviceInfo di;
+  if ((rc = device_info(di)) != WS_OK) return rc;
+  if (cudaFuncSetAttribute(k_tcn_fused, cudaFuncAttributeMaxDynamicSharedMemorySize, kFSmem) != cudaSuccess)
+    return set_error(WS_ECUDA, "tcn: shared memory attribute");
+  FusedArgs fa;
+  fa.in0 = s.in0;
+  fa.w1t = reinterpret_cast<const uint4*>(pk + kPW1T);
+  fa.w2 = reinterpret_cast<const uint4*>(pk + kPW2F);
+  fa.w3 = reinterpret_cast<const uint4*>(pk + kPW3F);
+  fa.w4t = pk + kPW4T;
+  fa.master = master;
+  fa.lam = lam;
+  fa.loglam = loglam;
+  fa.o_out = s.o;
+  fa.a1 = s.a1;
+  fa.a2 = s.a2;
+  fa.a3 = s.a3;
+  fa.R = R;
+  fa.T = b->T;
+  fa.P = b->n_series;
+  fa.n_tiles = (int)((R + kFuseUseful - 1) / kFuseUseful);
+  fa.lmin = b->log_lam_min;
+  fa.lmax = b->log_lam_max;
+  fa.err = s.err;
+  k_tcn_fused<<<std::max(1, std::min(fa.n_tiles, di.sm_count)), kFuseThreads, kFSmem, st>>>(fa);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return set_error(WS_ECUDA, "tcn forward launch: %s", cudaGetErrorString(e));
   return WS_OK;

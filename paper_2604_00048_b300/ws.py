@@ -385,7 +385,7 @@ class TcnBatch(ctypes.Structure):
                 ("log_lam_max", ctypes.c_float)]
 
 
-TCN_PARAMS, TCN_PACKED_BYTES, TCN_GAP = 75649, 298368, 4
+TCN_PARAMS, TCN_PACKED_BYTES, TCN_GAP = 75649, 304512, 4
 TCN_LOG_LAM = (float(np.log(1e-1)), float(np.log(1e6)))
 _TB = ctypes.POINTER(TcnBatch)
 _lib.ws_tcn_scratch_size.restype = _sz
