@@ -345,19 +345,28 @@ __global__ void __launch_bounds__(kFuseThreads, 1) k_tcn_fused(const FusedArgs a
   const int period = a.T + kGap;
   bool rowok[3];
   int rs[3], rt[3];
+  // the next tile's input rows are loaded into a register while the current tile computes
+  auto load_in0 = [&](int tl) -> uint32_t {
+    const int64_t r = (int64_t)tl * kFuseUseful - 16 - kHalf + tid;
+    return (tid < kInRows && tl < a.n_tiles && r >= 0 && r < a.R) ? a.in0[r] : 0u;
+  };
+  static_assert(kInRows <= kFuseThreads, "one staged input row per thread");
+  uint32_t in_next = load_in0(blockIdx.x);
   // epilogue of a 64-channel layer: bias, ReLU, zero off-series; in place at buffer row + 4.
   // With l4, also the layer-4 partial sums of this row's 16 channels.
   auto epi64 = [&](int64_t r0, const float* bias_s, uint4* store) {
     float bias[16];
 #pragma unroll
     for (int c = 0; c < 16; ++c) bias[c] = bias_s[part * 16 + c];
+    uint32_t vv[3][16];
+#pragma unroll
+    for (int b = 0; b < 3; ++b) tmem_ld16(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(b * 64 + part * 16), vv[b]);
+    tmem_ld_wait();
 #pragma unroll
     for (int b = 0; b < 3; ++b) {
       const int row = b * 128 + quarter * 32 + lane;
       const int64_t r = r0 + row;
-      uint32_t v[16];
-      tmem_ld16(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(b * 64 + part * 16), v);
-      tmem_ld_wait();
+      const uint32_t* v = vv[b];
       const bool zero = !rowok[b];
       uint4 q[2];
 #pragma unroll
@@ -395,10 +404,8 @@ __global__ void __launch_bounds__(kFuseThreads, 1) k_tcn_fused(const FusedArgs a
         rowok[b] = r >= 0 && r < a.R && rt[b] < a.T;
       }
     }
-    for (int i = tid; i < kInRows; i += kFuseThreads) {
-      const int64_t r = r0 - kHalf + i;
-      sin0[i] = (r >= 0 && r < a.R) ? a.in0[r] : 0u;
-    }
+    if (tid < kInRows) sin0[tid] = in_next;
+    in_next = load_in0(tile + gridDim.x);
     __syncthreads();
     // im2col of layer 1: row i, K index kk = 2 tap + c (c = 0: x, 1: w), 4 chunks of 8
     for (int e = tid; e < kTileRows * 4; e += kFuseThreads) {
