@@ -46,54 +46,80 @@ __global__ void __launch_bounds__(128) k_residual(const F* __restrict__ x, const
       zr[j][n] = F(0);
       qb[j][n] = F(0);
     }
-  for (int u = t0 - D; u < t1 + D; ++u) {
-    const int k = u - D;  // difference row whose last day is u
-    const bool row = k >= 0 && k <= T - D - 1;
-    const F lk = row ? (lam_scalar ? ls : lam[(size_t)k * sP + p]) : F(0);
-    const int t = k;      // residual day whose rows k-D..k are now all known
-    const bool emit = t >= t0 && t < t1;
-    const F wt = emit ? w[(size_t)t * sP + p] : F(0);
+  // Days are taken in groups of G: every load of a group (z0 and x of each band, w, lambda)
+  // is issued before any of them is used, so G days of reads are in flight per thread.
+  constexpr int G = 4;
+  for (int ug = t0 - D; ug < t1 + D; ug += G) {
+    F zl[G][NBR], xl[G][NBR], wl[G], ll[G];
 #pragma unroll
-    for (int j = 0; j < NBR; ++j) {
-      if (j >= nb) break;
-      const size_t col = (size_t)(b0 + j) * sP + p;
+    for (int g = 0; g < G; ++g) {
+      const int u = ug + g;
+      const int k = u - D, t = k;
+      const bool live_u = u < t1 + D;
+      const bool row = live_u && k >= 0 && k <= T - D - 1;
+      const bool emit = live_u && t >= t0 && t < t1;
+      ll[g] = row ? (lam_scalar ? ls : lam[(size_t)k * sP + p]) : F(0);
+      wl[g] = emit ? w[(size_t)t * sP + p] : F(0);
 #pragma unroll
-      for (int n = 0; n < D; ++n) zr[j][n] = zr[j][n + 1];
-      zr[j][D] = (u >= 0 && u < T) ? z0[(size_t)u * sBP + col] : F(0);
-#pragma unroll
-      for (int n = 0; n < D; ++n) qb[j][n] = qb[j][n + 1];
-      F q = F(0);
-      if (row) {
-        F lv[D + 1];
-#pragma unroll
-        for (int n = 0; n <= D; ++n) lv[n] = zr[j][n];
-#pragma unroll
-        for (int i = 0; i < D; ++i)
-#pragma unroll
-          for (int n = 0; n < D - i; ++n) lv[n] = lv[n + 1] - lv[n];
-        q = lk * lv[0];
+      for (int j = 0; j < NBR; ++j) {
+        const size_t col = (size_t)(b0 + j) * sP + p;
+        const bool band = j < nb;
+        zl[g][j] = (band && live_u && u >= 0 && u < T) ? z0[(size_t)u * sBP + col] : F(0);
+        xl[g][j] = (band && emit) ? x[(size_t)t * sBP + col] : F(0);
       }
-      qb[j][D] = q;
-      if (emit) {
-        // (D^T q)_t = sum_n c_n q_{t-n} = (-1)^D * (D-th backward difference of q at t)
-        F lv[D + 1];
+    }
 #pragma unroll
-        for (int n = 0; n <= D; ++n) lv[n] = qb[j][n];
+    for (int g = 0; g < G; ++g) {
+      const int u = ug + g;
+      if (u >= t1 + D) break;
+      const int k = u - D;  // difference row whose last day is u
+      const bool row = k >= 0 && k <= T - D - 1;
+      const F lk = ll[g];
+      const int t = k;      // residual day whose rows k-D..k are now all known
+      const bool emit = t >= t0 && t < t1;
+      const F wt = wl[g];
 #pragma unroll
-        for (int i = 0; i < D; ++i)
+      for (int j = 0; j < NBR; ++j) {
+        if (j >= nb) break;
+        const size_t col = (size_t)(b0 + j) * sP + p;
 #pragma unroll
-          for (int n = D; n > i; --n) lv[n] = lv[n] - lv[n - 1];
-        const F dtq = (D % 2) ? -lv[D] : lv[D];
-        const F xt = x[(size_t)t * sBP + col];
-        DW<F> acc;
-        if (raw) {
-          const DW<F> wz = two_prod(wt, zr[j][0]);  // zr[j][0] = z0_t (u = t + D)
-          acc = dw_add(DW<F>{xt, F(0)}, DW<F>{-wz.hi, -wz.lo});
-        } else {
-          acc = wt > F(0) ? dw_scale(two_sum(xt, -zr[j][0]), wt) : DW<F>{F(0), F(0)};
+        for (int n = 0; n < D; ++n) zr[j][n] = zr[j][n + 1];
+        zr[j][D] = zl[g][j];
+#pragma unroll
+        for (int n = 0; n < D; ++n) qb[j][n] = qb[j][n + 1];
+        F q = F(0);
+        if (row) {
+          F lv[D + 1];
+#pragma unroll
+          for (int n = 0; n <= D; ++n) lv[n] = zr[j][n];
+#pragma unroll
+          for (int i = 0; i < D; ++i)
+#pragma unroll
+            for (int n = 0; n < D - i; ++n) lv[n] = lv[n + 1] - lv[n];
+          q = lk * lv[0];
         }
-        acc = dw_add(acc, DW<F>{-dtq, F(0)});
-        r[(size_t)t * sBP + col] = acc.hi + acc.lo;
+        qb[j][D] = q;
+        if (emit) {
+          // (D^T q)_t = sum_n c_n q_{t-n} = (-1)^D * (D-th backward difference of q at t)
+          F lv[D + 1];
+#pragma unroll
+          for (int n = 0; n <= D; ++n) lv[n] = qb[j][n];
+#pragma unroll
+          for (int i = 0; i < D; ++i)
+#pragma unroll
+            for (int n = D; n > i; --n) lv[n] = lv[n] - lv[n - 1];
+          const F dtq = (D % 2) ? -lv[D] : lv[D];
+          const F xt = xl[g][j];
+          DW<F> acc;
+          if (raw) {
+            const DW<F> wz = two_prod(wt, zr[j][0]);  // zr[j][0] = z0_t (u = t + D)
+            acc = dw_add(DW<F>{xt, F(0)}, DW<F>{-wz.hi, -wz.lo});
+          } else {
+            acc = wt > F(0) ? dw_scale(two_sum(xt, -zr[j][0]), wt) : DW<F>{F(0), F(0)};
+          }
+          acc = dw_add(acc, DW<F>{-dtq, F(0)});
+          r[(size_t)t * sBP + col] = acc.hi + acc.lo;
+        }
       }
     }
   }
