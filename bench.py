@@ -47,6 +47,10 @@ def parse_args():
     ap.add_argument("--no-gcv", action="store_true")
     ap.add_argument("--no-learned", action="store_true")
     ap.add_argument("--tcn-ckpt", default=None, help="trained lambda network (else one epoch is trained first)")
+    ap.add_argument("--train-epochs", type=float, default=1.0, help="epochs of lambda-network training before timing")
+    ap.add_argument("--only", choices=["gcv", "learned", "ragged"], default=None,
+                    help="run one secondary measurement alone (profiling) and print it")
+    ap.add_argument("--series", type=int, default=None, help="series of the --only measurement")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU work of the oracle baseline")
     return ap.parse_args()
 
@@ -60,10 +64,15 @@ def peaks():
     return FALLBACK_HBM_GBS, "fallback"
 
 
-def kernel_sources_sha():
+# sources the tile kernels (smooth, refine, adjoint) are built from
+TILE_SOURCES = ["ws_df.cuh", "ws_internal.h", "ws_ptx.cuh", "ws_sweep.cuh", "ws_tile.cu", "ws_tile_d1.cu",
+                "ws_tile_d2.cu", "ws_tile_d3.cu", "ws_tile_d4.cu", "ws_tile_impl.cuh"]
+
+
+def kernel_sources_sha(names=TILE_SOURCES):
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2604_00048_b300", "csrc")
-    for name in sorted(os.listdir(csrc)):
+    for name in sorted(names):
         with open(os.path.join(csrc, name), "rb") as f:
             h.update(name.encode())
             h.update(f.read())
@@ -169,7 +178,7 @@ def cpu_oracle_rate(x, w, lam, gz, d, target_s, with_bwd=True):
     return n / dt, cores, f"{n} of the tile's series (all {x.shape[0]} days, {x.shape[1]} bands), FP64"
 
 
-def ragged_measure(dev, steps):
+def ragged_measure(dev, steps, n=1 << 20):
     """The ragged batch: 1,048,576 series, T ~ U{120..3288}, d in {1,2,3}, one band, FP32,
     one persistent launch replayed from a CUDA graph with the autotuned configuration."""
     import torch
@@ -177,7 +186,6 @@ def ragged_measure(dev, steps):
     from paper_2604_00048_b300 import synth, ws
 
     rc = synth.RECIPES["ragged"]
-    n = 1 << 20
     out = synth.generate_ragged(rc, n, device=dev)
     x, w, lam = out["x"], out["w"], out["lam"]
     N = x.numel()
@@ -203,7 +211,7 @@ def ragged_measure(dev, steps):
     hbm, _ = peaks()
     alg = 16.0 * N  # read x, w, lambda; write z (FP32), once
     info = plan.info()
-    res = {"workload": "ragged: 1,048,576 series, T~U{120..3288}, d in {1,2,3}, 1 band, FP32 + refinement",
+    res = {"workload": f"ragged: {n} series, T~U{{120..3288}}, d in {{1,2,3}}, 1 band, FP32 + refinement",
            "series_per_s": n / (ms / 1e3), "ms": ms, "pixel_days": N,
            "solve_only_ms": ms_solve, "solve_only_series_per_s": n / (ms_solve / 1e3),
            "solve_only_alg_gbs": alg / (ms_solve / 1e3) / 1e9,
@@ -216,7 +224,7 @@ def ragged_measure(dev, steps):
     return res
 
 
-def gcv_measure(dev, steps):
+def gcv_measure(dev, steps, P=262144):
     """GCV grid search (16 lambda values, log10 in {0, 1/3, ..., 5}) then the smoothing at the
     chosen lambda, on the learned-lambda evaluation set: 262,144 series x 730 days, d = 2,
     one band, FP32."""
@@ -224,7 +232,7 @@ def gcv_measure(dev, steps):
 
     from paper_2604_00048_b300 import synth, ws
 
-    P, T = 262144, 730
+    T = 730
     out = synth.generate_tile(synth.RECIPES["learned"], P, device=dev)
     x, w = out["x"], out["w"]
     ws.gcv_smooth(x, w, None, 2, want_scores=False)
@@ -246,7 +254,7 @@ def gcv_measure(dev, steps):
     return res
 
 
-def learned_measure(dev, steps, ckpt=None, train_epochs=1.0):
+def learned_measure(dev, steps, ckpt=None, train_epochs=1.0, P=262144):
     """Learned lambda vs the GCV grid on the evaluation set (262,144 new series x 730 days,
     d = 2, one band): the lambda network is trained first on the project's kernels (one
     epoch of 2,097,152 series in batches of 4096) unless a checkpoint is given. Timed: the
@@ -265,7 +273,7 @@ def learned_measure(dev, steps, ckpt=None, train_epochs=1.0):
         net, nb, hist = train.train(2097152, 4096, train_epochs, 2e-3, seed=0, log_every=10 ** 9, device=dev)
         torch.cuda.synchronize()
         trained = {"batches": nb, "batch": 4096, "epochs": train_epochs, "train_s": time.time() - t0}
-    P, T = 262144, 730
+    T = 730
     base = synth.RECIPES["learned"]
     rc = synth.Recipe(**{**base.__dict__, "seed": base.seed + 1000, "T": T})
     out = synth.generate_tile(rc, P, device=dev, want_clean=True)
@@ -337,11 +345,32 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def run_only(args):
+    """One secondary measurement alone (used by the profiling commands)."""
+    import torch
+
+    rank, world, local = dist_env()
+    if rank != 0:
+        return
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    steps = max(1, args.steps)
+    if args.only == "gcv":
+        res = gcv_measure(dev, steps, args.series or 262144)
+    elif args.only == "learned":
+        res = learned_measure(dev, steps, args.tcn_ckpt, args.train_epochs, args.series or 262144)
+    else:
+        res = ragged_measure(dev, steps, args.series or (1 << 20))
+    print(json.dumps({"only": args.only, **res}), flush=True)
+
+
 def run_ours(args):
     import numpy as np
     import torch
     import torch.distributed as dist
 
+    if args.only:
+        return run_only(args)
     rank, world, local = dist_env()
     torch.cuda.set_device(local)
     if world > 1:
@@ -496,7 +525,7 @@ def run_ours(args):
         torch.cuda.empty_cache()
         ragged = ragged_measure(dev, max(3, args.steps))
     gcv = None if args.no_gcv else gcv_measure(dev, max(3, args.steps))
-    learned = None if args.no_learned else learned_measure(dev, max(3, args.steps), args.tcn_ckpt)
+    learned = None if args.no_learned else learned_measure(dev, max(3, args.steps), args.tcn_ckpt, args.train_epochs)
     line = {"metric": METRIC, "value": value, "unit": "series/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
