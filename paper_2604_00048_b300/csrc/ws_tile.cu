@@ -60,12 +60,15 @@ int plan_tile(const ws_problem& pb, int mode, int nb, TileCfg& cfg) {
   cfg.S = S;
   cfg.stages = 2;
   // Aim at 16 resident warps per SM (latency of the sequential recurrence), but keep
-  // chunks of at least 5 days (checkpoint traffic grows as 1/C).
+  // chunks of at least 5 days (checkpoint traffic grows as 1/C); 4 for the correction and
+  // adjoint modes, whose per-day work is larger: on the 10-band tile their two CTAs per SM at
+  // 4 days beat one CTA at 12 days by 22% (adjoint) and 7% (correction solve).
   int ctas = g_tune_ctas > 0 ? g_tune_ctas : (S > 1 ? 2 : 4);
+  const long min_chunk = (mode == MODE_RAW || mode == MODE_ADJ) ? 4 : 5;
   long C = 0;
   for (; ctas >= 1; --ctas) {
     C = chunk_for(pb, mode, nb, S, ctas, di);
-    if (C >= 5 || ctas == 1 || g_tune_ctas > 0) break;
+    if (C >= min_chunk || ctas == 1 || g_tune_ctas > 0) break;
   }
   // registers may allow fewer CTAs than shared memory: then give the chunk the room
   const void* kern = tile_kernel_ptr(pb, mode, nb);
