@@ -32,7 +32,7 @@ struct RaggedArgs {
   const int64_t* off;     // n + 1
   const int32_t* order;   // n_items * 32 series ids (-1 = idle lane)
   const int8_t* item_d;   // order of each item
-  const int32_t* item_nch;
+  const int32_t* item_t;  // longest series of each item
   int n_items;
   int64_t N;              // off[n]
   int B, band;            // band of this launch
@@ -79,7 +79,7 @@ __device__ void ragged_item(const RaggedArgs& a, int item, float* sm, float* ck,
   const bool live = sid >= 0;
   const int64_t off = live ? a.off[sid] : 0;
   const int T = live ? (int)(a.off[sid + 1] - off) : 0;
-  const int nch = a.item_nch[item];
+  const int nch = (a.item_t[item] + RC - 1) / RC;
   if (MODE == MODE_RAW && !a.active[item]) return;  // every series of the item has settled
   const float* xb = MODE == MODE_RAW ? a.resid : a.x + (size_t)a.band * a.N;
   float* zb = a.z + (size_t)a.band * a.N;
@@ -235,7 +235,7 @@ __device__ void ragged_item(const RaggedArgs& a, int item, float* sm, float* ck,
 }
 
 template <int RC, int MODE>
-__global__ void __launch_bounds__(256) k_ragged(const RaggedArgs a) {
+__global__ void __launch_bounds__(512) k_ragged(const RaggedArgs a) {
   extern __shared__ __align__(16) float rsm[];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   float* sm = rsm + (size_t)wid * 2 * RaggedSmem<RC>::rows * kPitch;
@@ -423,13 +423,12 @@ using namespace ws;
 
 struct ws_plan {
   ws_ragged rg;
-  int n_items = 0, max_nch16 = 0, max_nch32 = 0;
+  int n_items = 0, max_t = 0;
   int RC = 16, warps = 8, grid = 0;
   int64_t N = 0;
   int32_t* d_order = nullptr;
   int8_t* d_item_d = nullptr;
-  int32_t* d_nch16 = nullptr;
-  int32_t* d_nch32 = nullptr;
+  int32_t* d_item_t = nullptr;
   int* d_counter = nullptr;
   unsigned* d_err = nullptr;
   float* d_ckpt = nullptr;
@@ -456,6 +455,7 @@ struct ws_plan {
 static size_t ragged_smem(int RC, int warps) { return (size_t)warps * 2 * (5 * RC + 4) * kPitch * sizeof(float); }
 
 static const void* ragged_kernel(int RC, int mode) {
+  if (RC == 8) return mode == MODE_RAW ? (const void*)k_ragged<8, MODE_RAW> : (const void*)k_ragged<8, MODE_SMOOTH>;
   if (RC == 16) return mode == MODE_RAW ? (const void*)k_ragged<16, MODE_RAW> : (const void*)k_ragged<16, MODE_SMOOTH>;
   return mode == MODE_RAW ? (const void*)k_ragged<32, MODE_RAW> : (const void*)k_ragged<32, MODE_SMOOTH>;
 }
@@ -503,7 +503,7 @@ static int ragged_launch(ws_plan* pl, const void* x, const void* w, const void* 
   a.off = pl->rg.offsets;
   a.order = pl->d_order;
   a.item_d = pl->d_item_d;
-  a.item_nch = pl->RC == 16 ? pl->d_nch16 : pl->d_nch32;
+  a.item_t = pl->d_item_t;
   a.n_items = pl->n_items;
   a.N = pl->N;
   a.B = pl->rg.n_bands;
@@ -515,20 +515,20 @@ static int ragged_launch(ws_plan* pl, const void* x, const void* w, const void* 
   a.z = (float*)z;
   a.status = status;
   a.ckpt = pl->d_ckpt;
-  a.max_nch = pl->RC == 16 ? pl->max_nch16 : pl->max_nch32;
+  a.max_nch = (pl->max_t + pl->RC - 1) / pl->RC;
   a.counter = pl->d_counter + band;
   a.err = pl->d_err;
   if (refine) fill_refine_args(pl, a);
   const size_t smem = ragged_smem(pl->RC, pl->warps);
   if (cudaMemsetAsync(a.counter, 0, sizeof(int), st) != cudaSuccess) return set_error(WS_ECUDA, "ragged: memset");
-  if (pl->RC == 16 && mode == MODE_RAW)
-    k_ragged<16, MODE_RAW><<<pl->grid, pl->warps * 32, smem, st>>>(a);
-  else if (pl->RC == 16)
-    k_ragged<16, MODE_SMOOTH><<<pl->grid, pl->warps * 32, smem, st>>>(a);
-  else if (mode == MODE_RAW)
-    k_ragged<32, MODE_RAW><<<pl->grid, pl->warps * 32, smem, st>>>(a);
-  else
-    k_ragged<32, MODE_SMOOTH><<<pl->grid, pl->warps * 32, smem, st>>>(a);
+  const dim3 g(pl->grid), blk(pl->warps * 32);
+  if (pl->RC == 8) {
+    if (mode == MODE_RAW) k_ragged<8, MODE_RAW><<<g, blk, smem, st>>>(a); else k_ragged<8, MODE_SMOOTH><<<g, blk, smem, st>>>(a);
+  } else if (pl->RC == 16) {
+    if (mode == MODE_RAW) k_ragged<16, MODE_RAW><<<g, blk, smem, st>>>(a); else k_ragged<16, MODE_SMOOTH><<<g, blk, smem, st>>>(a);
+  } else {
+    if (mode == MODE_RAW) k_ragged<32, MODE_RAW><<<g, blk, smem, st>>>(a); else k_ragged<32, MODE_SMOOTH><<<g, blk, smem, st>>>(a);
+  }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return set_error(WS_ECUDA, "ragged kernel launch: %s", cudaGetErrorString(e));
   return WS_OK;
@@ -595,7 +595,7 @@ static int ragged_config(ws_plan* pl, int RC, int warps) {
   pl->warps = warps;
   int rc = ragged_grid(RC, warps, pl->n_items, &pl->grid);
   if (rc != WS_OK) return rc;
-  const size_t need = (size_t)pl->grid * warps * (RC == 16 ? pl->max_nch16 : pl->max_nch32) * kFieldsMax * 32 * 4;
+  const size_t need = (size_t)pl->grid * warps * ((pl->max_t + RC - 1) / RC) * kFieldsMax * 32 * 4;
   if (need > pl->ckpt_bytes) {
     if (pl->d_ckpt) cudaFree(pl->d_ckpt);
     pl->d_ckpt = nullptr;
@@ -654,19 +654,17 @@ extern "C" int ws_plan_create(const ws_ragged* rg, ws_plan** out, void* stream) 
   pl->rg = *rg;
   pl->n_items = (int)items.size();
   pl->N = off[n];
-  std::vector<int32_t> order((size_t)pl->n_items * 32, -1), n16(pl->n_items), n32(pl->n_items);
+  std::vector<int32_t> order((size_t)pl->n_items * 32, -1), itt(pl->n_items);
   std::vector<int8_t> idd(pl->n_items);
   for (int k = 0; k < pl->n_items; ++k) {
     for (int l = 0; l < items[k].count; ++l) order[(size_t)k * 32 + l] = idx[items[k].first + l];
     idd[k] = (int8_t)items[k].d;
-    n16[k] = (int32_t)((items[k].tmax + 15) / 16);
-    n32[k] = (int32_t)((items[k].tmax + 31) / 32);
-    pl->max_nch16 = std::max(pl->max_nch16, n16[k]);
-    pl->max_nch32 = std::max(pl->max_nch32, n32[k]);
+    itt[k] = (int32_t)items[k].tmax;
+    pl->max_t = std::max(pl->max_t, itt[k]);
   }
   const size_t ni = std::max(1, pl->n_items);
   bool okm = cudaMalloc(&pl->d_order, ni * 32 * 4) == cudaSuccess && cudaMalloc(&pl->d_item_d, ni) == cudaSuccess &&
-             cudaMalloc(&pl->d_nch16, ni * 4) == cudaSuccess && cudaMalloc(&pl->d_nch32, ni * 4) == cudaSuccess &&
+             cudaMalloc(&pl->d_item_t, ni * 4) == cudaSuccess &&
              cudaMalloc(&pl->d_counter, sizeof(int) * rg->n_bands) == cudaSuccess &&
              cudaMalloc(&pl->d_err, 4) == cudaSuccess && cudaMalloc(&pl->d_dof, std::max(1, n)) == cudaSuccess;
   if (!okm) {
@@ -676,8 +674,7 @@ extern "C" int ws_plan_create(const ws_ragged* rg, ws_plan** out, void* stream) 
   if (pl->n_items > 0) {
     cudaMemcpy(pl->d_order, order.data(), order.size() * 4, cudaMemcpyHostToDevice);
     cudaMemcpy(pl->d_item_d, idd.data(), idd.size(), cudaMemcpyHostToDevice);
-    cudaMemcpy(pl->d_nch16, n16.data(), n16.size() * 4, cudaMemcpyHostToDevice);
-    cudaMemcpy(pl->d_nch32, n32.data(), n32.size() * 4, cudaMemcpyHostToDevice);
+    cudaMemcpy(pl->d_item_t, itt.data(), itt.size() * 4, cudaMemcpyHostToDevice);
     cudaMemcpy(pl->d_dof, dd.data(), n, cudaMemcpyHostToDevice);
   }
   for (const Item& it : items) pl->max_nch64 = std::max(pl->max_nch64, (int)((it.tmax + kRC64 - 1) / kRC64));
@@ -693,13 +690,13 @@ extern "C" int ws_plan_create(const ws_ragged* rg, ws_plan** out, void* stream) 
 
 // Autotuner: time every (chunk, warps per CTA) candidate on the plan's own data, keep the fastest.
 static int ragged_autotune(ws_plan* pl, const void* x, const void* w, const void* lam, void* z, cudaStream_t st) {
-  const int cands[][2] = {{16, 4}, {16, 8}, {32, 4}, {32, 8}};
+  const int cands[][2] = {{8, 8}, {8, 16}, {16, 4}, {16, 8}, {32, 4}};
   float best = 1e30f;
   int bi = 1;
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
-  for (int c = 0; c < 4; ++c) {
+  for (int c = 0; c < 5; ++c) {
     int rc = ragged_config(pl, cands[c][0], cands[c][1]);
     if (rc != WS_OK) continue;
     if ((rc = ragged_launch(pl, x, w, lam, z, nullptr, 0, st)) != WS_OK) return rc;  // warm-up
@@ -817,8 +814,7 @@ extern "C" void ws_plan_destroy(ws_plan* pl) {
   if (pl->graph) cudaGraphDestroy(pl->graph);
   cudaFree(pl->d_order);
   cudaFree(pl->d_item_d);
-  cudaFree(pl->d_nch16);
-  cudaFree(pl->d_nch32);
+  cudaFree(pl->d_item_t);
   cudaFree(pl->d_counter);
   cudaFree(pl->d_err);
   cudaFree(pl->d_ckpt);

@@ -159,9 +159,16 @@ def workspace_size(pb: Problem, flags: int = 0) -> int:
 _ws_cache = {}
 
 
-def workspace(pb: Problem, device, flags: int = 0) -> torch.Tensor:
-    """Device scratch for `pb` (cached per device and grown on demand; header zeroed once)."""
+def workspace(pb: Problem, device, flags: int = 0, given: Optional[torch.Tensor] = None) -> torch.Tensor:
+    """Device scratch for `pb`: `given` if not None (a uint8 tensor the caller owns, e.g. one
+    per stream for concurrent calls; its first 256 bytes must start at zero), else the
+    per-device cache (grown on demand; header zeroed once). Calls that may run at the same
+    time on different streams need different workspaces."""
     need = workspace_size(pb, flags)
+    if given is not None:
+        if given.numel() < need or given.dtype != torch.uint8 or not given.is_cuda:
+            raise ValueError(f"workspace needs {need} bytes (uint8, CUDA)")
+        return given
     if need == 0:
         raise WSError(WS_EINVAL, last_error() or "invalid problem")
     dev = torch.device(device)
@@ -196,7 +203,7 @@ def _check_tile(x, w, lam, d):
 
 
 def smooth(x: torch.Tensor, w: torch.Tensor, lam: torch.Tensor, d: int = 2, *, z=None, status=None,
-           factor=None, refine: bool = False, stream=None):
+           factor=None, refine: bool = False, stream=None, workspace_buf=None):
     """z = (W + D^T Lambda D)^{-1} W x per series and band (Eq. 3; Eq. 2 for scalar lam).
 
     refine: one step of iterative refinement with a double-word residual.
@@ -210,7 +217,7 @@ def smooth(x: torch.Tensor, w: torch.Tensor, lam: torch.Tensor, d: int = 2, *, z
         status = torch.empty(P, dtype=torch.uint8, device=x.device)
     if factor is not None and (tuple(factor.shape) != (T, d + 1, P) or factor.dtype != x.dtype):
         raise ValueError("factor must be [T, d+1, P] of x's dtype")
-    ws = workspace(pb, x.device, flags)
+    ws = workspace(pb, x.device, flags, workspace_buf)
     rc = _lib.ws_smooth_batch(ctypes.byref(pb), _ptr(x), _ptr(w), _ptr(lam), _ptr(z), _ptr(factor),
                               _ptr(status), flags, _ptr(ws), ws.numel(), _stream_ptr(stream))
     _check(rc)
@@ -259,11 +266,12 @@ def smooth_noalloc(x: torch.Tensor, w: torch.Tensor, lam: torch.Tensor, d: int =
     return z, status
 
 
-def refine(x: torch.Tensor, w: torch.Tensor, lam: torch.Tensor, z: torch.Tensor, d: int = 2, *, stream=None):
+def refine(x: torch.Tensor, w: torch.Tensor, lam: torch.Tensor, z: torch.Tensor, d: int = 2, *, stream=None,
+           workspace_buf=None):
     """One step of iterative refinement of z (in place) with a double-word residual."""
     T, B, P, lm = _check_tile(x, w, lam, d)
     pb = make_problem(T, B, P, d, _dtype_code(x), lm)
-    ws = workspace(pb, x.device, REFINE)
+    ws = workspace(pb, x.device, REFINE, workspace_buf)
     _check(_lib.ws_refine(ctypes.byref(pb), _ptr(x), _ptr(w), _ptr(lam), _ptr(z), _ptr(ws), ws.numel(),
                           _stream_ptr(stream)))
     return z
@@ -271,7 +279,7 @@ def refine(x: torch.Tensor, w: torch.Tensor, lam: torch.Tensor, z: torch.Tensor,
 
 def smooth_adjoint(w: torch.Tensor, lam: torch.Tensor, z: torch.Tensor, gz: torch.Tensor, d: int = 2, *,
                    gx=None, glam=None, want_gx: bool = True, want_glam: bool = True, log_lambda: bool = False,
-                   factor=None, status=None, refine: bool = False, stream=None):
+                   factor=None, status=None, refine: bool = False, stream=None, workspace_buf=None):
     """Vector-Jacobian products of z = Omega^{-1} W x (Eqs. 4-5): returns (gx, glam, status).
 
     gx = W Omega^{-1} gz; glam_k = -sum_b (D g_b)_k (D z_b)_k (k < T-d, 0 after), times
@@ -287,7 +295,7 @@ def smooth_adjoint(w: torch.Tensor, lam: torch.Tensor, z: torch.Tensor, gz: torc
     if status is None:
         status = torch.empty(P, dtype=torch.uint8, device=gz.device)
     flags = (GRAD_LOGLAM if log_lambda else 0) | (REFINE_ADJOINT if refine else 0)
-    ws = workspace(pb, gz.device, flags | (REFINE if factor is not None else 0))
+    ws = workspace(pb, gz.device, flags | (REFINE if factor is not None else 0), workspace_buf)
     rc = _lib.ws_solve_adjoint(ctypes.byref(pb), _ptr(factor), _ptr(w), _ptr(lam), _ptr(z), _ptr(gz), _ptr(gx),
                                _ptr(glam), flags, _ptr(status), _ptr(ws), ws.numel(), _stream_ptr(stream))
     _check(rc)
