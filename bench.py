@@ -292,7 +292,7 @@ def learned_measure(dev, steps, ckpt=None, train_epochs=1.0, P=262144):
         return e0.elapsed_time(e1) / steps, r
 
     ms_l, (zl, lam, _) = timed(lambda: train.learned_smooth(net, x, w))
-    ms_tcn, _ = timed(lambda: net.forward(x[:, 0, :], w))
+    ms_tcn, _ = timed(lambda: net.forward(x[:, 0, :], w, want_loglam=False))
     ms_g, (zg, _, _, _) = timed(lambda: ws.gcv_smooth(x, w, None, 2, want_scores=False))
     rl, rg = train.rmse(zl, clean), train.rmse(zg, clean)
     flop = 150912.0 * P * T  # network multiply-adds x 2 per position

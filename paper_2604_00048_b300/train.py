@@ -60,7 +60,7 @@ def batch(rc: synth.Recipe, first: int, n: int, device="cuda"):
 
 def train_step(net: "ws.Tcn", x, w, clean, lr: float, d: int = 2):
     """One Adam step on one batch; returns the batch loss (mean squared error to clean)."""
-    lam, _ = net.forward(x[:, 0, :], w, training=True)
+    lam, _ = net.forward(x[:, 0, :], w, training=True, want_loglam=False)
     z, _ = ws.smooth(x, w, lam, d)
     loss = torch.zeros(1, device=x.device)
     gz = ws.mse_grad(z[:, 0, :].contiguous(), clean, 2.0 / clean.numel(), loss)
@@ -71,7 +71,7 @@ def train_step(net: "ws.Tcn", x, w, clean, lr: float, d: int = 2):
 
 
 def learned_smooth(net: "ws.Tcn", x, w, d: int = 2, refine: bool = False):
-    lam, _ = net.forward(x[:, 0, :], w)
+    lam, _ = net.forward(x[:, 0, :], w, want_loglam=False)
     z, st = ws.smooth(x, w, lam, d, refine=refine)
     return z, lam, st
 

@@ -462,14 +462,16 @@ class Tcn:
             self._scratch = torch.zeros(need, dtype=torch.uint8, device=device)
         return self._scratch
 
-    def forward(self, x: torch.Tensor, w: torch.Tensor, training: bool = False, stream=None):
-        """x, w: [T, P] FP32 (one band). Returns (lam, loglam), both [T, P]."""
+    def forward(self, x: torch.Tensor, w: torch.Tensor, training: bool = False, stream=None,
+                want_loglam: bool = True):
+        """x, w: [T, P] FP32 (one band). Returns (lam, loglam), both [T, P] (loglam None
+        unless want_loglam)."""
         T, P = w.shape
         x2 = x.reshape(T, P)
         b = self._batch(T, P)
         sc = self._scratch_for(b, training, x.device)
         lam = torch.empty(T, P, dtype=torch.float32, device=x.device)
-        loglam = torch.empty_like(lam)
+        loglam = torch.empty_like(lam) if want_loglam else None
         _check(_lib.ws_tcn_forward(ctypes.byref(b), _ptr(self.packed), _ptr(self.theta), _ptr(x2), _ptr(w),
                                    _ptr(lam), _ptr(loglam), _ptr(sc), sc.numel(), int(training),
                                    _stream_ptr(stream)))
