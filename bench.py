@@ -145,6 +145,28 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def rank_series0(rank: int, per_rank: int) -> int:
+    """First series id of a rank's shard: ranks process disjoint, consecutive id ranges."""
+    return rank * per_rank
+
+
+def max_over_ranks(ms: float, device) -> float:
+    """The slowest rank's time (all ranks take part; identity without a process group)."""
+    import torch
+    import torch.distributed as dist
+
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return ms
+    tt = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    return float(tt.item())
+
+
+def aggregate_rate(per_rank: int, world: int, steps: int, ms: float) -> float:
+    """Whole-job throughput: the series of all ranks over the slowest rank's time."""
+    return per_rank * world * steps / (ms / 1e3)
+
+
 def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -381,7 +403,7 @@ def run_ours(args):
 
     rc = synth.RECIPES["hetero_tile"]
     P, T, B, d = args.pixels, rc.T, rc.n_bands, rc.d
-    series0 = rank * P
+    series0 = rank_series0(rank, P)
     inp = synth.generate_tile(rc, P, series0=series0, device=dev, dtype=torch.float32)
     x, w, lam = inp["x"], inp["w"], inp["lam"]
     del inp
@@ -436,15 +458,12 @@ def run_ours(args):
     ck = clocks.stop()
     ms = t_start.elapsed_time(t_end)
     ws.sync_status(dev, stream)
-    if world > 1:
-        tt = torch.tensor([ms], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms = float(tt.item())
+    ms = max_over_ranks(ms, dev)
     fwd_ms = statistics.median([e[0].elapsed_time(e[1]) for e in ev])
     ref_ms = statistics.median([e[1].elapsed_time(e[2]) for e in ev])
     bwd_ms = statistics.median([e[2].elapsed_time(e[3]) for e in ev]) if has_bwd else 0.0
     ms_step = ms / args.steps
-    value = P * world * args.steps / (ms / 1e3)
+    value = aggregate_rate(P, world, args.steps, ms)
 
     # roofline of the dominant kernel: algorithmic bytes per pixel-day, FP32
     pd = float(P) * T
