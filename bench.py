@@ -145,6 +145,15 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def tile_config(P, T, B, d, world, has_bwd=True):
+    """The workload both arms report (the reference arm times a bounded sample of it)."""
+    return {"workload": f"hetero_tile: {P} px x {T} d x {B} bands, d={d}, per-day lambda, "
+                        + ("smooth + refinement step + adjoint" if has_bwd else "smooth + refinement step"),
+            "pixels_per_rank": P, "T": T, "bands": B, "d": d,
+            "parallelism": f"replicas x{world} (pixel shards, no collective)",
+            "l2": "inputs larger than L2 (34.5 GB of x per rank), no flush"}
+
+
 def rank_series0(rank: int, per_rank: int) -> int:
     """First series id of a rank's shard: ranks process disjoint, consecutive id ranges."""
     return rank * per_rank
@@ -359,8 +368,9 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": val, "unit": "series/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / len(times),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": "hetero_tile: 262144 px x 3288 d x 10 bands, d=2, fwd+bwd",
-                       "sample_series_per_step": n, "parallelism": "cpu"},
+            "config": tile_config(262144, 3288, 10, 2, 1),
+            "sample": {"series_per_step": n, "parallelism": "host cores",
+                       "note": "FP64 banded oracle: smooth + adjoint (FP64 needs no refinement step)"},
             "cpu_baseline": {"value": val, "unit": "series/s", "cores": cores, "kind": "oracle",
                              "sample": f"{n} series per step of the tile (3288 days, 10 bands), FP64 banded oracle"},
             "e2e": {"value": val, "unit": "series/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -565,11 +575,7 @@ def run_ours(args):
     line = {"metric": METRIC, "value": value, "unit": "series/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": f"hetero_tile: {P} px x {T} d x {B} bands, d={d}, per-day lambda, "
-                                   + ("smooth + refinement step + adjoint" if has_bwd else "smooth + refinement step"),
-                       "pixels_per_rank": P, "T": T, "bands": B, "d": d,
-                       "parallelism": f"replicas x{world} (pixel shards, no collective)",
-                       "l2": "inputs larger than L2 (34.5 GB of x per rank), no flush"},
+            "config": tile_config(P, T, B, d, world, has_bwd),
             "fwd_series_per_s": P * world / ((fwd_ms + ref_ms) / 1e3),
             "fwd_unrefined_series_per_s": P * world / (fwd_ms / 1e3),
             "smooth_ms": fwd_ms, "refine_ms": ref_ms, "adjoint_ms": bwd_ms,
