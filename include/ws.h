@@ -181,11 +181,11 @@ int ws_mse_grad(const float* z, const float* target, float* gz, float* loss_sum,
  * where the device-wide synchronisation of cudaFree must be avoided). Same arguments,
  * results and per-series status as ws_smooth_batch, whose kernels it runs; the scratch
  * is a file-scope device array of WS_NOALLOC_MAX_BYTES per device.
- *   - Problems with ws_workspace_size(pb, flags) > WS_NOALLOC_MAX_BYTES (32 MiB)
+ *   - Problems with ws_workspace_size(pb, flags) > WS_NOALLOC_MAX_BYTES (64 MiB)
  *     return WS_ENOMEM_WS before anything is launched. That size is the checkpoints of
  *     the persistent grid (up to grid x ceil(T/C) x (d(d+1) + B d) x 128 elements, C the
  *     planned chunk) plus, with WS_REFINE, a T x B x P residual: 4096 FP64 series of
- *     T = 365, d = 2, one band, with WS_REFINE fit (about 18 MiB).
+ *     T = 365, d = 2, one band, with WS_REFINE fit (about 35 MiB).
  *   - No cudaMalloc, cudaFree or allocating library routine is called.
  *   - The first call on each device does the set-up with that device current
  *     (cudaGetSymbolAddress, then a synchronous cudaMemset clearing the error word):
@@ -194,7 +194,7 @@ int ws_mse_grad(const float* z, const float* target, float* gz, float* loss_sum,
  *     threads, or streams without ordering between them) race on it.
  *   - A device-side wait that gives up sets the array's error word, which this entry
  *     point does not report; use ws_smooth_batch and ws_sync_status for that report. */
-#define WS_NOALLOC_MAX_BYTES (32u << 20)
+#define WS_NOALLOC_MAX_BYTES (64u << 20)
 int ws_smooth_batch_noalloc(const ws_problem* pb, const void* x, const void* w, const void* lam, void* z,
                             void* factor_out, uint8_t* status, uint32_t flags, void* stream);
 

@@ -64,7 +64,7 @@ _lib.ws_gcv_smooth.argtypes = [_PP, _vp, _vp, ctypes.POINTER(ctypes.c_float), ct
                                _u32, _vp, _sz, _vp]
 _lib.ws_smooth_batch_noalloc.restype = ctypes.c_int
 _lib.ws_smooth_batch_noalloc.argtypes = [_PP, _vp, _vp, _vp, _vp, _vp, _vp, _u32, _vp]
-NOALLOC_MAX_BYTES = 32 << 20
+NOALLOC_MAX_BYTES = 64 << 20
 _lib.ws_tune_set.restype = ctypes.c_int
 _lib.ws_tune_set.argtypes = [ctypes.c_int32, ctypes.c_int32]
 _lib.ws_sync_status.restype = ctypes.c_int

@@ -37,7 +37,7 @@ def _oracle_ragged(out, ids, lam_scalar=False, mp_orders=()):
         z, st = banded.smooth_tile(x[a:b, None, None], w[a:b, None], li, int(ords[i]))
         z = z[:, 0, 0]
         if int(ords[i]) in mp_orders and st[0] == 0:
-            z = multiprec.smooth_mp(x[a:b], w[a:b], li[0, 0] if lam_scalar else li[:, 0], int(ords[i]))
+            z = multiprec.smooth_mp(x[a:b], w[a:b], float(li[0]) if lam_scalar else li[:, 0], int(ords[i]))
         res[i] = (z, int(st[0]))
     return res
 
@@ -144,3 +144,18 @@ def test_ragged_full_size_sampled(ws):
     ws.sync_status()
     ids = np.random.default_rng(11).choice(1 << 20, 64, replace=False)
     _check(out, z, st, ids, tol=1e-4, mp_orders=(3,))
+
+
+def test_ragged_scalar_lambda_refined(ws):
+    """One lambda per series (Eq. 2), sparse weights, orders 1..3, with refinement."""
+    rc = synth.Recipe(**{**synth.RECIPES["ragged"].__dict__, "lam_kind": "scalar", "lam_log10": (0.0, 5.0)})
+    out = synth.generate_ragged(rc, 300, device="cuda", t_range=(60, 400))
+    lam = out["lam"]
+    off = out["offsets"]
+    lam_s = lam[off[:-1].clamp(max=lam.numel() - 1)].contiguous()  # per series: its first day's value
+    plan = ws.RaggedPlan(out["offsets"], out["order"], lam_scalar=True)
+    z, st = plan.execute(out["x"], out["w"], lam_s, refine=True)
+    ws.sync_status()
+    out2 = dict(out)
+    out2["lam"] = lam_s
+    _check(out2, z, st, range(300), tol=1e-4, lam_scalar=True, mp_orders=(3,))

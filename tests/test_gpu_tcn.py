@@ -169,3 +169,28 @@ def test_training_reduces_loss(ws):
         losses.append(loss.item())
     assert np.all(np.isfinite(losses))
     assert losses[-1] < 0.9 * losses[0], losses
+
+
+def test_checkpoint_round_trip(ws, tmp_path):
+    """Weights, Adam moments and the step count survive save/load exactly; continuing from
+    the loaded copy matches continuing from the original up to the order of the weight-
+    gradient kernels' floating-point atomic sums (not bit-identical from run to run)."""
+    from paper_2604_00048_b300 import train
+
+    T, P = 120, 64
+    x, w, clean = _tcn_inputs(T, P, 4)
+    net = ws.Tcn(ws.tcn_init(21))
+    for _ in range(2):
+        train.train_step(net, x[:, None, :].contiguous(), w, clean, 1e-3)
+    path = str(tmp_path / "net.ckpt")
+    train.save_checkpoint(path, net, 2)
+    net2, drawn = train.load_checkpoint(path)
+    assert drawn == 2 and net2.step_count == net.step_count
+    assert torch.equal(net2.theta, net.theta) and torch.equal(net2.m, net.m) and torch.equal(net2.v, net.v)
+    before = net.theta.clone()
+    train.train_step(net, x[:, None, :].contiguous(), w, clean, 1e-3)
+    train.train_step(net2, x[:, None, :].contiguous(), w, clean, 1e-3)
+    torch.cuda.synchronize()
+    step = (net.theta - before).abs().max().item()
+    assert step > 0
+    assert (net.theta - net2.theta).abs().max().item() <= 1e-3 * step
