@@ -225,26 +225,28 @@ def ragged_measure(dev, steps, n=1 << 20):
     st = torch.empty(n, dtype=torch.uint8, device=dev)
     plan.execute(x, w, lam, z=z, status=st, autotune=True, graph=True)
 
-    def timed(refine):
+    def timed(refine, tiles=True):
         for _ in range(2):
-            plan.execute(x, w, lam, z=z, status=st, graph=True, refine=refine)
+            plan.execute(x, w, lam, z=z, status=st, graph=True, refine=refine, tiles=tiles)
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record()
         for _ in range(steps):
-            plan.execute(x, w, lam, z=z, status=st, graph=True, refine=refine)
+            plan.execute(x, w, lam, z=z, status=st, graph=True, refine=refine, tiles=tiles)
         e1.record()
         torch.cuda.synchronize()
         return e0.elapsed_time(e1) / steps
 
-    ms_solve = timed(False)
-    ms = timed(True)  # the accuracy-gated result: refinement + FP64 re-solve of unsettled series
+    ms_lanes = timed(False, tiles=False)  # every series on the per-lane kernel
+    ms_solve = timed(False)  # length-class tiles (+ short series per lane)
+    ms = timed(True)  # the accuracy-gated result: refinement + double-float re-solve of unsettled series
     hbm, _ = peaks()
     alg = 16.0 * N  # read x, w, lambda; write z (FP32), once
     info = plan.info()
     res = {"workload": f"ragged: {n} series, T~U{{120..3288}}, d in {{1,2,3}}, 1 band, FP32 + refinement",
            "series_per_s": n / (ms / 1e3), "ms": ms, "pixel_days": N,
            "solve_only_ms": ms_solve, "solve_only_series_per_s": n / (ms_solve / 1e3),
+           "solve_per_lane_kernel_ms": ms_lanes,
            "solve_only_alg_gbs": alg / (ms_solve / 1e3) / 1e9,
            "frac_of_measured_hbm_solve_only": alg / (ms_solve / 1e3) / 1e9 / hbm,
            "hp_resolved_series": info["hp_series"],

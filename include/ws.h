@@ -285,6 +285,11 @@ typedef struct ws_plan_stats {
 
 #define WS_PLAN_AUTOTUNE 0x1u  /* ws_plan_execute: time the (chunk, warps/CTA) candidates once */
 #define WS_PLAN_GRAPH 0x2u     /* ws_plan_execute: replay a captured CUDA graph (one band) */
+#define WS_PLAN_TILES 0x8u     /* ws_plan_execute: series of at least 64 days (one band) are
+                                  solved as length-class tiles by the tile kernels: padded
+                                  with zero weights to a multiple of 32 days, which leaves
+                                  the solution unchanged; the plan allocates four float
+                                  arrays of the padded size on first use */
 #define WS_PLAN_REFINE 0x4u    /* ws_plan_execute: iterative refinement (the paper
                                   fixes no precision): up to two FP32 steps, r = W x - Omega z with a
                                   double-word combination, z += Omega^{-1} r, until the

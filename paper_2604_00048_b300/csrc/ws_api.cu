@@ -226,6 +226,19 @@ static int run_tile(const ws_problem& P, int mode, const void* rhs, const void* 
   return WS_OK;
 }
 
+// Smoothing of one tile problem (the ragged plan's length classes): validation is the
+// caller's; the workspace is tile_workspace_bytes(P) long, 256-byte aligned, header zeroed.
+int tile_smooth(const ws_problem& P, const void* x, const void* w, const void* lam, void* z, uint8_t* status,
+                void* workspace, cudaStream_t st) {
+  return run_tile(P, MODE_SMOOTH, x, w, lam, nullptr, nullptr, z, nullptr, nullptr, status, 0, 0, workspace, st);
+}
+
+size_t tile_workspace_bytes(const ws_problem& P) {
+  size_t ck = 0;
+  if (tile_ckpt_bytes(P, ck) != WS_OK) return 0;
+  return kHeaderBytes + ck;
+}
+
 }  // namespace ws
 
 using namespace ws;

@@ -87,6 +87,11 @@ int set_error(int code, const char* fmt, ...);
 int make_tmap(CUtensorMap* map, int dtype, int rank, const void* base, const uint64_t* dims,
               const uint64_t* strides_bytes, const uint32_t* box);
 
+// One smoothing tile launch sequence (ws_api.cu), used by the ragged plan's length classes.
+int tile_smooth(const ws_problem& P, const void* x, const void* w, const void* lam, void* z, uint8_t* status,
+                void* workspace, cudaStream_t st);
+size_t tile_workspace_bytes(const ws_problem& P);
+
 // GCV grid search (ws_gcv.cu): persistent grid, chunks and checkpoint bytes; launch.
 int gcv_plan(const ws_problem& pb, int& grid, int& nch, size_t& ck_bytes);
 int launch_gcv(const ws_problem& pb, const void* x, const void* w, const float* grid_vals, int n_grid,

@@ -16,6 +16,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <map>
 #include <numeric>
 #include <vector>
 
@@ -57,6 +58,7 @@ struct RaggedArgs {
   const int8_t* d_of;     // per series order
   int max_nch64;
   float tau;
+  const uint8_t* item_tiled;  // per item: 1 = its series are solved through the length-class tiles
 };
 
 constexpr int kFieldsMax = 4 * 5 + 4;  // d(d+1) + d for d <= 4, one band
@@ -81,6 +83,7 @@ __device__ void ragged_item(const RaggedArgs& a, int item, float* sm, float* ck,
   const int T = live ? (int)(a.off[sid + 1] - off) : 0;
   const int nch = (a.item_t[item] + RC - 1) / RC;
   if (MODE == MODE_RAW && !a.active[item]) return;  // every series of the item has settled
+  if (MODE == MODE_SMOOTH && a.item_tiled != nullptr && a.item_tiled[item]) return;  // solved as tiles
   const float* xb = MODE == MODE_RAW ? a.resid : a.x + (size_t)a.band * a.N;
   float* zb = a.z + (size_t)a.band * a.N;
   auto stg = [&](int st) -> float* { return sm + (size_t)st * L::rows * kPitch; };
@@ -417,9 +420,92 @@ __global__ void __launch_bounds__(128) k_ragged64(const RaggedArgs a) {
   }
 }
 
+// Length classes: series of one order whose lengths round up to the same T_c are solved as
+// one [T_c][P_c] tile problem by the tile kernels (TMA staging, two CTAs per SM). A series
+// of length T is padded to T_c with w = 0, x = 0 (lambda = 1 on padded rows): the padded
+// problem's minimiser agrees with the original one on days 0..T-1, because z on the padded
+// days can continue the last d values so that every added difference row is zero.
+// Gather: packed series -> tile columns (a 32 x 32 transpose through shared memory, reads
+// coalesced along days, writes along series). Scatter: back, with the status codes and the
+// per-series max |z| the refinement's settle test needs.
+constexpr int kTileMinT = 64;  // shorter series stay on the per-lane kernel
+constexpr int kTileStreams = 8;  // a class's tile launch fills only part of the GPU: run 8 at a time
+constexpr int kClassRound = 32;
+
+__global__ void __launch_bounds__(256) k_gather(const RaggedArgs a, const int32_t* __restrict__ sids, int Pc,
+                                                int Tc, float* __restrict__ tx, float* __restrict__ tw,
+                                                float* __restrict__ tl) {
+  __shared__ float sx[32][33], sw[32][33], sl[32][33];
+  const int p0 = blockIdx.x * 32, t0 = blockIdx.y * 32, lx = threadIdx.x, ly = threadIdx.y;
+  for (int j = ly; j < 32; j += 8) {
+    const int p = p0 + j, t = t0 + lx;
+    const int sid = p < Pc ? sids[p] : -1;
+    float xv = 0.f, wv = 0.f, lv = 1.f;
+    if (sid >= 0) {
+      const int64_t os = a.off[sid];
+      const int T = (int)(a.off[sid + 1] - os);
+      if (t < T) {
+        xv = a.x[os + t];
+        wv = a.w[os + t];
+        lv = a.lam_scalar ? a.lam[sid] : a.lam[os + t];
+      }
+    }
+    sx[j][lx] = xv;
+    sw[j][lx] = wv;
+    sl[j][lx] = lv;
+  }
+  __syncthreads();
+  for (int j = ly; j < 32; j += 8) {
+    const int t = t0 + j, p = p0 + lx;
+    if (t < Tc && p < Pc) {
+      const size_t o = (size_t)t * Pc + p;
+      tx[o] = sx[lx][j];
+      tw[o] = sw[lx][j];
+      tl[o] = sl[lx][j];
+    }
+  }
+}
+
+__global__ void __launch_bounds__(256) k_scatter(const RaggedArgs a, const int32_t* __restrict__ sids, int Pc,
+                                                 int Tc, const float* __restrict__ tz,
+                                                 const uint8_t* __restrict__ tst) {
+  __shared__ float sz[32][33];
+  const int p0 = blockIdx.x * 32, t0 = blockIdx.y * 32, lx = threadIdx.x, ly = threadIdx.y;
+  for (int j = ly; j < 32; j += 8) {
+    const int t = t0 + j, p = p0 + lx;
+    sz[lx][j] = (t < Tc && p < Pc) ? tz[(size_t)t * Pc + p] : 0.f;
+  }
+  __syncthreads();
+  for (int j = ly; j < 32; j += 8) {
+    const int p = p0 + j, t = t0 + lx;
+    const int sid = p < Pc ? sids[p] : -1;
+    if (sid < 0) continue;
+    const int64_t os = a.off[sid];
+    const int T = (int)(a.off[sid + 1] - os);
+    float m = 0.f;
+    if (t < T) {
+      const float v = sz[j][lx];
+      a.z[os + t] = v;
+      m = fabsf(v);
+    }
+    if (a.zmax != nullptr) {  // max |z| over the series (non-negative floats order as integers)
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+      if (lx == 0) atomicMax(reinterpret_cast<int*>(a.zmax) + sid, __float_as_int(m));
+    }
+    if (blockIdx.y == 0 && lx == 0 && a.status != nullptr) a.status[sid] = tst[p];
+  }
+}
+
 }  // namespace ws
 
 using namespace ws;
+
+struct LenClass {
+  int d, Tc, Pc;
+  size_t base;     // element offset of the class tile in the tile arrays
+  int sid_base;    // offset of the class's series ids in d_class_sid
+};
 
 struct ws_plan {
   ws_ragged rg;
@@ -448,8 +534,18 @@ struct ws_plan {
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   std::vector<cudaGraphNode_t> knodes;
+  // length-class tiles (WS_PLAN_TILES)
+  std::vector<LenClass> classes;
+  int32_t* d_class_sid = nullptr;
+  uint8_t* d_item_tiled = nullptr;
+  size_t tile_elems = 0, tile_ws_bytes = 0, tile_st_bytes = 0;
+  float* d_tiles = nullptr;        // 4 * tile_elems floats: x, w, lambda, z
+  uint8_t* d_tile_st = nullptr;    // status of every class column
+  void* d_tile_ws = nullptr;       // kTileStreams tile-kernel workspaces (the largest class's size each)
+  cudaStream_t tstream[8] = {};    // classes run concurrently, class i on stream i % kTileStreams
+  cudaEvent_t tev[9] = {};         // fork + one join event per stream
   int graph_rc = 0, graph_warps = 0;
-  bool graph_refine = false;
+  bool graph_refine = false, graph_tiles = false;
 };
 
 static size_t ragged_smem(int RC, int warps) { return (size_t)warps * 2 * (5 * RC + 4) * kPitch * sizeof(float); }
@@ -479,8 +575,8 @@ static int ragged_grid(int RC, int warps, int items, int* grid) {
   return WS_OK;
 }
 
-constexpr int kRefineSteps = 2;     // FP32 refinement steps before the double-float re-solve
-constexpr float kRefineTau = 1e-5f;  // settled: correction <= tau * max|z|
+constexpr int kRefineSteps = 3;     // FP32 refinement steps before the double-float re-solve
+constexpr float kRefineTau = 3e-5f;  // settled: correction <= tau * max|z|
 constexpr int kHPBlocksPerSM = 4;    // double-float re-solve: 4 x 128 threads per SM (128 registers each)
 
 static void fill_refine_args(const ws_plan* pl, RaggedArgs& a) {
@@ -497,9 +593,11 @@ static void fill_refine_args(const ws_plan* pl, RaggedArgs& a) {
 }
 
 static int ragged_launch(ws_plan* pl, const void* x, const void* w, const void* lam, void* z, uint8_t* status,
-                         int band, cudaStream_t st, int mode = MODE_SMOOTH, bool refine = false) {
+                         int band, cudaStream_t st, int mode = MODE_SMOOTH, bool refine = false,
+                         bool tiles = false) {
   RaggedArgs a;
   memset(&a, 0, sizeof(a));
+  a.item_tiled = (tiles && mode == MODE_SMOOTH) ? pl->d_item_tiled : nullptr;
   a.off = pl->rg.offsets;
   a.order = pl->d_order;
   a.item_d = pl->d_item_d;
@@ -569,6 +667,93 @@ static int ragged_refine(ws_plan* pl, const void* x, const void* w, const void* 
   k_ragged64<<<pl->grid64, 128, 0, st>>>(a);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return set_error(WS_ECUDA, "ragged double-float re-solve launch: %s", cudaGetErrorString(e));
+  return WS_OK;
+}
+
+// The length classes: gather -> tile smoothing -> scatter, one class after another.
+static int ragged_tiles(ws_plan* pl, const void* x, const void* w, const void* lam, void* z, uint8_t* status,
+                        bool refine, cudaStream_t st) {
+  RaggedArgs a;
+  memset(&a, 0, sizeof(a));
+  a.off = pl->rg.offsets;
+  a.N = pl->N;
+  a.B = 1;
+  a.lam_scalar = pl->rg.lam_mode == WS_LAM_SCALAR;
+  a.x = (const float*)x;
+  a.w = (const float*)w;
+  a.lam = (const float*)lam;
+  a.z = (float*)z;
+  a.status = status;
+  a.zmax = refine ? pl->d_zmax : nullptr;
+  float* tx = pl->d_tiles;
+  float* tw = tx + pl->tile_elems;
+  float* tl = tw + pl->tile_elems;
+  float* tz = tl + pl->tile_elems;
+  size_t stoff = 0;
+  // fork: the class streams wait for the work queued before on st (also under capture)
+  if (cudaEventRecord(pl->tev[0], st) != cudaSuccess) return set_error(WS_ECUDA, "ragged tiles: fork");
+  for (int k = 0; k < kTileStreams; ++k)
+    if (cudaStreamWaitEvent(pl->tstream[k], pl->tev[0], 0) != cudaSuccess) return set_error(WS_ECUDA, "ragged tiles: fork");
+  int ci = 0;
+  for (const LenClass& c : pl->classes) {
+    const int k = ci++ % kTileStreams;
+    cudaStream_t cs = pl->tstream[k];
+    void* wsk = static_cast<char*>(pl->d_tile_ws) + (size_t)k * pl->tile_ws_bytes;
+    const dim3 blk(32, 8), grd((unsigned)((c.Pc + 31) / 32), (unsigned)((c.Tc + 31) / 32));
+    const int32_t* sids = pl->d_class_sid + c.sid_base;
+    k_gather<<<grd, blk, 0, cs>>>(a, sids, c.Pc, c.Tc, tx + c.base, tw + c.base, tl + c.base);
+    ws_problem P;
+    memset(&P, 0, sizeof(P));
+    P.n_series = c.Pc;
+    P.T = c.Tc;
+    P.d = c.d;
+    P.n_bands = 1;
+    P.layout = WS_LAYOUT_TILE;
+    P.dtype = WS_F32;
+    P.lam_mode = WS_LAM_PER_DAY;
+    int rc = tile_smooth(P, tx + c.base, tw + c.base, tl + c.base, tz + c.base, pl->d_tile_st + stoff, wsk, cs);
+    if (rc != WS_OK) return rc;
+    k_scatter<<<grd, blk, 0, cs>>>(a, sids, c.Pc, c.Tc, tz + c.base, pl->d_tile_st + stoff);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return set_error(WS_ECUDA, "ragged tiles launch: %s", cudaGetErrorString(e));
+    stoff += (size_t)c.Pc;
+  }
+  // join: st waits for every class stream
+  for (int k = 0; k < kTileStreams; ++k) {
+    if (cudaEventRecord(pl->tev[1 + k], pl->tstream[k]) != cudaSuccess ||
+        cudaStreamWaitEvent(st, pl->tev[1 + k], 0) != cudaSuccess)
+      return set_error(WS_ECUDA, "ragged tiles: join");
+  }
+  return WS_OK;
+}
+
+static int tiles_alloc(ws_plan* pl) {
+  if (pl->d_tiles != nullptr || pl->classes.empty()) return WS_OK;
+  size_t wsb = 0;
+  for (const LenClass& c : pl->classes) {
+    ws_problem P;
+    memset(&P, 0, sizeof(P));
+    P.n_series = c.Pc;
+    P.T = c.Tc;
+    P.d = c.d;
+    P.n_bands = 1;
+    P.layout = WS_LAYOUT_TILE;
+    P.dtype = WS_F32;
+    P.lam_mode = WS_LAM_PER_DAY;
+    const size_t b = tile_workspace_bytes(P);
+    if (b == 0) return WS_ECUDA;
+    wsb = std::max(wsb, b);
+  }
+  wsb = (wsb + 255) & ~(size_t)255;
+  bool ok = cudaMalloc(&pl->d_tiles, 4 * pl->tile_elems * sizeof(float)) == cudaSuccess &&
+            cudaMalloc(&pl->d_tile_st, std::max<size_t>(1, pl->tile_st_bytes)) == cudaSuccess &&
+            cudaMalloc(&pl->d_tile_ws, wsb * kTileStreams) == cudaSuccess;
+  for (int k = 0; ok && k < kTileStreams; ++k)
+    ok = cudaStreamCreateWithFlags(&pl->tstream[k], cudaStreamNonBlocking) == cudaSuccess;
+  for (int k = 0; ok && k <= kTileStreams; ++k) ok = cudaEventCreateWithFlags(&pl->tev[k], cudaEventDisableTiming) == cudaSuccess;
+  if (!ok) return set_error(WS_ECUDA, "plan: length-class tile allocation (%zu elements)", pl->tile_elems);
+  cudaMemset(pl->d_tile_ws, 0, wsb * kTileStreams);  // the tile kernels' error words
+  pl->tile_ws_bytes = wsb;
   return WS_OK;
 }
 
@@ -678,6 +863,62 @@ extern "C" int ws_plan_create(const ws_ragged* rg, ws_plan** out, void* stream) 
     cudaMemcpy(pl->d_dof, dd.data(), n, cudaMemcpyHostToDevice);
   }
   for (const Item& it : items) pl->max_nch64 = std::max(pl->max_nch64, (int)((it.tmax + kRC64 - 1) / kRC64));
+  // Length classes for WS_PLAN_TILES (one band, FP32): the series of items whose shortest
+  // series has at least kTileMinT days, grouped by (order, length rounded up to kClassRound)
+  if (rg->n_bands == 1 && pl->n_items > 0) {
+    std::vector<uint8_t> tiled(pl->n_items, 0);
+    std::vector<std::vector<int>> byk;  // per (d, Tc) key
+    std::vector<std::pair<int, int>> keys;
+    std::map<int64_t, int> keymap;
+    for (int k = 0; k < pl->n_items; ++k) {
+      const Item& it = items[k];
+      const int sid_last = idx[it.first + it.count - 1];
+      if (off[sid_last + 1] - off[sid_last] < kTileMinT) continue;
+      tiled[k] = 1;
+      for (int l = 0; l < it.count; ++l) {
+        const int sid = idx[it.first + l];
+        const int T = (int)(off[sid + 1] - off[sid]);
+        const int Tc = (T + kClassRound - 1) / kClassRound * kClassRound;
+        const int64_t kk = (int64_t)it.d * (1LL << 40) + Tc;
+        auto fk = keymap.find(kk);
+        int key = fk == keymap.end() ? -1 : fk->second;
+        if (key < 0) {
+          keymap[kk] = (int)keys.size();
+          key = (int)keys.size();
+          keys.push_back({it.d, Tc});
+          byk.emplace_back();
+        }
+        byk[key].push_back(sid);
+      }
+    }
+    std::vector<int32_t> csid;
+    size_t base = 0, st = 0;
+    for (size_t q = 0; q < keys.size(); ++q) {
+      LenClass c;
+      c.d = keys[q].first;
+      c.Tc = keys[q].second;
+      c.Pc = ((int)byk[q].size() + 3) / 4 * 4;  // a multiple of 4 columns: 16-byte rows for TMA
+      c.base = base;
+      c.sid_base = (int)csid.size();
+      for (int sid : byk[q]) csid.push_back(sid);
+      for (int e = (int)byk[q].size(); e < c.Pc; ++e) csid.push_back(-1);
+      base += (size_t)c.Tc * c.Pc;
+      st += (size_t)c.Pc;
+      pl->classes.push_back(c);
+    }
+    pl->tile_elems = base;
+    pl->tile_st_bytes = st;
+    if (!csid.empty()) {
+      bool ok = cudaMalloc(&pl->d_class_sid, csid.size() * 4) == cudaSuccess &&
+                cudaMalloc(&pl->d_item_tiled, pl->n_items) == cudaSuccess;
+      if (!ok) {
+        ws_plan_destroy(pl);
+        return set_error(WS_ECUDA, "plan: class tables");
+      }
+      cudaMemcpy(pl->d_class_sid, csid.data(), csid.size() * 4, cudaMemcpyHostToDevice);
+      cudaMemcpy(pl->d_item_tiled, tiled.data(), pl->n_items, cudaMemcpyHostToDevice);
+    }
+  }
   cudaMemset(pl->d_err, 0, 4);
   int rc = ragged_config(pl, 16, 8);
   if (rc != WS_OK) {
@@ -721,23 +962,30 @@ static int ragged_autotune(ws_plan* pl, const void* x, const void* w, const void
 extern "C" int ws_plan_execute(ws_plan* pl, const void* x, const void* w, const void* lam, void* z, uint8_t* status,
                                uint32_t flags, void* stream) {
   if (pl == nullptr) return set_error(WS_EINVAL, "plan is NULL");
-  if (flags & ~(WS_PLAN_AUTOTUNE | WS_PLAN_GRAPH | WS_PLAN_REFINE)) return set_error(WS_EINVAL, "unknown flags 0x%x", flags);
+  if (flags & ~(WS_PLAN_AUTOTUNE | WS_PLAN_GRAPH | WS_PLAN_REFINE | WS_PLAN_TILES))
+    return set_error(WS_EINVAL, "unknown flags 0x%x", flags);
   const bool refine = (flags & WS_PLAN_REFINE) != 0;
+  const bool tiles = (flags & WS_PLAN_TILES) != 0 && pl->rg.n_bands == 1 && !pl->classes.empty();
   if (pl->n_items == 0) return WS_OK;
   int rc;
   if (refine && (rc = refine_alloc(pl)) != WS_OK) return rc;
+  if (tiles && (rc = tiles_alloc(pl)) != WS_OK) return rc;
   if (!x || !w || !lam || !z) return set_error(WS_EINVAL, "x, w, lam and z must be non-NULL");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   if ((flags & WS_PLAN_AUTOTUNE) && !pl->tuned && (rc = ragged_autotune(pl, x, w, lam, z, st)) != WS_OK) return rc;
   if (!(flags & WS_PLAN_GRAPH) || pl->rg.n_bands > 1) {
     for (int b = 0; b < pl->rg.n_bands; ++b) {
-      if ((rc = ragged_launch(pl, x, w, lam, z, status, b, st, MODE_SMOOTH, refine)) != WS_OK) return rc;
+      if (tiles && refine && cudaMemsetAsync(pl->d_zmax, 0, sizeof(float) * pl->rg.n_series, st) != cudaSuccess)
+        return set_error(WS_ECUDA, "ragged: memset");
+      if ((rc = ragged_launch(pl, x, w, lam, z, status, b, st, MODE_SMOOTH, refine, tiles)) != WS_OK) return rc;
+      if (tiles && (rc = ragged_tiles(pl, x, w, lam, z, status, refine, st)) != WS_OK) return rc;
       if (refine && (rc = ragged_refine(pl, x, w, lam, z, b, st)) != WS_OK) return rc;
     }
     return WS_OK;
   }
   // CUDA graph: captured once per configuration, kernel arguments updated on each replay
-  if (pl->exec == nullptr || pl->graph_rc != pl->RC || pl->graph_warps != pl->warps || pl->graph_refine != refine) {
+  if (pl->exec == nullptr || pl->graph_rc != pl->RC || pl->graph_warps != pl->warps || pl->graph_refine != refine ||
+      pl->graph_tiles != tiles) {
     if (pl->exec) cudaGraphExecDestroy(pl->exec);
     if (pl->graph) cudaGraphDestroy(pl->graph);
     pl->exec = nullptr;
@@ -748,7 +996,11 @@ extern "C" int ws_plan_execute(ws_plan* pl, const void* x, const void* w, const 
       cudaStreamDestroy(cs);
       return set_error(WS_ECUDA, "graph capture");
     }
-    rc = ragged_launch(pl, x, w, lam, z, status, 0, cs, MODE_SMOOTH, refine);
+    if (tiles && refine && cudaMemsetAsync(pl->d_zmax, 0, sizeof(float) * pl->rg.n_series, cs) != cudaSuccess)
+      rc = set_error(WS_ECUDA, "ragged: memset");
+    else
+      rc = ragged_launch(pl, x, w, lam, z, status, 0, cs, MODE_SMOOTH, refine, tiles);
+    if (rc == WS_OK && tiles) rc = ragged_tiles(pl, x, w, lam, z, status, refine, cs);
     if (rc == WS_OK && refine) rc = ragged_refine(pl, x, w, lam, z, 0, cs);
     cudaGraph_t g = nullptr;
     cudaError_t e = cudaStreamEndCapture(cs, &g);
@@ -762,6 +1014,7 @@ extern "C" int ws_plan_execute(ws_plan* pl, const void* x, const void* w, const 
     pl->graph_rc = pl->RC;
     pl->graph_warps = pl->warps;
     pl->graph_refine = refine;
+    pl->graph_tiles = tiles;
     size_t nn = 0;
     cudaGraphGetNodes(g, nullptr, &nn);
     std::vector<cudaGraphNode_t> nodes(nn);
@@ -773,18 +1026,31 @@ extern "C" int ws_plan_execute(ws_plan* pl, const void* x, const void* w, const 
       if (t == cudaGraphNodeTypeKernel) pl->knodes.push_back(nd);
     }
   } else {
-    // new buffers: every kernel node takes one RaggedArgs; only the user buffers change
+    // new buffers: the ragged kernels take RaggedArgs first (only its user buffers change; the
+    // other parameters are kept); the tile kernels of the length classes read plan-owned
+    // arrays only and are left as captured
     for (auto nd : pl->knodes) {
       cudaKernelNodeParams kp;
       if (cudaGraphKernelNodeGetParams(nd, &kp) != cudaSuccess) return set_error(WS_ECUDA, "graph params");
+      int nparams = 0;
+      if (kp.func == (void*)k_gather) nparams = 7;
+      else if (kp.func == (void*)k_scatter) nparams = 6;
+      else if (kp.func == (void*)k_ragged_resid || kp.func == (void*)k_ragged_collect || kp.func == (void*)k_ragged64)
+        nparams = 1;
+      else
+        for (int rcv : {8, 16, 32})
+          for (int m : {MODE_SMOOTH, MODE_RAW})
+            if (kp.func == ragged_kernel(rcv, m)) nparams = 1;
+      if (nparams == 0) continue;
       RaggedArgs na = *static_cast<RaggedArgs*>(kp.kernelParams[0]);
       na.x = (const float*)x;
       na.w = (const float*)w;
       na.lam = (const float*)lam;
       na.z = (float*)z;
-      na.status = status;  // read by the smoothing launch only
-      void* args1[1] = {&na};
-      kp.kernelParams = args1;
+      na.status = status;  // read by the smoothing and scatter launches only
+      void* args[8] = {&na};
+      for (int i = 1; i < nparams; ++i) args[i] = kp.kernelParams[i];
+      kp.kernelParams = args;
       if (cudaGraphExecKernelNodeSetParams(pl->exec, nd, &kp) != cudaSuccess)
         return set_error(WS_ECUDA, "graph update");
     }
@@ -815,6 +1081,15 @@ extern "C" void ws_plan_destroy(ws_plan* pl) {
   cudaFree(pl->d_order);
   cudaFree(pl->d_item_d);
   cudaFree(pl->d_item_t);
+  cudaFree(pl->d_class_sid);
+  cudaFree(pl->d_item_tiled);
+  cudaFree(pl->d_tiles);
+  cudaFree(pl->d_tile_st);
+  cudaFree(pl->d_tile_ws);
+  for (int k = 0; k < kTileStreams; ++k)
+    if (pl->tstream[k]) cudaStreamDestroy(pl->tstream[k]);
+  for (int k = 0; k <= kTileStreams; ++k)
+    if (pl->tev[k]) cudaEventDestroy(pl->tev[k]);
   cudaFree(pl->d_counter);
   cudaFree(pl->d_err);
   cudaFree(pl->d_ckpt);

@@ -87,7 +87,7 @@ class PlanStats(ctypes.Structure):
                 ("tuned_ms", ctypes.c_float), ("hp_series", ctypes.c_int32)]
 
 
-PLAN_AUTOTUNE, PLAN_GRAPH, PLAN_REFINE = 0x1, 0x2, 0x4
+PLAN_AUTOTUNE, PLAN_GRAPH, PLAN_REFINE, PLAN_TILES = 0x1, 0x2, 0x4, 0x8
 _lib.ws_plan_create.restype = ctypes.c_int
 _lib.ws_plan_create.argtypes = [ctypes.POINTER(Ragged), ctypes.POINTER(ctypes.c_void_p), ctypes.c_void_p]
 _lib.ws_plan_execute.restype = ctypes.c_int
@@ -365,12 +365,13 @@ class RaggedPlan:
         self._h = h
 
     def execute(self, x, w, lam, z=None, status=None, autotune: bool = False, graph: bool = False,
-                refine: bool = False, stream=None):
+                refine: bool = False, tiles: bool = False, stream=None):
         if z is None:
             z = torch.empty_like(x)
         if status is None:
             status = torch.empty(self.n, dtype=torch.uint8, device=x.device)
-        flags = (PLAN_AUTOTUNE if autotune else 0) | (PLAN_GRAPH if graph else 0) | (PLAN_REFINE if refine else 0)
+        flags = ((PLAN_AUTOTUNE if autotune else 0) | (PLAN_GRAPH if graph else 0) | (PLAN_REFINE if refine else 0)
+                 | (PLAN_TILES if tiles else 0))
         _check(_lib.ws_plan_execute(self._h, _ptr(x), _ptr(w), _ptr(lam), _ptr(z), _ptr(status), flags,
                                     _stream_ptr(stream)))
         return z, status

@@ -159,3 +159,28 @@ def test_ragged_scalar_lambda_refined(ws):
     out2 = dict(out)
     out2["lam"] = lam_s
     _check(out2, z, st, range(300), tol=1e-4, lam_scalar=True, mp_orders=(3,))
+
+
+@pytest.mark.parametrize("graph", [False, True])
+def test_ragged_tiles_mixed_lengths(ws, graph):
+    """WS_PLAN_TILES: series of 64 days or more go through length-class tiles (zero-weight
+    padding to a multiple of 32 days), shorter ones through the per-lane kernel; both agree
+    with the oracle, repeated executions (graph replay with new buffers) give the same z."""
+    rc = synth.Recipe(**{**synth.RECIPES["ragged"].__dict__, "p_valid": 1.0, "revisit": 1, "lam_log10": (0.0, 3.0)})
+    out = synth.generate_ragged(rc, 900, device="cuda", t_range=(0, 700), orders=(1, 2, 3, 4))
+    plan = ws.RaggedPlan(out["offsets"], out["order"])
+    z, st = plan.execute(out["x"], out["w"], out["lam"], graph=graph, tiles=True)
+    z2, st2 = plan.execute(out["x"].clone(), out["w"].clone(), out["lam"].clone(), graph=graph, tiles=True)
+    ws.sync_status()
+    assert torch.equal(z, z2) and torch.equal(st, st2)
+    _check(out, z, st, range(900), tol=1e-4)
+
+
+def test_ragged_tiles_sparse_refined(ws):
+    """The ragged recipe's sparse weights and unsmoothed lambda with tiles and refinement."""
+    rc = synth.RECIPES["ragged"]
+    out = synth.generate_ragged(rc, 400, device="cuda", t_range=(40, 600))
+    plan = ws.RaggedPlan(out["offsets"], out["order"])
+    z, st = plan.execute(out["x"], out["w"], out["lam"], refine=True, graph=True, tiles=True)
+    ws.sync_status()
+    _check(out, z, st, range(400), tol=1e-4, mp_orders=(3,))
