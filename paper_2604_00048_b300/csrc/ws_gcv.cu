@@ -11,10 +11,12 @@
 // backwards in t,
 //     Sigma[t][t+m] = - sum_{j=1..d} rho_{t,j} Sigma[t+j][t+m]       (m = 1..d)
 //     Sigma[t][t]   = invD_t - sum_{j=1..d} rho_{t,j} Sigma[t][t+j],
-// so a d x d window of Sigma rides along the back substitution. The window is carried in
-// double-word arithmetic: for large lambda rho approaches the difference coefficients and
-// rho^T Sigma rho is a d-th difference of a smooth function, so FP32 loses up to ~1e-2
-// of tr H at d = 3 (errors grow like t^(d-1) through the recursion); rho and invD stay FP32.
+// so a d x d window of Sigma rides along the back substitution. For d >= 3 the window is
+// carried in double-word arithmetic: for large lambda rho approaches the difference
+// coefficients and rho^T Sigma rho is a d-th difference of a smooth function, so FP32 loses
+// up to ~1e-2 of tr H at d = 3 (errors grow like t^(d-1) through the recursion). At d <= 2
+// FP32 keeps tr H to ~4e-4 at lambda = 1e5, which moves V by ~3e-5 (tr H << n there), so
+// the window stays FP32; rho and invD are FP32 in both cases.
 //
 // Mapping: one thread per (series, grid value). A CTA holds 16 series x 16 grid values;
 // the 16 lanes of a half-warp share a series, whose x and w chunks are staged once into
@@ -117,6 +119,7 @@ __global__ void __launch_bounds__(kGcvThreads, 2) k_gcv(const GcvArgs a) {
     const bool okser = live && !bad && npos >= (D < T ? D : T);
 
     using DWf = DW<float>;
+    constexpr bool kDWin = D >= 3;
     float zc[D];
     DWf Sg[D][D];
 #pragma unroll
@@ -162,16 +165,30 @@ __global__ void __launch_bounds__(kGcvThreads, 2) k_gcv(const GcvArgs a) {
           zc[0] = z;
           // selected inverse: Sg[a][b] = Sigma[t+1+a][t+1+b] on entry
           DWf sm[D];
-#pragma unroll
-          for (int m = 0; m < D; ++m) {
-            DWf acc = {0.f, 0.f};
-#pragma unroll
-            for (int j = 0; j < D; ++j) acc = dw_fma(acc, rk[k][j], Sg[j][m]);
-            sm[m] = DWf{-acc.hi, -acc.lo};  // Sigma[t][t+1+m]
-          }
           DWf s0 = {ik[k], 0.f};
+          if (kDWin) {
 #pragma unroll
-          for (int j = 0; j < D; ++j) s0 = dw_fma(s0, -rk[k][j], sm[j]);
+            for (int m = 0; m < D; ++m) {
+              DWf acc = {0.f, 0.f};
+#pragma unroll
+              for (int j = 0; j < D; ++j) acc = dw_fma(acc, rk[k][j], Sg[j][m]);
+              sm[m] = DWf{-acc.hi, -acc.lo};  // Sigma[t][t+1+m]
+            }
+#pragma unroll
+            for (int j = 0; j < D; ++j) s0 = dw_fma(s0, -rk[k][j], sm[j]);
+          } else {  // FP32 window (the lo parts stay zero)
+#pragma unroll
+            for (int m = 0; m < D; ++m) {
+              float acc = 0.f;
+#pragma unroll
+              for (int j = 0; j < D; ++j) acc = fmaf(rk[k][j], Sg[j][m].hi, acc);
+              sm[m] = DWf{-acc, 0.f};
+            }
+            float s0h = ik[k];
+#pragma unroll
+            for (int j = 0; j < D; ++j) s0h = fmaf(-rk[k][j], sm[j].hi, s0h);
+            s0 = DWf{s0h, 0.f};
+          }
 #pragma unroll
           for (int aa = D - 1; aa > 0; --aa)
 #pragma unroll
