@@ -970,7 +970,9 @@ extern "C" int ws_plan_execute(ws_plan* pl, const void* x, const void* w, const 
   int rc;
   if (refine && (rc = refine_alloc(pl)) != WS_OK) return rc;
   if (tiles && (rc = tiles_alloc(pl)) != WS_OK) return rc;
-  if (!x || !w || !lam || !z) return set_error(WS_EINVAL, "x, w, lam and z must be non-NULL");
+  // with no days at all (every series empty) only the status codes are written
+  if (pl->N > 0 && (!x || !w || !z)) return set_error(WS_EINVAL, "x, w and z must be non-NULL");
+  if (!lam && (pl->N > 0 || pl->rg.lam_mode == WS_LAM_SCALAR)) return set_error(WS_EINVAL, "lam must be non-NULL");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   if ((flags & WS_PLAN_AUTOTUNE) && !pl->tuned && (rc = ragged_autotune(pl, x, w, lam, z, st)) != WS_OK) return rc;
   if (!(flags & WS_PLAN_GRAPH) || pl->rg.n_bands > 1) {
