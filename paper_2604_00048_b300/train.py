@@ -115,8 +115,8 @@ def evaluate(net: "ws.Tcn", n: int = 262144, T: int = 730, seed_shift: int = 100
         m = min(chunk, n - s0)
         out = synth.generate_tile(rc, m, series0=s0, device=device, want_clean=True)
         x, w, clean = out["x"], out["w"], out["clean"][:, 0, :]
-        zl, _, _ = learned_smooth(net, x, w)
-        zg, _, _, _ = ws.gcv_smooth(x, w, None, 2, want_scores=False)
+        zl, _, _ = learned_smooth(net, x, w, refine=True)
+        zg, _, _, _ = ws.gcv_smooth(x, w, None, 2, refine=True, want_scores=False)
         se_l += float(torch.sum((zl[:, 0, :].double() - clean.double()) ** 2).item())
         se_g += float(torch.sum((zg[:, 0, :].double() - clean.double()) ** 2).item())
         cnt += clean.numel()
