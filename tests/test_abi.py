@@ -58,3 +58,54 @@ def test_empty_problem_is_a_no_op(ws):
     pb = ws.make_problem(10, 1, 0, 2, ws.F32, ws.LAM_PER_DAY)
     rc = ws.lib().ws_smooth_batch(ctypes.byref(pb), None, None, None, None, None, None, 0, None, 0, None)
     assert rc == ws.WS_OK
+
+
+def test_gcv_argument_checks(ws):
+    pb = ws.make_problem(30, 1, 8, 2, ws.F32, ws.LAM_SCALAR)
+    grid = (ctypes.c_float * 3)(1.0, 10.0, 100.0)
+    call = ws.lib().ws_gcv_smooth
+    assert call(ctypes.byref(pb), None, None, grid, 0, None, None, None, None, 0, None, 0, None) == ws.WS_EINVAL
+    assert call(ctypes.byref(pb), None, None, grid, 17, None, None, None, None, 0, None, 0, None) == ws.WS_EINVAL
+    bad = (ctypes.c_float * 2)(1.0, -2.0)
+    assert call(ctypes.byref(pb), None, None, bad, 2, None, None, None, None, 0, None, 0, None) == ws.WS_EINVAL
+    assert "lam_grid" in ws.last_error()
+    pb64 = ws.make_problem(30, 1, 8, 2, ws.F64, ws.LAM_SCALAR)
+    assert call(ctypes.byref(pb64), None, None, grid, 3, None, None, None, None, 0, None, 0, None) == ws.WS_EUNSUPPORTED
+    pb3 = ws.make_problem(30, 3, 8, 2, ws.F32, ws.LAM_SCALAR)
+    assert call(ctypes.byref(pb3), None, None, grid, 3, None, None, None, None, 0, None, 0, None) == ws.WS_EUNSUPPORTED
+
+
+def test_network_argument_checks(ws):
+    lib = ws.lib()
+    good = ws.TcnBatch(730, 16, *ws.TCN_LOG_LAM)
+    n0 = lib.ws_tcn_scratch_size(ctypes.byref(good), 0)
+    n1 = lib.ws_tcn_scratch_size(ctypes.byref(good), 1)
+    rows = 16 * (730 + ws.TCN_GAP)
+    assert n0 >= rows * 8 and n1 >= n0 + rows * 128 * 5  # training keeps 3 activation + 2 gradient arrays
+    assert lib.ws_tcn_scratch_size(ctypes.byref(ws.TcnBatch(0, 16, 0.0, 1.0)), 0) == 0
+    assert lib.ws_tcn_scratch_size(ctypes.byref(ws.TcnBatch(10, 16, 2.0, 1.0)), 0) == 0
+    assert lib.ws_tcn_forward(ctypes.byref(good), None, None, None, None, None, None, None, 0, 0, None) == ws.WS_EINVAL
+    fake = ctypes.c_void_p(256)  # never dereferenced: the size check fails first
+    assert lib.ws_tcn_forward(ctypes.byref(good), fake, fake, fake, fake, fake, None, fake, 16, 0, None) == ws.WS_ENOMEM_WS
+    assert lib.ws_tcn_backward(ctypes.byref(good), None, None, None, None, 0, None) == ws.WS_EINVAL
+    assert lib.ws_adam_step(None, None, None, None, 10, 1, 1e-3, 0.9, 0.999, 1e-8, None) == ws.WS_EINVAL
+    assert lib.ws_adam_step(fake, fake, fake, fake, 10, 0, 1e-3, 0.9, 0.999, 1e-8, None) == ws.WS_EINVAL
+    assert lib.ws_mse_grad(None, None, None, None, 10, 1.0, None) == ws.WS_EINVAL
+    assert lib.ws_tcn_conv64(fake, fake, None, None, fake, 10, 5, 0, fake, None) == ws.WS_EINVAL  # forward needs bias
+    assert lib.ws_tcn_conv64(fake, fake, None, None, fake, 10, 5, 1, fake, None) == ws.WS_EINVAL  # gradient needs mask
+    assert lib.ws_tcn_conv64(fake, fake, fake, fake, fake, 10, 5, 2, fake, None) == ws.WS_EINVAL  # mode
+
+
+def test_noalloc_and_plan_argument_checks(ws):
+    lib = ws.lib()
+    assert lib.ws_smooth_batch_noalloc(None, None, None, None, None, None, None, 0, None) == ws.WS_EINVAL
+    bad = ws.make_problem(10, 1, 8, 0, ws.F32, ws.LAM_PER_DAY)
+    assert lib.ws_smooth_batch_noalloc(ctypes.byref(bad), None, None, None, None, None, None, 0, None) == ws.WS_EINVAL
+    h = ctypes.c_void_p()
+    assert lib.ws_plan_create(None, ctypes.byref(h), None) == ws.WS_EINVAL
+    rg = ws.Ragged(4, None, None, 2, 1, ws.F32, ws.LAM_PER_DAY)
+    assert lib.ws_plan_create(ctypes.byref(rg), ctypes.byref(h), None) == ws.WS_EINVAL  # offsets NULL
+    rg64 = ws.Ragged(4, 256, None, 2, 1, ws.F64, ws.LAM_PER_DAY)  # rejected before the offsets are read
+    assert lib.ws_plan_create(ctypes.byref(rg64), ctypes.byref(h), None) == ws.WS_EUNSUPPORTED
+    assert lib.ws_plan_execute(None, None, None, None, None, None, 0, None) == ws.WS_EINVAL
+    assert lib.ws_plan_info(None, None) == ws.WS_EINVAL
