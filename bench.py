@@ -495,12 +495,12 @@ def run_ours(args):
             "algorithmic_bytes_per_launch": kbytes, "kernel_ms": kms}
 
     # end to end through the C-ABI with host buffers (pinned), on a block of the tile: the
-    # block is streamed as sub-blocks of series over two streams (each with its own device
+    # block is streamed as sub-blocks of series over three streams (each with its own device
     # buffers and workspace), so host-to-device copies, the solves and device-to-host copies
     # of different sub-blocks overlap (PCIe is full duplex)
     e2e = None
     if not args.no_e2e:
-        Pe, nsub = min(P, 32768), 4
+        Pe, nsub, nstr = min(P, 32768), 8, 3
         Ps = Pe // nsub
         host = []
         for k in range(nsub):
@@ -513,9 +513,9 @@ def run_ours(args):
                 hb["gx"] = torch.empty_like(hb["x"]).pin_memory()
                 hb["gl"] = torch.empty_like(hb["l"]).pin_memory()
             host.append(hb)
-        streams = [torch.cuda.Stream(device=dev) for _ in range(2)]
+        streams = [torch.cuda.Stream(device=dev) for _ in range(nstr)]
         devb = []
-        for k in range(2):
+        for k in range(nstr):
             db = {n: torch.empty_like(t, device=dev) for n, t in host[0].items()}
             db["st"] = torch.empty(Ps, dtype=torch.uint8, device=dev)
             pb = ws.make_problem(T, B, Ps, d, ws.F32, ws.LAM_PER_DAY)
@@ -525,7 +525,7 @@ def run_ours(args):
 
         def e2e_step():
             for k in range(nsub):
-                s_k, db, hb = streams[k % 2], devb[k % 2], host[k]
+                s_k, db, hb = streams[k % nstr], devb[k % nstr], host[k]
                 with torch.cuda.stream(s_k):
                     for n in ("x", "w", "l") + (("g",) if has_bwd else ()):
                         db[n].copy_(hb[n], non_blocking=True)
@@ -551,7 +551,7 @@ def run_ours(args):
         e2e = {"value": Pe * world * ke / dt, "unit": "series/s", "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": d2h, "series_per_step": Pe,
                "note": "pinned host buffers, copies + C-ABI calls + sync inside the timed region, "
-                       f"{Pe}-series block of the tile in {nsub} sub-blocks over 2 streams"}
+                       f"{Pe}-series block of the tile in {nsub} sub-blocks over {nstr} streams"}
         del host, devb
 
     cpu = None
