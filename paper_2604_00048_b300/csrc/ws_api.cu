@@ -333,7 +333,7 @@ extern "C" int ws_smooth_batch(const ws_problem* pb, const void* x, const void* 
   rc = run_tile(P, MODE_SMOOTH, x, w, lam, nullptr, nullptr, z, nullptr, factor_out, status, 0, 0, workspace, st);
   if (rc != WS_OK || !refine) return rc;
   void* r = static_cast<char*>(workspace) + kHeaderBytes + ck_bytes;
-  rc = launch_residual(P, x, w, lam, z, r, 0, st);
+  rc = launch_residual(P, x, w, lam, z, r, 0, static_cast<unsigned*>(workspace), st);
   if (rc != WS_OK) return rc;
   return run_tile(P, MODE_RAW, r, w, lam, /*zin*/ nullptr, /*g0*/ nullptr, /*out*/ z, /*out2*/ nullptr,
                   /*factor*/ nullptr, /*status*/ nullptr, /*accum*/ 1, /*loglam*/ 0, workspace, st);
@@ -354,7 +354,7 @@ extern "C" int ws_refine(const ws_problem* pb, const void* x, const void* w, con
   rc = check_workspace(P, workspace, ws_bytes, resid_bytes(P), ck_bytes);
   if (rc != WS_OK) return rc;
   void* r = static_cast<char*>(workspace) + kHeaderBytes + ck_bytes;
-  rc = launch_residual(P, x, w, lam, z, r, 0, st);
+  rc = launch_residual(P, x, w, lam, z, r, 0, static_cast<unsigned*>(workspace), st);
   if (rc != WS_OK) return rc;
   return run_tile(P, MODE_RAW, r, w, lam, /*zin*/ nullptr, /*g0*/ nullptr, /*out*/ z, /*out2*/ nullptr,
                   /*factor*/ nullptr, /*status*/ nullptr, /*accum*/ 1, /*loglam*/ 0, workspace, st);
@@ -425,7 +425,7 @@ extern "C" int ws_solve_adjoint(const ws_problem* pb, const void* factor_or_null
   void* r = base + resid_bytes(P);
   rc = run_tile(P, MODE_RAW, gz, w, lam, nullptr, nullptr, g0, nullptr, nullptr, nullptr, 0, 0, workspace, st);
   if (rc != WS_OK) return rc;
-  rc = launch_residual(P, gz, w, lam, g0, r, 1, st);
+  rc = launch_residual(P, gz, w, lam, g0, r, 1, static_cast<unsigned*>(workspace), st);
   if (rc != WS_OK) return rc;
   return run_tile(P, MODE_ADJ, r, w, lam, z, g0, gx, glam, nullptr, status, 1, loglam, workspace, st);
 }

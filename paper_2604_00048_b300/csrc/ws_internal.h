@@ -116,8 +116,9 @@ int launch_tile_d4(const ws_problem&, int, int, const TileCfg&, const TileArgs&,
 int launch_factored(int what, const ws_problem& pb, const void* fac_in, void* fac_out, const void* w,
                     const void* lam, const void* x, void* out, const void* z, const void* gs, void* gx, void* glam,
                     uint8_t* status, int weighted, int loglam, cudaStream_t st);
-// raw = 0: r = W x - Omega z0; raw = 1: r = x - Omega z0.
+// raw = 0: r = W x - Omega z0; raw = 1: r = x - Omega z0. err: the workspace's device
+// error word (set when a staging wait gives up).
 int launch_residual(const ws_problem& pb, const void* x, const void* w, const void* lam, const void* z0,
-                    void* r, int raw, cudaStream_t st);
+                    void* r, int raw, unsigned* err, cudaStream_t st);
 
 }  // namespace ws

@@ -47,6 +47,21 @@ def test_smooth_matches_dense_oracle_many_chunks(ws, dtype, d, P, B):
     assert np.all(z.cpu().numpy()[:, :, ~ok] == 0)
 
 
+@pytest.mark.parametrize("d", [1, 2, 3, 4])
+@pytest.mark.parametrize("P", [300, 301])           # 300: TMA-staged residual; 301: plain loads
+def test_refine_fp64_across_day_blocks(ws, d, P):
+    """FP64 smoothing followed by a refinement step: T = 300 days spans two 256-day blocks of
+    the residual kernel, so the difference rows that straddle a block edge are checked too."""
+    ws.tune_set(0, 0)
+    rc, g, c = tile_inputs("layer", P, T=300, B=2, dtype=torch.float64, revisit=1, p_valid=0.5)
+    z, st = ws.smooth(g["x"], g["w"], g["lam"], d, refine=True)
+    ws.sync_status()
+    zr, ok = dense.smooth_tile(c["x"], c["w"], c["lam"], d)
+    assert np.array_equal(st.cpu().numpy() == 0, ok)
+    err = rel_err_per_series(z.cpu().numpy()[:, :, ok], zr[:, :, ok])
+    assert err <= TOL[torch.float64], f"max rel err {err:.3e}"
+
+
 @pytest.mark.parametrize("refine", [False, True])
 @pytest.mark.parametrize("B", [1, 4, 8, 10, 13])
 def test_smooth_band_counts_auto_config(ws, B, refine):
