@@ -20,6 +20,7 @@ from __future__ import annotations
 import argparse
 import math
 import struct
+import sys
 import time
 
 import numpy as np
@@ -98,7 +99,8 @@ def train(series: int, batch_size: int, epochs: float, lr: float, seed: int = 0,
         b += 1
         if b % log_every == 0 or b == n_batches:
             hist.append((b, float(loss.item())))
-            print(f"batch {b}/{n_batches} loss {hist[-1][1]:.3e} ({time.time() - t0:.0f} s)", flush=True)
+            print(f"batch {b}/{n_batches} loss {hist[-1][1]:.3e} ({time.time() - t0:.0f} s)", file=sys.stderr,
+                  flush=True)
             if ckpt:
                 save_checkpoint(ckpt, net, b)
     return net, b, hist
