@@ -47,17 +47,20 @@ struct RaggedArgs {
   int max_nch;
   int* counter;
   unsigned* err;
+  int warp_rows;          // ragged_warp_rows(RC, largest order of the plan)
   // refinement (plan-owned; NULL without WS_PLAN_REFINE)
   float* resid;           // r = W x - Omega z, same packing as x
   uint8_t* active;        // per item: 1 while some series of the item has not settled
-  uint8_t* conv;          // per series: 1 once the last correction was below tau * max|z|
+  uint8_t* conv;          // per series, after the last correction: bit 0 set when it was below
+                          // tau * max|z| (settled), bit 1 when below tau_drop * max|z| (done:
+                          // later steps leave the series out)
   float* zmax;            // per series: max |z| of the unrefined solution
   int32_t* list64;        // series re-solved in double-float
   int* count64;
   double* ck64;           // double-float checkpoints (8 bytes each), kFieldsMax * max_nch64 per thread
   const int8_t* d_of;     // per series order
   int max_nch64;
-  float tau;
+  float tau, tau_drop;
   const uint8_t* item_tiled;  // per item: 1 = its series are solved through the length-class tiles
 };
 
@@ -65,9 +68,14 @@ constexpr int kFieldsMax = 4 * 5 + 4;  // d(d+1) + d for d <= 4, one band
 
 template <int RC>
 struct RaggedSmem {
-  // rows of kPitch floats: X [RC], W [RC + 4], L [RC], E [2 * RC] (rho_3, rho_4)
-  static constexpr int rowX = 0, rowW = RC, rowL = 2 * RC + 4, rowE = 3 * RC + 4, rows = 5 * RC + 4;
+  // one stage, rows of kPitch floats: X [RC], W [RC + 4], L [RC]
+  static constexpr int rowX = 0, rowW = RC, rowL = 2 * RC + 4, rows = 3 * RC + 4;
 };
+// Shared-memory rows of one warp: two stages, then E [(max_d - 2) * RC] rows holding rho_3..
+// of the chunk being back-substituted (pass 2 only, so a single copy).
+__host__ __device__ inline int ragged_warp_rows(int RC, int max_d) {
+  return 2 * (3 * RC + 4) + (max_d > 2 ? max_d - 2 : 0) * RC;
+}
 
 // One item (32 series of order D) on one warp. RAW: the right-hand side is taken as given
 // (the refinement residual) and the solution is added to z (z0 + correction).
@@ -87,6 +95,7 @@ __device__ void ragged_item(const RaggedArgs& a, int item, float* sm, float* ck,
   const float* xb = MODE == MODE_RAW ? a.resid : a.x + (size_t)a.band * a.N;
   float* zb = a.z + (size_t)a.band * a.N;
   auto stg = [&](int st) -> float* { return sm + (size_t)st * L::rows * kPitch; };
+  float* const E = sm + (size_t)2 * L::rows * kPitch;
   if (nch == 0) {  // every series of the item is empty
     if (live && a.status != nullptr && a.band == 0) a.status[sid] = WS_SERIES_OK;
     return;
@@ -164,6 +173,7 @@ __device__ void ragged_item(const RaggedArgs& a, int item, float* sm, float* ck,
       __syncwarp();
     }
     float* S = stg(st);
+    const int t0 = c * RC;
     const float* ckc = ck + (size_t)c * kF * 32 + lane;
     s.load_factor(ckc, 32);
     s.load_y(ckc + kFF * 32, 32);
@@ -184,14 +194,14 @@ __device__ void ragged_item(const RaggedArgs& a, int item, float* sm, float* ck,
       S[(L::rowL + k) * kPitch + lane] = rho[0];
       if (D >= 2) S[(L::rowW + k) * kPitch + lane] = rho[D >= 2 ? 1 : 0];
 #pragma unroll
-      for (int j = 3; j <= D; ++j) S[(L::rowE + (j - 3) * RC + k) * kPitch + lane] = rho[j - 1];
+      for (int j = 3; j <= D; ++j) E[((j - 3) * RC + k) * kPitch + lane] = rho[j - 1];
     }
     for (int k = nd - 1; k >= 0; --k) {
       float rho[D];
       rho[0] = S[(L::rowL + k) * kPitch + lane];
       if (D >= 2) rho[D >= 2 ? 1 : 0] = S[(L::rowW + k) * kPitch + lane];
 #pragma unroll
-      for (int j = 3; j <= D; ++j) rho[j - 1] = S[(L::rowE + (j - 3) * RC + k) * kPitch + lane];
+      for (int j = 3; j <= D; ++j) rho[j - 1] = E[((j - 3) * RC + k) * kPitch + lane];
       float acc = S[(L::rowX + k) * kPitch + lane];
 #pragma unroll
       for (int j = 1; j <= D; ++j) acc = fmaf(-rho[j - 1], zc[j - 1], acc);
@@ -205,28 +215,38 @@ __device__ void ragged_item(const RaggedArgs& a, int item, float* sm, float* ck,
     }
     __syncwarp();
     // transposed store of the chunk: consecutive lanes write consecutive days of series s
-    const int t0 = c * RC;
-    for (int s2 = 0; s2 < 32; ++s2) {
-      const int64_t os = __shfl_sync(0xffffffffu, off, s2);
-      const int Ts = __shfl_sync(0xffffffffu, T, s2);
-      for (int j = lane; j < RC; j += 32)
-        if (t0 + j < Ts) {
-          const float v = S[(L::rowX + j) * kPitch + s2];
-          if (MODE == MODE_RAW)
-            zb[os + t0 + j] += v;  // z0 + correction
-          else
-            zb[os + t0 + j] = v;
-        }
+    // (RC <= 32: one day per lane). RAW adds the correction to z0, whose loads are issued
+    // 8 series at a time ahead of the stores (they may alias as far as the compiler knows).
+    static_assert(RC <= 32, "one day per lane in the transposed store");
+    for (int s0 = 0; s0 < 32; s0 += 8) {
+      int64_t gi[8];
+      bool ok[8];
+      float z0v[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const int64_t os = __shfl_sync(0xffffffffu, off, s0 + q);
+        const int Ts = __shfl_sync(0xffffffffu, T, s0 + q);
+        gi[q] = os + t0 + lane;
+        ok[q] = lane < RC && t0 + lane < Ts;
+        z0v[q] = (MODE == MODE_RAW && ok[q]) ? zb[gi[q]] : 0.f;
+      }
+#pragma unroll
+      for (int q = 0; q < 8; ++q)
+        if (ok[q]) zb[gi[q]] = z0v[q] + S[(L::rowX + lane) * kPitch + s0 + q];  // RAW: z0 + correction
     }
     __syncwarp();
     if (c >= 2) issue(c - 2, st);
   }
   if (MODE == MODE_SMOOTH && live && a.zmax != nullptr) a.zmax[sid] = amax;
   if (MODE == MODE_RAW) {
-    // a series has settled when its correction is below tau * max|z| (NaN never settles)
-    const bool settled = !live || (amax <= a.tau * a.zmax[sid]);
-    if (live) a.conv[sid] = settled ? 1 : 0;
-    if (__all_sync(0xffffffffu, settled) && lane == 0) a.active[item] = 0;
+    // a series has settled when its correction is below tau * max|z| (NaN never settles);
+    // it is done, and leaves the later steps, below tau_drop * max|z|: a correction a little
+    // under tau can still leave an error several times tau when the step contracts slowly
+    const float zm = live ? a.zmax[sid] : 0.f;
+    const bool settled = !live || amax <= a.tau * zm;
+    const bool done = !live || amax <= a.tau_drop * zm;
+    if (live) a.conv[sid] = (settled ? 1 : 0) | (done ? 2 : 0);
+    if (__all_sync(0xffffffffu, done) && lane == 0) a.active[item] = 0;
   }
   if (MODE == MODE_SMOOTH && live && a.status != nullptr) {
     const bool nonfin = !(nanacc == 0.f);
@@ -241,7 +261,7 @@ template <int RC, int MODE>
 __global__ void __launch_bounds__(512) k_ragged(const RaggedArgs a) {
   extern __shared__ __align__(16) float rsm[];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  float* sm = rsm + (size_t)wid * 2 * RaggedSmem<RC>::rows * kPitch;
+  float* sm = rsm + (size_t)wid * a.warp_rows * kPitch;
   const int gw = blockIdx.x * (blockDim.x >> 5) + wid;  // persistent warp id
   float* ck = a.ckpt + (size_t)gw * a.max_nch * kFieldsMax * 32;
   for (;;) {
@@ -262,7 +282,10 @@ __global__ void __launch_bounds__(512) k_ragged(const RaggedArgs a) {
 // arithmetic from the first difference on: the series of this path reach cond(Omega) ~ 1e13
 // (unsmoothed lambda up to 1e5, d = 3, sparse weights), where a working-precision residual
 // would stall the refinement at the FP32 solution's own error. One warp per item, the lanes
-// over consecutive days of one series at a time (coalesced, no recurrence).
+// over 32 consecutive days of one series at a time (coalesced, no recurrence). Each lane forms
+// its own row q_t = lambda_t (D z0)_t once; D^T q at day t is the d-th backward difference
+// of q, built level by level from the previous lane's value (shuffle), lane 0 taking the last
+// lane's value of the previous 32 days.
 template <int D>
 __device__ void ragged_resid_item(const RaggedArgs& a, int item, int lane) {
   using DWf = DW<float>;
@@ -275,34 +298,38 @@ __device__ void ragged_resid_item(const RaggedArgs& a, int item, int lane) {
     const int64_t os = a.off[sid];
     const int T = (int)(a.off[sid + 1] - os);
     const float ls = a.lam_scalar ? a.lam[sid] : 0.f;
-    for (int t = lane; t < T; t += 32) {
-      // q_k = lambda_k (D z0)_k for the rows k = t-D..t that touch day t
-      DWf dtq[D + 1];
+    DWf carry[D];  // nabla^j q at the previous block's last day, j = 0..D-1
 #pragma unroll
-      for (int n = 0; n <= D; ++n) {
-        const int k = t - D + n;
-        DWf q = {0.f, 0.f};
-        if (k >= 0 && k <= T - D - 1) {
-          DWf lv[D];
+    for (int j = 0; j < D; ++j) carry[j] = DWf{0.f, 0.f};
+    for (int t0 = 0; t0 < T; t0 += 32) {
+      const int t = t0 + lane;
+      // q_t = lambda_t (D^D z0)_t, the nested first differences exact from the first on
+      DWf lv = {0.f, 0.f};
+      if (t <= T - D - 1) {
+        DWf dz[D];
 #pragma unroll
-          for (int m = 0; m < D; ++m) lv[m] = two_sum(zb[os + k + m + 1], -zb[os + k + m]);  // exact
+        for (int m = 0; m < D; ++m) dz[m] = two_sum(zb[os + t + m + 1], -zb[os + t + m]);
 #pragma unroll
-          for (int i = 1; i < D; ++i)
+        for (int i = 1; i < D; ++i)
 #pragma unroll
-            for (int m = 0; m < D - i; ++m) lv[m] = dw_add(lv[m + 1], DWf{-lv[m].hi, -lv[m].lo});
-          q = dw_scale(lv[0], a.lam_scalar ? ls : a.lam[os + k]);
-        }
-        dtq[n] = q;
+          for (int m = 0; m < D - i; ++m) dz[m] = dw_add(dz[m + 1], DWf{-dz[m].hi, -dz[m].lo});
+        lv = dw_scale(dz[0], a.lam_scalar ? ls : a.lam[os + t]);
       }
+      // nabla^j q_t = nabla^{j-1} q_t - nabla^{j-1} q_{t-1}
 #pragma unroll
-      for (int i = 0; i < D; ++i)
-#pragma unroll
-        for (int n = D; n > i; --n) dtq[n] = dw_add(dtq[n], DWf{-dtq[n - 1].hi, -dtq[n - 1].lo});
-      const DWf v = (D % 2) ? DWf{-dtq[D].hi, -dtq[D].lo} : dtq[D];
-      const float wt = a.w[os + t], xt = xb[os + t], zt = zb[os + t];
-      DWf acc = wt > 0.f ? dw_scale(two_sum(xt, -zt), wt) : DWf{0.f, 0.f};
-      acc = dw_add(acc, DWf{-v.hi, -v.lo});
-      rb[os + t] = acc.hi + acc.lo;
+      for (int j = 0; j < D; ++j) {
+        DWf prev = {__shfl_up_sync(0xffffffffu, lv.hi, 1), __shfl_up_sync(0xffffffffu, lv.lo, 1)};
+        if (lane == 0) prev = carry[j];
+        carry[j] = DWf{__shfl_sync(0xffffffffu, lv.hi, 31), __shfl_sync(0xffffffffu, lv.lo, 31)};
+        lv = dw_add(lv, DWf{-prev.hi, -prev.lo});
+      }
+      if (t < T) {
+        const DWf v = (D % 2) ? DWf{-lv.hi, -lv.lo} : lv;  // (D^T q)_t
+        const float wt = a.w[os + t], xt = xb[os + t], zt = zb[os + t];
+        DWf acc = wt > 0.f ? dw_scale(two_sum(xt, -zt), wt) : DWf{0.f, 0.f};
+        acc = dw_add(acc, DWf{-v.hi, -v.lo});
+        rb[os + t] = acc.hi + acc.lo;
+      }
     }
   }
 }
@@ -327,13 +354,64 @@ __global__ void __launch_bounds__(256) k_ragged_collect(const RaggedArgs a) {
   const int item = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   if (item >= a.n_items || !a.active[item]) return;
   const int sid = a.order[(size_t)item * 32 + lane];
-  const bool need = sid >= 0 && !a.conv[sid];
+  const bool need = sid >= 0 && !(a.conv[sid] & 1);
   const unsigned m = __ballot_sync(0xffffffffu, need);
   if (m == 0) return;
   int base = 0;
   if (lane == 0) base = atomicAdd(a.count64, __popc(m));
   base = __shfl_sync(0xffffffffu, base, 0);
   if (need) a.list64[base + __popc(m & ((1u << lane) - 1u))] = sid;
+}
+
+// Regrouping between refinement steps: the series not yet done after a step are listed
+// per order (one region of the compacted list per order, sized for all of that order's
+// series, in items of 32), so the next step runs those series only, in fresh items. One warp
+// per item, one atomic per warp; appends follow the items' (order, length) grouping.
+__global__ void __launch_bounds__(256) k_ragged_compact(const RaggedArgs a, int32_t* __restrict__ dst,
+                                                        int* __restrict__ cnt, int4 reg) {
+  const int lane = threadIdx.x & 31;
+  const int item = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (item >= a.n_items || !a.active[item]) return;
+  const int sid = a.order[(size_t)item * 32 + lane];
+  const bool need = sid >= 0 && !(a.conv[sid] & 2);
+  const unsigned m = __ballot_sync(0xffffffffu, need);
+  if (m == 0) return;
+  const int d = a.item_d[item];
+  int base = 0;
+  if (lane == 0) base = atomicAdd(&cnt[d - 1], __popc(m));
+  base = __shfl_sync(0xffffffffu, base, 0);
+  const int r0 = d == 1 ? reg.x : (d == 2 ? reg.y : (d == 3 ? reg.z : reg.w));
+  if (need) dst[r0 + base + __popc(m & ((1u << lane) - 1u))] = sid;
+}
+
+// Items of the compacted list: order and longest series of each, idle lanes marked -1,
+// items past their region's count inactive. reg: first slot of each order's region.
+__global__ void __launch_bounds__(256) k_ragged_regroup(const int64_t* __restrict__ off, int32_t* __restrict__ order,
+                                                        const int* __restrict__ cnt, int4 reg, int n_items,
+                                                        int8_t* __restrict__ item_d, int32_t* __restrict__ item_t,
+                                                        uint8_t* __restrict__ active) {
+  const int lane = threadIdx.x & 31;
+  const int item = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (item >= n_items) return;
+  const int slot = item * 32;
+  const int d = slot < reg.y ? 1 : (slot < reg.z ? 2 : (slot < reg.w ? 3 : 4));
+  const int r0 = d == 1 ? reg.x : (d == 2 ? reg.y : (d == 3 ? reg.z : reg.w));
+  const bool live = slot - r0 + lane < cnt[d - 1];
+  int T = 0;
+  if (live) {
+    const int sid = order[slot + lane];
+    T = (int)(off[sid + 1] - off[sid]);
+  } else {
+    order[slot + lane] = -1;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) T = max(T, __shfl_xor_sync(0xffffffffu, T, o));
+  const unsigned m = __ballot_sync(0xffffffffu, live);
+  if (lane == 0) {
+    item_d[item] = (int8_t)d;
+    item_t[item] = T;
+    active[item] = m != 0u ? 1 : 0;
+  }
 }
 
 // High-precision re-solve of one listed series by one thread: the same two-pass recurrence
@@ -509,7 +587,7 @@ struct LenClass {
 
 struct ws_plan {
   ws_ragged rg;
-  int n_items = 0, max_t = 0;
+  int n_items = 0, max_t = 0, max_d = 1;
   int RC = 16, warps = 8, grid = 0;
   int64_t N = 0;
   int32_t* d_order = nullptr;
@@ -529,6 +607,13 @@ struct ws_plan {
   double* d_ck64 = nullptr;
   int8_t* d_dof = nullptr;     // n_series
   int max_nch64 = 0, grid64 = 0;
+  // regrouped items of refinement steps 2.. (two sets, written alternately)
+  int creg[5] = {0, 0, 0, 0, 0};  // first slot of each order's region; creg[4] = all slots
+  int32_t* d_corder = nullptr;     // 2 x creg[4]
+  int8_t* d_citem_d = nullptr;     // 2 x creg[4] / 32
+  int32_t* d_citem_t = nullptr;
+  uint8_t* d_cactive = nullptr;
+  int* d_ccount = nullptr;         // 2 x 4
   bool tuned = false;
   float tuned_ms = 0.f;
   cudaGraph_t graph = nullptr;
@@ -548,7 +633,9 @@ struct ws_plan {
   bool graph_refine = false, graph_tiles = false;
 };
 
-static size_t ragged_smem(int RC, int warps) { return (size_t)warps * 2 * (5 * RC + 4) * kPitch * sizeof(float); }
+static size_t ragged_smem(int RC, int warps, int max_d) {
+  return (size_t)warps * ragged_warp_rows(RC, max_d) * kPitch * sizeof(float);
+}
 
 static const void* ragged_kernel(int RC, int mode) {
   if (RC == 8) return mode == MODE_RAW ? (const void*)k_ragged<8, MODE_RAW> : (const void*)k_ragged<8, MODE_SMOOTH>;
@@ -556,12 +643,13 @@ static const void* ragged_kernel(int RC, int mode) {
   return mode == MODE_RAW ? (const void*)k_ragged<32, MODE_RAW> : (const void*)k_ragged<32, MODE_SMOOTH>;
 }
 
-static int ragged_grid(int RC, int warps, int items, int* grid) {
+static int ragged_grid(int RC, int warps, int items, int max_d, int* grid) {
   DeviceInfo di;
   int rc = device_info(di);
   if (rc != WS_OK) return rc;
   const void* kern = ragged_kernel(RC, MODE_SMOOTH);
-  const size_t smem = ragged_smem(RC, warps);
+  const size_t smem = ragged_smem(RC, warps, max_d);
+  if (smem > (size_t)di.smem_optin) return WS_EUNSUPPORTED;  // the candidate does not fit
   for (int m : {MODE_SMOOTH, MODE_RAW})
     if (cudaFuncSetAttribute(ragged_kernel(RC, m), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
       return set_error(WS_ECUDA, "ragged: cudaFuncSetAttribute");
@@ -577,6 +665,7 @@ static int ragged_grid(int RC, int warps, int items, int* grid) {
 
 constexpr int kRefineSteps = 3;     // FP32 refinement steps before the double-float re-solve
 constexpr float kRefineTau = 3e-5f;  // settled: correction <= tau * max|z|
+constexpr float kRefineTauDrop = 3e-6f;  // done (left out of later steps): correction <= tau_drop * max|z|
 constexpr int kHPBlocksPerSM = 4;    // double-float re-solve: 4 x 128 threads per SM (128 registers each)
 
 static void fill_refine_args(const ws_plan* pl, RaggedArgs& a) {
@@ -590,11 +679,21 @@ static void fill_refine_args(const ws_plan* pl, RaggedArgs& a) {
   a.d_of = pl->d_dof;
   a.max_nch64 = pl->max_nch64;
   a.tau = kRefineTau;
+  a.tau_drop = kRefineTauDrop;
 }
+
+// The items a launch runs: the plan's own, or a regrouped set of a refinement step.
+struct ItemSet {
+  const int32_t* order;
+  const int8_t* item_d;
+  const int32_t* item_t;
+  uint8_t* active;
+  int n_items;
+};
 
 static int ragged_launch(ws_plan* pl, const void* x, const void* w, const void* lam, void* z, uint8_t* status,
                          int band, cudaStream_t st, int mode = MODE_SMOOTH, bool refine = false,
-                         bool tiles = false) {
+                         bool tiles = false, const ItemSet* items = nullptr) {
   RaggedArgs a;
   memset(&a, 0, sizeof(a));
   a.item_tiled = (tiles && mode == MODE_SMOOTH) ? pl->d_item_tiled : nullptr;
@@ -617,7 +716,15 @@ static int ragged_launch(ws_plan* pl, const void* x, const void* w, const void* 
   a.counter = pl->d_counter + band;
   a.err = pl->d_err;
   if (refine) fill_refine_args(pl, a);
-  const size_t smem = ragged_smem(pl->RC, pl->warps);
+  if (items != nullptr) {
+    a.order = items->order;
+    a.item_d = items->item_d;
+    a.item_t = items->item_t;
+    a.active = items->active;
+    a.n_items = items->n_items;
+  }
+  a.warp_rows = ragged_warp_rows(pl->RC, pl->max_d);
+  const size_t smem = ragged_smem(pl->RC, pl->warps, pl->max_d);
   if (cudaMemsetAsync(a.counter, 0, sizeof(int), st) != cudaSuccess) return set_error(WS_ECUDA, "ragged: memset");
   const dim3 g(pl->grid), blk(pl->warps * 32);
   if (pl->RC == 8) {
@@ -654,14 +761,42 @@ static int ragged_refine(ws_plan* pl, const void* x, const void* w, const void* 
   a.z = (float*)z;
   fill_refine_args(pl, a);
   if (cudaMemsetAsync(pl->d_active, 1, pl->n_items, st) != cudaSuccess) return set_error(WS_ECUDA, "ragged: memset");
-  const int gi = (pl->n_items + 7) / 8;
+  ItemSet cur{pl->d_order, pl->d_item_d, pl->d_item_t, pl->d_active, pl->n_items};
+  const int4 reg = make_int4(pl->creg[0], pl->creg[1], pl->creg[2], pl->creg[3]);
+  const int nci = pl->creg[4] / 32;
   for (int k = 0; k < kRefineSteps; ++k) {
+    a.order = cur.order;
+    a.item_d = cur.item_d;
+    a.item_t = cur.item_t;
+    a.active = cur.active;
+    a.n_items = cur.n_items;
+    const int gi = (cur.n_items + 7) / 8;
     k_ragged_resid<<<gi, 256, 0, st>>>(a);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return set_error(WS_ECUDA, "ragged residual launch: %s", cudaGetErrorString(e));
-    int rc = ragged_launch(pl, x, w, lam, z, nullptr, band, st, MODE_RAW, true);
+    int rc = ragged_launch(pl, x, w, lam, z, nullptr, band, st, MODE_RAW, true, false, &cur);
     if (rc != WS_OK) return rc;
+    if (k + 1 == kRefineSteps || nci == 0) continue;
+    // the next step runs the still unsettled series only, regrouped
+    const int q = k & 1;
+    ItemSet nxt{pl->d_corder + (size_t)q * pl->creg[4], pl->d_citem_d + (size_t)q * nci,
+                pl->d_citem_t + (size_t)q * nci, pl->d_cactive + (size_t)q * nci, nci};
+    int* cnt = pl->d_ccount + 4 * q;
+    if (cudaMemsetAsync(cnt, 0, 4 * sizeof(int), st) != cudaSuccess) return set_error(WS_ECUDA, "ragged: memset");
+    k_ragged_compact<<<gi, 256, 0, st>>>(a, const_cast<int32_t*>(nxt.order), cnt, reg);
+    k_ragged_regroup<<<(nci + 7) / 8, 256, 0, st>>>(pl->rg.offsets, const_cast<int32_t*>(nxt.order), cnt, reg, nci,
+                                                     const_cast<int8_t*>(nxt.item_d), const_cast<int32_t*>(nxt.item_t),
+                                                     nxt.active);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return set_error(WS_ECUDA, "ragged regroup launch: %s", cudaGetErrorString(e));
+    cur = nxt;
   }
+  a.order = cur.order;
+  a.item_d = cur.item_d;
+  a.item_t = cur.item_t;
+  a.active = cur.active;
+  a.n_items = cur.n_items;
+  const int gi = (cur.n_items + 7) / 8;
   if (cudaMemsetAsync(a.count64, 0, sizeof(int), st) != cudaSuccess) return set_error(WS_ECUDA, "ragged: memset");
   k_ragged_collect<<<gi, 256, 0, st>>>(a);
   k_ragged64<<<pl->grid64, 128, 0, st>>>(a);
@@ -770,7 +905,13 @@ static int refine_alloc(ws_plan* pl) {
                   cudaMalloc(&pl->d_zmax, 4 * n) == cudaSuccess && cudaMalloc(&pl->d_list64, 4 * n) == cudaSuccess &&
                   cudaMalloc(&pl->d_count64, sizeof(int) * pl->rg.n_bands) == cudaSuccess &&
                   cudaMalloc(&pl->d_ck64, ck) == cudaSuccess;
-  if (!ok) return set_error(WS_ECUDA, "plan: refinement allocation");
+  const size_t cs = (size_t)std::max(32, pl->creg[4]), cni = cs / 32;
+  const bool okc = ok && cudaMalloc(&pl->d_corder, 2 * cs * 4) == cudaSuccess &&
+                   cudaMalloc(&pl->d_citem_d, 2 * cni) == cudaSuccess &&
+                   cudaMalloc(&pl->d_citem_t, 2 * cni * 4) == cudaSuccess &&
+                   cudaMalloc(&pl->d_cactive, 2 * cni) == cudaSuccess &&
+                   cudaMalloc(&pl->d_ccount, 2 * 4 * sizeof(int)) == cudaSuccess;
+  if (!okc) return set_error(WS_ECUDA, "plan: refinement allocation");
   cudaMemset(pl->d_count64, 0, sizeof(int) * pl->rg.n_bands);
   return WS_OK;
 }
@@ -778,7 +919,7 @@ static int refine_alloc(ws_plan* pl) {
 static int ragged_config(ws_plan* pl, int RC, int warps) {
   pl->RC = RC;
   pl->warps = warps;
-  int rc = ragged_grid(RC, warps, pl->n_items, &pl->grid);
+  int rc = ragged_grid(RC, warps, pl->n_items, pl->max_d, &pl->grid);
   if (rc != WS_OK) return rc;
   const size_t need = (size_t)pl->grid * warps * ((pl->max_t + RC - 1) / RC) * kFieldsMax * 32 * 4;
   if (need > pl->ckpt_bytes) {
@@ -846,6 +987,7 @@ extern "C" int ws_plan_create(const ws_ragged* rg, ws_plan** out, void* stream) 
     idd[k] = (int8_t)items[k].d;
     itt[k] = (int32_t)items[k].tmax;
     pl->max_t = std::max(pl->max_t, itt[k]);
+    pl->max_d = std::max(pl->max_d, (int)idd[k]);
   }
   const size_t ni = std::max(1, pl->n_items);
   bool okm = cudaMalloc(&pl->d_order, ni * 32 * 4) == cudaSuccess && cudaMalloc(&pl->d_item_d, ni) == cudaSuccess &&
@@ -863,6 +1005,11 @@ extern "C" int ws_plan_create(const ws_ragged* rg, ws_plan** out, void* stream) 
     cudaMemcpy(pl->d_dof, dd.data(), n, cudaMemcpyHostToDevice);
   }
   for (const Item& it : items) pl->max_nch64 = std::max(pl->max_nch64, (int)((it.tmax + kRC64 - 1) / kRC64));
+  {
+    int nd[4] = {0, 0, 0, 0};
+    for (int i = 0; i < n; ++i) ++nd[dd[i] - 1];
+    for (int q = 0; q < 4; ++q) pl->creg[q + 1] = pl->creg[q] + (nd[q] + 31) / 32 * 32;
+  }
   // Length classes for WS_PLAN_TILES (one band, FP32): the series of items whose shortest
   // series has at least kTileMinT days, grouped by (order, length rounded up to kClassRound)
   if (rg->n_bands == 1 && pl->n_items > 0) {
@@ -931,15 +1078,17 @@ extern "C" int ws_plan_create(const ws_ragged* rg, ws_plan** out, void* stream) 
 
 // Autotuner: time every (chunk, warps per CTA) candidate on the plan's own data, keep the fastest.
 static int ragged_autotune(ws_plan* pl, const void* x, const void* w, const void* lam, void* z, cudaStream_t st) {
-  const int cands[][2] = {{8, 8}, {8, 16}, {16, 4}, {16, 8}, {32, 4}};
+  const int cands[][2] = {{8, 8}, {8, 16}, {16, 4}, {16, 6}, {16, 8}, {16, 12}, {16, 16}, {32, 4}, {32, 8}};
+  constexpr int kCands = sizeof(cands) / sizeof(cands[0]);
   float best = 1e30f;
-  int bi = 1;
+  int bi = -1;
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
-  for (int c = 0; c < 5; ++c) {
+  for (int c = 0; c < kCands; ++c) {
     int rc = ragged_config(pl, cands[c][0], cands[c][1]);
-    if (rc != WS_OK) continue;
+    if (rc == WS_EUNSUPPORTED) continue;  // more shared memory than a CTA may have
+    if (rc != WS_OK) return rc;
     if ((rc = ragged_launch(pl, x, w, lam, z, nullptr, 0, st)) != WS_OK) return rc;  // warm-up
     cudaEventRecord(e0, st);
     if ((rc = ragged_launch(pl, x, w, lam, z, nullptr, 0, st)) != WS_OK) return rc;
@@ -954,6 +1103,7 @@ static int ragged_autotune(ws_plan* pl, const void* x, const void* w, const void
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
+  if (bi < 0) return set_error(WS_EUNSUPPORTED, "ragged autotune: no configuration fits");
   pl->tuned = true;
   pl->tuned_ms = best;
   return ragged_config(pl, cands[bi][0], cands[bi][1]);
@@ -1098,6 +1248,11 @@ extern "C" void ws_plan_destroy(ws_plan* pl) {
   cudaFree(pl->d_resid);
   cudaFree(pl->d_active);
   cudaFree(pl->d_conv);
+  cudaFree(pl->d_corder);
+  cudaFree(pl->d_citem_d);
+  cudaFree(pl->d_citem_t);
+  cudaFree(pl->d_cactive);
+  cudaFree(pl->d_ccount);
   cudaFree(pl->d_zmax);
   cudaFree(pl->d_list64);
   cudaFree(pl->d_count64);
