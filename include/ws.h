@@ -281,9 +281,13 @@ typedef struct ws_plan_stats {
   float tuned_ms;         /* best time the autotuner measured */
   int32_t hp_series;      /* series of band 0 re-solved in double-float by the last refined
                              execute (reading it synchronises the device) */
+  int32_t tiles;          /* WS_PLAN_TILES is honoured: 0 once the autotuner found the
+                             per-lane kernel faster on this plan */
 } ws_plan_stats;
 
-#define WS_PLAN_AUTOTUNE 0x1u  /* ws_plan_execute: time the (chunk, warps/CTA) candidates once */
+#define WS_PLAN_AUTOTUNE 0x1u  /* ws_plan_execute: time the (chunk, warps/CTA) candidates once;
+                                  with WS_PLAN_TILES also the length-class tiles against the
+                                  best per-lane configuration, keeping them only if faster */
 #define WS_PLAN_GRAPH 0x2u     /* ws_plan_execute: replay a captured CUDA graph (one band) */
 #define WS_PLAN_TILES 0x8u     /* ws_plan_execute: series of at least 64 days (one band) are
                                   solved as length-class tiles by the tile kernels: padded
@@ -291,13 +295,15 @@ typedef struct ws_plan_stats {
                                   the solution unchanged; the plan allocates four float
                                   arrays of the padded size on first use */
 #define WS_PLAN_REFINE 0x4u    /* ws_plan_execute: iterative refinement (the paper
-                                  fixes no precision): up to two FP32 steps, r = W x - Omega z with a
-                                  double-word combination, z += Omega^{-1} r, until the
-                                  correction of a series is <= 1e-5 max|z|; series still
-                                  unsettled are solved again in double-float arithmetic
-                                  (hi + lo FP32 pairs, about 48 bits). On first use the plan
-                                  allocates N floats, 10 bytes per series and about
-                                  0.76 GB of checkpoints at T = 3288. */
+                                  fixes no precision): up to three FP32 steps, r = W x - Omega z
+                                  with a double-word combination, z += Omega^{-1} r; a series
+                                  leaves the steps once its correction is <= 3e-6 max|z| (the
+                                  others are regrouped into fresh items for the next step);
+                                  series whose last correction is still > 3e-5 max|z| are
+                                  solved again in double-float arithmetic (hi + lo FP32 pairs,
+                                  about 48 bits). On first use the plan allocates N floats,
+                                  about 30 bytes per series and about 0.76 GB of checkpoints
+                                  at T = 3288. */
 
 int ws_plan_create(const ws_ragged* rg, ws_plan** out, void* stream);
 

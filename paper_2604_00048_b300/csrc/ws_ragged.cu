@@ -615,6 +615,7 @@ struct ws_plan {
   uint8_t* d_cactive = nullptr;
   int* d_ccount = nullptr;         // 2 x 4
   bool tuned = false;
+  bool tiles_win = true;  // the autotuner found the length-class tiles faster (or has not run)
   float tuned_ms = 0.f;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
@@ -1076,8 +1077,13 @@ extern "C" int ws_plan_create(const ws_ragged* rg, ws_plan** out, void* stream) 
   return WS_OK;
 }
 
-// Autotuner: time every (chunk, warps per CTA) candidate on the plan's own data, keep the fastest.
-static int ragged_autotune(ws_plan* pl, const void* x, const void* w, const void* lam, void* z, cudaStream_t st) {
+static int ragged_tiles(ws_plan* pl, const void* x, const void* w, const void* lam, void* z, uint8_t* status,
+                        bool refine, cudaStream_t st);
+
+// Autotuner: time every (chunk, warps per CTA) candidate on the plan's own data, keep the
+// fastest; with try_tiles, time the length-class tiles (short series per lane) against it.
+static int ragged_autotune(ws_plan* pl, const void* x, const void* w, const void* lam, void* z, bool try_tiles,
+                           cudaStream_t st) {
   const int cands[][2] = {{8, 8}, {8, 16}, {16, 4}, {16, 6}, {16, 8}, {16, 12}, {16, 16}, {32, 4}, {32, 8}};
   constexpr int kCands = sizeof(cands) / sizeof(cands[0]);
   float best = 1e30f;
@@ -1101,12 +1107,26 @@ static int ragged_autotune(ws_plan* pl, const void* x, const void* w, const void
       bi = c;
     }
   }
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
   if (bi < 0) return set_error(WS_EUNSUPPORTED, "ragged autotune: no configuration fits");
+  int rc = ragged_config(pl, cands[bi][0], cands[bi][1]);
+  if (rc != WS_OK) return rc;
   pl->tuned = true;
   pl->tuned_ms = best;
-  return ragged_config(pl, cands[bi][0], cands[bi][1]);
+  if (try_tiles) {
+    float ms = 0.f;
+    for (int it = 0; it < 2; ++it) {  // warm-up, then timed
+      cudaEventRecord(e0, st);
+      if ((rc = ragged_launch(pl, x, w, lam, z, nullptr, 0, st, MODE_SMOOTH, false, true)) != WS_OK) return rc;
+      if ((rc = ragged_tiles(pl, x, w, lam, z, nullptr, false, st)) != WS_OK) return rc;
+      cudaEventRecord(e1, st);
+      cudaEventSynchronize(e1);
+      cudaEventElapsedTime(&ms, e0, e1);
+    }
+    pl->tiles_win = ms < best;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return WS_OK;
 }
 
 extern "C" int ws_plan_execute(ws_plan* pl, const void* x, const void* w, const void* lam, void* z, uint8_t* status,
@@ -1115,16 +1135,18 @@ extern "C" int ws_plan_execute(ws_plan* pl, const void* x, const void* w, const 
   if (flags & ~(WS_PLAN_AUTOTUNE | WS_PLAN_GRAPH | WS_PLAN_REFINE | WS_PLAN_TILES))
     return set_error(WS_EINVAL, "unknown flags 0x%x", flags);
   const bool refine = (flags & WS_PLAN_REFINE) != 0;
-  const bool tiles = (flags & WS_PLAN_TILES) != 0 && pl->rg.n_bands == 1 && !pl->classes.empty();
+  const bool tiles_req = (flags & WS_PLAN_TILES) != 0 && pl->rg.n_bands == 1 && !pl->classes.empty();
   if (pl->n_items == 0) return WS_OK;
   int rc;
   if (refine && (rc = refine_alloc(pl)) != WS_OK) return rc;
-  if (tiles && (rc = tiles_alloc(pl)) != WS_OK) return rc;
+  if (tiles_req && (rc = tiles_alloc(pl)) != WS_OK) return rc;
   // with no days at all (every series empty) only the status codes are written
   if (pl->N > 0 && (!x || !w || !z)) return set_error(WS_EINVAL, "x, w and z must be non-NULL");
   if (!lam && (pl->N > 0 || pl->rg.lam_mode == WS_LAM_SCALAR)) return set_error(WS_EINVAL, "lam must be non-NULL");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  if ((flags & WS_PLAN_AUTOTUNE) && !pl->tuned && (rc = ragged_autotune(pl, x, w, lam, z, st)) != WS_OK) return rc;
+  if ((flags & WS_PLAN_AUTOTUNE) && !pl->tuned && (rc = ragged_autotune(pl, x, w, lam, z, tiles_req, st)) != WS_OK)
+    return rc;
+  const bool tiles = tiles_req && pl->tiles_win;
   if (!(flags & WS_PLAN_GRAPH) || pl->rg.n_bands > 1) {
     for (int b = 0; b < pl->rg.n_bands; ++b) {
       if (tiles && refine && cudaMemsetAsync(pl->d_zmax, 0, sizeof(float) * pl->rg.n_series, st) != cudaSuccess)
@@ -1221,6 +1243,7 @@ extern "C" int ws_plan_info(const ws_plan* pl, ws_plan_stats* out) {
   out->tuned_ms = pl->tuned_ms;
   out->graph = pl->exec != nullptr ? 1 : 0;
   out->hp_series = 0;
+  out->tiles = pl->tiles_win ? 1 : 0;
   if (pl->d_count64 != nullptr && cudaMemcpy(&out->hp_series, pl->d_count64, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
     return set_error(WS_ECUDA, "plan info: reading the re-solve count");
   return WS_OK;

@@ -84,7 +84,7 @@ class Ragged(ctypes.Structure):
 class PlanStats(ctypes.Structure):
     _fields_ = [("n_items", ctypes.c_int32), ("chunk_days", ctypes.c_int32), ("warps_per_cta", ctypes.c_int32),
                 ("grid", ctypes.c_int32), ("tuned", ctypes.c_int32), ("graph", ctypes.c_int32),
-                ("tuned_ms", ctypes.c_float), ("hp_series", ctypes.c_int32)]
+                ("tuned_ms", ctypes.c_float), ("hp_series", ctypes.c_int32), ("tiles", ctypes.c_int32)]
 
 
 PLAN_AUTOTUNE, PLAN_GRAPH, PLAN_REFINE, PLAN_TILES = 0x1, 0x2, 0x4, 0x8

@@ -96,6 +96,22 @@ def test_ragged_refine_well_posed_stays_fp32(ws):
     _check(out, z, st, range(300), tol=1e-5)
 
 
+def test_ragged_autotune_decides_tiles(ws):
+    """With tiles and the autotuner both requested, the plan times the length-class tiles
+    against the best per-lane configuration and keeps the faster; the solution is the
+    same either way."""
+    rc = synth.Recipe(**{**synth.RECIPES["ragged"].__dict__, "p_valid": 1.0, "revisit": 1, "lam_log10": (0.0, 3.0)})
+    out = synth.generate_ragged(rc, 600, device="cuda", t_range=(64, 400), orders=(1, 2, 3))
+    plan = ws.RaggedPlan(out["offsets"], out["order"])
+    z, st = plan.execute(out["x"], out["w"], out["lam"], autotune=True, tiles=True)
+    info = plan.info()
+    assert info["tuned"] == 1 and info["tiles"] in (0, 1)
+    z2, _ = plan.execute(out["x"], out["w"], out["lam"], tiles=True)
+    ws.sync_status()
+    assert torch.equal(z, z2)
+    _check(out, z, st, range(600))
+
+
 def test_ragged_graph_updates_arguments_and_autotune(ws):
     rc = synth.Recipe(**{**synth.RECIPES["ragged"].__dict__, "p_valid": 1.0, "revisit": 1, "lam_log10": (0.0, 3.0)})
     out = synth.generate_ragged(rc, 300, device="cuda", t_range=(50, 400))
