@@ -197,6 +197,59 @@ def gcv_one(x, w, lam_grid, d: int):
     return best, scores, zb
 
 
+def posterior_one(x, w, lam, d: int, z=None):
+    """Posterior spread of the smooth, the credibility intervals of Fig. 4 (the paper takes
+    them from the Bayesian reading of the smoother it cites and does not restate them).
+
+    Reading: z is the posterior mean of the Gaussian model in which, on days with w_t > 0,
+    x_t given the signal s has precision w_t / sigma^2, and s has the (improper) prior density
+    proportional to exp(-s^T D^T Lambda D s / (2 sigma^2)). The posterior covariance of s is
+    then sigma^2 Omega^{-1}. sigma^2 is estimated per band by the residual variance
+    RSS_b / (n - tr H), RSS_b = sum_t w_t (x_tb - z_tb)^2, n = sum_t w_t, tr H =
+    sum_t w_t (Omega^{-1})_tt (H = Omega^{-1} W, the hat matrix).
+
+    x: [T] or [T, B]; z: the smooth (computed here when None). Returns (diag(Omega^{-1}) [T],
+    sigma2 [B], sd [T, B]) with sd_tb = sqrt(sigma2_b (Omega^{-1})_tt); the interval at level
+    q is z +- q sd."""
+    w = np.asarray(w, dtype=np.float64)
+    T = w.shape[0]
+    x2 = np.asarray(x, dtype=np.float64).reshape(T, -1)
+    if z is None:
+        z = smooth_one(x2, w, lam, d)
+    z2 = np.asarray(z, dtype=np.float64).reshape(T, -1)
+    Oi = np.linalg.inv(omega(w, lam, d))
+    dg = np.diag(Oi).copy()
+    n = float(np.sum(w))
+    trh = float(np.sum(w * dg))
+    xv = np.where(w[:, None] > 0, x2, 0.0)
+    rss = np.sum(w[:, None] * (xv - z2) ** 2, axis=0)
+    sigma2 = rss / (n - trh)
+    sd = np.sqrt(sigma2[None, :] * dg[:, None])
+    return dg, sigma2, sd
+
+
+def posterior_tile(x, w, lam, d: int, z=None):
+    """Tile layout: x, z [t, b, p], w [t, p], lam [t, p] or [p]. Returns (diag [t, p],
+    sigma2 [b, p], sd [t, b, p], ok [p]); series whose Omega is not positive definite get
+    zeros and ok = False."""
+    x = np.asarray(x, dtype=np.float64)
+    w = np.asarray(w, dtype=np.float64)
+    lam = np.asarray(lam, dtype=np.float64)
+    T, B, P = x.shape
+    dg = np.zeros((T, P))
+    s2 = np.zeros((B, P))
+    sd = np.zeros((T, B, P))
+    ok = np.zeros(P, dtype=bool)
+    for p in range(P):
+        lp = lam[p] if lam.ndim == 1 else lam[:, p]
+        if not is_pd(w[:, p], lp, d):
+            continue
+        ok[p] = True
+        zp = None if z is None else np.asarray(z, dtype=np.float64)[:, :, p]
+        dg[:, p], s2[:, p], sd[:, :, p] = posterior_one(x[:, :, p], w[:, p], lp, d, zp)
+    return dg, s2, sd, ok
+
+
 def mse_maxe(z, x, w):
     """Reconstruction metrics of Section 4.4: MSE = T^-1 sum_t W_tt (z_t - x_t)^2 and
     MaxE = max_t W_tt |z_t - x_t|."""
