@@ -46,9 +46,10 @@ def parse_args():
     ap.add_argument("--no-ragged", action="store_true")
     ap.add_argument("--no-gcv", action="store_true")
     ap.add_argument("--no-learned", action="store_true")
+    ap.add_argument("--no-posterior", action="store_true")
     ap.add_argument("--tcn-ckpt", default=None, help="trained lambda network (else one epoch is trained first)")
     ap.add_argument("--train-epochs", type=float, default=1.0, help="epochs of lambda-network training before timing")
-    ap.add_argument("--only", choices=["gcv", "learned", "ragged"], default=None,
+    ap.add_argument("--only", choices=["gcv", "learned", "ragged", "posterior"], default=None,
                     help="run one secondary measurement alone (profiling) and print it")
     ap.add_argument("--series", type=int, default=None, help="series of the --only measurement")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU work of the oracle baseline")
@@ -288,6 +289,48 @@ def gcv_measure(dev, steps, P=262144):
     return res
 
 
+def posterior_measure(dev, steps, x=None, w=None, lam=None, z=None, P=262144):
+    """Posterior spread (ws_posterior: diag(Omega^{-1}), sigma2 per band, sd) on the
+    heteroscedastic tile (the smooth z given; generated and smoothed here when absent).
+    Algorithmic bytes per pixel-day: read x, z (B bands each), w, lambda; write diag and sd
+    (B): 4 (3B + 3)."""
+    import torch
+
+    from paper_2604_00048_b300 import synth, ws
+
+    rc = synth.RECIPES["hetero_tile"]
+    if x is None:
+        out = synth.generate_tile(rc, P, device=dev)
+        x, w, lam = out["x"], out["w"], out["lam"]
+        del out
+        z, _ = ws.smooth(x, w, lam, rc.d, refine=True)
+    T, B, P = x.shape
+    outs = (torch.empty(T, P, device=dev), torch.empty(B, P, device=dev), torch.empty_like(x),
+            torch.empty(P, dtype=torch.uint8, device=dev))
+    stream = torch.cuda.Stream(device=dev)
+    with torch.cuda.stream(stream):
+        for _ in range(3):
+            ws.posterior(x, w, lam, z, rc.d, out=outs, stream=stream)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    with torch.cuda.stream(stream):
+        for _ in range(steps):
+            ws.posterior(x, w, lam, z, rc.d, out=outs, stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    hbm, _ = peaks()
+    byts = 4.0 * (3 * B + 3) * float(P) * T
+    res = {"workload": f"posterior: {P} series x {T} days x {B} bands, d={rc.d}, FP32 (diag of Omega^-1, "
+                       "sigma2 per band, sd)",
+           "ms": ms, "series_per_s": P / (ms / 1e3), "algorithmic_bytes": byts,
+           "achieved_gbs": byts / (ms / 1e3) / 1e9, "frac_of_measured_hbm": byts / (ms / 1e3) / 1e9 / hbm,
+           "series_with_status": int((outs[3] != 0).sum().item()), "launches_per_call": 2}
+    del outs
+    return res
+
+
 def learned_measure(dev, steps, ckpt=None, train_epochs=1.0, P=262144):
     """Learned lambda vs the GCV grid on the evaluation set (262,144 new series x 730 days,
     d = 2, one band): the lambda network is trained first on the project's kernels (one
@@ -392,6 +435,8 @@ def run_only(args):
     steps = max(1, args.steps)
     if args.only == "gcv":
         res = gcv_measure(dev, steps, args.series or 262144)
+    elif args.only == "posterior":
+        res = posterior_measure(dev, steps, P=args.series or 262144)
     elif args.only == "learned":
         res = learned_measure(dev, steps, args.tcn_ckpt, args.train_epochs, args.series or 262144)
     else:
@@ -565,11 +610,14 @@ def run_ours(args):
         cpu = {"value": rate, "unit": "series/s", "cores": cores, "kind": "oracle", "sample": sample}
 
     launches_per_step = 3 + (1 if has_bwd else 0)
+    if has_bwd:
+        del gz, gx, glam
+    ws._ws_cache.clear()
+    torch.cuda.empty_cache()
+    posterior = None if args.no_posterior else posterior_measure(dev, max(3, args.steps), x, w, lam, z)
     ragged = None
     if not args.no_ragged:
         del x, w, lam, z, status
-        if has_bwd:
-            del gz, gx, glam
         ws._ws_cache.clear()
         torch.cuda.empty_cache()
         ragged = ragged_measure(dev, max(3, args.steps))
@@ -583,6 +631,7 @@ def run_ours(args):
             "fwd_unrefined_series_per_s": P * world / (fwd_ms / 1e3),
             "smooth_ms": fwd_ms, "refine_ms": ref_ms, "adjoint_ms": bwd_ms,
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "ragged": ragged, "gcv": gcv, "learned": learned,
+            "posterior": posterior,
             "gpu_launches": launches_per_step * args.steps, "clocks": ck,
             "series_with_status": bad}
     if rank == 0:

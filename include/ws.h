@@ -78,6 +78,7 @@ extern "C" {
 #define WS_REFINE 0x2u        /* ws_smooth_batch: one step of iterative refinement */
 #define WS_GCV 0x8u           /* ws_workspace_size: size for ws_gcv_smooth */
 #define WS_REFINE_ADJOINT 0x4u /* ws_solve_adjoint: one step of iterative refinement of g */
+#define WS_POSTERIOR 0x10u     /* ws_workspace_size: size for ws_posterior */
 
 typedef struct ws_problem {
   int64_t n_series; /* P >= 0: number of series (pixels) */
@@ -129,6 +130,33 @@ int ws_smooth_batch(const ws_problem* pb, const void* x, const void* w, const vo
 int ws_gcv_smooth(const ws_problem* pb, const void* x, const void* w, const float* lam_grid, int n_grid,
                   void* z, float* lam_best, float* scores, uint8_t* status, uint32_t flags,
                   void* workspace, size_t ws_bytes, void* stream);
+
+/* Posterior spread of the smooth: the pointwise credibility intervals drawn in Fig. 4.
+ * The paper plots them and borrows their formula from the Bayesian reading of the smoother
+ * it cites; this call computes that reading. z = Omega^{-1} W x (Eq. 3) is the posterior
+ * mean of a signal whose observations on days with w_t > 0 have precision w_t / sigma^2 and
+ * whose improper prior has precision D^T Lambda D / sigma^2; the posterior covariance is
+ * sigma^2 Omega^{-1}, with sigma^2 estimated per band by RSS_b / (n - tr H), RSS_b =
+ * sum_t w_t (x_tb - z_tb)^2 over days with w_t > 0, n = sum_t w_t, tr H = sum_t w_t
+ * (Omega^{-1})_tt. Outputs (device, caller-owned, tile layout):
+ *   diag   [T][P]     (Omega^{-1})_tt, by the banded selected-inverse recursion on the
+ *                     rotation factor of the solve (double-word window in FP32);
+ *   sigma2 [B][P]     the residual variance per band (NaN where n - tr H <= 1e-4 n in
+ *                     FP32, 1e-10 n in FP64: the smoother interpolates the observations
+ *                     and the residual degrees of freedom are within rounding of zero);
+ *   sd     [T][B][P]  optional (NULL to skip): sqrt(sigma2_b diag_t); the interval at level
+ *                     q is z +- q sd.
+ * Inputs: x, w, lam as for ws_smooth_batch (FP32 or FP64, per-day or scalar lambda), z the
+ * smooth of x (normally ws_smooth_batch's output; any z is accepted and enters RSS only).
+ * Series whose Omega is not positive definite (status WS_SERIES_NOT_PD) or with invalid
+ * w/lambda (WS_SERIES_BADARG) get zeros in all three outputs; WS_SERIES_NONFINITE marks a
+ * non-finite diagonal or an undetermined sigma2 (NaN). Outputs may not overlap the inputs or each other
+ * (WS_EINVAL). Workspace: ws_workspace_size(pb, WS_POSTERIOR), 256-byte aligned (its
+ * error header is not used). Two kernel launches on `stream`; no allocation, no
+ * synchronisation. T = 0: sigma2 is zeroed and every status is WS_SERIES_NOT_PD. */
+int ws_posterior(const ws_problem* pb, const void* x, const void* w, const void* lam, const void* z,
+                 void* diag, void* sigma2, void* sd, uint8_t* status, void* workspace, size_t ws_bytes,
+                 void* stream);
 
 /* ---- Learned lambda: temporal convolution network g_theta (Section 4.2 names a network
  * with a sigmoid output range; this one is a 4-layer 1-D convolution net) ----

@@ -262,6 +262,16 @@ static int ws_adjoint_factored(const ws_problem* pb, const void* factor, const v
                          (flags & WS_GRAD_LOGLAM) ? 1 : 0, st);
 }
 
+// ws_posterior's scratch after the header: checkpoints, then n - tr H per series.
+static int post_bytes(const ws_problem& pb, size_t& bytes) {
+  int grid = 0, nch = 0;
+  size_t ck = 0;
+  int rc = post_plan(pb, grid, nch, ck);
+  if (rc != WS_OK) return rc;
+  bytes = round256(ck) + round256((size_t)pb.n_series * elem_size(pb));
+  return WS_OK;
+}
+
 extern "C" size_t ws_workspace_size(const ws_problem* pb, uint32_t flags) {
   clear_error();
   if (validate_problem(pb) != WS_OK) return 0;
@@ -276,7 +286,57 @@ extern "C" size_t ws_workspace_size(const ws_problem* pb, uint32_t flags) {
     if (gcv_plan(*pb, grid, nch, gck) != WS_OK) return 0;
     need = std::max(need, kHeaderBytes + round256(gck));
   }
+  if (flags & WS_POSTERIOR) {
+    size_t pck = 0;
+    if (post_bytes(*pb, pck) != WS_OK) return 0;
+    need = std::max(need, kHeaderBytes + pck);
+  }
   return need;
+}
+
+extern "C" int ws_posterior(const ws_problem* pb, const void* x, const void* w, const void* lam, const void* z,
+                            void* diag, void* sigma2, void* sd, uint8_t* status, void* workspace, size_t ws_bytes,
+                            void* stream) {
+  clear_error();
+  int rc = validate_problem(pb);
+  if (rc != WS_OK) return rc;
+  const ws_problem& P = *pb;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (P.n_series == 0) return WS_OK;
+  const int es = elem_size(P);
+  const size_t nx = (size_t)P.T * P.n_bands * P.n_series * es, nd = (size_t)P.T * P.n_series * es;
+  const size_t ns = (size_t)P.n_bands * P.n_series * es;
+  if (!sigma2) return set_error(WS_EINVAL, "sigma2 must be non-NULL");
+  if (P.T == 0) {  // no days: no valid observation, no posterior
+    if (cudaMemsetAsync(sigma2, 0, ns, st) != cudaSuccess ||
+        (status != nullptr && cudaMemsetAsync(status, WS_SERIES_NOT_PD, (size_t)P.n_series, st) != cudaSuccess))
+      return set_error(WS_ECUDA, "memset failed");
+    return WS_OK;
+  }
+  if (!x || !w || !lam || !z || !diag) return set_error(WS_EINVAL, "x, w, lam, z and diag must be non-NULL");
+  const size_t nl = P.lam_mode == WS_LAM_SCALAR ? (size_t)P.n_series * es : nd;
+  const void* ins[4] = {x, w, lam, z};
+  const size_t nin[4] = {nx, nd, nl, nx};
+  for (int i = 0; i < 4; ++i) {
+    if (overlaps(diag, nd, ins[i], nin[i]) || overlaps(sigma2, ns, ins[i], nin[i]) ||
+        (sd != nullptr && overlaps(sd, nx, ins[i], nin[i])))
+      return set_error(WS_EINVAL, "diag, sigma2 and sd must not overlap the inputs");
+  }
+  if (overlaps(diag, nd, sigma2, ns) || (sd != nullptr && (overlaps(sd, nx, diag, nd) || overlaps(sd, nx, sigma2, ns))))
+    return set_error(WS_EINVAL, "diag, sigma2 and sd must not overlap each other");
+  size_t need = 0;
+  rc = post_bytes(P, need);
+  if (rc != WS_OK) return rc;
+  need += kHeaderBytes;
+  if (workspace == nullptr || (reinterpret_cast<uintptr_t>(workspace) & 255u) != 0)
+    return set_error(WS_EINVAL, "workspace must be non-NULL and 256-byte aligned");
+  if (ws_bytes < need) return set_error(WS_ENOMEM_WS, "workspace too small: %zu < %zu", ws_bytes, need);
+  int grid = 0, nch = 0;
+  size_t ck = 0;
+  rc = post_plan(P, grid, nch, ck);
+  if (rc != WS_OK) return rc;
+  char* base = static_cast<char*>(workspace) + kHeaderBytes;
+  return launch_posterior(P, x, w, lam, z, diag, sigma2, sd, status, base, base + round256(ck), st);
 }
 
 extern "C" int ws_gcv_smooth(const ws_problem* pb, const void* x, const void* w, const float* lam_grid, int n_grid,

@@ -97,6 +97,12 @@ int gcv_plan(const ws_problem& pb, int& grid, int& nch, size_t& ck_bytes);
 int launch_gcv(const ws_problem& pb, const void* x, const void* w, const float* grid_vals, int n_grid,
                float* lam_best, float* scores, void* ckpt, cudaStream_t st);
 
+// Posterior spread (ws_post.cu): persistent grid, chunks and checkpoint bytes; launch of the
+// diagonal kernel and the spread kernel. den: P elements of scratch.
+int post_plan(const ws_problem& pb, int& grid, int& nch, size_t& ck_bytes);
+int launch_posterior(const ws_problem& pb, const void* x, const void* w, const void* lam, const void* z,
+                     void* diag, void* sigma2, void* sd, uint8_t* status, void* ckpt, void* den, cudaStream_t st);
+
 // Launchers (return WS_OK or an error code, errors recorded via set_error).
 extern int g_tune_ctas, g_tune_chunk;  // ws_tune_set() overrides (0 = automatic)
 int plan_tile(const ws_problem& pb, int mode, int nb, TileCfg& cfg);

@@ -62,6 +62,8 @@ _lib.ws_refine.argtypes = [_PP, _vp, _vp, _vp, _vp, _vp, _sz, _vp]
 _lib.ws_gcv_smooth.restype = ctypes.c_int
 _lib.ws_gcv_smooth.argtypes = [_PP, _vp, _vp, ctypes.POINTER(ctypes.c_float), ctypes.c_int, _vp, _vp, _vp, _vp,
                                _u32, _vp, _sz, _vp]
+_lib.ws_posterior.restype = ctypes.c_int
+_lib.ws_posterior.argtypes = [_PP, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _sz, _vp]
 _lib.ws_smooth_batch_noalloc.restype = ctypes.c_int
 _lib.ws_smooth_batch_noalloc.argtypes = [_PP, _vp, _vp, _vp, _vp, _vp, _vp, _u32, _vp]
 NOALLOC_MAX_BYTES = 64 << 20
@@ -248,6 +250,34 @@ def gcv_smooth(x: torch.Tensor, w: torch.Tensor, lam_grid=None, d: int = 2, *, r
     _check(_lib.ws_gcv_smooth(ctypes.byref(pb), _ptr(x), _ptr(w), arr, len(grid), _ptr(z), _ptr(lam_best),
                               _ptr(scores), _ptr(status), flags, _ptr(ws), ws.numel(), _stream_ptr(stream)))
     return z, lam_best, scores, status
+
+
+POSTERIOR = 0x10
+
+
+def posterior(x: torch.Tensor, w: torch.Tensor, lam: torch.Tensor, z: torch.Tensor, d: int = 2, *,
+              want_sd: bool = True, stream=None, workspace_buf=None, out=None):
+    """Posterior spread of the smooth z of x (the credibility intervals of Fig. 4):
+    diag(Omega^{-1}) per day, the residual variance sigma2_b = RSS_b / (n - tr H) per band,
+    and sd = sqrt(sigma2_b diag_t); the interval at level q is z +- q sd.
+
+    x, z: [T, B, P]; w: [T, P]; lam: [T, P] or [P]. out: optional (diag, sigma2, sd, status)
+    to write into. Returns (diag [T, P], sigma2 [B, P], sd [T, B, P] or None, status [P])."""
+    T, B, P, lm = _check_tile(x, w, lam, d)
+    if tuple(z.shape) != tuple(x.shape) or z.dtype != x.dtype or not z.is_cuda or not z.is_contiguous():
+        raise ValueError("z must be a contiguous CUDA tensor shaped and typed like x")
+    pb = make_problem(T, B, P, d, _dtype_code(x), lm)
+    if out is not None:
+        diag, sigma2, sd, status = out
+    else:
+        diag = torch.empty(T, P, dtype=x.dtype, device=x.device)
+        sigma2 = torch.empty(B, P, dtype=x.dtype, device=x.device)
+        sd = torch.empty_like(x) if want_sd else None
+        status = torch.empty(P, dtype=torch.uint8, device=x.device)
+    ws = workspace(pb, x.device, POSTERIOR, workspace_buf)
+    _check(_lib.ws_posterior(ctypes.byref(pb), _ptr(x), _ptr(w), _ptr(lam), _ptr(z), _ptr(diag), _ptr(sigma2),
+                             _ptr(sd), _ptr(status), _ptr(ws), ws.numel(), _stream_ptr(stream)))
+    return diag, sigma2, sd, status
 
 
 def smooth_noalloc(x: torch.Tensor, w: torch.Tensor, lam: torch.Tensor, d: int = 2, *, z, status,

@@ -109,3 +109,30 @@ def test_noalloc_and_plan_argument_checks(ws):
     assert lib.ws_plan_create(ctypes.byref(rg64), ctypes.byref(h), None) == ws.WS_EUNSUPPORTED
     assert lib.ws_plan_execute(None, None, None, None, None, None, 0, None) == ws.WS_EINVAL
     assert lib.ws_plan_info(None, None) == ws.WS_EINVAL
+
+
+def test_posterior_arguments_rejected_before_cuda(ws):
+    """ws_posterior: invalid problem, NULL outputs or inputs, outputs overlapping the inputs
+    or each other, all rejected with WS_EINVAL before any CUDA call; P = 0 is a no-op."""
+    L = ws.lib()
+    pb = ws.make_problem(10, 2, 8, 5, ws.F32, ws.LAM_PER_DAY)
+    assert L.ws_posterior(ctypes.byref(pb), *([None] * 8), None, 0, None) == ws.WS_EINVAL
+    pb = ws.make_problem(10, 2, 8, 2, ws.F32, ws.LAM_PER_DAY)
+    assert L.ws_posterior(ctypes.byref(pb), *([None] * 8), None, 0, None) == ws.WS_EINVAL
+    assert "sigma2" in ws.last_error()
+    # fake, never dereferenced device addresses: x, w, lam, z at distinct ranges
+    T, B, P = 10, 2, 8
+    nx, nd = T * B * P * 4, T * P * 4
+    base = 1 << 40
+    x, w, lam, z = base, base + 4096, base + 8192, base + 12288
+    diag, s2, sd = base + 16384, base + 20480, base + 24576
+    assert L.ws_posterior(ctypes.byref(pb), x, w, lam, z, None, s2, sd, None, None, 0, None) == ws.WS_EINVAL
+    assert "non-NULL" in ws.last_error()
+    assert L.ws_posterior(ctypes.byref(pb), x, w, lam, z, x + 64, s2, sd, None, None, 0, None) == ws.WS_EINVAL
+    assert "overlap" in ws.last_error()
+    assert L.ws_posterior(ctypes.byref(pb), x, w, lam, z, diag, diag + 16, sd, None, None, 0, None) == ws.WS_EINVAL
+    assert "overlap" in ws.last_error()
+    assert L.ws_posterior(ctypes.byref(pb), x, w, lam, z, diag, s2, z + nx - 4, None, None, 0, None) == ws.WS_EINVAL
+    assert nd < 4096 and nx < 4096
+    pb0 = ws.make_problem(10, 2, 0, 2, ws.F32, ws.LAM_PER_DAY)
+    assert L.ws_posterior(ctypes.byref(pb0), *([None] * 8), None, 0, None) == ws.WS_OK

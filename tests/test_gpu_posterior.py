@@ -1,0 +1,186 @@
+"""Posterior spread (ws_posterior: the credibility intervals of Fig. 4) against the dense
+FP64 oracle: diag(Omega^{-1}) per day, the residual variance per band and sd, on seeded
+inputs that span several 128-series tiles, 16-day chunks and a ragged tail of both; the
+orders 1..4, per-day and scalar lambda, FP32 and FP64; status codes and zero fill; empty
+problems; the full 262,144-series tile on sampled series.
+
+The GPU is given the oracle's own smooth z (rounded to its dtype) so that the comparison
+isolates the posterior; the full-size test runs the bench's pipeline (GPU smooth, then the
+posterior) and the oracle computes everything itself.
+
+Tolerance: diag(Omega^{-1}) is built from the FP32 rotation factor (double-word window of
+the selected inverse), a second-order quantity like the gradients: 1e-3 per series
+(||a - b||_inf / ||b||_inf), the same for sigma2 and sd; FP64 to 1e-8."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import dense
+from paper_2604_00048_b300 import synth
+
+pytestmark = pytest.mark.gpu
+
+TOL32 = 1e-3
+TOL64 = 1e-8
+
+
+@pytest.fixture(scope="module")
+def ws():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA device")
+    from paper_2604_00048_b300 import ws as mod
+    return mod
+
+
+def _rel(a, b, axis=0):
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    num = np.max(np.abs(a - b), axis=axis)
+    den = np.maximum(np.max(np.abs(b), axis=axis), 1e-30)
+    return float(np.max(num / den)) if num.size else 0.0
+
+
+def _inputs(recipe, P, T, B, dtype, **over):
+    base = synth.RECIPES[recipe].__dict__
+    rc = synth.Recipe(**{**base, "T": T, "n_bands": B, **over})
+    out = synth.generate_tile(rc, P, device="cpu", dtype=dtype)
+    return {k: v.numpy() for k, v in out.items()}
+
+
+def _run(ws, inp, d, dtype, want_sd=True):
+    """Oracle first (its own z), then the GPU posterior given that z."""
+    x, w, lam = inp["x"], inp["w"], inp["lam"]
+    zr, ok = dense.smooth_tile(x, w, lam, d)
+    dg_r, s2_r, sd_r, ok_r = dense.posterior_tile(x, w, lam, d)
+    assert np.array_equal(ok, ok_r)
+    dev = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=dtype, device="cuda")
+    dg, s2, sd, st = ws.posterior(dev(x), dev(w), dev(lam), dev(zr), d, want_sd=want_sd)
+    torch.cuda.synchronize()
+    out = (dg.cpu().double().numpy(), s2.cpu().double().numpy(),
+           None if sd is None else sd.cpu().double().numpy(), st.cpu().numpy())
+    return (dg_r, s2_r, sd_r, ok_r), out
+
+
+def _check(ref, got, tol, errs=None):
+    dg_r, s2_r, sd_r, ok = ref
+    dg, s2, sd, st = got
+    assert np.array_equal(st == 0, ok), "status mismatch"
+    assert np.all(dg[:, ~ok] == 0) and np.all(s2[:, ~ok] == 0)
+    e_dg = _rel(dg[:, ok], dg_r[:, ok])
+    e_s2 = _rel(s2[:, ok], s2_r[:, ok])  # per band and series (a single value each)
+    e_sd = _rel(sd[:, :, ok], sd_r[:, :, ok]) if sd is not None else 0.0
+    if sd is not None:
+        assert np.all(sd[:, :, ~ok] == 0)
+    if errs is not None:
+        errs.append((e_dg, e_s2, e_sd))
+    assert e_dg <= tol and e_s2 <= tol and e_sd <= tol, (e_dg, e_s2, e_sd)
+
+
+@pytest.mark.parametrize("d", [1, 2, 3, 4])
+def test_posterior_fp32_orders(ws, d):
+    """Heteroscedastic workload (per-day lambda 10^U[1,5], 15-day average, 5-day revisits
+    with p = 0.35) at 300 series (three tiles, the last ragged) x 200 days (13 chunks, the
+    last of 8 days) x 3 bands."""
+    inp = _inputs("hetero_tile", 300, 200, 3, torch.float32)
+    ref, got = _run(ws, inp, d, torch.float32)
+    _check(ref, got, TOL32)
+
+
+def test_posterior_fp32_scalar_lambda_no_sd(ws):
+    """One lambda per series (Eq. 2), 10^U[0,4], one band, sd not requested."""
+    inp = _inputs("homo_fp64", 260, 365, 1, torch.float32)
+    ref, got = _run(ws, inp, 2, torch.float32, want_sd=False)
+    assert got[2] is None
+    _check(ref, got, TOL32)
+
+
+def test_posterior_fp64(ws):
+    """FP64 path (64 series per CTA): the one-year homoscedastic workload, two bands."""
+    inp = _inputs("homo_fp64", 150, 365, 2, torch.float64)
+    ref, got = _run(ws, inp, 2, torch.float64)
+    _check(ref, got, TOL64)
+
+
+def test_posterior_status_and_short_series(ws):
+    """Series without a posterior: no valid day, fewer valid days than d (NOT_PD), a
+    negative weight (BADARG); short grids T = 1..5 around d = 2."""
+    inp = _inputs("hetero_tile", 40, 90, 2, torch.float32)
+    w = inp["w"].copy()
+    w[:, 0] = 0.0                      # no valid day
+    w[:, 1] = 0.0
+    w[10, 1] = 1.0                     # one valid day < d
+    w[5, 2] = -1.0                     # invalid weight
+    inp["w"] = w
+    x, lam = inp["x"], inp["lam"]
+    zr, ok = dense.smooth_tile(x, w, lam, 2)
+    dev = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float32, device="cuda")
+    dg, s2, sd, st = ws.posterior(dev(x), dev(w), dev(lam), dev(zr), 2)
+    torch.cuda.synchronize()
+    st = st.cpu().numpy()
+    assert st[0] == ws.SERIES_NOT_PD and st[1] == ws.SERIES_NOT_PD and st[2] == ws.SERIES_BADARG
+    for a in (dg.cpu().numpy()[:, :3], s2.cpu().numpy()[:, :3], sd.cpu().numpy()[:, :, :3]):
+        assert np.all(a == 0)
+    keep = np.arange(3, 40)
+    dg_r, s2_r, sd_r, okr = dense.posterior_tile(x[:, :, keep], w[:, keep], lam[:, keep], 2)
+    _check((dg_r, s2_r, sd_r, okr), (dg.cpu().double().numpy()[:, keep], s2.cpu().double().numpy()[:, keep],
+                                     sd.cpu().double().numpy()[:, :, keep], st[keep]), TOL32)
+    for T in (1, 2, 3, 5):
+        inp = _inputs("hetero_tile", 7, T, 1, torch.float32)
+        inp["w"][:] = 1.0
+        with np.errstate(divide="ignore", invalid="ignore"):
+            ref, got = _run(ws, inp, 2, torch.float32)
+        dg_r, _, _, ok = ref
+        dg, s2, _, st = got
+        # T <= d: Omega = W, z = x and n - tr H = 0: the spread is not determined (NaN,
+        # NONFINITE); T = 3: n - tr H = 1 - 1/(1 + 6 lambda) > 0
+        n = inp["w"].sum(axis=0)
+        und = ok & (n - (inp["w"] * dg_r).sum(axis=0) <= 1e-4 * n)
+        assert (T <= 2) == bool(und.all()) and (T <= 2 or not und.any())
+        assert np.all(st[und] == ws.SERIES_NONFINITE) and np.all(st[ok & ~und] == 0) and ok.all()
+        assert np.all(np.isnan(s2[:, und]))
+        assert _rel(dg, dg_r) <= TOL32
+        if not und.any():
+            _check(ref, got, TOL32)
+
+
+def test_posterior_empty(ws):
+    """P = 0 is a no-op; T = 0 zeroes sigma2 and marks every series NOT_PD."""
+    x = torch.zeros(0, 2, 5, device="cuda")
+    w = torch.zeros(0, 5, device="cuda")
+    lam = torch.zeros(0, 5, device="cuda")
+    dg, s2, sd, st = ws.posterior(x, w, lam, x.clone(), 2)
+    torch.cuda.synchronize()
+    assert torch.all(s2 == 0) and torch.all(st == ws.SERIES_NOT_PD)
+    x = torch.zeros(10, 1, 0, device="cuda")
+    dg, s2, sd, st = ws.posterior(x, torch.zeros(10, 0, device="cuda"), torch.zeros(10, 0, device="cuda"),
+                                  x.clone(), 2)
+    torch.cuda.synchronize()
+    assert dg.numel() == 0 and s2.numel() == 0
+
+
+def test_posterior_full_tile_sampled(ws):
+    """The 512 x 512 x 3288-day x 10-band tile: GPU smooth with its refinement step, then the
+    posterior, in bench.py's launch configuration; 4 sampled series against the dense
+    oracle (which solves for its own z)."""
+    rc = synth.RECIPES["hetero_tile"]
+    P = 262144
+    inp = synth.generate_tile(rc, P, device="cuda")
+    x, w, lam = inp["x"], inp["w"], inp["lam"]
+    del inp
+    z, st = ws.smooth(x, w, lam, 2, refine=True)
+    dg, s2, sd, st2 = ws.posterior(x, w, lam, z, 2)
+    ws.sync_status()
+    ids = np.sort(np.random.default_rng(11).choice(P, 4, replace=False))
+    it = torch.as_tensor(ids, device="cuda")
+    xs, wsn, ls = (t.index_select(-1, it).cpu().double().numpy() for t in (x, w, lam))
+    dg_r, s2_r, sd_r, ok = dense.posterior_tile(xs, wsn, ls, 2)
+    got = (dg.index_select(1, it).cpu().double().numpy(), s2.index_select(1, it).cpu().double().numpy(),
+           sd.index_select(2, it).cpu().double().numpy(), st2.cpu().numpy()[ids])
+    _check((dg_r, s2_r, sd_r, ok), got, TOL32)
+    # every series of the tile has a finite, positive spread where it has a posterior
+    okall = st2 == 0
+    assert int(okall.sum().item()) >= P - 16
+    assert bool(torch.all(dg[:, okall] > 0).item()) and bool(torch.all(torch.isfinite(s2[:, okall])).item())
+    del x, w, lam, z, dg, s2, sd
+    ws._ws_cache.clear()
+    torch.cuda.empty_cache()
