@@ -103,6 +103,37 @@ def vjp_one(w, lam, d: int, z, gz, per_day: bool = True):
     return gx.reshape(np.shape(z)), glam
 
 
+def vjp_w_one(x, w, lam, d: int, z, gz):
+    """dL/dw through z = Omega^{-1} W x, the weights of the objective (Eq. 1) taken as
+    parameters (soft weights). Differentiating Omega z = W x in w_t: e_t z_t + Omega dz =
+    e_t x_t, so dz/dw_t = Omega^{-1} e_t (x_t - z_t) and, with g = Omega^{-1} dL/dz
+    (Omega symmetric), dL/dw_t = sum_b g_tb (x_tb - z_tb). A day with w_t = 0 contributes
+    x_t = 0 (the smoother ignores the value observed there). Returns an array of length T."""
+    w = np.asarray(w, dtype=np.float64)
+    T = w.shape[0]
+    x2 = np.where(w[:, None] > 0, np.asarray(x, dtype=np.float64).reshape(T, -1), 0.0)
+    z2 = np.asarray(z, dtype=np.float64).reshape(T, -1)
+    g2 = solve_one(w, lam, d, np.asarray(gz, dtype=np.float64).reshape(T, -1))
+    return np.sum(g2 * (x2 - z2), axis=1)
+
+
+def vjp_w_tile(x, w, lam, d: int, z, gz):
+    """Tile layout: x, z, gz [t, b, p], w [t, p], lam [t, p] or [p]. Returns dL/dw [t, p],
+    zero for series whose Omega is not positive definite."""
+    x = np.asarray(x, dtype=np.float64)
+    w = np.asarray(w, dtype=np.float64)
+    lam = np.asarray(lam, dtype=np.float64)
+    z = np.asarray(z, dtype=np.float64)
+    gz = np.asarray(gz, dtype=np.float64)
+    T, B, P = x.shape
+    gw = np.zeros((T, P))
+    for p in range(P):
+        lp = lam[p] if lam.ndim == 1 else lam[:, p]
+        if is_pd(w[:, p], lp, d):
+            gw[:, p] = vjp_w_one(x[:, :, p], w[:, p], lp, d, z[:, :, p], gz[:, :, p])
+    return gw
+
+
 def is_pd(w, lam, d: int) -> bool:
     """Omega = W + D^T Lambda D is positive definite iff every lambda row weight is > 0
     (finite), every w >= 0 (finite), and at least min(d, T) weights are positive: the

@@ -249,6 +249,33 @@ def test_vjp_finite_differences(rng):
             assert abs(fd4(fl, 1e-3) - gll[k]) <= 1e-6 * max(1.0, np.max(np.abs(gll)))
 
 
+def test_weight_gradient_finite_differences(rng):
+    """dL/dw (weights of Eq. 1 as parameters) against FP64 fourth-order central finite
+    differences of L = <gz, z(w)>, on valid days and on gaps (x = 0 there, so the map is
+    smooth in w_t across 0); T = 60, 3 bands, per-day lambda. A dropped z, a sign flip or
+    W applied twice each give O(1) errors."""
+    T, B, d = 60, 3, 2
+
+    def fd4(f, h):
+        return (-f(2 * h) + 8 * f(h) - 8 * f(-h) + f(-2 * h)) / (12 * h)
+
+    for _ in range(6):
+        x, w, lam = _rand_case(rng, T, d, B=B, p=0.35, lam_lo=1, lam_hi=4)
+        x = np.where(w[:, None] > 0, x, 0.0)
+        gz = rng.normal(size=(T, B))
+        z = dense.smooth_one(x, w, lam, d)
+        gw = dense.vjp_w_one(x, w, lam, d, z, gz)
+        on, off = np.flatnonzero(w > 0), np.flatnonzero(w == 0)
+        days = list(rng.choice(on, 4, replace=False)) + list(rng.choice(off, 4, replace=False))
+        for t in days:
+            def f(h):
+                wp = w.copy()
+                wp[t] += h
+                zz = np.linalg.solve(dense.omega(wp, lam, d), wp[:, None] * x)
+                return float(np.sum(gz * zz))
+            assert abs(fd4(f, 1e-3) - gw[t]) <= 1e-6 * max(1.0, np.max(np.abs(gw))), (t, w[t])
+
+
 def test_dot_product_transpose_of_eq5(rng):
     """<g, J v> = <J^T g, v> with J = Omega^{-1} W (forward map) and J^T g = W Omega^{-1} g
     (the VJP): pins the transposed reading of Eq. 5."""
