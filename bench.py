@@ -52,6 +52,7 @@ def parse_args():
     ap.add_argument("--only", choices=["gcv", "learned", "ragged", "posterior"], default=None,
                     help="run one secondary measurement alone (profiling) and print it")
     ap.add_argument("--series", type=int, default=None, help="series of the --only measurement")
+    ap.add_argument("--days", type=int, default=None, help="days of the --only posterior measurement (profiling)")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU work of the oracle baseline")
     return ap.parse_args()
 
@@ -289,7 +290,7 @@ def gcv_measure(dev, steps, P=262144):
     return res
 
 
-def posterior_measure(dev, steps, x=None, w=None, lam=None, z=None, P=262144):
+def posterior_measure(dev, steps, x=None, w=None, lam=None, z=None, P=262144, T=None):
     """Posterior spread (ws_posterior: diag(Omega^{-1}), sigma2 per band, sd) on the
     heteroscedastic tile (the smooth z given; generated and smoothed here when absent).
     Algorithmic bytes per pixel-day: read x, z (B bands each), w, lambda; write diag and sd
@@ -299,6 +300,8 @@ def posterior_measure(dev, steps, x=None, w=None, lam=None, z=None, P=262144):
     from paper_2604_00048_b300 import synth, ws
 
     rc = synth.RECIPES["hetero_tile"]
+    if T is not None:
+        rc = synth.Recipe(**{**rc.__dict__, "T": T})
     if x is None:
         out = synth.generate_tile(rc, P, device=dev)
         x, w, lam = out["x"], out["w"], out["lam"]
@@ -436,7 +439,7 @@ def run_only(args):
     if args.only == "gcv":
         res = gcv_measure(dev, steps, args.series or 262144)
     elif args.only == "posterior":
-        res = posterior_measure(dev, steps, P=args.series or 262144)
+        res = posterior_measure(dev, steps, P=args.series or 262144, T=args.days)
     elif args.only == "learned":
         res = learned_measure(dev, steps, args.tcn_ckpt, args.train_epochs, args.series or 262144)
     else:

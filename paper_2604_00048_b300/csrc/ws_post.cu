@@ -28,7 +28,8 @@
 //     diag[t][p] and summing tr H.
 //   k_post_sd: per (series, band) thread: RSS over the days (compensated sum), sigma2_b,
 //     then sd over the days from diag. Pure streaming; the CTAs of the bands of one block
-//     of series are adjacent in launch order, so w and diag reach them through L2.
+//     of series are adjacent in launch order, so w and diag reach them through L2. FP32 with
+//     P % 4 == 0 takes the 16-byte form k_post_sd4 (four series per thread).
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
@@ -276,6 +277,55 @@ __global__ void __launch_bounds__(kSdNP) k_post_sd(int T, int B, int P, const F*
   for (int t = 0; t < T; ++t) sp[(size_t)t * sBP] = sqrt(s2b * dp[(size_t)t * sP]);
 }
 
+// k_post_sd for FP32 with P % 4 == 0 and 16-byte aligned arrays: one thread per (4
+// consecutive series, band), 16-byte loads and stores (512 bytes per warp instruction), four
+// days of loads in flight per thread.
+__global__ void __launch_bounds__(kSdNP) k_post_sd4(int T, int B, int P4, const float4* __restrict__ x,
+                                                    const float4* __restrict__ z, const float4* __restrict__ w,
+                                                    const float4* __restrict__ den, const float4* __restrict__ diag,
+                                                    float4* __restrict__ sigma2, float4* __restrict__ sd) {
+  const int b = blockIdx.x % B;
+  const int q = (blockIdx.x / B) * kSdNP + threadIdx.x;
+  if (q >= P4) return;
+  const size_t sP = (size_t)P4, sBP = (size_t)B * P4;
+  const float4* xp = x + (size_t)b * P4 + q;
+  const float4* zp = z + (size_t)b * P4 + q;
+  const float4* wp = w + q;
+  float sum[4] = {0.f, 0.f, 0.f, 0.f}, comp[4] = {0.f, 0.f, 0.f, 0.f};
+  auto acc = [&](int j, float wt, float xv, float zv) {
+    const float r = xv - zv;
+    const float term = wt > 0.f ? wt * r * r : 0.f;
+    const float y = term - comp[j];
+    const float s2 = sum[j] + y;
+    comp[j] = (s2 - sum[j]) - y;
+    sum[j] = s2;
+  };
+#pragma unroll 4
+  for (int t = 0; t < T; ++t) {
+    const float4 wt = __ldg(wp + (size_t)t * sP);
+    const float4 xv = __ldcs(xp + (size_t)t * sBP), zv = __ldcs(zp + (size_t)t * sBP);
+    acc(0, wt.x, xv.x, zv.x);
+    acc(1, wt.y, xv.y, zv.y);
+    acc(2, wt.z, xv.z, zv.z);
+    acc(3, wt.w, xv.w, zv.w);
+  }
+  const float4 dn = den[q];
+  const float dv[4] = {dn.x, dn.y, dn.z, dn.w};
+  float s2b[4];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) s2b[j] = dv[j] < 0.f ? 0.f : sum[j] / dv[j];
+  sigma2[(size_t)b * P4 + q] = make_float4(s2b[0], s2b[1], s2b[2], s2b[3]);
+  if (sd == nullptr) return;
+  float4* sp = sd + (size_t)b * P4 + q;
+  const float4* dp = diag + q;
+#pragma unroll 4
+  for (int t = 0; t < T; ++t) {
+    const float4 g = __ldg(dp + (size_t)t * sP);
+    __stcs(sp + (size_t)t * sBP, make_float4(sqrtf(s2b[0] * g.x), sqrtf(s2b[1] * g.y), sqrtf(s2b[2] * g.z),
+                                            sqrtf(s2b[3] * g.w)));
+  }
+}
+
 template <typename F, int D>
 static int post_occ(int& occ) {
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_post_diag<F, D>, post_np<F>(), 0) != cudaSuccess ||
@@ -338,12 +388,22 @@ static int launch_post_t(const ws_problem& pb, const void* x, const void* w, con
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return set_error(WS_ECUDA, "posterior diagonal kernel launch: %s", cudaGetErrorString(e));
   const int B = pb.n_bands;
-  const long long blocks = ((pb.n_series + kSdNP - 1) / kSdNP) * (long long)B;
+  auto al16 = [](const void* q) { return (reinterpret_cast<uintptr_t>(q) & 15u) == 0; };
+  const bool vec = sizeof(F) == 4 && pb.n_series % 4 == 0 && al16(x) && al16(z) && al16(w) && al16(den) &&
+                   al16(diag) && al16(sigma2) && (sd == nullptr || al16(sd));
+  const long long per = vec ? pb.n_series / 4 : pb.n_series;
+  const long long blocks = ((per + kSdNP - 1) / kSdNP) * (long long)B;
   if (blocks > 0x7fffffffLL) return set_error(WS_EINVAL, "posterior: too many series x bands");
-  k_post_sd<F><<<(unsigned)blocks, kSdNP, 0, st>>>(pb.T, B, (int)pb.n_series, static_cast<const F*>(x),
-                                                   static_cast<const F*>(z), static_cast<const F*>(w),
-                                                   static_cast<const F*>(den), static_cast<const F*>(diag),
-                                                   static_cast<F*>(sigma2), static_cast<F*>(sd));
+  if (vec)
+    k_post_sd4<<<(unsigned)blocks, kSdNP, 0, st>>>(pb.T, B, (int)per, static_cast<const float4*>(x),
+                                                   static_cast<const float4*>(z), static_cast<const float4*>(w),
+                                                   static_cast<const float4*>(den), static_cast<const float4*>(diag),
+                                                   static_cast<float4*>(sigma2), static_cast<float4*>(sd));
+  else
+    k_post_sd<F><<<(unsigned)blocks, kSdNP, 0, st>>>(pb.T, B, (int)pb.n_series, static_cast<const F*>(x),
+                                                     static_cast<const F*>(z), static_cast<const F*>(w),
+                                                     static_cast<const F*>(den), static_cast<const F*>(diag),
+                                                     static_cast<F*>(sigma2), static_cast<F*>(sd));
   e = cudaGetLastError();
   if (e != cudaSuccess) return set_error(WS_ECUDA, "posterior spread kernel launch: %s", cudaGetErrorString(e));
   return WS_OK;
