@@ -79,6 +79,8 @@ extern "C" {
 #define WS_GCV 0x8u           /* ws_workspace_size: size for ws_gcv_smooth */
 #define WS_REFINE_ADJOINT 0x4u /* ws_solve_adjoint: one step of iterative refinement of g */
 #define WS_POSTERIOR 0x10u     /* ws_workspace_size: size for ws_posterior */
+#define WS_ADJ_RAW_G 0x20u     /* ws_solve_adjoint: gx receives g = Omega^{-1} gz itself (not W g),
+                                  the input of ws_weight_grad */
 
 typedef struct ws_problem {
   int64_t n_series; /* P >= 0: number of series (pixels) */
@@ -130,6 +132,19 @@ int ws_smooth_batch(const ws_problem* pb, const void* x, const void* w, const vo
 int ws_gcv_smooth(const ws_problem* pb, const void* x, const void* w, const float* lam_grid, int n_grid,
                   void* z, float* lam_best, float* scores, uint8_t* status, uint32_t flags,
                   void* workspace, size_t ws_bytes, void* stream);
+
+/* Gradient with respect to the observation weights (soft weights): the weights of the
+ * objective (Eq. 1) taken as parameters. From Omega z = W x, dz/dw_t = Omega^{-1} e_t
+ * (x_t - z_t), so dL/dw_t = sum_b g_tb (x_tb - z_tb) with g = Omega^{-1} dL/dz, the solution
+ * of the adjoint system (Section 2.3); a day with w_t = 0 contributes x_t = 0 (its value is
+ * ignored, selected away rather than multiplied). g: device [T][B][P], the output of
+ * ws_solve_adjoint with WS_ADJ_RAW_G. gw: device [T][P] output. gx: NULL, or g itself (then
+ * overwritten in place), or a separate [T][B][P] array: receives dL/dx = W g. x, w, z: the
+ * smoothing's inputs and output (tile layout). Series that failed in the adjoint have
+ * g = 0 and so gw = 0. Outputs may not overlap the inputs (WS_EINVAL); one kernel launch
+ * on `stream`, no workspace. */
+int ws_weight_grad(const ws_problem* pb, const void* x, const void* w, const void* z, void* g, void* gx,
+                   void* gw, void* stream);
 
 /* Posterior spread of the smooth: the pointwise credibility intervals drawn in Fig. 4.
  * The paper plots them and borrows their formula from the Bayesian reading of the smoother
@@ -263,7 +278,8 @@ int ws_solve(const ws_problem* pb, const void* factor, const void* w, const void
  * factor_or_null: a stored factor (ws_factor layout), or NULL to recompute it from
  * (w, lam) inside the sweeps (less memory). With a stored factor the workspace must be
  * ws_workspace_size(pb, WS_REFINE) bytes (g is held there) and `status` is not written.
- * gx and glam are each optional (NULL). */
+ * gx and glam are each optional (NULL). With WS_ADJ_RAW_G, gx receives g itself instead of
+ * W g (the input of ws_weight_grad). */
 int ws_solve_adjoint(const ws_problem* pb, const void* factor_or_null, const void* w,
                      const void* lam, const void* z, const void* gz, void* gx, void* glam,
                      uint32_t flags, uint8_t* status, void* workspace, size_t ws_bytes,

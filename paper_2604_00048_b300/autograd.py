@@ -4,7 +4,9 @@ Forward: the CUDA smooth (with one refinement step by default). Backward: the CU
 (Eqs. 4-5): dL/dx = W Omega^{-1} dL/dz and dL/dlambda_k = -sum_b (D g_b)_k (D z_b)_k.
 `store_factor=True` keeps the factor of Omega from the forward pass ((d+1) words per
 pixel-day) and reuses it in the backward pass; the default recomputes it from (w, lambda),
-which saves that memory. Weights w are data (no gradient). For a log-lambda
+which saves that memory. The weights w get a gradient when they require one (soft
+weights of Eq. 1: dL/dw_t = sum_b g_tb (x_tb - z_tb), x taken as 0 on days with w_t = 0;
+x is then kept for the backward pass). For a log-lambda
 parametrisation pass lam = loglam.exp(): autograd applies the chain rule outside the layer.
 
 Tensors use the tile layout: x [T, B, P], w [T, P], lam [T, P] (per day) or [P] (scalar).
@@ -27,21 +29,26 @@ class WhittakerSmooth(torch.autograd.Function):
         z, status = ws.smooth(x, w, lam, d, factor=fac, refine=refine)
         ctx.d = d
         ctx.store = store_factor
-        ctx.save_for_backward(w, lam, z, fac if store_factor else z.new_empty(0))
+        ctx.save_for_backward(w, lam, z, fac if store_factor else z.new_empty(0),
+                              x if ctx.needs_input_grad[1] else z.new_empty(0))
         ctx.mark_non_differentiable(status)
         return z, status
 
     @staticmethod
     def backward(ctx, gz, gstatus):
-        w, lam, z, fac = ctx.saved_tensors
-        need_x, need_lam = ctx.needs_input_grad[0], ctx.needs_input_grad[2]
-        if gz is None or not (need_x or need_lam):
+        w, lam, z, fac, x = ctx.saved_tensors
+        need_x, need_w, need_lam = ctx.needs_input_grad[0], ctx.needs_input_grad[1], ctx.needs_input_grad[2]
+        if gz is None or not (need_x or need_w or need_lam):
             return None, None, None, None, None, None
+        if need_w:
+            gx, glam, gw, _ = ws.smooth_adjoint_weights(x, w, lam, z, gz.contiguous(), ctx.d, want_gx=need_x,
+                                                        want_glam=need_lam, factor=fac if ctx.store else None)
+            return gx, gw, glam, None, None, None
         gx, glam, _ = ws.smooth_adjoint(w, lam, z, gz.contiguous(), ctx.d, want_gx=need_x, want_glam=need_lam,
                                         factor=fac if ctx.store else None)
         return gx, None, glam, None, None, None
 
 
 def whittaker_smooth(x, w, lam, d: int = 2, refine: bool = True, store_factor: bool = False):
-    """z = (W + D^T Lambda D)^{-1} W x, differentiable in x and lam. Returns (z, status)."""
+    """z = (W + D^T Lambda D)^{-1} W x, differentiable in x, w and lam. Returns (z, status)."""
     return WhittakerSmooth.apply(x, w, lam, d, refine, store_factor)

@@ -157,7 +157,8 @@ static int check_workspace(const ws_problem& pb, void* workspace, size_t ws_byte
 // One tile-kernel mode over every band group of the problem.
 static int run_tile(const ws_problem& P, int mode, const void* rhs, const void* w, const void* lam,
                     const void* zin, const void* g0, void* out, void* out2, void* factor, uint8_t* status,
-                    int accum, int grad_loglam, void* workspace, cudaStream_t st) {
+                    int accum, int adj_flags, void* workspace, cudaStream_t st) {
+  // adj_flags (MODE_ADJ): bit 0 gradient in log lambda, bit 1 output g instead of W g
   // pointer contract of each mode (an inconsistent internal call is an error, never a fault)
   if (rhs == nullptr || w == nullptr || lam == nullptr) return set_error(WS_EINVAL, "tile: missing input");
   if (mode != MODE_ADJ && out == nullptr) return set_error(WS_EINVAL, "tile: missing output");
@@ -217,7 +218,8 @@ static int run_tile(const ws_problem& P, int mode, const void* rhs, const void* 
     a.ckpt = static_cast<char*>(workspace) + kHeaderBytes;
     a.err = static_cast<unsigned*>(workspace);
     a.stage_elems = cfg.stage_elems;
-    a.grad_loglam = grad_loglam;
+    a.grad_loglam = adj_flags & 1;
+    a.raw_g = (adj_flags >> 1) & 1;
     a.accum = accum;
     rc = launch_tile(P, mode, nb, cfg, a, maps, st);
     if (rc != WS_OK) return rc;
@@ -259,7 +261,7 @@ static int ws_adjoint_factored(const ws_problem* pb, const void* factor, const v
   rc = launch_factored(1, P, factor, nullptr, w, lam, gz, gs, nullptr, nullptr, nullptr, nullptr, nullptr, 0, 0, st);
   if (rc != WS_OK) return rc;
   return launch_factored(2, P, factor, nullptr, w, lam, nullptr, nullptr, z, gs, gx, glam, nullptr, 0,
-                         (flags & WS_GRAD_LOGLAM) ? 1 : 0, st);
+                         ((flags & WS_GRAD_LOGLAM) ? 1 : 0) | ((flags & WS_ADJ_RAW_G) ? 2 : 0), st);
 }
 
 // ws_posterior's scratch after the header: checkpoints, then n - tr H per series.
@@ -292,6 +294,28 @@ extern "C" size_t ws_workspace_size(const ws_problem* pb, uint32_t flags) {
     need = std::max(need, kHeaderBytes + pck);
   }
   return need;
+}
+
+extern "C" int ws_weight_grad(const ws_problem* pb, const void* x, const void* w, const void* z, void* g,
+                              void* gx, void* gw, void* stream) {
+  clear_error();
+  int rc = validate_problem(pb);
+  if (rc != WS_OK) return rc;
+  const ws_problem& P = *pb;
+  if (P.n_series == 0 || P.T == 0) return WS_OK;
+  if (!x || !w || !z || !g || !gw) return set_error(WS_EINVAL, "x, w, z, g and gw must be non-NULL");
+  const int es = elem_size(P);
+  const size_t nx = (size_t)P.T * P.n_bands * P.n_series * es, nd = (size_t)P.T * P.n_series * es;
+  if (gx != nullptr && gx != g && overlaps(gx, nx, g, nx))
+    return set_error(WS_EINVAL, "gx must be g itself or not overlap it");
+  const void* ins[4] = {x, w, z, g};
+  const size_t nin[4] = {nx, nd, nx, nx};
+  for (int i = 0; i < 4; ++i)
+    if (overlaps(gw, nd, ins[i], nin[i])) return set_error(WS_EINVAL, "gw must not overlap the inputs");
+  if (gx != nullptr && (overlaps(gx, nx, x, nx) || overlaps(gx, nx, w, nd) || overlaps(gx, nx, z, nx) ||
+                        overlaps(gx, nx, gw, nd)))
+    return set_error(WS_EINVAL, "gx must not overlap x, w, z or gw");
+  return launch_wgrad(P, x, w, z, g, gx, gw, static_cast<cudaStream_t>(stream));
 }
 
 extern "C" int ws_posterior(const ws_problem* pb, const void* x, const void* w, const void* lam, const void* z,
@@ -453,7 +477,8 @@ extern "C" int ws_solve_adjoint(const ws_problem* pb, const void* factor_or_null
   clear_error();
   int rc = validate_problem(pb);
   if (rc != WS_OK) return rc;
-  if (flags & ~(WS_GRAD_LOGLAM | WS_REFINE_ADJOINT)) return set_error(WS_EINVAL, "unknown flags 0x%x", flags);
+  if (flags & ~(WS_GRAD_LOGLAM | WS_REFINE_ADJOINT | WS_ADJ_RAW_G))
+    return set_error(WS_EINVAL, "unknown flags 0x%x", flags);
   const ws_problem& P = *pb;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   if (P.n_series == 0) return WS_OK;
@@ -472,7 +497,7 @@ extern "C" int ws_solve_adjoint(const ws_problem* pb, const void* factor_or_null
   if (factor_or_null != nullptr) return ws_adjoint_factored(pb, factor_or_null, w, lam, z, gz, gx, glam, flags,
                                                             status, workspace, ws_bytes, stream);
   const bool refine = (flags & WS_REFINE_ADJOINT) != 0;
-  const int loglam = (flags & WS_GRAD_LOGLAM) ? 1 : 0;
+  const int loglam = ((flags & WS_GRAD_LOGLAM) ? 1 : 0) | ((flags & WS_ADJ_RAW_G) ? 2 : 0);
   size_t ck_bytes = 0;
   rc = check_workspace(P, workspace, ws_bytes, refine ? 2 * resid_bytes(P) : 0, ck_bytes);
   if (rc != WS_OK) return rc;

@@ -101,7 +101,8 @@ __global__ void __launch_bounds__(128) k_solve_factored(const F* __restrict__ fa
 
 // Adjoint with the stored factor: g = Omega^{-1} gz (per band, g held in `gs`, a scratch
 // array of T*B*P), gx = W g, glam_k = -sum_b (D g_b)_k (D z_b)_k [* lambda_k], nested
-// first differences as in the tile kernel.
+// first differences as in the tile kernel. loglam: bit 0 gradient in log lambda, bit 1
+// gx receives g itself.
 template <typename F, int D>
 __global__ void __launch_bounds__(128) k_adjoint_factored(const F* __restrict__ fac, const F* __restrict__ w,
                                                           const F* __restrict__ lam, const F* __restrict__ z,
@@ -131,7 +132,7 @@ __global__ void __launch_bounds__(128) k_adjoint_factored(const F* __restrict__ 
       }
       gl[0] = g;
       zl[0] = zv;
-      if (gx) gx[o] = w[(size_t)t * sP + p] * g;
+      if (gx) gx[o] = (loglam & 2) ? g : w[(size_t)t * sP + p] * g;
       if (glam && t < T - D) {
         F a[D + 1], c[D + 1];
 #pragma unroll
@@ -147,7 +148,7 @@ __global__ void __launch_bounds__(128) k_adjoint_factored(const F* __restrict__ 
             c[n] = c[n + 1] - c[n];
           }
         F v = -a[0] * c[0];
-        if (loglam) v *= lam_scalar ? lam[p] : lam[(size_t)t * sP + p];
+        if (loglam & 1) v *= lam_scalar ? lam[p] : lam[(size_t)t * sP + p];
         if (lam_scalar)
           gsum += v;
         else {

@@ -71,6 +71,7 @@ struct TileArgs {
   unsigned* err;
   size_t stage_elems;
   int grad_loglam;
+  int raw_g;              // ADJOINT: out receives g itself instead of W g
   int accum;              // RAW: out += solution (refinement correction)
 };
 
@@ -117,6 +118,9 @@ int launch_tile_d1(const ws_problem&, int, int, const TileCfg&, const TileArgs&,
 int launch_tile_d2(const ws_problem&, int, int, const TileCfg&, const TileArgs&, const CUtensorMap*, cudaStream_t);
 int launch_tile_d3(const ws_problem&, int, int, const TileCfg&, const TileArgs&, const CUtensorMap*, cudaStream_t);
 int launch_tile_d4(const ws_problem&, int, int, const TileCfg&, const TileArgs&, const CUtensorMap*, cudaStream_t);
+// dL/dw_t = sum_b g_tb (x_tb [w_t > 0] - z_tb) and gx = W g (ws_wgrad.cu).
+int launch_wgrad(const ws_problem& pb, const void* x, const void* w, const void* z, void* g, void* gx, void* gw,
+                 cudaStream_t st);
 // r = W x - Omega z0 with double-word accumulation (refinement residual).
 // Stored-factor kernels (ws_factored.cu): what = 0 factor, 1 solve, 2 adjoint epilogue.
 int launch_factored(int what, const ws_problem& pb, const void* fac_in, void* fac_out, const void* w,

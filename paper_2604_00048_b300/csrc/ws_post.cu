@@ -21,7 +21,7 @@
 //     lambda, rho approaches the difference coefficients and each new entry is a d-th
 //     difference of a smooth sequence, which single precision loses digits on); rho and
 //     invD are FP32. One series per thread, 128 per CTA; each thread stages its own column
-//     of w and lambda (chunks of 16 days, two stages, LDGSTS), so no block barrier is
+//     of w and lambda (chunks of 8 days, two stages, LDGSTS), so no block barrier is
 //     needed. Pass 1 runs the factor forward and stores its state (the d(d+1)/2 partial
 //     row entries) per chunk; pass 2 goes back over the chunks, recomputes each chunk's
 //     rho and invD into registers from its checkpoint, and runs the recursion, writing
@@ -47,7 +47,7 @@ namespace ws {
 // series per CTA of k_post_diag (one per thread): 128 in FP32, 64 in FP64 (static shared memory)
 template <typename F>
 constexpr int post_np() { return sizeof(F) == 8 ? 64 : 128; }
-constexpr int kPostC = 16;    // days per chunk (pass 2 holds a chunk's factor rows in registers)
+constexpr int kPostC = 8;     // days per chunk (pass 2 holds a chunk's factor rows in registers)
 constexpr int kSdNP = 128;    // series per CTA of k_post_sd
 
 template <typename F>
@@ -66,7 +66,7 @@ template <typename F>
 __device__ __forceinline__ bool finite_post(F v) { return isfinite(v); }
 
 template <typename F, int D>
-__global__ void __launch_bounds__(post_np<F>()) k_post_diag(const PostArgs<F> a) {
+__global__ void __launch_bounds__(post_np<F>(), sizeof(F) == 4 ? (D <= 2 ? 7 : (D == 3 ? 6 : 4)) : 1) k_post_diag(const PostArgs<F> a) {
   constexpr int kPostNP = post_np<F>();
   using SW = Sweep<F, D, 1>;
   constexpr int kPr = D * (D + 1) / 2;  // partial-row words in a checkpoint
@@ -190,9 +190,9 @@ __global__ void __launch_bounds__(post_np<F>()) k_post_diag(const PostArgs<F> a)
           if (kDW) {
 #pragma unroll
             for (int m = 0; m < D; ++m) {
-              DWt acc = {F(0), F(0)};
+              DWt acc = dw_scale(Sg[0][m], rk[k][0]);
 #pragma unroll
-              for (int j = 0; j < D; ++j) acc = dw_fma(acc, rk[k][j], Sg[j][m]);
+              for (int j = 1; j < D; ++j) acc = dw_fma(acc, rk[k][j], Sg[j][m]);
               sm[m] = DWt{-acc.hi, -acc.lo};
             }
 #pragma unroll
@@ -219,9 +219,10 @@ __global__ void __launch_bounds__(post_np<F>()) k_post_diag(const PostArgs<F> a)
           for (int m = 1; m < D; ++m) Sg[0][m] = Sg[m][0] = sm[m - 1];
           const F dv = s0.hi + s0.lo;
           const F wi = sw[st][k][tid];
-          if (wi > F(0)) {
-            const DWt tw = two_prod(wi, dv);
-            trh = dw_add(trh, tw);
+          if (wi > F(0)) {  // tr H: each term rounded once, the running sum kept exact
+            const DWt s2 = two_sum(trh.hi, wi * dv);
+            trh.hi = s2.hi;
+            trh.lo += s2.lo;
           }
           nanacc = fma(dv, F(0), nanacc);
           if (act) a.diag[(size_t)i * P + p] = okser ? dv : F(0);

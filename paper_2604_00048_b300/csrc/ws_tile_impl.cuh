@@ -9,6 +9,7 @@
 //                                                          refinement: x is the residual)
 //   MODE_ADJ:    g = [g0 +] Omega^{-1} gz, gx = W g,      (Section 2.3, Eqs. 4-5)
 //                glam_k = -sum_b (D g_b)_k (D z_b)_k [* lambda_k]
+//                (raw_g: the output is g itself, for the gradient in the weights)
 //
 // Data flow per tile (persistent CTAs loop over tiles):
 //   pass 1 (forward in time): chunks of C days of the right-hand sides, w (C+d days: the
@@ -392,7 +393,7 @@ __global__ void __launch_bounds__(kNP* S, S > 1 ? 2 : 4) k_tile(const __grid_con
                 cz = nz;
               }
               dl = fma(cg, cz, dl);
-              out = wk * out;
+              if (!a.raw_g) out = wk * out;
             }
             nanacc = fma(out, F(0), nanacc);
             Sx[j * kNP] = out;

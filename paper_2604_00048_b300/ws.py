@@ -62,6 +62,8 @@ _lib.ws_refine.argtypes = [_PP, _vp, _vp, _vp, _vp, _vp, _sz, _vp]
 _lib.ws_gcv_smooth.restype = ctypes.c_int
 _lib.ws_gcv_smooth.argtypes = [_PP, _vp, _vp, ctypes.POINTER(ctypes.c_float), ctypes.c_int, _vp, _vp, _vp, _vp,
                                _u32, _vp, _sz, _vp]
+_lib.ws_weight_grad.restype = ctypes.c_int
+_lib.ws_weight_grad.argtypes = [_PP, _vp, _vp, _vp, _vp, _vp, _vp, _vp]
 _lib.ws_posterior.restype = ctypes.c_int
 _lib.ws_posterior.argtypes = [_PP, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _sz, _vp]
 _lib.ws_smooth_batch_noalloc.restype = ctypes.c_int
@@ -309,7 +311,8 @@ def refine(x: torch.Tensor, w: torch.Tensor, lam: torch.Tensor, z: torch.Tensor,
 
 def smooth_adjoint(w: torch.Tensor, lam: torch.Tensor, z: torch.Tensor, gz: torch.Tensor, d: int = 2, *,
                    gx=None, glam=None, want_gx: bool = True, want_glam: bool = True, log_lambda: bool = False,
-                   factor=None, status=None, refine: bool = False, stream=None, workspace_buf=None):
+                   factor=None, status=None, refine: bool = False, stream=None, workspace_buf=None,
+                   _raw_g: bool = False):
     """Vector-Jacobian products of z = Omega^{-1} W x (Eqs. 4-5): returns (gx, glam, status).
 
     gx = W Omega^{-1} gz; glam_k = -sum_b (D g_b)_k (D z_b)_k (k < T-d, 0 after), times
@@ -326,10 +329,38 @@ def smooth_adjoint(w: torch.Tensor, lam: torch.Tensor, z: torch.Tensor, gz: torc
         status = torch.empty(P, dtype=torch.uint8, device=gz.device)
     flags = (GRAD_LOGLAM if log_lambda else 0) | (REFINE_ADJOINT if refine else 0)
     ws = workspace(pb, gz.device, flags | (REFINE if factor is not None else 0), workspace_buf)
+    if _raw_g:
+        flags |= ADJ_RAW_G
     rc = _lib.ws_solve_adjoint(ctypes.byref(pb), _ptr(factor), _ptr(w), _ptr(lam), _ptr(z), _ptr(gz), _ptr(gx),
                                _ptr(glam), flags, _ptr(status), _ptr(ws), ws.numel(), _stream_ptr(stream))
     _check(rc)
     return gx, glam, status
+
+
+ADJ_RAW_G = 0x20
+
+
+def smooth_adjoint_weights(x: torch.Tensor, w: torch.Tensor, lam: torch.Tensor, z: torch.Tensor, gz: torch.Tensor,
+                           d: int = 2, *, gx=None, glam=None, gw=None, want_gx: bool = True,
+                           want_glam: bool = True, log_lambda: bool = False, factor=None, refine: bool = False,
+                           stream=None, workspace_buf=None):
+    """smooth_adjoint() plus the gradient with respect to the weights (soft weights of Eq. 1):
+    dL/dw_t = sum_b g_tb (x_tb [w_t > 0] - z_tb), g = Omega^{-1} gz. Two C-ABI calls: the
+    adjoint with WS_ADJ_RAW_G (g into the gx buffer), then ws_weight_grad (gw, and gx = W g
+    in place). Returns (gx or None, glam or None, gw [T, P], status)."""
+    T, B, P, lm = _check_tile(gz, w, lam, d)
+    if tuple(x.shape) != tuple(gz.shape) or x.dtype != gz.dtype or not x.is_cuda or not x.is_contiguous():
+        raise ValueError("x must match gz")
+    g = gx if gx is not None else torch.empty_like(gz)
+    if gw is None:
+        gw = torch.empty_like(w)
+    _, glam, status = smooth_adjoint(w, lam, z, gz, d, gx=g, glam=glam, want_glam=want_glam, log_lambda=log_lambda,
+                                     factor=factor, refine=refine, stream=stream, workspace_buf=workspace_buf,
+                                     _raw_g=True)
+    pb = make_problem(T, B, P, d, _dtype_code(gz), lm)
+    _check(_lib.ws_weight_grad(ctypes.byref(pb), _ptr(x), _ptr(w), _ptr(z), _ptr(g), _ptr(g) if want_gx else None,
+                               _ptr(gw), _stream_ptr(stream)))
+    return (g if want_gx else None), glam, gw, status
 
 
 def factor(w: torch.Tensor, lam: torch.Tensor, d: int = 2, *, out=None, status=None, stream=None):

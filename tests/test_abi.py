@@ -136,3 +136,27 @@ def test_posterior_arguments_rejected_before_cuda(ws):
     assert nd < 4096 and nx < 4096
     pb0 = ws.make_problem(10, 2, 0, 2, ws.F32, ws.LAM_PER_DAY)
     assert L.ws_posterior(ctypes.byref(pb0), *([None] * 8), None, 0, None) == ws.WS_OK
+
+
+def test_weight_grad_arguments_rejected_before_cuda(ws):
+    """ws_weight_grad: NULL inputs/outputs and overlaps rejected with WS_EINVAL before any
+    CUDA call; gx == g (in place) is accepted by the checks; empty problems are no-ops."""
+    L = ws.lib()
+    T, B, P = 10, 2, 8
+    pb = ws.make_problem(T, B, P, 2, ws.F32, ws.LAM_PER_DAY)
+    nx, nd = T * B * P * 4, T * P * 4
+    base = 1 << 40
+    x, w, z, g, gw, gx = base, base + 4096, base + 8192, base + 12288, base + 16384, base + 20480
+    assert L.ws_weight_grad(ctypes.byref(pb), None, w, z, g, gx, gw, None) == ws.WS_EINVAL
+    assert "non-NULL" in ws.last_error()
+    assert L.ws_weight_grad(ctypes.byref(pb), x, w, z, g, gx, None, None) == ws.WS_EINVAL
+    assert L.ws_weight_grad(ctypes.byref(pb), x, w, z, g, g + 4, gw, None) == ws.WS_EINVAL
+    assert "gx" in ws.last_error()
+    assert L.ws_weight_grad(ctypes.byref(pb), x, w, z, g, gx, z + 16, None) == ws.WS_EINVAL
+    assert L.ws_weight_grad(ctypes.byref(pb), x, w, z, g, x, gw, None) == ws.WS_EINVAL
+    assert nx < 4096 and nd < 4096
+    for pb0 in (ws.make_problem(T, B, 0, 2, ws.F32, ws.LAM_PER_DAY), ws.make_problem(0, B, P, 2, ws.F32, ws.LAM_PER_DAY)):
+        assert L.ws_weight_grad(ctypes.byref(pb0), None, None, None, None, None, None, None) == ws.WS_OK
+    pb = ws.make_problem(T, B, P, 2, ws.F32, ws.LAM_PER_DAY)
+    rc = L.ws_solve_adjoint(ctypes.byref(pb), None, None, None, None, None, None, None, 0x40, None, None, 0, None)
+    assert rc == ws.WS_EINVAL and "flags" in ws.last_error()
