@@ -40,6 +40,63 @@ def difference_matrix(T: int, d: int) -> np.ndarray:
     return D
 
 
+def difference_matrix_dates(t, d: int) -> np.ndarray:
+    """The order-d discrete difference operator on unevenly spaced sample times t_0 < ... <
+    t_{T-1} (Section 2 takes the discrete-derivative construction of the divided-difference
+    literature it cites for uneven spacing): row k is d! times the weights of the divided
+    difference f[t_k, ..., t_{k+d}],
+        c_{k,j} = d! / prod_{m != j} (t_{k+j} - t_{k+m}),   j = 0..d.
+    On t = 0, 1, ..., T-1 this is the binomial difference matrix."""
+    t = np.asarray(t, dtype=np.float64)
+    T = t.shape[0]
+    D = np.zeros((max(T - d, 0), T), dtype=np.float64)
+    fact = float(np.prod(np.arange(1, d + 1)))
+    for k in range(T - d):
+        for j in range(d + 1):
+            den = 1.0
+            for m in range(d + 1):
+                if m != j:
+                    den *= t[k + j] - t[k + m]
+            D[k, k + j] = fact / den
+    return D
+
+
+def omega_dates(w, lam, d: int, t) -> np.ndarray:
+    """Omega = W + D^T Lambda D with D on the sample times t (difference_matrix_dates)."""
+    w = np.asarray(w, dtype=np.float64)
+    T = w.shape[0]
+    D = difference_matrix_dates(t, d)
+    return np.diag(w) + D.T @ (lam_rows(lam, T, d)[:, None] * D)
+
+
+def smooth_one_dates(x, w, lam, d: int, t) -> np.ndarray:
+    """z = Omega^{-1} W x with the uneven-spacing operator (dense Cholesky; x [T] or [T, B])."""
+    x = np.asarray(x, dtype=np.float64)
+    w = np.asarray(w, dtype=np.float64)
+    L = np.linalg.cholesky(omega_dates(w, lam, d, t))
+    wx = np.where(w[:, None] > 0, w[:, None] * np.nan_to_num(x.reshape(len(w), -1)), 0.0)
+    y = sla.solve_triangular(L, wx, lower=True)
+    return sla.solve_triangular(L.T, y, lower=False).reshape(x.shape)
+
+
+def smooth_tile_dates(x, w, lam, d: int, t):
+    """Tile layout (x [t, b, p], w [t, p], lam [t, p] or [p]) on sample times t shared by the
+    tile's series. Returns (z, ok) as smooth_tile."""
+    x = np.asarray(x, dtype=np.float64)
+    w = np.asarray(w, dtype=np.float64)
+    lam = np.asarray(lam, dtype=np.float64)
+    T, B, P = x.shape
+    z = np.zeros_like(x)
+    ok = np.ones(P, dtype=bool)
+    for p in range(P):
+        lp = lam[p] if lam.ndim == 1 else lam[:, p]
+        if not is_pd(w[:, p], lp, d):
+            ok[p] = False
+            continue
+        z[:, :, p] = smooth_one_dates(x[:, :, p], w[:, p], lp, d, t)
+    return z, ok
+
+
 def lam_rows(lam, T: int, d: int) -> np.ndarray:
     """Diagonal of Lambda (length T-d) from a scalar (Eq. 2) or a length-T per-day array (Eq. 3)."""
     lam = np.asarray(lam, dtype=np.float64)

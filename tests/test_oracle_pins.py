@@ -354,3 +354,71 @@ def test_pd_rule_matches_spectrum(rng, d):
         scale = np.max(np.abs(ev))
         assert dense.is_pd(w, lam, d) == (ev[0] > 1e-10 * scale)
     assert not dense.is_pd(np.ones(T), np.concatenate([[-1.0], np.ones(T - 1)]), d)
+
+
+def _dates(rng, T, gap_hi=12):
+    return np.cumsum(rng.integers(1, gap_hi, size=T)).astype(float)
+
+
+@pytest.mark.parametrize("d", [1, 2, 3, 4])
+def test_dates_operator_uniform_grid_is_binomial(d):
+    """On t = 0..T-1 the uneven-spacing operator is the binomial difference matrix; on
+    t = t0 + h (0..T-1) it is that matrix over h^d."""
+    T = 20
+    assert np.allclose(dense.difference_matrix_dates(np.arange(T, dtype=float), d), dense.difference_matrix(T, d),
+                       rtol=0, atol=1e-12)
+    Dh = dense.difference_matrix_dates(7.0 + 5.0 * np.arange(T), d)
+    assert np.allclose(Dh * 5.0 ** d, dense.difference_matrix(T, d), rtol=0, atol=1e-10)
+
+
+@pytest.mark.parametrize("d", [1, 2, 3, 4])
+def test_dates_operator_recursive_construction(rng, d):
+    """An independent construction: first differences divided by the spacing, applied
+    recursively with the k-th level divided by (t_{i+k} - t_i)/k (the discrete-derivative
+    recursion); it must equal d! times the divided-difference weights."""
+    T = 25
+    t = _dates(rng, T)
+    Dk = np.eye(T)
+    for k in range(1, d + 1):
+        n = T - k + 1
+        Dbar = np.zeros((n - 1, n))
+        for i in range(n - 1):
+            Dbar[i, i], Dbar[i, i + 1] = -1.0, 1.0
+        scale = k / (t[k:] - t[:-k])
+        Dk = scale[:, None] * (Dbar @ Dk)
+    assert np.allclose(dense.difference_matrix_dates(t, d), Dk, rtol=1e-10, atol=1e-12)
+
+
+@pytest.mark.parametrize("d", [1, 2, 3])
+def test_dates_operator_on_polynomials(rng, d):
+    """Exact on polynomials: degree < d is annihilated; t^d maps to d! (its d-th
+    derivative), whatever the spacing."""
+    T = 30
+    t = _dates(rng, T, gap_hi=6)
+    t = t - t.mean()
+    D = dense.difference_matrix_dates(t, d)
+    for q in range(d):
+        assert np.max(np.abs(D @ t ** q)) <= 1e-9 * max(1.0, np.max(np.abs(t)) ** q)
+    fact = float(np.prod(np.arange(1, d + 1)))
+    assert np.allclose(D @ t ** d, fact, rtol=1e-8)
+
+
+@pytest.mark.parametrize("d", [1, 2, 3])
+def test_dates_smoother_limits(rng, d):
+    """Polynomials of degree < d in t are reproduced for any lambda; lambda -> infinity gives
+    the weighted least-squares polynomial of degree d - 1 in t; lambda -> 0 with w = 1 gives x."""
+    T = 40
+    t = _dates(rng, T, gap_hi=8)
+    w = (rng.random(T) < 0.6).astype(float)
+    w[rng.choice(T, d + 1, replace=False)] = 1.0
+    lam = 10 ** rng.uniform(0, 3, T)
+    tc = (t - t.mean()) / t.std()
+    poly = sum(rng.normal() * tc ** q for q in range(d))
+    assert np.max(np.abs(dense.smooth_one_dates(poly, w, lam, d, t) - poly)) <= 1e-8
+    x = rng.normal(size=T)
+    z = dense.smooth_one_dates(x, w, np.full(T, 1e12), d, t)
+    V = np.vander(tc, d, increasing=True)
+    coef = np.linalg.lstsq(np.sqrt(w)[:, None] * V, np.sqrt(w) * x, rcond=None)[0]
+    assert np.max(np.abs(z - V @ coef)) <= 1e-4
+    z0 = dense.smooth_one_dates(x, np.ones(T), np.full(T, 1e-12), d, t)
+    assert np.max(np.abs(z0 - x)) <= 1e-6
