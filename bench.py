@@ -47,9 +47,11 @@ def parse_args():
     ap.add_argument("--no-gcv", action="store_true")
     ap.add_argument("--no-learned", action="store_true")
     ap.add_argument("--no-posterior", action="store_true")
+    ap.add_argument("--no-wgrad", action="store_true")
+    ap.add_argument("--no-dates", action="store_true")
     ap.add_argument("--tcn-ckpt", default=None, help="trained lambda network (else one epoch is trained first)")
     ap.add_argument("--train-epochs", type=float, default=1.0, help="epochs of lambda-network training before timing")
-    ap.add_argument("--only", choices=["gcv", "learned", "ragged", "posterior"], default=None,
+    ap.add_argument("--only", choices=["gcv", "learned", "ragged", "posterior", "dates"], default=None,
                     help="run one secondary measurement alone (profiling) and print it")
     ap.add_argument("--series", type=int, default=None, help="series of the --only measurement")
     ap.add_argument("--days", type=int, default=None, help="days of the --only posterior measurement (profiling)")
@@ -290,6 +292,94 @@ def gcv_measure(dev, steps, P=262144):
     return res
 
 
+def wgrad_measure(dev, steps, x, w, lam, z, gz, gx, glam):
+    """Gradient with respect to the weights on the heteroscedastic tile: the adjoint with the
+    raw-g flag, then ws_weight_grad (dL/dw and gx = W g in one streaming pass). Times the
+    two C-ABI calls separately; algorithmic bytes of the weight-gradient pass per pixel-day:
+    read g, x, z (B each) and w, write gx (B) and gw: 4 (4B + 2)."""
+    import ctypes
+
+    import torch
+
+    from paper_2604_00048_b300 import ws
+
+    T, B, P = x.shape
+    gw = torch.empty_like(w)
+    pb = ws.make_problem(T, B, P, 2, ws.F32, ws.LAM_PER_DAY)
+    stream = torch.cuda.Stream(device=dev)
+
+    def run(ev=None):
+        if ev is not None:
+            ev[0].record(stream)
+        ws.smooth_adjoint(w, lam, z, gz, 2, gx=gx, glam=glam, log_lambda=True, stream=stream, _raw_g=True)
+        if ev is not None:
+            ev[1].record(stream)
+        ws._check(ws.lib().ws_weight_grad(ctypes.byref(pb), ws._ptr(x), ws._ptr(w), ws._ptr(z), ws._ptr(gx),
+                                          ws._ptr(gx), ws._ptr(gw), ws._stream_ptr(stream)))
+        if ev is not None:
+            ev[2].record(stream)
+
+    with torch.cuda.stream(stream):
+        for _ in range(2):
+            run()
+    torch.cuda.synchronize()
+    evs = []
+    with torch.cuda.stream(stream):
+        for _ in range(steps):
+            e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+            run(e)
+            evs.append(e)
+    torch.cuda.synchronize()
+    adj = statistics.median([e[0].elapsed_time(e[1]) for e in evs])
+    wg = statistics.median([e[1].elapsed_time(e[2]) for e in evs])
+    hbm, _ = peaks()
+    byts = 4.0 * (4 * B + 2) * float(P) * T
+    del gw
+    return {"workload": f"weight gradient: {P} series x {T} days x {B} bands, d=2, FP32 (adjoint with raw g, "
+                        "then dL/dw and gx = W g)",
+            "adjoint_raw_g_ms": adj, "weight_grad_ms": wg, "series_per_s": P / ((adj + wg) / 1e3),
+            "weight_grad_achieved_gbs": byts / (wg / 1e3) / 1e9,
+            "weight_grad_frac_of_measured_hbm": byts / (wg / 1e3) / 1e9 / hbm}
+
+
+def dates_measure(dev, steps, P=262144):
+    """Smoothing on acquisition dates (ws_smooth_dates): the heteroscedastic tile kept on each
+    series' 657 acquisition days of 3288 (5-day revisit) instead of the daily grid, 10 bands,
+    d = 2, FP32. Algorithmic bytes per series-acquisition: read x (B), w, lambda, t; write z
+    (B): 4 (2B + 3)."""
+    import torch
+
+    from paper_2604_00048_b300 import synth, ws
+
+    rc = synth.RECIPES["hetero_tile"]
+    out = synth.generate_dates_tile(rc, P, device=dev)
+    t, x, w, lam = out["t"], out["x"], out["w"], out["lam"]
+    del out
+    z = torch.empty_like(x)
+    st = torch.empty(P, dtype=torch.uint8, device=dev)
+    for _ in range(3):
+        ws.smooth_dates(t, x, w, lam, rc.d, z=z, status=st)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        ws.smooth_dates(t, x, w, lam, rc.d, z=z, status=st)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    Ta, B, _ = x.shape
+    hbm, _ = peaks()
+    byts = 4.0 * (2 * B + 3) * float(P) * Ta
+    res = {"workload": f"dates: {P} series x {Ta} acquisition dates (5-day revisit over {rc.T} days) x {B} bands, "
+                       f"d={rc.d}, FP32",
+           "ms": ms, "series_per_s": P / (ms / 1e3), "achieved_gbs": byts / (ms / 1e3) / 1e9,
+           "frac_of_measured_hbm": byts / (ms / 1e3) / 1e9 / hbm,
+           "series_with_status": int((st != 0).sum().item())}
+    del t, x, w, lam, z, st
+    torch.cuda.empty_cache()
+    return res
+
+
 def posterior_measure(dev, steps, x=None, w=None, lam=None, z=None, P=262144, T=None):
     """Posterior spread (ws_posterior: diag(Omega^{-1}), sigma2 per band, sd) on the
     heteroscedastic tile (the smooth z given; generated and smoothed here when absent).
@@ -438,6 +528,8 @@ def run_only(args):
     steps = max(1, args.steps)
     if args.only == "gcv":
         res = gcv_measure(dev, steps, args.series or 262144)
+    elif args.only == "dates":
+        res = dates_measure(dev, steps, P=args.series or 262144)
     elif args.only == "posterior":
         res = posterior_measure(dev, steps, P=args.series or 262144, T=args.days)
     elif args.only == "learned":
@@ -613,6 +705,9 @@ def run_ours(args):
         cpu = {"value": rate, "unit": "series/s", "cores": cores, "kind": "oracle", "sample": sample}
 
     launches_per_step = 3 + (1 if has_bwd else 0)
+    wgrad = None
+    if has_bwd and not args.no_wgrad:
+        wgrad = wgrad_measure(dev, max(3, args.steps), x, w, lam, z, gz, gx, glam)
     if has_bwd:
         del gz, gx, glam
     ws._ws_cache.clear()
@@ -624,6 +719,7 @@ def run_ours(args):
         ws._ws_cache.clear()
         torch.cuda.empty_cache()
         ragged = ragged_measure(dev, max(3, args.steps))
+    dates = None if args.no_dates else dates_measure(dev, max(3, args.steps))
     gcv = None if args.no_gcv else gcv_measure(dev, max(3, args.steps))
     learned = None if args.no_learned else learned_measure(dev, max(3, args.steps), args.tcn_ckpt, args.train_epochs)
     line = {"metric": METRIC, "value": value, "unit": "series/s", "n_gpus": world, "steps": args.steps,
@@ -634,7 +730,7 @@ def run_ours(args):
             "fwd_unrefined_series_per_s": P * world / (fwd_ms / 1e3),
             "smooth_ms": fwd_ms, "refine_ms": ref_ms, "adjoint_ms": bwd_ms,
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "ragged": ragged, "gcv": gcv, "learned": learned,
-            "posterior": posterior,
+            "posterior": posterior, "weight_grad": wgrad, "dates": dates,
             "gpu_launches": launches_per_step * args.steps, "clocks": ck,
             "series_with_status": bad}
     if rank == 0:

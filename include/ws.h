@@ -79,6 +79,7 @@ extern "C" {
 #define WS_GCV 0x8u           /* ws_workspace_size: size for ws_gcv_smooth */
 #define WS_REFINE_ADJOINT 0x4u /* ws_solve_adjoint: one step of iterative refinement of g */
 #define WS_POSTERIOR 0x10u     /* ws_workspace_size: size for ws_posterior */
+#define WS_DATES 0x40u         /* ws_workspace_size: size for ws_smooth_dates */
 #define WS_ADJ_RAW_G 0x20u     /* ws_solve_adjoint: gx receives g = Omega^{-1} gz itself (not W g),
                                   the input of ws_weight_grad */
 
@@ -132,6 +133,22 @@ int ws_smooth_batch(const ws_problem* pb, const void* x, const void* w, const vo
 int ws_gcv_smooth(const ws_problem* pb, const void* x, const void* w, const float* lam_grid, int n_grid,
                   void* z, float* lam_best, float* scores, uint8_t* status, uint32_t flags,
                   void* workspace, size_t ws_bytes, void* stream);
+
+/* Smoothing on unevenly spaced sample times (Section 2): each series stays on its own
+ * acquisition dates t_0 < ... < t_{T-1} (e.g. day numbers) instead of a padded daily grid,
+ * and D is the discrete derivative for uneven spacing that the paper adopts: row k is d!
+ * times the weights of the divided difference f[t_k, ..., t_{k+d}], c_{k,j} = d! /
+ * prod_{m != j} (t_{k+j} - t_{k+m}); on t = 0, 1, 2, ... it is the daily grid's binomial
+ * difference, so z matches ws_smooth_batch there. z = (W + D^T Lambda D)^{-1} W x per series
+ * and band. t: device [T][P] in pb->dtype (per-series dates); x, z: [T][B][P]; w: [T][P];
+ * lam: [T][P] (entry k weights row k; the last d unused) or [P] (WS_LAM_SCALAR). Dates that
+ * are not strictly increasing or not finite give the series status WS_SERIES_BADARG; the
+ * other codes as ws_smooth_batch (zeros where not WS_SERIES_OK). Workspace:
+ * ws_workspace_size(pb, WS_DATES), 256-byte aligned. No refinement step: on acquisition
+ * dates T is about a fifth of the daily grid's and FP32 meets 1e-4 on the test workloads
+ * (FP64 is available). One launch per band group on `stream`. */
+int ws_smooth_dates(const ws_problem* pb, const void* t, const void* x, const void* w, const void* lam, void* z,
+                    uint8_t* status, void* workspace, size_t ws_bytes, void* stream);
 
 /* Gradient with respect to the observation weights (soft weights): the weights of the
  * objective (Eq. 1) taken as parameters. From Omega z = W x, dz/dw_t = Omega^{-1} e_t

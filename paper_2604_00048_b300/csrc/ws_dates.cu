@@ -1,0 +1,412 @@
+// Smoothing on unevenly spaced sample times (Section 2): the series are kept on their
+// acquisition dates t_0 < ... < t_{T-1} instead of a padded daily grid, and the order-d
+// difference operator is the discrete derivative for uneven spacing that the paper adopts
+// from the divided-difference literature it cites: row k is d! times the weights of the
+// divided difference f[t_k, ..., t_{k+d}],
+//     c_{k,j} = d! / prod_{m != j} (t_{k+j} - t_{k+m}),   j = 0..d,
+// which on t = 0, 1, 2, ... is the binomial difference of the daily grid. Omega = W +
+// D^T Lambda D keeps bandwidth d, so the solve is the same two-sweep rotation recurrence as
+// on the daily grid (ws_sweep.cuh) with these per-row coefficients in place of the binomial
+// ones; each thread forms its rows from a window of d + 1 dates.
+//
+// Layout: tile, time-major; t [T][P] (each series its own dates, e.g. a different
+// acquisition phase), x, z [T][B][P], w, lambda [T][P] (entry k weights row k) or [P].
+// One series per thread (128 per CTA in FP32, 64 in FP64), each thread staging its own
+// column of x, w, t and lambda (chunks of 8 days, two LDGSTS stages, no block barrier).
+// Pass 1: rotations + forward substitution, state checkpointed per chunk. Pass 2, chunks in
+// reverse: the chunk is recomputed from its checkpoint (rho into registers, yhat written in
+// place over the staged x), then back-substituted, z stored with coalesced plain stores.
+// Bands beyond the per-thread group (up to 5 in FP32, 2 in FP64) run as further groups.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+#include <string.h>
+
+#include <algorithm>
+
+#include "ws_internal.h"
+#include "ws_ptx.cuh"
+#include "ws_sweep.cuh"
+
+namespace ws {
+
+template <typename F>
+constexpr int dates_np() { return sizeof(F) == 8 ? 64 : 128; }
+constexpr int kDatesC = 8;
+
+template <typename F>
+struct DatesArgs {
+  int T, P, B, b0, nch, n_tiles, lam_scalar, write_status;
+  const F* t;      // [T][P]
+  const F* x;      // [T][B][P]
+  const F* w;      // [T][P]
+  const F* lam;    // [T][P] or [P]
+  F* z;            // [T][B][P]
+  uint8_t* status; // [P] or null
+  F* ckpt;         // per CTA: nch * kFields * NP
+};
+
+// Shared memory of one stage, in rows of NP elements: x (C * NB), w (C + D), t (C + D), lambda (C).
+__host__ __device__ constexpr int dates_stage_rows(int NB, int D) { return kDatesC * NB + 2 * (kDatesC + D) + kDatesC; }
+
+// Row coefficients of day i from the dates tw[0..D] = t_i..t_{i+D}.
+template <typename F, int D>
+__device__ __forceinline__ void dates_coef(const F (&tw)[D + 1], F (&c)[D + 1]) {
+  F fact = F(1);
+#pragma unroll
+  for (int q = 2; q <= D; ++q) fact *= F(q);
+#pragma unroll
+  for (int j = 0; j <= D; ++j) {
+    F den = F(1);
+#pragma unroll
+    for (int m = 0; m <= D; ++m)
+      if (m != j) den *= tw[j] - tw[m];
+    c[j] = fact / den;
+  }
+}
+
+// The rotation step of day i (the plane rotations of Sweep::factor_step) with the row
+// coefficients c instead of the binomial ones: difference row i, sqrt(lambda_i) c at
+// columns i..i+D, is rotated into the partial rows; its remainder starts row i+D, which
+// absorbs sqrt(w_{i+D}); row i is then final.
+template <typename F, int D, int NB>
+__device__ __forceinline__ void dates_factor_step(Sweep<F, D, NB>& s, bool has_row, F lam, F w_ahead,
+                                                  const F (&c)[D + 1], F (&rho)[D], F& invD) {
+  F v[D + 1];
+  F nd = F(0);
+  F inv = F(0);
+  if (has_row) {
+    const F sl = lam > F(0) ? lam * rsqrt_(lam) : F(0);
+#pragma unroll
+    for (int n = 0; n <= D; ++n) v[n] = sl * c[n];
+#pragma unroll
+    for (int m = 0; m < D; ++m) {
+      const F a = s.pr[m][m], b = v[m];
+      const F h = fma(a, a, b * b);
+      const F ir = h > F(0) ? rsqrt_(h) : F(0);
+      const F cs = h > F(0) ? a * ir : F(1);
+      const F sn = b * ir;
+      s.pr[m][m] = h * ir;
+      if (m == 0) inv = ir;
+#pragma unroll
+      for (int n = m + 1; n < D; ++n) {
+        const F p = s.pr[m][n];
+        s.pr[m][n] = fma(cs, p, sn * v[n]);
+        v[n] = fma(cs, v[n], -(sn * p));
+      }
+      s.pr[m][D] = sn * v[D];
+      v[D] = cs * v[D];
+    }
+    const F hn = fma(v[D], v[D], w_ahead > F(0) ? w_ahead : F(0));
+    nd = hn > F(0) ? hn * rsqrt_(hn) : F(0);
+  } else {
+#pragma unroll
+    for (int m = 0; m < D; ++m) s.pr[m][D] = F(0);
+    const F h0 = s.pr[0][0] * s.pr[0][0];
+    inv = h0 > F(0) ? rsqrt_(h0) : F(0);
+  }
+  invD = inv * inv;
+#pragma unroll
+  for (int n = 1; n <= D; ++n) rho[n - 1] = s.pr[0][n] * inv;
+#pragma unroll
+  for (int m = 0; m + 1 < D; ++m)
+#pragma unroll
+    for (int n = m; n < D; ++n) s.pr[m][n] = s.pr[m + 1][n + 1];
+  s.pr[D - 1][D - 1] = nd;
+}
+
+template <typename F, int D, int NB>
+__global__ void __launch_bounds__(dates_np<F>()) k_dates(const DatesArgs<F> a) {
+  constexpr int NP = dates_np<F>(), C = kDatesC;
+  using SW = Sweep<F, D, NB>;
+  constexpr int kF = SW::kFields;
+  constexpr int SR = dates_stage_rows(NB, D);
+  constexpr int rW = C * NB, rT = rW + C + D, rL = rT + C + D;
+  extern __shared__ __align__(16) unsigned char dates_smem[];
+  F* const sm = reinterpret_cast<F*>(dates_smem);
+  const int tid = threadIdx.x;
+  const int T = a.T, P = a.P, nch = a.nch;
+  F* const ck = a.ckpt + (size_t)blockIdx.x * nch * kF * NP + tid;
+  auto row = [&](int st, int r) -> F* { return sm + ((size_t)st * SR + r) * NP + tid; };
+
+  for (int tile = blockIdx.x; tile < a.n_tiles; tile += gridDim.x) {
+    const int p = tile * NP + tid;
+    const bool act = p < P;
+    auto issue = [&](int c, int st) {
+      const int t0 = c * C;
+#pragma unroll
+      for (int k = 0; k < C; ++k) {
+        const int t = t0 + k;
+        const bool v = act && t < T;
+#pragma unroll
+        for (int b = 0; b < NB; ++b)
+          cp_async_elem<sizeof(F)>(row(st, k * NB + b), v ? a.x + ((size_t)t * a.B + a.b0 + b) * P + p : a.x, v);
+        if (!a.lam_scalar) cp_async_elem<sizeof(F)>(row(st, rL + k), v ? a.lam + (size_t)t * P + p : a.lam, v);
+      }
+#pragma unroll
+      for (int k = 0; k < C + D; ++k) {
+        const int t = t0 + k;
+        const bool v = act && t < T;
+        cp_async_elem<sizeof(F)>(row(st, rW + k), v ? a.w + (size_t)t * P + p : a.w, v);
+        cp_async_elem<sizeof(F)>(row(st, rT + k), v ? a.t + (size_t)t * P + p : a.t, v);
+      }
+      cp_async_commit();
+    };
+
+    // ---- pass 1: rotations + forward substitution, checkpoints ----
+    SW s;
+    s.reset();
+    int npos = 0;
+    bool bad = false;
+    const F lam_s = (a.lam_scalar && act) ? a.lam[p] : F(0);
+    issue(0, 0);
+    if (nch > 1) issue(1, 1);
+    for (int c = 0; c < nch; ++c) {
+      if (c + 1 < nch) cp_async_wait<1>(); else cp_async_wait<0>();
+      const int st = c & 1;
+      if (c == 0) {
+#pragma unroll
+        for (int m = 0; m < D; ++m)
+          if (m < T) s.init_weight(m, *row(0, rW + m));
+      }
+      s.save(ck + (size_t)c * kF * NP, NP);
+      const int nd = min(C, T - c * C);
+      for (int k = 0; k < nd; ++k) {
+        const int i = c * C + k;
+        const F wi = *row(st, rW + k), wa = *row(st, rW + k + D);
+        const F li = a.lam_scalar ? lam_s : *row(st, rL + k);
+        const bool has_row = i < T - D;
+        F tw[D + 1], cf[D + 1];
+#pragma unroll
+        for (int j = 0; j <= D; ++j) tw[j] = *row(st, rT + k + j);
+        bad |= !(wi >= F(0)) || !finite_(wi) || !finite_(tw[0]);
+        if (i + 1 < T) bad |= !(tw[1] > tw[0]);
+        if (has_row) bad |= !(li > F(0)) || !finite_(li);
+        npos += wi > F(0);
+        if (has_row) dates_coef<F, D>(tw, cf);
+        F bv[NB], rho[D], yh[NB], invD;
+#pragma unroll
+        for (int b = 0; b < NB; ++b) {
+          const F xv = *row(st, k * NB + b);
+          bv[b] = wi > F(0) ? wi * xv : F(0);
+        }
+        dates_factor_step(s, has_row, li, wa, cf, rho, invD);
+        s.subst_step(rho, invD, bv, yh);
+      }
+      if (c + 2 < nch) issue(c + 2, st);
+    }
+    const int dmin = D < T ? D : T;
+    const uint8_t code = bad ? WS_SERIES_BADARG : (npos < dmin ? WS_SERIES_NOT_PD : WS_SERIES_OK);
+    const bool okser = act && code == WS_SERIES_OK;
+
+    // ---- pass 2: chunk recompute, back substitution ----
+    F zc[NB][D];
+#pragma unroll
+    for (int b = 0; b < NB; ++b)
+#pragma unroll
+      for (int q = 0; q < D; ++q) zc[b][q] = F(0);
+    F nanacc = F(0);
+    for (int c = nch - 1; c >= 0; --c) {
+      const int st = c & 1;
+      if (c < nch - 2) {
+        if (c >= 1) cp_async_wait<1>(); else cp_async_wait<0>();
+      }
+      s.load(ck + (size_t)c * kF * NP, NP);
+      const int nd = min(C, T - c * C);
+      F rk[C][D];
+#pragma unroll
+      for (int k = 0; k < C; ++k) {
+        if (k < nd) {
+          const int i = c * C + k;
+          const F wi = *row(st, rW + k), wa = *row(st, rW + k + D);
+          const F li = a.lam_scalar ? lam_s : *row(st, rL + k);
+          const bool has_row = i < T - D;
+          F tw[D + 1], cf[D + 1];
+#pragma unroll
+          for (int j = 0; j <= D; ++j) tw[j] = *row(st, rT + k + j);
+          if (has_row) dates_coef<F, D>(tw, cf);
+          F bv[NB], rho[D], yh[NB], invD;
+#pragma unroll
+          for (int b = 0; b < NB; ++b) {
+            const F xv = *row(st, k * NB + b);
+            bv[b] = wi > F(0) ? wi * xv : F(0);
+          }
+          dates_factor_step(s, has_row, li, wa, cf, rho, invD);
+          s.subst_step(rho, invD, bv, yh);
+#pragma unroll
+          for (int b = 0; b < NB; ++b) *row(st, k * NB + b) = yh[b];
+#pragma unroll
+          for (int j = 0; j < D; ++j) rk[k][j] = rho[j];
+        }
+      }
+#pragma unroll
+      for (int k = C - 1; k >= 0; --k) {
+        if (k < nd) {
+          const int i = c * C + k;
+#pragma unroll
+          for (int b = 0; b < NB; ++b) {
+            F acc = *row(st, k * NB + b);
+#pragma unroll
+            for (int q = 0; q < D; ++q) acc = fma(-rk[k][q], zc[b][q], acc);
+#pragma unroll
+            for (int q = D - 1; q > 0; --q) zc[b][q] = zc[b][q - 1];
+            zc[b][0] = acc;
+            const F out = okser ? acc : F(0);
+            nanacc = fma(out, F(0), nanacc);
+            if (act) a.z[((size_t)i * a.B + a.b0 + b) * P + p] = out;
+          }
+        }
+      }
+      if (c >= 2) issue(c - 2, st);
+    }
+    if (act && a.status != nullptr) {
+      const bool nonfin = !(nanacc == F(0));
+      if (a.write_status)
+        a.status[p] = code != WS_SERIES_OK ? code : (nonfin ? WS_SERIES_NONFINITE : WS_SERIES_OK);
+      else if (nonfin && a.status[p] == WS_SERIES_OK)
+        a.status[p] = WS_SERIES_NONFINITE;
+    }
+  }
+}
+
+template <typename F, int D, int NB>
+static int dates_cfg_t(int n_tiles, int& grid, size_t& smem) {
+  DeviceInfo di;
+  int rc = device_info(di);
+  if (rc != WS_OK) return rc;
+  constexpr int NP = dates_np<F>();
+  smem = (size_t)2 * dates_stage_rows(NB, D) * NP * sizeof(F);
+  auto kern = k_dates<F, D, NB>;
+  if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+    return set_error(WS_ECUDA, "dates: shared memory attribute");
+  int occ = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, NP, smem) != cudaSuccess || occ < 1)
+    return set_error(WS_ECUDA, "dates: occupancy query");
+  grid = std::max(1, std::min(n_tiles, di.sm_count * occ));
+  return WS_OK;
+}
+
+template <typename F, int D, int NB>
+static int dates_launch_t(const DatesArgs<F>& a0, cudaStream_t st) {
+  DatesArgs<F> a = a0;
+  int grid = 0;
+  size_t smem = 0;
+  int rc = dates_cfg_t<F, D, NB>(a.n_tiles, grid, smem);
+  if (rc != WS_OK) return rc;
+  k_dates<F, D, NB><<<grid, dates_np<F>(), smem, st>>>(a);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return set_error(WS_ECUDA, "dates kernel launch: %s", cudaGetErrorString(e));
+  return WS_OK;
+}
+
+// Bands per thread of a group: FP32 1, 2, 4 or 5; FP64 1 or 2.
+static int dates_group(const ws_problem& pb, int left) {
+  if (pb.dtype == WS_F64) return left >= 2 ? 2 : 1;
+  if (left >= 5) return left == 8 ? 4 : 5;
+  if (left == 4) return 4;
+  return left >= 2 ? 2 : 1;
+}
+
+// Grid, checkpoint bytes per group (the largest over the groups of the problem).
+int dates_plan(const ws_problem& pb, size_t& ck_bytes) {
+  ck_bytes = 0;
+  const bool f64 = pb.dtype == WS_F64;
+  const int np = f64 ? dates_np<double>() : dates_np<float>();
+  const int n_tiles = (int)((pb.n_series + np - 1) / np);
+  const int nch = (pb.T + kDatesC - 1) / kDatesC;
+  for (int b0 = 0; b0 < pb.n_bands;) {
+    const int nb = dates_group(pb, pb.n_bands - b0);
+    int grid = 0;
+    size_t smem = 0;
+    int rc = WS_EINVAL;
+#define WS_DATES_CFG(FT, DD, NBB) rc = dates_cfg_t<FT, DD, NBB>(n_tiles, grid, smem)
+#define WS_DATES_NB(FT, DD)                    \
+  switch (nb) {                                \
+    case 1: WS_DATES_CFG(FT, DD, 1); break;    \
+    case 2: WS_DATES_CFG(FT, DD, 2); break;    \
+    case 4: WS_DATES_CFG(FT, DD, 4); break;    \
+    case 5: WS_DATES_CFG(FT, DD, 5); break;    \
+  }
+    if (f64) {
+      switch (pb.d) {
+        case 1: rc = nb == 2 ? dates_cfg_t<double, 1, 2>(n_tiles, grid, smem) : dates_cfg_t<double, 1, 1>(n_tiles, grid, smem); break;
+        case 2: rc = nb == 2 ? dates_cfg_t<double, 2, 2>(n_tiles, grid, smem) : dates_cfg_t<double, 2, 1>(n_tiles, grid, smem); break;
+        case 3: rc = nb == 2 ? dates_cfg_t<double, 3, 2>(n_tiles, grid, smem) : dates_cfg_t<double, 3, 1>(n_tiles, grid, smem); break;
+        case 4: rc = nb == 2 ? dates_cfg_t<double, 4, 2>(n_tiles, grid, smem) : dates_cfg_t<double, 4, 1>(n_tiles, grid, smem); break;
+      }
+    } else {
+      switch (pb.d) {
+        case 1: WS_DATES_NB(float, 1); break;
+        case 2: WS_DATES_NB(float, 2); break;
+        case 3: WS_DATES_NB(float, 3); break;
+        case 4: WS_DATES_NB(float, 4); break;
+      }
+    }
+    if (rc != WS_OK) return rc;
+    const int fields = pb.d * (pb.d + 1) + nb * pb.d;
+    ck_bytes = std::max(ck_bytes, (size_t)grid * nch * fields * np * (f64 ? 8 : 4));
+    b0 += nb;
+  }
+  return WS_OK;
+}
+
+template <typename F>
+static int dates_run_t(const ws_problem& pb, const void* t, const void* x, const void* w, const void* lam, void* z,
+                       uint8_t* status, void* ckpt, cudaStream_t st) {
+  DatesArgs<F> a;
+  memset(&a, 0, sizeof(a));
+  constexpr int np = dates_np<F>();
+  a.T = pb.T;
+  a.P = (int)pb.n_series;
+  a.B = pb.n_bands;
+  a.nch = (pb.T + kDatesC - 1) / kDatesC;
+  a.n_tiles = (int)((pb.n_series + np - 1) / np);
+  a.lam_scalar = pb.lam_mode == WS_LAM_SCALAR;
+  a.t = static_cast<const F*>(t);
+  a.x = static_cast<const F*>(x);
+  a.w = static_cast<const F*>(w);
+  a.lam = static_cast<const F*>(lam);
+  a.z = static_cast<F*>(z);
+  a.status = status;
+  a.ckpt = static_cast<F*>(ckpt);
+  for (int b0 = 0; b0 < pb.n_bands;) {
+    const int nb = dates_group(pb, pb.n_bands - b0);
+    a.b0 = b0;
+    a.write_status = b0 == 0;
+    int rc = WS_EINVAL;
+#define WS_DATES_L(DD, NBB) rc = dates_launch_t<F, DD, NBB>(a, st)
+    if constexpr (sizeof(F) == 8) {
+      switch (pb.d) {
+        case 1: if (nb == 2) WS_DATES_L(1, 2); else WS_DATES_L(1, 1); break;
+        case 2: if (nb == 2) WS_DATES_L(2, 2); else WS_DATES_L(2, 1); break;
+        case 3: if (nb == 2) WS_DATES_L(3, 2); else WS_DATES_L(3, 1); break;
+        case 4: if (nb == 2) WS_DATES_L(4, 2); else WS_DATES_L(4, 1); break;
+      }
+    } else {
+#define WS_DATES_LNB(DD)                       \
+  switch (nb) {                                \
+    case 1: WS_DATES_L(DD, 1); break;          \
+    case 2: WS_DATES_L(DD, 2); break;          \
+    case 4: WS_DATES_L(DD, 4); break;          \
+    case 5: WS_DATES_L(DD, 5); break;          \
+  }
+      switch (pb.d) {
+        case 1: WS_DATES_LNB(1); break;
+        case 2: WS_DATES_LNB(2); break;
+        case 3: WS_DATES_LNB(3); break;
+        case 4: WS_DATES_LNB(4); break;
+      }
+    }
+    if (rc != WS_OK) return rc;
+    b0 += nb;
+  }
+  return WS_OK;
+}
+
+int launch_dates(const ws_problem& pb, const void* t, const void* x, const void* w, const void* lam, void* z,
+                 uint8_t* status, void* ckpt, cudaStream_t st) {
+  if (pb.dtype == WS_F64) return dates_run_t<double>(pb, t, x, w, lam, z, status, ckpt, st);
+  return dates_run_t<float>(pb, t, x, w, lam, z, status, ckpt, st);
+}
+
+}  // namespace ws

@@ -233,6 +233,41 @@ def generate_tile(rc: Recipe, n_series: int, series0: int = 0, device="cpu",
     return out
 
 
+def generate_dates_tile(rc: Recipe, n_series: int, series0: int = 0, device="cpu", dtype=torch.float32,
+                        block: int = 16384):
+    """The tile of generate_tile kept on each series' acquisition days only (the revisit grid
+    from its random phase) instead of the padded daily grid: Ta = (T - revisit) // revisit + 1
+    acquisitions per series (every phase has that many inside T days). Returns t [Ta,P]
+    (day numbers), x [Ta,B,P], w [Ta,P] (1 on valid acquisitions), lam [Ta,P] (the daily
+    field at those days times the revisit: rows 5 days apart stand for 5 daily rows, so the
+    smoothing is comparable to the daily grid's) or [P] for scalar recipes. Generated a block
+    of series at a time from the daily tile."""
+    T, B, P, r = rc.T, rc.n_bands, n_series, rc.revisit
+    Ta = (T - r) // r + 1
+    dev = torch.device(device)
+    t = torch.empty((Ta, P), dtype=dtype, device=dev)
+    x = torch.empty((Ta, B, P), dtype=dtype, device=dev)
+    w = torch.empty((Ta, P), dtype=dtype, device=dev)
+    scalar = rc.lam_kind == "scalar"
+    lam = torch.empty((P,) if scalar else (Ta, P), dtype=dtype, device=dev)
+    k = torch.arange(Ta, device=dev, dtype=torch.int64).view(Ta, 1)
+    for s0 in range(0, P, block):
+        n = min(block, P - s0)
+        daily = generate_tile(rc, n, series0=series0 + s0, device=dev, dtype=dtype)
+        p = torch.arange(series0 + s0, series0 + s0 + n, device=dev, dtype=torch.int64).view(1, n)
+        phase = hash_u32(rc.seed, S_PHASE, p) % r
+        days = phase + r * k                                   # [Ta, n]
+        t[:, s0:s0 + n] = days.to(dtype)
+        w[:, s0:s0 + n] = torch.gather(daily["w"], 0, days)
+        x[:, :, s0:s0 + n] = torch.gather(daily["x"], 0, days.view(Ta, 1, n).expand(Ta, B, n))
+        if scalar:
+            lam[s0:s0 + n] = daily["lam"] * r
+        else:
+            lam[:, s0:s0 + n] = torch.gather(daily["lam"], 0, days) * r
+        del daily
+    return {"t": t, "x": x, "w": w, "lam": lam}
+
+
 def generate_lambda(rc: Recipe, n_series: int, series0: int = 0, device="cpu",
                     dtype=torch.float32, chunk_days: int = 128):
     """Per-day lambda [T,P] (entry k weights difference row k) or scalar [P]."""

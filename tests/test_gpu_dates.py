@@ -1,0 +1,135 @@
+"""Smoothing on unevenly spaced sample times (ws_smooth_dates) against the dense FP64
+oracle with the uneven-spacing operator: series kept on their acquisition dates (5-day
+revisit from a random phase per series, the daily tile's values there), several 128-series
+tiles and 8-day chunks with ragged tails, orders 1..4, one and several band groups,
+per-day and scalar lambda, FP32 and FP64; the uniform grid against the daily-grid path;
+invalid dates; empty problems; the full 262,144-series tile on sampled series.
+Tolerance on z as for the daily grid: 1e-4 per series and band in FP32."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import dense
+from paper_2604_00048_b300 import synth
+from tests.gpu_util import rel_err_per_series
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ws():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA device")
+    from paper_2604_00048_b300 import ws as mod
+    return mod
+
+
+def _inputs(recipe, P, T, B, dtype, **over):
+    rc = synth.Recipe(**{**synth.RECIPES[recipe].__dict__, "T": T, "n_bands": B, **over})
+    out = synth.generate_dates_tile(rc, P, device="cpu", dtype=dtype)
+    return {k: v.to("cuda") for k, v in out.items()}, {k: v.double().numpy() for k, v in out.items()}
+
+
+def _oracle(c, d):
+    """Per series: its own dates."""
+    T, B, P = c["x"].shape
+    z = np.zeros((T, B, P))
+    ok = np.zeros(P, dtype=bool)
+    for p in range(P):
+        lp = c["lam"][p] if c["lam"].ndim == 1 else c["lam"][:, p]
+        if dense.is_pd(c["w"][:, p], lp, d):
+            ok[p] = True
+            z[:, :, p] = dense.smooth_one_dates(c["x"][:, :, p], c["w"][:, p], lp, d, c["t"][:, p])
+    return z, ok
+
+
+@pytest.mark.parametrize("d,B", [(1, 3), (2, 3), (2, 10), (3, 4)])
+def test_dates_fp32_matches_oracle(ws, d, B):
+    """Heteroscedastic recipe on 401 daily steps -> 80 acquisitions, 300 series."""
+    g, c = _inputs("hetero_tile", 300, 401, B, torch.float32)
+    z, st = ws.smooth_dates(g["t"], g["x"], g["w"], g["lam"], d)
+    torch.cuda.synchronize()
+    zr, ok = _oracle(c, d)
+    assert np.array_equal(st.cpu().numpy() == 0, ok)
+    err = rel_err_per_series(z.cpu().numpy()[:, :, ok], zr[:, :, ok])
+    assert err <= 1e-4, err
+    assert np.all(z.cpu().numpy()[:, :, ~ok] == 0)
+
+
+@pytest.mark.parametrize("d", [1, 2, 3, 4])
+def test_dates_fp64_matches_oracle(ws, d):
+    """FP64 (64 series per CTA), 130 series, 2 bands, per-day lambda."""
+    g, c = _inputs("hetero_tile", 130, 321, 2, torch.float64)
+    z, st = ws.smooth_dates(g["t"], g["x"], g["w"], g["lam"], d)
+    torch.cuda.synchronize()
+    zr, ok = _oracle(c, d)
+    assert np.array_equal(st.cpu().numpy() == 0, ok)
+    assert rel_err_per_series(z.cpu().numpy()[:, :, ok], zr[:, :, ok]) <= 1e-8
+
+
+def test_dates_scalar_lambda(ws):
+    """One lambda per series (Eq. 2), the homoscedastic recipe, one band."""
+    g, c = _inputs("homo_fp64", 257, 365, 1, torch.float32)
+    z, st = ws.smooth_dates(g["t"], g["x"], g["w"], g["lam"], 2)
+    torch.cuda.synchronize()
+    zr, ok = _oracle(c, 2)
+    assert np.array_equal(st.cpu().numpy() == 0, ok)
+    assert rel_err_per_series(z.cpu().numpy()[:, :, ok], zr[:, :, ok]) <= 1e-4
+
+
+@pytest.mark.parametrize("dtype,tol", [(torch.float32, 2e-5), (torch.float64, 1e-11)])
+def test_dates_uniform_grid_equals_daily_path(ws, dtype, tol):
+    """On t = 0, 1, ..., T-1 the operator is the binomial difference: the dates path and
+    the daily-grid path (ws_smooth_batch) give the same z."""
+    rc = synth.Recipe(**{**synth.RECIPES["layer"].__dict__, "T": 150, "n_bands": 2})
+    out = synth.generate_tile(rc, 200, device="cuda", dtype=dtype)
+    t = torch.arange(150, dtype=dtype, device="cuda").view(150, 1).expand(150, 200).contiguous()
+    z1, s1 = ws.smooth_dates(t, out["x"], out["w"], out["lam"], 2)
+    z2, s2 = ws.smooth(out["x"], out["w"], out["lam"], 2)
+    torch.cuda.synchronize()
+    assert torch.equal(s1, s2)
+    ok = (s1 == 0).cpu().numpy()
+    assert rel_err_per_series(z1.cpu().numpy()[:, :, ok], z2.cpu().double().numpy()[:, :, ok]) <= tol
+
+
+def test_dates_invalid_and_empty(ws):
+    """Dates that do not increase, or a NaN date, give BADARG and zeros; the other series
+    are untouched; P = 0 and T = 0 are no-ops."""
+    g, c = _inputs("hetero_tile", 40, 200, 1, torch.float32)
+    t = g["t"].clone()
+    t[7, 3] = t[6, 3]
+    t[0, 5] = float("nan")
+    z, st = ws.smooth_dates(t, g["x"], g["w"], g["lam"], 2)
+    z0, st0 = ws.smooth_dates(g["t"], g["x"], g["w"], g["lam"], 2)
+    torch.cuda.synchronize()
+    st, st0 = st.cpu().numpy(), st0.cpu().numpy()
+    assert st[3] == ws.SERIES_BADARG and st[5] == ws.SERIES_BADARG
+    assert torch.all(z[:, :, [3, 5]] == 0)
+    keep = [p for p in range(40) if p not in (3, 5)]
+    assert np.array_equal(st[keep], st0[keep]) and torch.equal(z[:, :, keep], z0[:, :, keep])
+    e = torch.empty(5, 1, 0, device="cuda")
+    ws.smooth_dates(torch.empty(5, 0, device="cuda"), e, torch.empty(5, 0, device="cuda"),
+                    torch.empty(5, 0, device="cuda"), 2)
+    e = torch.empty(0, 2, 6, device="cuda")
+    z, st = ws.smooth_dates(torch.empty(0, 6, device="cuda"), e, torch.empty(0, 6, device="cuda"),
+                            torch.empty(0, 6, device="cuda"), 2)
+    torch.cuda.synchronize()
+    assert torch.all(st == 0)
+
+
+def test_dates_full_tile_sampled(ws):
+    """The 512 x 512 tile on its acquisition dates: 657 acquisitions of 3288 days x 10 bands,
+    the configuration bench.py times; 12 sampled series against the oracle."""
+    rc = synth.RECIPES["hetero_tile"]
+    out = synth.generate_dates_tile(rc, 262144, device="cuda")
+    z, st = ws.smooth_dates(out["t"], out["x"], out["w"], out["lam"], 2)
+    torch.cuda.synchronize()
+    ids = np.sort(np.random.default_rng(12).choice(262144, 12, replace=False))
+    it = torch.as_tensor(ids, device="cuda")
+    c = {k: v.index_select(-1, it).cpu().double().numpy() for k, v in out.items()}
+    zr, ok = _oracle(c, 2)
+    assert np.array_equal(st.cpu().numpy()[ids] == 0, ok)
+    zs = z.index_select(2, it).cpu().double().numpy()
+    assert rel_err_per_series(zs[:, :, ok], zr[:, :, ok]) <= 1e-4
+    del out, z
+    torch.cuda.empty_cache()
