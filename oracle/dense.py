@@ -97,6 +97,27 @@ def smooth_tile_dates(x, w, lam, d: int, t):
     return z, ok
 
 
+def vjp_one_dates(w, lam, d: int, t, z, gz, per_day: bool = True):
+    """Reverse-mode derivatives through z = Omega^{-1} W x with the uneven-spacing operator
+    (Section 2.3 on sample times t): g = Omega^{-1} dL/dz, dL/dx = W g (Eq. 5, transposed),
+    dL/dlam_k = -sum_b (D g_b)_k (D z_b)_k (Eq. 4, k < T-d; zeros after, or the sum over k
+    for a scalar lambda)."""
+    w = np.asarray(w, dtype=np.float64)
+    T = w.shape[0]
+    z2 = np.asarray(z, dtype=np.float64).reshape(T, -1)
+    L = np.linalg.cholesky(omega_dates(w, lam, d, t))
+    r = np.asarray(gz, dtype=np.float64).reshape(T, -1)
+    g2 = sla.solve_triangular(L.T, sla.solve_triangular(L, r, lower=True), lower=False)
+    D = difference_matrix_dates(t, d)
+    rows = -np.sum((D @ g2) * (D @ z2), axis=1)
+    if per_day:
+        glam = np.zeros(T)
+        glam[: T - d] = rows
+    else:
+        glam = np.array(rows.sum())
+    return (w[:, None] * g2).reshape(np.shape(z)), glam
+
+
 def lam_rows(lam, T: int, d: int) -> np.ndarray:
     """Diagonal of Lambda (length T-d) from a scalar (Eq. 2) or a length-T per-day array (Eq. 3)."""
     lam = np.asarray(lam, dtype=np.float64)
