@@ -150,6 +150,18 @@ int ws_gcv_smooth(const ws_problem* pb, const void* x, const void* w, const floa
 int ws_smooth_dates(const ws_problem* pb, const void* t, const void* x, const void* w, const void* lam, void* z,
                     uint8_t* status, void* workspace, size_t ws_bytes, void* stream);
 
+/* Reverse-mode derivatives of ws_smooth_dates (Section 2.3 on sample times): g = Omega^{-1}
+ * gz with the uneven-spacing Omega, gx = W g (Eq. 5, transposed), glam_k = -sum_b (D g_b)_k
+ * (D z_b)_k (Eq. 4) for k < T-d and 0 after (WS_LAM_SCALAR: the sum over k), times lambda_k
+ * with WS_GRAD_LOGLAM; (D f)_k as nested divided differences. t, w, lam, z (the forward
+ * output), gz: inputs as for ws_smooth_dates; gx: [T][B][P] output (required); glam:
+ * optional. Series that are not positive definite or have invalid inputs get zeros and their
+ * status code. Workspace: ws_workspace_size(pb, WS_DATES). One launch per band group (up to
+ * 4 bands in FP32, 2 in FP64). */
+int ws_smooth_dates_adjoint(const ws_problem* pb, const void* t, const void* w, const void* lam, const void* z,
+                            const void* gz, void* gx, void* glam, uint32_t flags, uint8_t* status, void* workspace,
+                            size_t ws_bytes, void* stream);
+
 /* Gradient with respect to the observation weights (soft weights): the weights of the
  * objective (Eq. 1) taken as parameters. From Omega z = W x, dz/dw_t = Omega^{-1} e_t
  * (x_t - z_t), so dL/dw_t = sum_b g_tb (x_tb - z_tb) with g = Omega^{-1} dL/dz, the solution

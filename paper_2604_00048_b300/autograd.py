@@ -52,3 +52,31 @@ class WhittakerSmooth(torch.autograd.Function):
 def whittaker_smooth(x, w, lam, d: int = 2, refine: bool = True, store_factor: bool = False):
     """z = (W + D^T Lambda D)^{-1} W x, differentiable in x, w and lam. Returns (z, status)."""
     return WhittakerSmooth.apply(x, w, lam, d, refine, store_factor)
+
+
+class WhittakerSmoothDates(torch.autograd.Function):
+    """The layer on unevenly spaced sample times t [T, P] (the divided-difference operator):
+    forward ws.smooth_dates, backward ws.smooth_dates_adjoint; differentiable in x and lam."""
+
+    @staticmethod
+    def forward(ctx, t, x, w, lam, d: int = 2):
+        t, x, w, lam = t.contiguous(), x.contiguous(), w.contiguous(), lam.contiguous()
+        z, status = ws.smooth_dates(t, x, w, lam, d)
+        ctx.d = d
+        ctx.save_for_backward(t, w, lam, z)
+        ctx.mark_non_differentiable(status)
+        return z, status
+
+    @staticmethod
+    def backward(ctx, gz, gstatus):
+        t, w, lam, z = ctx.saved_tensors
+        need_x, need_lam = ctx.needs_input_grad[1], ctx.needs_input_grad[3]
+        if gz is None or not (need_x or need_lam):
+            return None, None, None, None, None
+        gx, glam, _ = ws.smooth_dates_adjoint(t, w, lam, z, gz.contiguous(), ctx.d, want_glam=need_lam)
+        return None, gx if need_x else None, None, glam, None
+
+
+def whittaker_smooth_dates(t, x, w, lam, d: int = 2):
+    """z = (W + D^T Lambda D)^{-1} W x on sample times t, differentiable in x and lam."""
+    return WhittakerSmoothDates.apply(t, x, w, lam, d)

@@ -290,7 +290,9 @@ extern "C" size_t ws_workspace_size(const ws_problem* pb, uint32_t flags) {
   }
   if (flags & WS_DATES) {
     size_t dck = 0;
-    if (dates_plan(*pb, dck) != WS_OK) return 0;
+    size_t dck2 = 0;
+    if (dates_plan(*pb, false, dck) != WS_OK || dates_plan(*pb, true, dck2) != WS_OK) return 0;
+    dck = std::max(dck, dck2);
     need = std::max(need, kHeaderBytes + round256(dck));
   }
   if (flags & WS_POSTERIOR) {
@@ -321,13 +323,53 @@ extern "C" int ws_smooth_dates(const ws_problem* pb, const void* t, const void* 
   if (overlaps(z, nx, x, nx) || overlaps(z, nx, t, nd) || overlaps(z, nx, w, nd) || overlaps(z, nx, lam, nl))
     return set_error(WS_EINVAL, "z must not overlap the inputs");
   size_t ck = 0;
-  rc = dates_plan(P, ck);
+  rc = dates_plan(P, false, ck);
   if (rc != WS_OK) return rc;
   const size_t need = kHeaderBytes + round256(ck);
   if (workspace == nullptr || (reinterpret_cast<uintptr_t>(workspace) & 255u) != 0)
     return set_error(WS_EINVAL, "workspace must be non-NULL and 256-byte aligned");
   if (ws_bytes < need) return set_error(WS_ENOMEM_WS, "workspace too small: %zu < %zu", ws_bytes, need);
-  return launch_dates(P, t, x, w, lam, z, status, static_cast<char*>(workspace) + kHeaderBytes, st);
+  return launch_dates(P, false, t, x, w, lam, z, nullptr, nullptr, 0, status,
+                      static_cast<char*>(workspace) + kHeaderBytes, st);
+}
+
+extern "C" int ws_smooth_dates_adjoint(const ws_problem* pb, const void* t, const void* w, const void* lam,
+                                       const void* z, const void* gz, void* gx, void* glam, uint32_t flags,
+                                       uint8_t* status, void* workspace, size_t ws_bytes, void* stream) {
+  clear_error();
+  int rc = validate_problem(pb);
+  if (rc != WS_OK) return rc;
+  if (flags & ~WS_GRAD_LOGLAM) return set_error(WS_EINVAL, "unknown flags 0x%x", flags);
+  const ws_problem& P = *pb;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (P.n_series == 0) return WS_OK;
+  if (P.T == 0) {
+    if (status != nullptr && cudaMemsetAsync(status, 0, (size_t)P.n_series, st) != cudaSuccess)
+      return set_error(WS_ECUDA, "status memset failed");
+    if (glam != nullptr && P.lam_mode == WS_LAM_SCALAR &&
+        cudaMemsetAsync(glam, 0, (size_t)P.n_series * elem_size(P), st) != cudaSuccess)
+      return set_error(WS_ECUDA, "glam memset failed");
+    return WS_OK;
+  }
+  if (!t || !w || !lam || !z || !gz || !gx) return set_error(WS_EINVAL, "t, w, lam, z, gz and gx must be non-NULL");
+  const int es = elem_size(P);
+  const size_t nx = (size_t)P.T * P.n_bands * P.n_series * es, nd = (size_t)P.T * P.n_series * es;
+  const size_t nl = P.lam_mode == WS_LAM_SCALAR ? (size_t)P.n_series * es : nd;
+  if (overlaps(gx, nx, gz, nx) || overlaps(gx, nx, z, nx) || overlaps(gx, nx, t, nd) || overlaps(gx, nx, w, nd) ||
+      overlaps(gx, nx, lam, nl))
+    return set_error(WS_EINVAL, "gx must not overlap the inputs");
+  if (glam != nullptr && (overlaps(glam, nl, gz, nx) || overlaps(glam, nl, z, nx) || overlaps(glam, nl, gx, nx) ||
+                          overlaps(glam, nl, lam, nl) || overlaps(glam, nl, w, nd) || overlaps(glam, nl, t, nd)))
+    return set_error(WS_EINVAL, "glam must not overlap the inputs or gx");
+  size_t ck = 0;
+  rc = dates_plan(P, true, ck);
+  if (rc != WS_OK) return rc;
+  const size_t need = kHeaderBytes + round256(ck);
+  if (workspace == nullptr || (reinterpret_cast<uintptr_t>(workspace) & 255u) != 0)
+    return set_error(WS_EINVAL, "workspace must be non-NULL and 256-byte aligned");
+  if (ws_bytes < need) return set_error(WS_ENOMEM_WS, "workspace too small: %zu < %zu", ws_bytes, need);
+  return launch_dates(P, true, t, gz, w, lam, gx, z, glam, (flags & WS_GRAD_LOGLAM) ? 1 : 0, status,
+                      static_cast<char*>(workspace) + kHeaderBytes, st);
 }
 
 extern "C" int ws_weight_grad(const ws_problem* pb, const void* x, const void* w, const void* z, void* g,

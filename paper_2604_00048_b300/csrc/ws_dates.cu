@@ -12,17 +12,25 @@
 // Layout: tile, time-major; t [T][P] (each series its own dates, e.g. a different
 // acquisition phase), x, z [T][B][P], w, lambda [T][P] (entry k weights row k) or [P].
 // One series per thread (128 per CTA in FP32, 64 in FP64), each thread staging its own
-// column of x, w, t and lambda (chunks of 8 days, two LDGSTS stages, no block barrier).
+// column of x, w, t and lambda (chunks of 4 days, two LDGSTS stages, no block barrier).
 // Pass 1: rotations + forward substitution, state checkpointed per chunk. Pass 2, chunks in
 // reverse: the chunk is recomputed from its checkpoint (rho into registers, yhat written in
 // place over the staged x), then back-substituted, z stored with coalesced plain stores.
 // Bands beyond the per-thread group (up to 5 in FP32, 2 in FP64) run as further groups.
+//
+// Adjoint (ADJ, Section 2.3 on sample times): the same sweeps solve Omega g = dL/dz (the
+// right-hand side unweighted); the backward pass then writes gx = W g and
+// dL/dlambda_k = -sum_b (D g_b)_k (D z_b)_k [* lambda_k], with (D f)_k formed as nested
+// divided differences (level q at day k: (level q-1 at k+1 - level q-1 at k) * q / (t_{k+q}
+// - t_k), the recursive discrete derivative): on smooth sequences each subtraction is
+// exact, where the expanded weights would cancel digits in FP32. z is read with plain loads.
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
 #include <string.h>
 
 #include <algorithm>
+#include <type_traits>
 
 #include "ws_internal.h"
 #include "ws_ptx.cuh"
@@ -32,7 +40,7 @@ namespace ws {
 
 template <typename F>
 constexpr int dates_np() { return sizeof(F) == 8 ? 64 : 128; }
-constexpr int kDatesC = 8;
+constexpr int kDatesC = 4;
 
 template <typename F>
 struct DatesArgs {
@@ -41,7 +49,10 @@ struct DatesArgs {
   const F* x;      // [T][B][P]
   const F* w;      // [T][P]
   const F* lam;    // [T][P] or [P]
-  F* z;            // [T][B][P]
+  F* z;            // [T][B][P]: z, or gx (ADJ)
+  const F* zin;    // ADJ: the forward output z [T][B][P]
+  F* glam;         // ADJ: dL/dlambda [T][P] or [P] (may be null)
+  int loglam;      // ADJ: glam multiplied by lambda (the derivative in log lambda)
   uint8_t* status; // [P] or null
   F* ckpt;         // per CTA: nch * kFields * NP
 };
@@ -115,8 +126,8 @@ __device__ __forceinline__ void dates_factor_step(Sweep<F, D, NB>& s, bool has_r
   s.pr[D - 1][D - 1] = nd;
 }
 
-template <typename F, int D, int NB>
-__global__ void __launch_bounds__(dates_np<F>()) k_dates(const DatesArgs<F> a) {
+template <typename F, int D, int NB, bool ADJ>
+__global__ void __launch_bounds__(dates_np<F>(), sizeof(F) == 4 ? 4 : 1) k_dates(const DatesArgs<F> a) {
   constexpr int NP = dates_np<F>(), C = kDatesC;
   using SW = Sweep<F, D, NB>;
   constexpr int kF = SW::kFields;
@@ -188,7 +199,7 @@ __global__ void __launch_bounds__(dates_np<F>()) k_dates(const DatesArgs<F> a) {
 #pragma unroll
         for (int b = 0; b < NB; ++b) {
           const F xv = *row(st, k * NB + b);
-          bv[b] = wi > F(0) ? wi * xv : F(0);
+          bv[b] = ADJ ? xv : (wi > F(0) ? wi * xv : F(0));
         }
         dates_factor_step(s, has_row, li, wa, cf, rho, invD);
         s.subst_step(rho, invD, bv, yh);
@@ -201,11 +212,17 @@ __global__ void __launch_bounds__(dates_np<F>()) k_dates(const DatesArgs<F> a) {
 
     // ---- pass 2: chunk recompute, back substitution ----
     F zc[NB][D];
+    F lg[NB][D], lz[NB][D];  // ADJ: levels 0..D-1 of the divided differences of g, z at day i+1
 #pragma unroll
     for (int b = 0; b < NB; ++b)
 #pragma unroll
-      for (int q = 0; q < D; ++q) zc[b][q] = F(0);
+      for (int q = 0; q < D; ++q) {
+        zc[b][q] = F(0);
+        lg[b][q] = F(0);
+        lz[b][q] = F(0);
+      }
     F nanacc = F(0);
+    F glam_sum = F(0);
     for (int c = nch - 1; c >= 0; --c) {
       const int st = c & 1;
       if (c < nch - 2) {
@@ -229,7 +246,7 @@ __global__ void __launch_bounds__(dates_np<F>()) k_dates(const DatesArgs<F> a) {
 #pragma unroll
           for (int b = 0; b < NB; ++b) {
             const F xv = *row(st, k * NB + b);
-            bv[b] = wi > F(0) ? wi * xv : F(0);
+            bv[b] = ADJ ? xv : (wi > F(0) ? wi * xv : F(0));
           }
           dates_factor_step(s, has_row, li, wa, cf, rho, invD);
           s.subst_step(rho, invD, bv, yh);
@@ -243,6 +260,15 @@ __global__ void __launch_bounds__(dates_np<F>()) k_dates(const DatesArgs<F> a) {
       for (int k = C - 1; k >= 0; --k) {
         if (k < nd) {
           const int i = c * C + k;
+          F sq[D + 1];  // ADJ: q / (t_{i+q} - t_i), 0 where day i+q is past the end
+          F wk = F(0);
+          if (ADJ) {
+            wk = *row(st, rW + k);
+            const F t0 = *row(st, rT + k);
+#pragma unroll
+            for (int q = 1; q <= D; ++q) sq[q] = i + q < T ? F(q) / (*row(st, rT + k + q) - t0) : F(0);
+          }
+          F dl = F(0);
 #pragma unroll
           for (int b = 0; b < NB; ++b) {
             F acc = *row(st, k * NB + b);
@@ -251,14 +277,39 @@ __global__ void __launch_bounds__(dates_np<F>()) k_dates(const DatesArgs<F> a) {
 #pragma unroll
             for (int q = D - 1; q > 0; --q) zc[b][q] = zc[b][q - 1];
             zc[b][0] = acc;
-            const F out = okser ? acc : F(0);
+            F out = okser ? acc : F(0);
+            if (ADJ) {
+              const F zv = act ? a.zin[((size_t)i * a.B + a.b0 + b) * P + p] : F(0);
+              F cg = out, cz = zv;
+#pragma unroll
+              for (int q = 1; q <= D; ++q) {
+                const F ng = (lg[b][q - 1] - cg) * sq[q], nz = (lz[b][q - 1] - cz) * sq[q];
+                lg[b][q - 1] = cg;
+                lz[b][q - 1] = cz;
+                cg = ng;
+                cz = nz;
+              }
+              dl = fma(cg, cz, dl);
+              out = wk * out;
+            }
             nanacc = fma(out, F(0), nanacc);
             if (act) a.z[((size_t)i * a.B + a.b0 + b) * P + p] = out;
+          }
+          if (ADJ && a.glam != nullptr && act) {
+            F gl_i = (okser && i < T - D) ? -dl : F(0);
+            if (a.loglam) gl_i *= a.lam_scalar ? lam_s : *row(st, rL + k);
+            if (a.lam_scalar) {
+              glam_sum += gl_i;
+            } else {
+              F* dst = a.glam + (size_t)i * P + p;
+              *dst = a.b0 == 0 ? gl_i : *dst + gl_i;
+            }
           }
         }
       }
       if (c >= 2) issue(c - 2, st);
     }
+    if (ADJ && a.glam != nullptr && a.lam_scalar && act) a.glam[p] = a.b0 == 0 ? glam_sum : a.glam[p] + glam_sum;
     if (act && a.status != nullptr) {
       const bool nonfin = !(nanacc == F(0));
       if (a.write_status)
@@ -269,14 +320,14 @@ __global__ void __launch_bounds__(dates_np<F>()) k_dates(const DatesArgs<F> a) {
   }
 }
 
-template <typename F, int D, int NB>
+template <typename F, int D, int NB, bool ADJ>
 static int dates_cfg_t(int n_tiles, int& grid, size_t& smem) {
   DeviceInfo di;
   int rc = device_info(di);
   if (rc != WS_OK) return rc;
   constexpr int NP = dates_np<F>();
   smem = (size_t)2 * dates_stage_rows(NB, D) * NP * sizeof(F);
-  auto kern = k_dates<F, D, NB>;
+  auto kern = k_dates<F, D, NB, ADJ>;
   if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
     return set_error(WS_ECUDA, "dates: shared memory attribute");
   int occ = 0;
@@ -286,62 +337,73 @@ static int dates_cfg_t(int n_tiles, int& grid, size_t& smem) {
   return WS_OK;
 }
 
-template <typename F, int D, int NB>
-static int dates_launch_t(const DatesArgs<F>& a0, cudaStream_t st) {
-  DatesArgs<F> a = a0;
-  int grid = 0;
-  size_t smem = 0;
-  int rc = dates_cfg_t<F, D, NB>(a.n_tiles, grid, smem);
-  if (rc != WS_OK) return rc;
-  k_dates<F, D, NB><<<grid, dates_np<F>(), smem, st>>>(a);
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return set_error(WS_ECUDA, "dates kernel launch: %s", cudaGetErrorString(e));
-  return WS_OK;
-}
-
-// Bands per thread of a group: FP32 1, 2, 4 or 5; FP64 1 or 2.
-static int dates_group(const ws_problem& pb, int left) {
+// Bands per thread of a group: FP32 1, 2, 4 or 5 (the adjoint, with its difference
+// triangles, at most 4); FP64 1 or 2.
+static int dates_group(const ws_problem& pb, int left, bool adj) {
   if (pb.dtype == WS_F64) return left >= 2 ? 2 : 1;
-  if (left >= 5) return left == 8 ? 4 : 5;
-  if (left == 4) return 4;
+  if (left >= 5 && !adj) return left == 8 ? 4 : 5;
+  if (left >= 4) return 4;
   return left >= 2 ? 2 : 1;
 }
 
-// Grid, checkpoint bytes per group (the largest over the groups of the problem).
-int dates_plan(const ws_problem& pb, size_t& ck_bytes) {
+template <typename T>
+struct type_tag {
+  using type = T;
+};
+
+// Runs `fn` (a generic lambda taking the kernel's compile-time parameters as
+// integral_constant arguments) for the instantiation of (dtype, d, nb, adj).
+template <typename Fn>
+static int dates_dispatch(const ws_problem& pb, int nb, bool adj, Fn&& fn) {
+  using std::integral_constant;
+  auto by_nb = [&](auto ft, auto dd, auto aj) -> int {
+    using FT = typename decltype(ft)::type;
+    if constexpr (sizeof(FT) == 8) {
+      if (nb == 2) return fn(ft, dd, integral_constant<int, 2>{}, aj);
+      return fn(ft, dd, integral_constant<int, 1>{}, aj);
+    } else {
+      switch (nb) {
+        case 1: return fn(ft, dd, integral_constant<int, 1>{}, aj);
+        case 2: return fn(ft, dd, integral_constant<int, 2>{}, aj);
+        case 4: return fn(ft, dd, integral_constant<int, 4>{}, aj);
+        case 5:
+          if constexpr (!decltype(aj)::value) return fn(ft, dd, integral_constant<int, 5>{}, aj);
+          break;
+      }
+      return set_error(WS_EUNSUPPORTED, "dates: band group of %d", nb);
+    }
+  };
+  auto by_d = [&](auto ft, auto aj) -> int {
+    switch (pb.d) {
+      case 1: return by_nb(ft, integral_constant<int, 1>{}, aj);
+      case 2: return by_nb(ft, integral_constant<int, 2>{}, aj);
+      case 3: return by_nb(ft, integral_constant<int, 3>{}, aj);
+      case 4: return by_nb(ft, integral_constant<int, 4>{}, aj);
+    }
+    return set_error(WS_EINVAL, "unsupported order d=%d", pb.d);
+  };
+  auto by_adj = [&](auto ft) -> int {
+    return adj ? by_d(ft, std::true_type{}) : by_d(ft, std::false_type{});
+  };
+  if (pb.dtype == WS_F64) return by_adj(type_tag<double>{});
+  return by_adj(type_tag<float>{});
+}
+
+// Checkpoint bytes (the largest over the problem's band groups; groups run in turn).
+int dates_plan(const ws_problem& pb, bool adj, size_t& ck_bytes) {
   ck_bytes = 0;
   const bool f64 = pb.dtype == WS_F64;
   const int np = f64 ? dates_np<double>() : dates_np<float>();
   const int n_tiles = (int)((pb.n_series + np - 1) / np);
   const int nch = (pb.T + kDatesC - 1) / kDatesC;
   for (int b0 = 0; b0 < pb.n_bands;) {
-    const int nb = dates_group(pb, pb.n_bands - b0);
+    const int nb = dates_group(pb, pb.n_bands - b0, adj);
     int grid = 0;
     size_t smem = 0;
-    int rc = WS_EINVAL;
-#define WS_DATES_CFG(FT, DD, NBB) rc = dates_cfg_t<FT, DD, NBB>(n_tiles, grid, smem)
-#define WS_DATES_NB(FT, DD)                    \
-  switch (nb) {                                \
-    case 1: WS_DATES_CFG(FT, DD, 1); break;    \
-    case 2: WS_DATES_CFG(FT, DD, 2); break;    \
-    case 4: WS_DATES_CFG(FT, DD, 4); break;    \
-    case 5: WS_DATES_CFG(FT, DD, 5); break;    \
-  }
-    if (f64) {
-      switch (pb.d) {
-        case 1: rc = nb == 2 ? dates_cfg_t<double, 1, 2>(n_tiles, grid, smem) : dates_cfg_t<double, 1, 1>(n_tiles, grid, smem); break;
-        case 2: rc = nb == 2 ? dates_cfg_t<double, 2, 2>(n_tiles, grid, smem) : dates_cfg_t<double, 2, 1>(n_tiles, grid, smem); break;
-        case 3: rc = nb == 2 ? dates_cfg_t<double, 3, 2>(n_tiles, grid, smem) : dates_cfg_t<double, 3, 1>(n_tiles, grid, smem); break;
-        case 4: rc = nb == 2 ? dates_cfg_t<double, 4, 2>(n_tiles, grid, smem) : dates_cfg_t<double, 4, 1>(n_tiles, grid, smem); break;
-      }
-    } else {
-      switch (pb.d) {
-        case 1: WS_DATES_NB(float, 1); break;
-        case 2: WS_DATES_NB(float, 2); break;
-        case 3: WS_DATES_NB(float, 3); break;
-        case 4: WS_DATES_NB(float, 4); break;
-      }
-    }
+    int rc = dates_dispatch(pb, nb, adj, [&](auto ft, auto dd, auto nbb, auto aj) -> int {
+      return dates_cfg_t<typename decltype(ft)::type, decltype(dd)::value, decltype(nbb)::value,
+                         decltype(aj)::value>(n_tiles, grid, smem);
+    });
     if (rc != WS_OK) return rc;
     const int fields = pb.d * (pb.d + 1) + nb * pb.d;
     ck_bytes = std::max(ck_bytes, (size_t)grid * nch * fields * np * (f64 ? 8 : 4));
@@ -351,8 +413,9 @@ int dates_plan(const ws_problem& pb, size_t& ck_bytes) {
 }
 
 template <typename F>
-static int dates_run_t(const ws_problem& pb, const void* t, const void* x, const void* w, const void* lam, void* z,
-                       uint8_t* status, void* ckpt, cudaStream_t st) {
+static int dates_run_t(const ws_problem& pb, bool adj, const void* t, const void* x, const void* w,
+                       const void* lam, void* out, const void* zin, void* glam, int loglam, uint8_t* status,
+                       void* ckpt, cudaStream_t st) {
   DatesArgs<F> a;
   memset(&a, 0, sizeof(a));
   constexpr int np = dates_np<F>();
@@ -366,47 +429,43 @@ static int dates_run_t(const ws_problem& pb, const void* t, const void* x, const
   a.x = static_cast<const F*>(x);
   a.w = static_cast<const F*>(w);
   a.lam = static_cast<const F*>(lam);
-  a.z = static_cast<F*>(z);
+  a.z = static_cast<F*>(out);
+  a.zin = static_cast<const F*>(zin);
+  a.glam = static_cast<F*>(glam);
+  a.loglam = loglam;
   a.status = status;
   a.ckpt = static_cast<F*>(ckpt);
   for (int b0 = 0; b0 < pb.n_bands;) {
-    const int nb = dates_group(pb, pb.n_bands - b0);
+    const int nb = dates_group(pb, pb.n_bands - b0, adj);
     a.b0 = b0;
     a.write_status = b0 == 0;
-    int rc = WS_EINVAL;
-#define WS_DATES_L(DD, NBB) rc = dates_launch_t<F, DD, NBB>(a, st)
-    if constexpr (sizeof(F) == 8) {
-      switch (pb.d) {
-        case 1: if (nb == 2) WS_DATES_L(1, 2); else WS_DATES_L(1, 1); break;
-        case 2: if (nb == 2) WS_DATES_L(2, 2); else WS_DATES_L(2, 1); break;
-        case 3: if (nb == 2) WS_DATES_L(3, 2); else WS_DATES_L(3, 1); break;
-        case 4: if (nb == 2) WS_DATES_L(4, 2); else WS_DATES_L(4, 1); break;
+    int rc = dates_dispatch(pb, nb, adj, [&](auto ft, auto dd, auto nbb, auto aj) -> int {
+      using FT = typename decltype(ft)::type;
+      constexpr int DD = decltype(dd)::value, NBB = decltype(nbb)::value;
+      constexpr bool AJ = decltype(aj)::value;
+      if constexpr (!std::is_same_v<FT, F>) {
+        return set_error(WS_EINVAL, "dates: dtype mismatch");
+      } else {
+        int grid = 0;
+        size_t smem = 0;
+        int rc2 = dates_cfg_t<F, DD, NBB, AJ>(a.n_tiles, grid, smem);
+        if (rc2 != WS_OK) return rc2;
+        k_dates<F, DD, NBB, AJ><<<grid, np, smem, st>>>(a);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return set_error(WS_ECUDA, "dates kernel launch: %s", cudaGetErrorString(e));
+        return WS_OK;
       }
-    } else {
-#define WS_DATES_LNB(DD)                       \
-  switch (nb) {                                \
-    case 1: WS_DATES_L(DD, 1); break;          \
-    case 2: WS_DATES_L(DD, 2); break;          \
-    case 4: WS_DATES_L(DD, 4); break;          \
-    case 5: WS_DATES_L(DD, 5); break;          \
-  }
-      switch (pb.d) {
-        case 1: WS_DATES_LNB(1); break;
-        case 2: WS_DATES_LNB(2); break;
-        case 3: WS_DATES_LNB(3); break;
-        case 4: WS_DATES_LNB(4); break;
-      }
-    }
+    });
     if (rc != WS_OK) return rc;
     b0 += nb;
   }
   return WS_OK;
 }
 
-int launch_dates(const ws_problem& pb, const void* t, const void* x, const void* w, const void* lam, void* z,
-                 uint8_t* status, void* ckpt, cudaStream_t st) {
-  if (pb.dtype == WS_F64) return dates_run_t<double>(pb, t, x, w, lam, z, status, ckpt, st);
-  return dates_run_t<float>(pb, t, x, w, lam, z, status, ckpt, st);
+int launch_dates(const ws_problem& pb, bool adj, const void* t, const void* x, const void* w, const void* lam,
+                 void* out, const void* zin, void* glam, int loglam, uint8_t* status, void* ckpt, cudaStream_t st) {
+  if (pb.dtype == WS_F64) return dates_run_t<double>(pb, adj, t, x, w, lam, out, zin, glam, loglam, status, ckpt, st);
+  return dates_run_t<float>(pb, adj, t, x, w, lam, out, zin, glam, loglam, status, ckpt, st);
 }
 
 }  // namespace ws

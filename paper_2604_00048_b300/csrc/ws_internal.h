@@ -105,9 +105,10 @@ int launch_posterior(const ws_problem& pb, const void* x, const void* w, const v
                      void* diag, void* sigma2, void* sd, uint8_t* status, void* ckpt, void* den, cudaStream_t st);
 
 // Smoothing on uneven sample times (ws_dates.cu): checkpoint bytes; launch of the band groups.
-int dates_plan(const ws_problem& pb, size_t& ck_bytes);
-int launch_dates(const ws_problem& pb, const void* t, const void* x, const void* w, const void* lam, void* z,
-                 uint8_t* status, void* ckpt, cudaStream_t st);
+// adj: the adjoint (x is dL/dz, out receives gx, zin the forward z, glam dL/dlambda).
+int dates_plan(const ws_problem& pb, bool adj, size_t& ck_bytes);
+int launch_dates(const ws_problem& pb, bool adj, const void* t, const void* x, const void* w, const void* lam,
+                 void* out, const void* zin, void* glam, int loglam, uint8_t* status, void* ckpt, cudaStream_t st);
 
 // Launchers (return WS_OK or an error code, errors recorded via set_error).
 extern int g_tune_ctas, g_tune_chunk;  // ws_tune_set() overrides (0 = automatic)

@@ -64,6 +64,8 @@ _lib.ws_gcv_smooth.argtypes = [_PP, _vp, _vp, ctypes.POINTER(ctypes.c_float), ct
                                _u32, _vp, _sz, _vp]
 _lib.ws_smooth_dates.restype = ctypes.c_int
 _lib.ws_smooth_dates.argtypes = [_PP, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _sz, _vp]
+_lib.ws_smooth_dates_adjoint.restype = ctypes.c_int
+_lib.ws_smooth_dates_adjoint.argtypes = [_PP, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _u32, _vp, _vp, _sz, _vp]
 _lib.ws_weight_grad.restype = ctypes.c_int
 _lib.ws_weight_grad.argtypes = [_PP, _vp, _vp, _vp, _vp, _vp, _vp, _vp]
 _lib.ws_posterior.restype = ctypes.c_int
@@ -360,6 +362,31 @@ def smooth_dates(t: torch.Tensor, x: torch.Tensor, w: torch.Tensor, lam: torch.T
     _check(_lib.ws_smooth_dates(ctypes.byref(pb), _ptr(t), _ptr(x), _ptr(w), _ptr(lam), _ptr(z), _ptr(status),
                                 _ptr(ws), ws.numel(), _stream_ptr(stream)))
     return z, status
+
+
+def smooth_dates_adjoint(t: torch.Tensor, w: torch.Tensor, lam: torch.Tensor, z: torch.Tensor, gz: torch.Tensor,
+                         d: int = 2, *, gx=None, glam=None, want_glam: bool = True, log_lambda: bool = False,
+                         status=None, stream=None, workspace_buf=None):
+    """Vector-Jacobian products of smooth_dates (Eqs. 4-5 on sample times): returns
+    (gx = W Omega^{-1} gz, glam or None, status); glam_k = -sum_b (D g_b)_k (D z_b)_k, times
+    lambda_k with log_lambda."""
+    T, B, P, lm = _check_tile(gz, w, lam, d)
+    if tuple(z.shape) != tuple(gz.shape) or z.dtype != gz.dtype or not z.is_contiguous():
+        raise ValueError("z must match gz")
+    if tuple(t.shape) != (T, P) or t.dtype != gz.dtype or not t.is_cuda or not t.is_contiguous():
+        raise ValueError("t must be a contiguous [T, P] CUDA tensor of gz's dtype")
+    pb = make_problem(T, B, P, d, _dtype_code(gz), lm)
+    if gx is None:
+        gx = torch.empty_like(gz)
+    if glam is None and want_glam:
+        glam = torch.empty_like(lam)
+    if status is None:
+        status = torch.empty(P, dtype=torch.uint8, device=gz.device)
+    ws = workspace(pb, gz.device, DATES, workspace_buf)
+    _check(_lib.ws_smooth_dates_adjoint(ctypes.byref(pb), _ptr(t), _ptr(w), _ptr(lam), _ptr(z), _ptr(gz), _ptr(gx),
+                                        _ptr(glam), GRAD_LOGLAM if log_lambda else 0, _ptr(status), _ptr(ws),
+                                        ws.numel(), _stream_ptr(stream)))
+    return gx, glam, status
 
 
 ADJ_RAW_G = 0x20
