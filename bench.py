@@ -367,15 +367,29 @@ def dates_measure(dev, steps, P=262144):
     e1.record()
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / steps
+    # the adjoint on the same dates (gx and dL/dlog lambda)
+    gz = torch.randn(x.shape, generator=torch.Generator(device=dev).manual_seed(5), device=dev)
+    gx, glam = torch.empty_like(x), torch.empty_like(lam)
+    for _ in range(2):
+        ws.smooth_dates_adjoint(t, w, lam, z, gz, rc.d, gx=gx, glam=glam, log_lambda=True, status=st)
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(steps):
+        ws.smooth_dates_adjoint(t, w, lam, z, gz, rc.d, gx=gx, glam=glam, log_lambda=True, status=st)
+    e1.record()
+    torch.cuda.synchronize()
+    ms_adj = e0.elapsed_time(e1) / steps
     Ta, B, _ = x.shape
     hbm, _ = peaks()
     byts = 4.0 * (2 * B + 3) * float(P) * Ta
+    byts_adj = 4.0 * (3 * B + 4) * float(P) * Ta  # read gz, z, w, lambda, t; write gx, glam
     res = {"workload": f"dates: {P} series x {Ta} acquisition dates (5-day revisit over {rc.T} days) x {B} bands, "
                        f"d={rc.d}, FP32",
            "ms": ms, "series_per_s": P / (ms / 1e3), "achieved_gbs": byts / (ms / 1e3) / 1e9,
            "frac_of_measured_hbm": byts / (ms / 1e3) / 1e9 / hbm,
+           "adjoint_ms": ms_adj, "adjoint_achieved_gbs": byts_adj / (ms_adj / 1e3) / 1e9,
            "series_with_status": int((st != 0).sum().item())}
-    del t, x, w, lam, z, st
+    del t, x, w, lam, z, st, gz, gx, glam
     torch.cuda.empty_cache()
     return res
 

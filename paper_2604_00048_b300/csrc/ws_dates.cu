@@ -60,6 +60,11 @@ struct DatesArgs {
 // Shared memory of one stage, in rows of NP elements: x (C * NB), w (C + D), t (C + D), lambda (C).
 __host__ __device__ constexpr int dates_stage_rows(int NB, int D) { return kDatesC * NB + 2 * (kDatesC + D) + kDatesC; }
 
+// d! / den: FP32 takes the fast division (two ulp; the coefficients scale the penalty rows,
+// where that is far below the solve's own rounding), FP64 the IEEE one.
+__device__ __forceinline__ float coef_div(float num, float den) { return __fdividef(num, den); }
+__device__ __forceinline__ double coef_div(double num, double den) { return num / den; }
+
 // Row coefficients of day i from the dates tw[0..D] = t_i..t_{i+D}.
 template <typename F, int D>
 __device__ __forceinline__ void dates_coef(const F (&tw)[D + 1], F (&c)[D + 1]) {
@@ -72,7 +77,7 @@ __device__ __forceinline__ void dates_coef(const F (&tw)[D + 1], F (&c)[D + 1]) 
 #pragma unroll
     for (int m = 0; m <= D; ++m)
       if (m != j) den *= tw[j] - tw[m];
-    c[j] = fact / den;
+    c[j] = coef_div(fact, den);
   }
 }
 
@@ -143,23 +148,28 @@ __global__ void __launch_bounds__(dates_np<F>(), sizeof(F) == 4 ? 4 : 1) k_dates
   for (int tile = blockIdx.x; tile < a.n_tiles; tile += gridDim.x) {
     const int p = tile * NP + tid;
     const bool act = p < P;
+    const size_t sBP = (size_t)a.B * P;
+    const F* const xcol = a.x + (size_t)a.b0 * P + (act ? p : 0);  // this thread's column
+    const size_t ocol = act ? (size_t)p : 0;
     auto issue = [&](int c, int st) {
       const int t0 = c * C;
+      const F* xr = xcol + (size_t)t0 * sBP;
+      const F* lr = a.lam + (size_t)t0 * P + ocol;
+      const F* wr = a.w + (size_t)t0 * P + ocol;
+      const F* tr = a.t + (size_t)t0 * P + ocol;
 #pragma unroll
       for (int k = 0; k < C; ++k) {
-        const int t = t0 + k;
-        const bool v = act && t < T;
+        const bool v = act && t0 + k < T;
 #pragma unroll
         for (int b = 0; b < NB; ++b)
-          cp_async_elem<sizeof(F)>(row(st, k * NB + b), v ? a.x + ((size_t)t * a.B + a.b0 + b) * P + p : a.x, v);
-        if (!a.lam_scalar) cp_async_elem<sizeof(F)>(row(st, rL + k), v ? a.lam + (size_t)t * P + p : a.lam, v);
+          cp_async_elem<sizeof(F)>(row(st, k * NB + b), v ? xr + (size_t)k * sBP + (size_t)b * P : a.x, v);
+        if (!a.lam_scalar) cp_async_elem<sizeof(F)>(row(st, rL + k), v ? lr + (size_t)k * P : a.lam, v);
       }
 #pragma unroll
       for (int k = 0; k < C + D; ++k) {
-        const int t = t0 + k;
-        const bool v = act && t < T;
-        cp_async_elem<sizeof(F)>(row(st, rW + k), v ? a.w + (size_t)t * P + p : a.w, v);
-        cp_async_elem<sizeof(F)>(row(st, rT + k), v ? a.t + (size_t)t * P + p : a.t, v);
+        const bool v = act && t0 + k < T;
+        cp_async_elem<sizeof(F)>(row(st, rW + k), v ? wr + (size_t)k * P : a.w, v);
+        cp_async_elem<sizeof(F)>(row(st, rT + k), v ? tr + (size_t)k * P : a.t, v);
       }
       cp_async_commit();
     };
