@@ -58,7 +58,7 @@ extern "C" {
 #define WS_ENOMEM_WS (-2)     /* workspace smaller than ws_workspace_size() */
 #define WS_ECUDA (-3)         /* a CUDA runtime call failed (launch, attribute, ...) */
 #define WS_ETIMEOUT (-4)      /* a device-side wait gave up (reported by ws_sync_status) */
-#define WS_EUNSUPPORTED (-5)  /* valid request this build does not implement */
+#define WS_EUNSUPPORTED (-5)  /* valid request the library does not implement (e.g. an instantiation left out) */
 
 /* per-series status codes */
 #define WS_SERIES_OK 0
@@ -143,12 +143,14 @@ int ws_gcv_smooth(const ws_problem* pb, const void* x, const void* w, const floa
  * and band. t: device [T][P] in pb->dtype (per-series dates); x, z: [T][B][P]; w: [T][P];
  * lam: [T][P] (entry k weights row k; the last d unused) or [P] (WS_LAM_SCALAR). Dates that
  * are not strictly increasing or not finite give the series status WS_SERIES_BADARG; the
- * other codes as ws_smooth_batch (zeros where not WS_SERIES_OK). Workspace:
- * ws_workspace_size(pb, WS_DATES), 256-byte aligned. No refinement step: on acquisition
- * dates T is about a fifth of the daily grid's and FP32 meets 1e-4 on the test workloads
- * (FP64 is available). One launch per band group on `stream`. */
+ * other codes as ws_smooth_batch (zeros where not WS_SERIES_OK). flags: 0 or WS_REFINE: one
+ * step of iterative refinement as for ws_smooth_batch (residual W x - Omega z with D z and
+ * D^T (Lambda D z) as nested divided differences and the cancelling combination rounded
+ * once, then Omega d = r with the same rotations, z += d). Workspace:
+ * ws_workspace_size(pb, WS_DATES | flags), 256-byte aligned. One launch per band group
+ * on `stream` (plus the residual and the correction with WS_REFINE). */
 int ws_smooth_dates(const ws_problem* pb, const void* t, const void* x, const void* w, const void* lam, void* z,
-                    uint8_t* status, void* workspace, size_t ws_bytes, void* stream);
+                    uint8_t* status, uint32_t flags, void* workspace, size_t ws_bytes, void* stream);
 
 /* Reverse-mode derivatives of ws_smooth_dates (Section 2.3 on sample times): g = Omega^{-1}
  * gz with the uneven-spacing Omega, gx = W g (Eq. 5, transposed), glam_k = -sum_b (D g_b)_k

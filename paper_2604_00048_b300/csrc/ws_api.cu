@@ -241,6 +241,11 @@ size_t tile_workspace_bytes(const ws_problem& P) {
   return kHeaderBytes + ck;
 }
 
+// Refinement on sample times (ws_dates.cu): residual into r, then the correction solve
+// accumulated onto z in place.
+int launch_dates_refine(const ws_problem& pb, const void* t, const void* x, const void* w, const void* lam, void* z,
+                        void* r, void* ckpt, cudaStream_t st);
+
 }  // namespace ws
 
 using namespace ws;
@@ -293,7 +298,7 @@ extern "C" size_t ws_workspace_size(const ws_problem* pb, uint32_t flags) {
     size_t dck2 = 0;
     if (dates_plan(*pb, false, dck) != WS_OK || dates_plan(*pb, true, dck2) != WS_OK) return 0;
     dck = std::max(dck, dck2);
-    need = std::max(need, kHeaderBytes + round256(dck));
+    need = std::max(need, kHeaderBytes + round256(dck) + ((flags & WS_REFINE) ? resid_bytes(*pb) : 0));
   }
   if (flags & WS_POSTERIOR) {
     size_t pck = 0;
@@ -304,10 +309,12 @@ extern "C" size_t ws_workspace_size(const ws_problem* pb, uint32_t flags) {
 }
 
 extern "C" int ws_smooth_dates(const ws_problem* pb, const void* t, const void* x, const void* w, const void* lam,
-                               void* z, uint8_t* status, void* workspace, size_t ws_bytes, void* stream) {
+                               void* z, uint8_t* status, uint32_t flags, void* workspace, size_t ws_bytes,
+                               void* stream) {
   clear_error();
   int rc = validate_problem(pb);
   if (rc != WS_OK) return rc;
+  if (flags & ~WS_REFINE) return set_error(WS_EINVAL, "unknown flags 0x%x", flags);
   const ws_problem& P = *pb;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   if (P.n_series == 0) return WS_OK;
@@ -325,12 +332,15 @@ extern "C" int ws_smooth_dates(const ws_problem* pb, const void* t, const void* 
   size_t ck = 0;
   rc = dates_plan(P, false, ck);
   if (rc != WS_OK) return rc;
-  const size_t need = kHeaderBytes + round256(ck);
+  const bool refine = (flags & WS_REFINE) != 0;
+  const size_t need = kHeaderBytes + round256(ck) + (refine ? resid_bytes(P) : 0);
   if (workspace == nullptr || (reinterpret_cast<uintptr_t>(workspace) & 255u) != 0)
     return set_error(WS_EINVAL, "workspace must be non-NULL and 256-byte aligned");
   if (ws_bytes < need) return set_error(WS_ENOMEM_WS, "workspace too small: %zu < %zu", ws_bytes, need);
-  return launch_dates(P, false, t, x, w, lam, z, nullptr, nullptr, 0, status,
-                      static_cast<char*>(workspace) + kHeaderBytes, st);
+  char* ckpt = static_cast<char*>(workspace) + kHeaderBytes;
+  rc = launch_dates(P, false, t, x, w, lam, z, nullptr, nullptr, 0, status, ckpt, st);
+  if (rc != WS_OK || !refine) return rc;
+  return launch_dates_refine(P, t, x, w, lam, z, ckpt + round256(ck), ckpt, st);
 }
 
 extern "C" int ws_smooth_dates_adjoint(const ws_problem* pb, const void* t, const void* w, const void* lam,

@@ -32,6 +32,7 @@
 #include <algorithm>
 #include <type_traits>
 
+#include "ws_df.cuh"
 #include "ws_internal.h"
 #include "ws_ptx.cuh"
 #include "ws_sweep.cuh"
@@ -131,8 +132,9 @@ __device__ __forceinline__ void dates_factor_step(Sweep<F, D, NB>& s, bool has_r
   s.pr[D - 1][D - 1] = nd;
 }
 
-template <typename F, int D, int NB, bool ADJ>
+template <typename F, int D, int NB, int MODE>
 __global__ void __launch_bounds__(dates_np<F>(), sizeof(F) == 4 ? 4 : 1) k_dates(const DatesArgs<F> a) {
+  constexpr bool ADJ = MODE == 1, RAW = MODE == 2;
   constexpr int NP = dates_np<F>(), C = kDatesC;
   using SW = Sweep<F, D, NB>;
   constexpr int kF = SW::kFields;
@@ -209,7 +211,7 @@ __global__ void __launch_bounds__(dates_np<F>(), sizeof(F) == 4 ? 4 : 1) k_dates
 #pragma unroll
         for (int b = 0; b < NB; ++b) {
           const F xv = *row(st, k * NB + b);
-          bv[b] = ADJ ? xv : (wi > F(0) ? wi * xv : F(0));
+          bv[b] = (ADJ || RAW) ? xv : (wi > F(0) ? wi * xv : F(0));
         }
         dates_factor_step(s, has_row, li, wa, cf, rho, invD);
         s.subst_step(rho, invD, bv, yh);
@@ -256,7 +258,7 @@ __global__ void __launch_bounds__(dates_np<F>(), sizeof(F) == 4 ? 4 : 1) k_dates
 #pragma unroll
           for (int b = 0; b < NB; ++b) {
             const F xv = *row(st, k * NB + b);
-            bv[b] = ADJ ? xv : (wi > F(0) ? wi * xv : F(0));
+            bv[b] = (ADJ || RAW) ? xv : (wi > F(0) ? wi * xv : F(0));
           }
           dates_factor_step(s, has_row, li, wa, cf, rho, invD);
           s.subst_step(rho, invD, bv, yh);
@@ -302,6 +304,7 @@ __global__ void __launch_bounds__(dates_np<F>(), sizeof(F) == 4 ? 4 : 1) k_dates
               dl = fma(cg, cz, dl);
               out = wk * out;
             }
+            if (RAW && act) out += a.zin[((size_t)i * a.B + a.b0 + b) * P + p];  // z0 + correction
             nanacc = fma(out, F(0), nanacc);
             if (act) a.z[((size_t)i * a.B + a.b0 + b) * P + p] = out;
           }
@@ -330,14 +333,14 @@ __global__ void __launch_bounds__(dates_np<F>(), sizeof(F) == 4 ? 4 : 1) k_dates
   }
 }
 
-template <typename F, int D, int NB, bool ADJ>
+template <typename F, int D, int NB, int MODE>
 static int dates_cfg_t(int n_tiles, int& grid, size_t& smem) {
   DeviceInfo di;
   int rc = device_info(di);
   if (rc != WS_OK) return rc;
   constexpr int NP = dates_np<F>();
   smem = (size_t)2 * dates_stage_rows(NB, D) * NP * sizeof(F);
-  auto kern = k_dates<F, D, NB, ADJ>;
+  auto kern = k_dates<F, D, NB, MODE>;
   if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
     return set_error(WS_ECUDA, "dates: shared memory attribute");
   int occ = 0;
@@ -349,9 +352,9 @@ static int dates_cfg_t(int n_tiles, int& grid, size_t& smem) {
 
 // Bands per thread of a group: FP32 1, 2, 4 or 5 (the adjoint, with its difference
 // triangles, at most 4); FP64 1 or 2.
-static int dates_group(const ws_problem& pb, int left, bool adj) {
+static int dates_group(const ws_problem& pb, int left, int mode) {
   if (pb.dtype == WS_F64) return left >= 2 ? 2 : 1;
-  if (left >= 5 && !adj) return left == 8 ? 4 : 5;
+  if (left >= 5 && mode != 1) return left == 8 ? 4 : 5;
   if (left >= 4) return 4;
   return left >= 2 ? 2 : 1;
 }
@@ -362,9 +365,9 @@ struct type_tag {
 };
 
 // Runs `fn` (a generic lambda taking the kernel's compile-time parameters as
-// integral_constant arguments) for the instantiation of (dtype, d, nb, adj).
+// integral_constant arguments) for the instantiation of (dtype, d, nb, mode).
 template <typename Fn>
-static int dates_dispatch(const ws_problem& pb, int nb, bool adj, Fn&& fn) {
+static int dates_dispatch(const ws_problem& pb, int nb, int mode, Fn&& fn) {
   using std::integral_constant;
   auto by_nb = [&](auto ft, auto dd, auto aj) -> int {
     using FT = typename decltype(ft)::type;
@@ -377,7 +380,7 @@ static int dates_dispatch(const ws_problem& pb, int nb, bool adj, Fn&& fn) {
         case 2: return fn(ft, dd, integral_constant<int, 2>{}, aj);
         case 4: return fn(ft, dd, integral_constant<int, 4>{}, aj);
         case 5:
-          if constexpr (!decltype(aj)::value) return fn(ft, dd, integral_constant<int, 5>{}, aj);
+          if constexpr (decltype(aj)::value != 1) return fn(ft, dd, integral_constant<int, 5>{}, aj);
           break;
       }
       return set_error(WS_EUNSUPPORTED, "dates: band group of %d", nb);
@@ -393,24 +396,26 @@ static int dates_dispatch(const ws_problem& pb, int nb, bool adj, Fn&& fn) {
     return set_error(WS_EINVAL, "unsupported order d=%d", pb.d);
   };
   auto by_adj = [&](auto ft) -> int {
-    return adj ? by_d(ft, std::true_type{}) : by_d(ft, std::false_type{});
+    if (mode == 1) return by_d(ft, integral_constant<int, 1>{});
+    if (mode == 2) return by_d(ft, integral_constant<int, 2>{});
+    return by_d(ft, integral_constant<int, 0>{});
   };
   if (pb.dtype == WS_F64) return by_adj(type_tag<double>{});
   return by_adj(type_tag<float>{});
 }
 
 // Checkpoint bytes (the largest over the problem's band groups; groups run in turn).
-int dates_plan(const ws_problem& pb, bool adj, size_t& ck_bytes) {
+static int dates_plan_mode(const ws_problem& pb, int mode, size_t& ck_bytes) {
   ck_bytes = 0;
   const bool f64 = pb.dtype == WS_F64;
   const int np = f64 ? dates_np<double>() : dates_np<float>();
   const int n_tiles = (int)((pb.n_series + np - 1) / np);
   const int nch = (pb.T + kDatesC - 1) / kDatesC;
   for (int b0 = 0; b0 < pb.n_bands;) {
-    const int nb = dates_group(pb, pb.n_bands - b0, adj);
+    const int nb = dates_group(pb, pb.n_bands - b0, mode);
     int grid = 0;
     size_t smem = 0;
-    int rc = dates_dispatch(pb, nb, adj, [&](auto ft, auto dd, auto nbb, auto aj) -> int {
+    int rc = dates_dispatch(pb, nb, mode, [&](auto ft, auto dd, auto nbb, auto aj) -> int {
       return dates_cfg_t<typename decltype(ft)::type, decltype(dd)::value, decltype(nbb)::value,
                          decltype(aj)::value>(n_tiles, grid, smem);
     });
@@ -422,8 +427,16 @@ int dates_plan(const ws_problem& pb, bool adj, size_t& ck_bytes) {
   return WS_OK;
 }
 
+int dates_plan(const ws_problem& pb, bool adj, size_t& ck_bytes) {
+  size_t a = 0, b = 0;
+  int rc = dates_plan_mode(pb, adj ? 1 : 0, a);
+  if (rc == WS_OK && !adj) rc = dates_plan_mode(pb, 2, b);
+  ck_bytes = std::max(a, b);
+  return rc;
+}
+
 template <typename F>
-static int dates_run_t(const ws_problem& pb, bool adj, const void* t, const void* x, const void* w,
+static int dates_run_t(const ws_problem& pb, int mode, const void* t, const void* x, const void* w,
                        const void* lam, void* out, const void* zin, void* glam, int loglam, uint8_t* status,
                        void* ckpt, cudaStream_t st) {
   DatesArgs<F> a;
@@ -446,13 +459,13 @@ static int dates_run_t(const ws_problem& pb, bool adj, const void* t, const void
   a.status = status;
   a.ckpt = static_cast<F*>(ckpt);
   for (int b0 = 0; b0 < pb.n_bands;) {
-    const int nb = dates_group(pb, pb.n_bands - b0, adj);
+    const int nb = dates_group(pb, pb.n_bands - b0, mode);
     a.b0 = b0;
-    a.write_status = b0 == 0;
-    int rc = dates_dispatch(pb, nb, adj, [&](auto ft, auto dd, auto nbb, auto aj) -> int {
+    a.write_status = b0 == 0 && mode != 2;
+    int rc = dates_dispatch(pb, nb, mode, [&](auto ft, auto dd, auto nbb, auto aj) -> int {
       using FT = typename decltype(ft)::type;
       constexpr int DD = decltype(dd)::value, NBB = decltype(nbb)::value;
-      constexpr bool AJ = decltype(aj)::value;
+      constexpr int AJ = decltype(aj)::value;
       if constexpr (!std::is_same_v<FT, F>) {
         return set_error(WS_EINVAL, "dates: dtype mismatch");
       } else {
@@ -474,8 +487,115 @@ static int dates_run_t(const ws_problem& pb, bool adj, const void* t, const void
 
 int launch_dates(const ws_problem& pb, bool adj, const void* t, const void* x, const void* w, const void* lam,
                  void* out, const void* zin, void* glam, int loglam, uint8_t* status, void* ckpt, cudaStream_t st) {
-  if (pb.dtype == WS_F64) return dates_run_t<double>(pb, adj, t, x, w, lam, out, zin, glam, loglam, status, ckpt, st);
-  return dates_run_t<float>(pb, adj, t, x, w, lam, out, zin, glam, loglam, status, ckpt, st);
+  const int mode = adj ? 1 : 0;
+  if (pb.dtype == WS_F64) return dates_run_t<double>(pb, mode, t, x, w, lam, out, zin, glam, loglam, status, ckpt, st);
+  return dates_run_t<float>(pb, mode, t, x, w, lam, out, zin, glam, loglam, status, ckpt, st);
+}
+
+// ---- refinement on dates: residual r = W x - Omega z0, then Omega d = r, z = z0 + d ----
+
+// One thread per (series, band); CTA index = series block * B + b (the bands of a block of
+// series are adjacent, so w, lambda and t reach them through L2). Streaming over the days
+// with delay lines of d + 1 values:
+//   (D z0)_k as nested divided differences (level l at day k from level l - 1 at days k,
+//     k + 1, times l / (t_{k+l} - t_k)), available when day k + d is read;
+//   q_k = lambda_k (D z0)_k;
+//   (D^T q)_k by the transposed recursion: v = u * l / (t_{k+l} - t_k) for l = d .. 1 (0 past
+//     the level's last row), u <- v_{k-1} - v_k (a backward difference);
+//   r_k = w_k (x_k - z0_k) - (D^T q)_k, with x - z0 split exactly by TwoSum and the
+//     combination rounded once (FMA): the result is small against its terms.
+template <typename F, int D>
+__global__ void __launch_bounds__(128) k_dates_resid(int T, int B, int P, const F* __restrict__ t,
+                                                     const F* __restrict__ x, const F* __restrict__ w,
+                                                     const F* __restrict__ lam, int lam_scalar,
+                                                     const F* __restrict__ z0, F* __restrict__ r) {
+  const int b = blockIdx.x % B;
+  const int p = (blockIdx.x / B) * 128 + threadIdx.x;
+  if (p >= P) return;
+  const size_t sP = (size_t)P, sBP = (size_t)B * P, ob = (size_t)b * P + p;
+  const F lam_s = lam_scalar ? lam[p] : F(0);
+  F tw[D + 1];               // t_{s}, t_{s-1}, ..., t_{s-D}
+  F fl[D];                   // forward levels 0..D-1 at the previous step
+  F zq[D + 1], xq[D + 1], wq[D + 1], lq[D + 1];  // delay lines (index j: day s - j)
+  F vv[D + 1];               // transposed levels 1..D at the previous column
+#pragma unroll
+  for (int j = 0; j <= D; ++j) {
+    tw[j] = F(0);
+    zq[j] = xq[j] = wq[j] = lq[j] = vv[j] = F(0);
+  }
+#pragma unroll
+  for (int j = 0; j < D; ++j) fl[j] = F(0);
+  for (int s = 0; s < T + D; ++s) {
+    const bool in = s < T;
+    const F ts = in ? t[(size_t)s * sP + p] : tw[0];
+    const F zs = in ? z0[(size_t)s * sBP + ob] : F(0);
+    const F ws = in ? w[(size_t)s * sP + p] : F(0);
+    const F xs = (in && ws > F(0)) ? x[(size_t)s * sBP + ob] : zs;  // gaps: x - z0 = 0
+    const F ls = in ? (lam_scalar ? lam_s : lam[(size_t)s * sP + p]) : F(0);
+#pragma unroll
+    for (int j = D; j > 0; --j) {
+      tw[j] = tw[j - 1];
+      zq[j] = zq[j - 1];
+      xq[j] = xq[j - 1];
+      wq[j] = wq[j - 1];
+      lq[j] = lq[j - 1];
+    }
+    tw[0] = ts;
+    zq[0] = zs;
+    xq[0] = xs;
+    wq[0] = ws;
+    lq[0] = ls;
+    // forward: levels of day s - l, the last one (D z0)_{s-D}
+    F cur = zs;
+    if (in) {
+#pragma unroll
+      for (int l = 1; l <= D; ++l) {
+        const F nw = s >= l ? (cur - fl[l - 1]) * (F(l) / (ts - tw[l])) : F(0);
+        fl[l - 1] = cur;
+        cur = nw;
+      }
+    }
+    const int k = s - D;  // the column finished at this step
+    if (k < 0) continue;
+    const F q = (in && k <= T - D - 1) ? lq[D] * cur : F(0);
+    // transposed recursion down to level 0
+    F u = q;
+#pragma unroll
+    for (int l = D; l >= 1; --l) {
+      const F v = (k <= T - l - 1) ? u * (F(l) / (tw[D - l] - tw[D])) : F(0);
+      const F un = vv[l] - v;
+      vv[l] = v;
+      u = un;
+    }
+    // r_k = w_k (x_k - z0_k) - (D^T q)_k
+    const DW<F> e = two_sum(xq[D], -zq[D]);
+    r[(size_t)k * sBP + ob] = fma(wq[D], e.lo, fma(wq[D], e.hi, -u));
+  }
+}
+
+int launch_dates_refine(const ws_problem& pb, const void* t, const void* x, const void* w, const void* lam, void* z,
+                        void* r, void* ckpt, cudaStream_t st) {
+  const int B = pb.n_bands, P = (int)pb.n_series;
+  const long long blocks = ((pb.n_series + 127) / 128) * (long long)B;
+  if (blocks > 0x7fffffffLL) return set_error(WS_EINVAL, "dates refinement: too many series x bands");
+  const int ls = pb.lam_mode == WS_LAM_SCALAR;
+  const bool f64 = pb.dtype == WS_F64;
+#define WS_DR(FT, DD)                                                                                        \
+  k_dates_resid<FT, DD><<<(unsigned)blocks, 128, 0, st>>>(pb.T, B, P, (const FT*)t, (const FT*)x, (const FT*)w, \
+                                                         (const FT*)lam, ls, (const FT*)z, (FT*)r)
+  switch (pb.d) {
+    case 1: if (f64) WS_DR(double, 1); else WS_DR(float, 1); break;
+    case 2: if (f64) WS_DR(double, 2); else WS_DR(float, 2); break;
+    case 3: if (f64) WS_DR(double, 3); else WS_DR(float, 3); break;
+    case 4: if (f64) WS_DR(double, 4); else WS_DR(float, 4); break;
+    default: return set_error(WS_EINVAL, "unsupported order d=%d", pb.d);
+  }
+#undef WS_DR
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return set_error(WS_ECUDA, "dates residual launch: %s", cudaGetErrorString(e));
+  // correction: Omega d = r with the same rotations, accumulated onto z in place
+  if (f64) return dates_run_t<double>(pb, 2, t, r, w, lam, z, z, nullptr, 0, nullptr, ckpt, st);
+  return dates_run_t<float>(pb, 2, t, r, w, lam, z, z, nullptr, 0, nullptr, ckpt, st);
 }
 
 }  // namespace ws

@@ -63,7 +63,7 @@ _lib.ws_gcv_smooth.restype = ctypes.c_int
 _lib.ws_gcv_smooth.argtypes = [_PP, _vp, _vp, ctypes.POINTER(ctypes.c_float), ctypes.c_int, _vp, _vp, _vp, _vp,
                                _u32, _vp, _sz, _vp]
 _lib.ws_smooth_dates.restype = ctypes.c_int
-_lib.ws_smooth_dates.argtypes = [_PP, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _sz, _vp]
+_lib.ws_smooth_dates.argtypes = [_PP, _vp, _vp, _vp, _vp, _vp, _vp, _u32, _vp, _sz, _vp]
 _lib.ws_smooth_dates_adjoint.restype = ctypes.c_int
 _lib.ws_smooth_dates_adjoint.argtypes = [_PP, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _u32, _vp, _vp, _sz, _vp]
 _lib.ws_weight_grad.restype = ctypes.c_int
@@ -345,11 +345,11 @@ DATES = 0x40
 
 
 def smooth_dates(t: torch.Tensor, x: torch.Tensor, w: torch.Tensor, lam: torch.Tensor, d: int = 2, *, z=None,
-                 status=None, stream=None, workspace_buf=None):
+                 status=None, refine: bool = False, stream=None, workspace_buf=None):
     """z = (W + D^T Lambda D)^{-1} W x on unevenly spaced sample times: t [T, P] (each
     series' strictly increasing dates, x's dtype), D the uneven-spacing discrete derivative
     (row k: d! times the divided-difference weights on t_k..t_{k+d}). x [T, B, P], w [T, P],
-    lam [T, P] or [P]. Returns (z, status)."""
+    lam [T, P] or [P]. refine: one step of iterative refinement. Returns (z, status)."""
     T, B, P, lm = _check_tile(x, w, lam, d)
     if tuple(t.shape) != (T, P) or t.dtype != x.dtype or not t.is_cuda or not t.is_contiguous():
         raise ValueError("t must be a contiguous [T, P] CUDA tensor of x's dtype")
@@ -358,9 +358,10 @@ def smooth_dates(t: torch.Tensor, x: torch.Tensor, w: torch.Tensor, lam: torch.T
         z = torch.empty_like(x)
     if status is None:
         status = torch.empty(P, dtype=torch.uint8, device=x.device)
-    ws = workspace(pb, x.device, DATES, workspace_buf)
+    flags = REFINE if refine else 0
+    ws = workspace(pb, x.device, DATES | flags, workspace_buf)
     _check(_lib.ws_smooth_dates(ctypes.byref(pb), _ptr(t), _ptr(x), _ptr(w), _ptr(lam), _ptr(z), _ptr(status),
-                                _ptr(ws), ws.numel(), _stream_ptr(stream)))
+                                flags, _ptr(ws), ws.numel(), _stream_ptr(stream)))
     return z, status
 
 

@@ -170,15 +170,17 @@ def test_dates_arguments_rejected_before_cuda(ws):
     pb = ws.make_problem(T, B, P, 2, ws.F32, ws.LAM_PER_DAY)
     base = 1 << 40
     t, x, w, lam, z, gz, gx, gl = (base + 4096 * i for i in range(8))
-    assert L.ws_smooth_dates(ctypes.byref(pb), None, x, w, lam, z, None, None, 0, None) == ws.WS_EINVAL
+    assert L.ws_smooth_dates(ctypes.byref(pb), None, x, w, lam, z, None, 0, None, 0, None) == ws.WS_EINVAL
     assert "non-NULL" in ws.last_error()
-    assert L.ws_smooth_dates(ctypes.byref(pb), t, x, w, lam, x + 8, None, None, 0, None) == ws.WS_EINVAL
+    assert L.ws_smooth_dates(ctypes.byref(pb), t, x, w, lam, x + 8, None, 0, None, 0, None) == ws.WS_EINVAL
     assert "overlap" in ws.last_error()
+    assert L.ws_smooth_dates(ctypes.byref(pb), t, x, w, lam, z, None, 0x80, None, 0, None) == ws.WS_EINVAL
+    assert "flags" in ws.last_error()
     assert L.ws_smooth_dates_adjoint(ctypes.byref(pb), t, w, lam, z, gz, None, gl, 0, None, None, 0, None) == ws.WS_EINVAL
     assert L.ws_smooth_dates_adjoint(ctypes.byref(pb), t, w, lam, z, gz, gz + 4, gl, 0, None, None, 0, None) == ws.WS_EINVAL
     assert L.ws_smooth_dates_adjoint(ctypes.byref(pb), t, w, lam, z, gz, gx, gx, 0, None, None, 0, None) == ws.WS_EINVAL
     assert L.ws_smooth_dates_adjoint(ctypes.byref(pb), t, w, lam, z, gz, gx, gl, 0x80, None, None, 0, None) == ws.WS_EINVAL
     assert "flags" in ws.last_error()
     pb0 = ws.make_problem(T, B, 0, 2, ws.F32, ws.LAM_PER_DAY)
-    assert L.ws_smooth_dates(ctypes.byref(pb0), None, None, None, None, None, None, None, 0, None) == ws.WS_OK
+    assert L.ws_smooth_dates(ctypes.byref(pb0), None, None, None, None, None, None, 0, None, 0, None) == ws.WS_OK
     assert L.ws_smooth_dates_adjoint(ctypes.byref(pb0), *([None] * 7), 0, None, None, 0, None) == ws.WS_OK

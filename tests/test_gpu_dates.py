@@ -59,6 +59,31 @@ def test_dates_fp32_matches_oracle(ws, d, B):
     assert np.all(z.cpu().numpy()[:, :, ~ok] == 0)
 
 
+@pytest.mark.parametrize("d,B", [(1, 3), (2, 10), (3, 4)])
+def test_dates_fp32_refined(ws, d, B):
+    """One refinement step (residual by nested divided differences, correction solve with
+    the same rotations): FP32 reaches 1e-4 at d = 3 as well, where the plain solve does not."""
+    g, c = _inputs("hetero_tile", 300, 401, B, torch.float32)
+    z, st = ws.smooth_dates(g["t"], g["x"], g["w"], g["lam"], d, refine=True)
+    torch.cuda.synchronize()
+    zr, ok = _oracle(c, d)
+    assert np.array_equal(st.cpu().numpy() == 0, ok)
+    err = rel_err_per_series(z.cpu().numpy()[:, :, ok], zr[:, :, ok])
+    assert err <= 1e-4, err
+    assert np.all(z.cpu().numpy()[:, :, ~ok] == 0)
+
+
+@pytest.mark.parametrize("d", [2, 4])
+def test_dates_fp64_refined(ws, d):
+    """The refinement step in FP64 leaves an accurate solve accurate (and exercises the FP64
+    residual kernel)."""
+    g, c = _inputs("hetero_tile", 130, 321, 2, torch.float64)
+    z, st = ws.smooth_dates(g["t"], g["x"], g["w"], g["lam"], d, refine=True)
+    torch.cuda.synchronize()
+    zr, ok = _oracle(c, d)
+    assert rel_err_per_series(z.cpu().numpy()[:, :, ok], zr[:, :, ok]) <= 1e-8
+
+
 @pytest.mark.parametrize("d", [1, 2, 3, 4])
 def test_dates_fp64_matches_oracle(ws, d):
     """FP64 (64 series per CTA), 130 series, 2 bands, per-day lambda."""
@@ -87,12 +112,13 @@ def test_dates_uniform_grid_equals_daily_path(ws, dtype, tol):
     rc = synth.Recipe(**{**synth.RECIPES["layer"].__dict__, "T": 150, "n_bands": 2})
     out = synth.generate_tile(rc, 200, device="cuda", dtype=dtype)
     t = torch.arange(150, dtype=dtype, device="cuda").view(150, 1).expand(150, 200).contiguous()
-    z1, s1 = ws.smooth_dates(t, out["x"], out["w"], out["lam"], 2)
-    z2, s2 = ws.smooth(out["x"], out["w"], out["lam"], 2)
-    torch.cuda.synchronize()
-    assert torch.equal(s1, s2)
-    ok = (s1 == 0).cpu().numpy()
-    assert rel_err_per_series(z1.cpu().numpy()[:, :, ok], z2.cpu().double().numpy()[:, :, ok]) <= tol
+    for refine in (False, True):
+        z1, s1 = ws.smooth_dates(t, out["x"], out["w"], out["lam"], 2, refine=refine)
+        z2, s2 = ws.smooth(out["x"], out["w"], out["lam"], 2, refine=refine)
+        torch.cuda.synchronize()
+        assert torch.equal(s1, s2)
+        ok = (s1 == 0).cpu().numpy()
+        assert rel_err_per_series(z1.cpu().numpy()[:, :, ok], z2.cpu().double().numpy()[:, :, ok]) <= tol
 
 
 def test_dates_invalid_and_empty(ws):
