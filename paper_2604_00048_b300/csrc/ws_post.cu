@@ -41,6 +41,7 @@
 #include "ws_internal.h"
 #include "ws_ptx.cuh"
 #include "ws_sweep.cuh"
+#include "ws_dates.cuh"
 
 namespace ws {
 
@@ -60,19 +61,24 @@ struct PostArgs {
                      // residual degrees of freedom are within rounding of zero
   uint8_t* status;   // [P] or null
   F* ckpt;           // per CTA: nch * kPr * (series per CTA)
+  const F* t;        // sample times [T][P] (the uneven-spacing operator) or null (daily grid)
 };
 
 template <typename F>
 __device__ __forceinline__ bool finite_post(F v) { return isfinite(v); }
 
-template <typename F, int D>
-__global__ void __launch_bounds__(post_np<F>(), sizeof(F) == 4 ? (D <= 2 ? 7 : (D == 3 ? 6 : 4)) : 1) k_post_diag(const PostArgs<F> a) {
+// DT: the rows of D come from each series' sample times (staged like w) instead of the
+// binomial coefficients of the daily grid.
+template <typename F, int D, bool DT>
+__global__ void __launch_bounds__(post_np<F>(), sizeof(F) == 4 ? (D <= 2 ? (DT ? 6 : 7) : (D == 3 ? 6 : 4)) : 1)
+    k_post_diag(const PostArgs<F> a) {
   constexpr int kPostNP = post_np<F>();
   using SW = Sweep<F, D, 1>;
   constexpr int kPr = D * (D + 1) / 2;  // partial-row words in a checkpoint
   constexpr bool kDW = sizeof(F) == 4;  // double-word window in FP32
   __shared__ F sw[2][kPostC + D][kPostNP];
   __shared__ F sl[2][kPostC][kPostNP];
+  __shared__ F stt[2][DT ? kPostC + D : 1][kPostNP];
   const int tid = threadIdx.x;
   const int T = a.T, nch = a.nch, P = a.P;
   F* const ck = a.ckpt + (size_t)blockIdx.x * nch * kPr * kPostNP + tid;
@@ -88,6 +94,7 @@ __global__ void __launch_bounds__(post_np<F>(), sizeof(F) == 4 ? (D <= 2 ? 7 : (
         const int t = t0 + k;
         const bool v = act && t < T;
         cp_async_elem<sizeof(F)>(&sw[st][k][tid], v ? a.w + (size_t)t * P + p : a.w, v);
+        if constexpr (DT) cp_async_elem<sizeof(F)>(&stt[st][k][tid], v ? a.t + (size_t)t * P + p : a.t, v);
       }
       if (!a.lam_scalar) {
 #pragma unroll
@@ -136,7 +143,17 @@ __global__ void __launch_bounds__(post_np<F>(), sizeof(F) == 4 ? (D <= 2 ? 7 : (
         npos += wi > F(0);
         n += wi;
         F rho[D], invD;
-        s.factor_step(has_row, li, wa, rho, invD);
+        if constexpr (DT) {
+          F tw[D + 1], cf[D + 1];
+#pragma unroll
+          for (int j = 0; j <= D; ++j) tw[j] = stt[st][k + j][tid];
+          bad |= !finite_post(tw[0]);
+          if (i + 1 < T) bad |= !(tw[1] > tw[0]);
+          if (has_row) dates_coef<F, D>(tw, cf);
+          dates_factor_step(s, has_row, li, wa, cf, rho, invD);
+        } else {
+          s.factor_step(has_row, li, wa, rho, invD);
+        }
       }
       if (c + 2 < nch) issue(c + 2, st);
     }
@@ -175,7 +192,15 @@ __global__ void __launch_bounds__(post_np<F>(), sizeof(F) == 4 ? (D <= 2 ? 7 : (
           const F wa = sw[st][k + D][tid];
           const F li = a.lam_scalar ? lam_s : sl[st][k][tid];
           F rho[D], invD;
-          s.factor_step(i < T - D, li, wa, rho, invD);
+          if constexpr (DT) {
+            F tw[D + 1], cf[D + 1];
+#pragma unroll
+            for (int j = 0; j <= D; ++j) tw[j] = stt[st][k + j][tid];
+            if (i < T - D) dates_coef<F, D>(tw, cf);
+            dates_factor_step(s, i < T - D, li, wa, cf, rho, invD);
+          } else {
+            s.factor_step(i < T - D, li, wa, rho, invD);
+          }
           ik[k] = invD;
 #pragma unroll
           for (int j = 0; j < D; ++j) rk[k][j] = rho[j];
@@ -327,25 +352,26 @@ __global__ void __launch_bounds__(kSdNP) k_post_sd4(int T, int B, int P4, const 
   }
 }
 
-template <typename F, int D>
+template <typename F, int D, bool DT = false>
 static int post_occ(int& occ) {
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_post_diag<F, D>, post_np<F>(), 0) != cudaSuccess ||
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_post_diag<F, D, DT>, post_np<F>(), 0) != cudaSuccess ||
       occ < 1)
     return set_error(WS_ECUDA, "posterior: occupancy query");
   return WS_OK;
 }
 
-int post_plan(const ws_problem& pb, int& grid, int& nch, size_t& ck_bytes) {
+template <bool DT>
+static int post_plan_t(const ws_problem& pb, int& grid, int& nch, size_t& ck_bytes) {
   DeviceInfo di;
   int rc = device_info(di);
   if (rc != WS_OK) return rc;
   const bool f64 = pb.dtype == WS_F64;
   int occ = 0;
   switch (pb.d) {
-    case 1: rc = f64 ? post_occ<double, 1>(occ) : post_occ<float, 1>(occ); break;
-    case 2: rc = f64 ? post_occ<double, 2>(occ) : post_occ<float, 2>(occ); break;
-    case 3: rc = f64 ? post_occ<double, 3>(occ) : post_occ<float, 3>(occ); break;
-    case 4: rc = f64 ? post_occ<double, 4>(occ) : post_occ<float, 4>(occ); break;
+    case 1: rc = f64 ? post_occ<double, 1, DT>(occ) : post_occ<float, 1, DT>(occ); break;
+    case 2: rc = f64 ? post_occ<double, 2, DT>(occ) : post_occ<float, 2, DT>(occ); break;
+    case 3: rc = f64 ? post_occ<double, 3, DT>(occ) : post_occ<float, 3, DT>(occ); break;
+    case 4: rc = f64 ? post_occ<double, 4, DT>(occ) : post_occ<float, 4, DT>(occ); break;
     default: return set_error(WS_EINVAL, "unsupported order d=%d", pb.d);
   }
   if (rc != WS_OK) return rc;
@@ -358,13 +384,26 @@ int post_plan(const ws_problem& pb, int& grid, int& nch, size_t& ck_bytes) {
   return WS_OK;
 }
 
+int post_plan(const ws_problem& pb, int& grid, int& nch, size_t& ck_bytes) {
+  return post_plan_t<false>(pb, grid, nch, ck_bytes);
+}
+int post_plan_dates(const ws_problem& pb, int& grid, int& nch, size_t& ck_bytes) {
+  return post_plan_t<true>(pb, grid, nch, ck_bytes);
+}
+
+int post_plan_dates(const ws_problem& pb, int& grid, int& nch, size_t& ck_bytes);
+int launch_posterior_dates(const ws_problem& pb, const void* t, const void* x, const void* w, const void* lam,
+                           const void* z, void* diag, void* sigma2, void* sd, uint8_t* status, void* ckpt, void* den,
+                           cudaStream_t st);
+
 template <typename F>
-static int launch_post_t(const ws_problem& pb, const void* x, const void* w, const void* lam, const void* z,
-                         void* diag, void* sigma2, void* sd, uint8_t* status, void* ckpt, void* den,
+static int launch_post_t(const ws_problem& pb, const void* tt, const void* x, const void* w, const void* lam,
+                         const void* z, void* diag, void* sigma2, void* sd, uint8_t* status, void* ckpt, void* den,
                          cudaStream_t st) {
   int grid = 0, nch = 0;
   size_t ckb = 0;
-  int rc = post_plan(pb, grid, nch, ckb);
+  const bool dt = tt != nullptr;
+  int rc = dt ? post_plan_dates(pb, grid, nch, ckb) : post_plan(pb, grid, nch, ckb);
   if (rc != WS_OK) return rc;
   PostArgs<F> a;
   memset(&a, 0, sizeof(a));
@@ -380,11 +419,21 @@ static int launch_post_t(const ws_problem& pb, const void* x, const void* w, con
   a.den = static_cast<F*>(den);
   a.status = status;
   a.ckpt = static_cast<F*>(ckpt);
-  switch (pb.d) {
-    case 1: k_post_diag<F, 1><<<grid, np, 0, st>>>(a); break;
-    case 2: k_post_diag<F, 2><<<grid, np, 0, st>>>(a); break;
-    case 3: k_post_diag<F, 3><<<grid, np, 0, st>>>(a); break;
-    case 4: k_post_diag<F, 4><<<grid, np, 0, st>>>(a); break;
+  a.t = static_cast<const F*>(tt);
+  if (dt) {
+    switch (pb.d) {
+      case 1: k_post_diag<F, 1, true><<<grid, np, 0, st>>>(a); break;
+      case 2: k_post_diag<F, 2, true><<<grid, np, 0, st>>>(a); break;
+      case 3: k_post_diag<F, 3, true><<<grid, np, 0, st>>>(a); break;
+      case 4: k_post_diag<F, 4, true><<<grid, np, 0, st>>>(a); break;
+    }
+  } else {
+    switch (pb.d) {
+      case 1: k_post_diag<F, 1, false><<<grid, np, 0, st>>>(a); break;
+      case 2: k_post_diag<F, 2, false><<<grid, np, 0, st>>>(a); break;
+      case 3: k_post_diag<F, 3, false><<<grid, np, 0, st>>>(a); break;
+      case 4: k_post_diag<F, 4, false><<<grid, np, 0, st>>>(a); break;
+    }
   }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return set_error(WS_ECUDA, "posterior diagonal kernel launch: %s", cudaGetErrorString(e));
@@ -412,9 +461,15 @@ static int launch_post_t(const ws_problem& pb, const void* x, const void* w, con
 
 int launch_posterior(const ws_problem& pb, const void* x, const void* w, const void* lam, const void* z,
                      void* diag, void* sigma2, void* sd, uint8_t* status, void* ckpt, void* den, cudaStream_t st) {
+  return launch_posterior_dates(pb, nullptr, x, w, lam, z, diag, sigma2, sd, status, ckpt, den, st);
+}
+
+int launch_posterior_dates(const ws_problem& pb, const void* t, const void* x, const void* w, const void* lam,
+                           const void* z, void* diag, void* sigma2, void* sd, uint8_t* status, void* ckpt, void* den,
+                           cudaStream_t st) {
   if (pb.dtype == WS_F64)
-    return launch_post_t<double>(pb, x, w, lam, z, diag, sigma2, sd, status, ckpt, den, st);
-  return launch_post_t<float>(pb, x, w, lam, z, diag, sigma2, sd, status, ckpt, den, st);
+    return launch_post_t<double>(pb, t, x, w, lam, z, diag, sigma2, sd, status, ckpt, den, st);
+  return launch_post_t<float>(pb, t, x, w, lam, z, diag, sigma2, sd, status, ckpt, den, st);
 }
 
 }  // namespace ws
