@@ -306,7 +306,7 @@ def gcv_one(x, w, lam_grid, d: int):
     return best, scores, zb
 
 
-def posterior_one(x, w, lam, d: int, z=None):
+def posterior_one(x, w, lam, d: int, z=None, t=None):
     """Posterior spread of the smooth, the credibility intervals of Fig. 4 (the paper takes
     them from the Bayesian reading of the smoother it cites and does not restate them).
 
@@ -317,16 +317,17 @@ def posterior_one(x, w, lam, d: int, z=None):
     RSS_b / (n - tr H), RSS_b = sum_t w_t (x_tb - z_tb)^2, n = sum_t w_t, tr H =
     sum_t w_t (Omega^{-1})_tt (H = Omega^{-1} W, the hat matrix).
 
-    x: [T] or [T, B]; z: the smooth (computed here when None). Returns (diag(Omega^{-1}) [T],
-    sigma2 [B], sd [T, B]) with sd_tb = sqrt(sigma2_b (Omega^{-1})_tt); the interval at level
-    q is z +- q sd."""
+    x: [T] or [T, B]; z: the smooth (computed here when None); t: sample times for the
+    uneven-spacing operator (None: the daily grid). Returns (diag(Omega^{-1}) [T], sigma2 [B],
+    sd [T, B]) with sd_tb = sqrt(sigma2_b (Omega^{-1})_tt); the interval at level q is
+    z +- q sd."""
     w = np.asarray(w, dtype=np.float64)
     T = w.shape[0]
     x2 = np.asarray(x, dtype=np.float64).reshape(T, -1)
     if z is None:
-        z = smooth_one(x2, w, lam, d)
+        z = smooth_one(x2, w, lam, d) if t is None else smooth_one_dates(x2, w, lam, d, t)
     z2 = np.asarray(z, dtype=np.float64).reshape(T, -1)
-    Oi = np.linalg.inv(omega(w, lam, d))
+    Oi = np.linalg.inv(omega(w, lam, d) if t is None else omega_dates(w, lam, d, t))
     dg = np.diag(Oi).copy()
     n = float(np.sum(w))
     trh = float(np.sum(w * dg))
@@ -337,8 +338,9 @@ def posterior_one(x, w, lam, d: int, z=None):
     return dg, sigma2, sd
 
 
-def posterior_tile(x, w, lam, d: int, z=None):
-    """Tile layout: x, z [t, b, p], w [t, p], lam [t, p] or [p]. Returns (diag [t, p],
+def posterior_tile(x, w, lam, d: int, z=None, t=None):
+    """Tile layout: x, z [t, b, p], w [t, p], lam [t, p] or [p], t (sample times) [t, p] or
+    None. Returns (diag [t, p],
     sigma2 [b, p], sd [t, b, p], ok [p]); series whose Omega is not positive definite get
     zeros and ok = False."""
     x = np.asarray(x, dtype=np.float64)
@@ -355,7 +357,8 @@ def posterior_tile(x, w, lam, d: int, z=None):
             continue
         ok[p] = True
         zp = None if z is None else np.asarray(z, dtype=np.float64)[:, :, p]
-        dg[:, p], s2[:, p], sd[:, :, p] = posterior_one(x[:, :, p], w[:, p], lp, d, zp)
+        tp = None if t is None else np.asarray(t, dtype=np.float64)[:, p]
+        dg[:, p], s2[:, p], sd[:, :, p] = posterior_one(x[:, :, p], w[:, p], lp, d, zp, tp)
     return dg, s2, sd, ok
 
 

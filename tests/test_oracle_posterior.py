@@ -78,3 +78,31 @@ def test_sd_scales_with_data_and_bands_are_independent(d):
     for b in range(3):
         _, s1, _ = dense.posterior_one(x[:, b], w, lam, d)
         assert np.isclose(s1[0], s2[b], rtol=1e-10)
+
+
+def test_posterior_on_sample_times():
+    """With the uneven-spacing operator: on t = 0..T-1 it is the daily posterior; on uneven
+    dates the error of the posterior mean under the Bayesian model has covariance
+    sigma^2 Omega^{-1} (40,000 draws against sigma^2 diag(Omega^{-1}), as for the daily grid)."""
+    rng = np.random.default_rng(17)
+    T, d = 14, 2
+    w = (rng.random(T) < 0.6).astype(float)
+    w[[0, 5, 9]] = 1.0
+    lam = 10 ** rng.uniform(-0.5, 1.0, T)
+    x = rng.normal(size=(T, 2))
+    a = dense.posterior_one(x, w, lam, d)
+    b = dense.posterior_one(x, w, lam, d, t=np.arange(T, dtype=float))
+    for u, v in zip(a, b):
+        assert np.allclose(u, v, rtol=1e-11, atol=1e-14)
+    t = np.cumsum(rng.integers(1, 4, size=T)).astype(float)
+    sigma, eps, N = 0.3, 1e-6, 40000
+    Dm = dense.difference_matrix_dates(t, d)
+    prior_prec = Dm.T @ np.diag(dense.lam_rows(lam, T, d)) @ Dm + eps * np.eye(T)
+    Lc = np.linalg.cholesky(np.linalg.inv(prior_prec))
+    s = sigma * (Lc @ rng.normal(size=(T, N)))
+    noise = np.where(w[:, None] > 0, sigma * rng.normal(size=(T, N)), 0.0)
+    xs = np.where(w[:, None] > 0, s + noise, 0.0)
+    z = np.linalg.solve(np.diag(w) + prior_prec, w[:, None] * xs)
+    emp = np.mean((s - z) ** 2, axis=1)
+    dg, _, _ = dense.posterior_one(np.zeros(T), w, lam, d, t=t)
+    assert np.max(np.abs(emp / (sigma ** 2 * dg) - 1.0)) < 0.04
