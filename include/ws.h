@@ -204,6 +204,14 @@ int ws_posterior(const ws_problem* pb, const void* x, const void* w, const void*
                  void* diag, void* sigma2, void* sd, uint8_t* status, void* workspace, size_t ws_bytes,
                  void* stream);
 
+/* ws_posterior on unevenly spaced sample times: Omega = W + D^T Lambda D with D the
+ * uneven-spacing operator of ws_smooth_dates (rows from t [T][P], each series' strictly
+ * increasing dates); z is the smooth on those dates. Same outputs, codes (dates that do not
+ * increase: WS_SERIES_BADARG) and workspace (ws_workspace_size(pb, WS_POSTERIOR)). */
+int ws_posterior_dates(const ws_problem* pb, const void* t, const void* x, const void* w, const void* lam,
+                       const void* z, void* diag, void* sigma2, void* sd, uint8_t* status, void* workspace,
+                       size_t ws_bytes, void* stream);
+
 /* ---- Learned lambda: temporal convolution network g_theta (Section 4.2 names a network
  * with a sigmoid output range; this one is a 4-layer 1-D convolution net) ----
  * Per series, per day: (x_t [w_t > 0], w_t) -> conv(2->64, k=9) -> ReLU -> conv(64->64) ->

@@ -241,6 +241,13 @@ size_t tile_workspace_bytes(const ws_problem& P) {
   return kHeaderBytes + ck;
 }
 
+// Posterior spread on sample times (ws_post.cu): the diagonal kernel with the rows of D
+// formed from t.
+int post_plan_dates(const ws_problem& pb, int& grid, int& nch, size_t& ck_bytes);
+int launch_posterior_dates(const ws_problem& pb, const void* t, const void* x, const void* w, const void* lam,
+                           const void* z, void* diag, void* sigma2, void* sd, uint8_t* status, void* ckpt, void* den,
+                           cudaStream_t st);
+
 // Refinement on sample times (ws_dates.cu): residual into r, then the correction solve
 // accumulated onto z in place.
 int launch_dates_refine(const ws_problem& pb, const void* t, const void* x, const void* w, const void* lam, void* z,
@@ -404,7 +411,7 @@ extern "C" int ws_weight_grad(const ws_problem* pb, const void* x, const void* w
   return launch_wgrad(P, x, w, z, g, gx, gw, static_cast<cudaStream_t>(stream));
 }
 
-extern "C" int ws_posterior(const ws_problem* pb, const void* x, const void* w, const void* lam, const void* z,
+static int posterior_impl(const ws_problem* pb, const void* t_dates, const void* x, const void* w, const void* lam, const void* z,
                             void* diag, void* sigma2, void* sd, uint8_t* status, void* workspace, size_t ws_bytes,
                             void* stream) {
   clear_error();
@@ -424,6 +431,7 @@ extern "C" int ws_posterior(const ws_problem* pb, const void* x, const void* w, 
     return WS_OK;
   }
   if (!x || !w || !lam || !z || !diag) return set_error(WS_EINVAL, "x, w, lam, z and diag must be non-NULL");
+  const bool dt = t_dates != nullptr;
   const size_t nl = P.lam_mode == WS_LAM_SCALAR ? (size_t)P.n_series * es : nd;
   const void* ins[4] = {x, w, lam, z};
   const size_t nin[4] = {nx, nd, nl, nx};
@@ -438,15 +446,33 @@ extern "C" int ws_posterior(const ws_problem* pb, const void* x, const void* w, 
   rc = post_bytes(P, need);
   if (rc != WS_OK) return rc;
   need += kHeaderBytes;
+  if (dt && overlaps(t_dates, nd, diag, nd)) return set_error(WS_EINVAL, "diag must not overlap t");
   if (workspace == nullptr || (reinterpret_cast<uintptr_t>(workspace) & 255u) != 0)
     return set_error(WS_EINVAL, "workspace must be non-NULL and 256-byte aligned");
   if (ws_bytes < need) return set_error(WS_ENOMEM_WS, "workspace too small: %zu < %zu", ws_bytes, need);
   int grid = 0, nch = 0;
   size_t ck = 0;
-  rc = post_plan(P, grid, nch, ck);
+  rc = dt ? post_plan_dates(P, grid, nch, ck) : post_plan(P, grid, nch, ck);
   if (rc != WS_OK) return rc;
   char* base = static_cast<char*>(workspace) + kHeaderBytes;
-  return launch_posterior(P, x, w, lam, z, diag, sigma2, sd, status, base, base + round256(ck), st);
+  return launch_posterior_dates(P, t_dates, x, w, lam, z, diag, sigma2, sd, status, base, base + round256(ck), st);
+}
+
+
+extern "C" int ws_posterior(const ws_problem* pb, const void* x, const void* w, const void* lam, const void* z,
+                            void* diag, void* sigma2, void* sd, uint8_t* status, void* workspace, size_t ws_bytes,
+                            void* stream) {
+  return posterior_impl(pb, nullptr, x, w, lam, z, diag, sigma2, sd, status, workspace, ws_bytes, stream);
+}
+
+extern "C" int ws_posterior_dates(const ws_problem* pb, const void* t, const void* x, const void* w, const void* lam,
+                                  const void* z, void* diag, void* sigma2, void* sd, uint8_t* status,
+                                  void* workspace, size_t ws_bytes, void* stream) {
+  if (pb != nullptr && pb->n_series > 0 && pb->T > 0 && t == nullptr) {
+    clear_error();
+    return set_error(WS_EINVAL, "t must be non-NULL");
+  }
+  return posterior_impl(pb, t, x, w, lam, z, diag, sigma2, sd, status, workspace, ws_bytes, stream);
 }
 
 extern "C" int ws_gcv_smooth(const ws_problem* pb, const void* x, const void* w, const float* lam_grid, int n_grid,

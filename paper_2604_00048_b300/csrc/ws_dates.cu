@@ -455,6 +455,7 @@ __global__ void __launch_bounds__(128) k_dates_resid(int T, int B, int P, const 
   }
 #pragma unroll
   for (int j = 0; j < D; ++j) fl[j] = F(0);
+#pragma unroll 4
   for (int s = 0; s < T + D; ++s) {
     const bool in = s < T;
     const F ts = in ? t[(size_t)s * sP + p] : tw[0];

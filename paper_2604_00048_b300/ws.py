@@ -66,6 +66,8 @@ _lib.ws_smooth_dates.restype = ctypes.c_int
 _lib.ws_smooth_dates.argtypes = [_PP, _vp, _vp, _vp, _vp, _vp, _vp, _u32, _vp, _sz, _vp]
 _lib.ws_smooth_dates_adjoint.restype = ctypes.c_int
 _lib.ws_smooth_dates_adjoint.argtypes = [_PP, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _u32, _vp, _vp, _sz, _vp]
+_lib.ws_posterior_dates.restype = ctypes.c_int
+_lib.ws_posterior_dates.argtypes = [_PP, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _sz, _vp]
 _lib.ws_weight_grad.restype = ctypes.c_int
 _lib.ws_weight_grad.argtypes = [_PP, _vp, _vp, _vp, _vp, _vp, _vp, _vp]
 _lib.ws_posterior.restype = ctypes.c_int
@@ -262,13 +264,15 @@ POSTERIOR = 0x10
 
 
 def posterior(x: torch.Tensor, w: torch.Tensor, lam: torch.Tensor, z: torch.Tensor, d: int = 2, *,
-              want_sd: bool = True, stream=None, workspace_buf=None, out=None):
+              want_sd: bool = True, stream=None, workspace_buf=None, out=None, t=None):
     """Posterior spread of the smooth z of x (the credibility intervals of Fig. 4):
     diag(Omega^{-1}) per day, the residual variance sigma2_b = RSS_b / (n - tr H) per band,
     and sd = sqrt(sigma2_b diag_t); the interval at level q is z +- q sd.
 
     x, z: [T, B, P]; w: [T, P]; lam: [T, P] or [P]. out: optional (diag, sigma2, sd, status)
-    to write into. Returns (diag [T, P], sigma2 [B, P], sd [T, B, P] or None, status [P])."""
+    to write into. t: optional [T, P] sample times (the uneven-spacing operator of
+    smooth_dates; z is then the smooth on those dates). Returns (diag [T, P], sigma2 [B, P],
+    sd [T, B, P] or None, status [P])."""
     T, B, P, lm = _check_tile(x, w, lam, d)
     if tuple(z.shape) != tuple(x.shape) or z.dtype != x.dtype or not z.is_cuda or not z.is_contiguous():
         raise ValueError("z must be a contiguous CUDA tensor shaped and typed like x")
@@ -281,6 +285,13 @@ def posterior(x: torch.Tensor, w: torch.Tensor, lam: torch.Tensor, z: torch.Tens
         sd = torch.empty_like(x) if want_sd else None
         status = torch.empty(P, dtype=torch.uint8, device=x.device)
     ws = workspace(pb, x.device, POSTERIOR, workspace_buf)
+    if t is not None:
+        if tuple(t.shape) != (T, P) or t.dtype != x.dtype or not t.is_cuda or not t.is_contiguous():
+            raise ValueError("t must be a contiguous [T, P] CUDA tensor of x's dtype")
+        _check(_lib.ws_posterior_dates(ctypes.byref(pb), _ptr(t), _ptr(x), _ptr(w), _ptr(lam), _ptr(z), _ptr(diag),
+                                       _ptr(sigma2), _ptr(sd), _ptr(status), _ptr(ws), ws.numel(),
+                                       _stream_ptr(stream)))
+        return diag, sigma2, sd, status
     _check(_lib.ws_posterior(ctypes.byref(pb), _ptr(x), _ptr(w), _ptr(lam), _ptr(z), _ptr(diag), _ptr(sigma2),
                              _ptr(sd), _ptr(status), _ptr(ws), ws.numel(), _stream_ptr(stream)))
     return diag, sigma2, sd, status

@@ -184,3 +184,18 @@ def test_dates_arguments_rejected_before_cuda(ws):
     pb0 = ws.make_problem(T, B, 0, 2, ws.F32, ws.LAM_PER_DAY)
     assert L.ws_smooth_dates(ctypes.byref(pb0), None, None, None, None, None, None, 0, None, 0, None) == ws.WS_OK
     assert L.ws_smooth_dates_adjoint(ctypes.byref(pb0), *([None] * 7), 0, None, None, 0, None) == ws.WS_OK
+
+
+def test_posterior_dates_arguments_rejected_before_cuda(ws):
+    """ws_posterior_dates: a NULL t (with days and series), and the other checks of
+    ws_posterior, before any CUDA call; P = 0 is a no-op."""
+    L = ws.lib()
+    pb = ws.make_problem(10, 2, 8, 2, ws.F32, ws.LAM_PER_DAY)
+    base = 1 << 40
+    x, w, lam, z, diag, s2, sd = (base + 4096 * i for i in range(7))
+    assert L.ws_posterior_dates(ctypes.byref(pb), None, x, w, lam, z, diag, s2, sd, None, None, 0, None) == ws.WS_EINVAL
+    assert "t must be" in ws.last_error()
+    t = base + 4096 * 8
+    assert L.ws_posterior_dates(ctypes.byref(pb), t, x, w, lam, z, x + 4, s2, sd, None, None, 0, None) == ws.WS_EINVAL
+    pb0 = ws.make_problem(10, 2, 0, 2, ws.F32, ws.LAM_PER_DAY)
+    assert L.ws_posterior_dates(ctypes.byref(pb0), *([None] * 9), None, 0, None) == ws.WS_OK

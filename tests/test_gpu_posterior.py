@@ -204,3 +204,27 @@ def test_posterior_full_tile_sampled(ws):
     del x, w, lam, z, dg, s2, sd
     ws._ws_cache.clear()
     torch.cuda.empty_cache()
+
+
+@pytest.mark.parametrize("dtype,d,tol", [(torch.float32, 1, TOL32), (torch.float32, 2, TOL32),
+                                        (torch.float64, 2, 1e-8), (torch.float64, 3, 1e-7)])
+def test_posterior_on_acquisition_dates(ws, dtype, d, tol):
+    """ws_posterior_dates: the tile kept on each series' acquisition dates (5-day revisit from
+    a random phase), 300 series x 80 dates x 3 bands, the oracle's own z on those dates given
+    to the GPU, against the dense posterior with the uneven-spacing operator."""
+    base = synth.RECIPES["hetero_tile"].__dict__
+    rc = synth.Recipe(**{**base, "T": 401, "n_bands": 3})
+    out = synth.generate_dates_tile(rc, 300, device="cpu", dtype=dtype)
+    c = {k: v.double().numpy() for k, v in out.items()}
+    T, B, P = c["x"].shape
+    zr = np.zeros((T, B, P))
+    for p in range(P):
+        if dense.is_pd(c["w"][:, p], c["lam"][:, p], d):
+            zr[:, :, p] = dense.smooth_one_dates(c["x"][:, :, p], c["w"][:, p], c["lam"][:, p], d, c["t"][:, p])
+    ref = dense.posterior_tile(c["x"], c["w"], c["lam"], d, t=c["t"])
+    g = {k: v.to("cuda") for k, v in out.items()}
+    dg, s2, sd, st = ws.posterior(g["x"], g["w"], g["lam"], torch.as_tensor(zr, dtype=dtype, device="cuda"), d,
+                                  t=g["t"])
+    torch.cuda.synchronize()
+    got = (dg.cpu().double().numpy(), s2.cpu().double().numpy(), sd.cpu().double().numpy(), st.cpu().numpy())
+    _check(ref, got, tol)
