@@ -269,10 +269,11 @@ def vjp_tile(w, lam, d: int, z, gz, log_lambda: bool = False):
     return gx, glam
 
 
-def hat_trace(w, lam, d: int) -> float:
-    """tr H with H = Omega^{-1} W: sum_t w_t (Omega^{-1})_tt, from the dense inverse."""
+def hat_trace(w, lam, d: int, t=None) -> float:
+    """tr H with H = Omega^{-1} W: sum_t w_t (Omega^{-1})_tt, from the dense inverse (t: sample
+    times for the uneven-spacing operator, None for the daily grid)."""
     w = np.asarray(w, dtype=np.float64)
-    Oi = np.linalg.inv(omega(w, lam, d))
+    Oi = np.linalg.inv(omega(w, lam, d) if t is None else omega_dates(w, lam, d, t))
     return float(np.sum(w * np.diag(Oi)))
 
 
@@ -281,13 +282,14 @@ def inverse_diag(w, lam, d: int) -> np.ndarray:
     return np.diag(np.linalg.inv(omega(np.asarray(w, dtype=np.float64), lam, d))).copy()
 
 
-def gcv_one(x, w, lam_grid, d: int):
+def gcv_one(x, w, lam_grid, d: int, t=None):
     """Grid search of a scalar lambda by generalized cross-validation.
 
     For each grid value: z = Omega^{-1} W x (bands as right-hand sides),
     RSS = sum_b sum_t w_t (x_tb - z_tb)^2, tr H = sum_t w_t (Omega^{-1})_tt,
     n = sum_t w_t, and V = (n B) RSS / (n B - B tr H)^2. The smallest V wins;
-    ties go to the smaller lambda. Returns (best index, scores, z at the best)."""
+    ties go to the smaller lambda. t: sample times for the uneven-spacing operator (None: the
+    daily grid). Returns (best index, scores, z at the best)."""
     x = np.asarray(x, dtype=np.float64)
     w = np.asarray(w, dtype=np.float64)
     T = w.shape[0]
@@ -295,14 +297,15 @@ def gcv_one(x, w, lam_grid, d: int):
     B = x2.shape[1]
     n = float(np.sum(w))
     scores = []
+    solve = (lambda lv: smooth_one(x2, w, lv, d)) if t is None else (lambda lv: smooth_one_dates(x2, w, lv, d, t))
     for lam in lam_grid:
-        z = smooth_one(x2, w, float(lam), d)
+        z = solve(float(lam))
         rss = float(np.sum(w[:, None] * (np.where(w[:, None] > 0, x2, 0.0) - z) ** 2))
-        tr = hat_trace(w, float(lam), d)
+        tr = hat_trace(w, float(lam), d, t)
         scores.append(n * B * rss / (n * B - B * tr) ** 2)
     scores = np.array(scores)
     best = int(np.argmin(scores))          # argmin returns the first (smallest lambda) on ties
-    zb = smooth_one(x2, w, float(lam_grid[best]), d).reshape(x.shape)
+    zb = solve(float(lam_grid[best])).reshape(x.shape)
     return best, scores, zb
 
 

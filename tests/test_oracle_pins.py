@@ -462,3 +462,22 @@ def test_dates_vjp_finite_differences(rng):
         Jv = dense.smooth_one_dates(v, w, lam, d, t)
         JTg, _ = dense.vjp_one_dates(w, lam, d, t, np.zeros(T), g1)
         assert abs(np.dot(g1, Jv) - np.dot(JTg, v)) <= 1e-10 * np.linalg.norm(g1) * np.linalg.norm(v)
+
+
+@pytest.mark.parametrize("d", [1, 2, 3])
+def test_dates_hat_trace_limits_and_gcv(rng, d):
+    """On sample times: tr H -> number of valid days as lambda -> 0 (w binary) and -> d as
+    lambda -> infinity (the weighted polynomial fit of degree d - 1 has d parameters); the
+    GCV search on t = 0..T-1 is the daily one."""
+    T = 40
+    t = _dates(rng, T, gap_hi=6)
+    ts = t / np.mean(np.diff(t))
+    w = (rng.random(T) < 0.5).astype(float)
+    w[rng.choice(T, d + 2, replace=False)] = 1.0
+    assert abs(dense.hat_trace(w, 1e-9, d, ts) - w.sum()) <= 1e-5
+    assert abs(dense.hat_trace(w, 1e9, d, ts) - d) <= 1e-3
+    x = rng.normal(size=T)
+    grid = [10.0 ** (i / 2) for i in range(8)]
+    a = dense.gcv_one(x, w, grid, d)
+    b = dense.gcv_one(x, w, grid, d, t=np.arange(T, dtype=float))
+    assert a[0] == b[0] and np.allclose(a[1], b[1], rtol=1e-9)
