@@ -212,6 +212,14 @@ int ws_posterior_dates(const ws_problem* pb, const void* t, const void* x, const
                        const void* z, void* diag, void* sigma2, void* sd, uint8_t* status, void* workspace,
                        size_t ws_bytes, void* stream);
 
+/* ws_gcv_smooth on unevenly spaced sample times: the grid search and the final smooth use
+ * the uneven-spacing operator of ws_smooth_dates (rows from t [T][P], each series' strictly
+ * increasing dates). Same arguments otherwise; workspace ws_workspace_size(pb, WS_GCV |
+ * WS_DATES | flags) (pb->lam_mode is ignored, as for ws_gcv_smooth). */
+int ws_gcv_smooth_dates(const ws_problem* pb, const void* t, const void* x, const void* w, const float* lam_grid,
+                        int n_grid, void* z, float* lam_best, float* scores, uint8_t* status, uint32_t flags,
+                        void* workspace, size_t ws_bytes, void* stream);
+
 /* ---- Learned lambda: temporal convolution network g_theta (Section 4.2 names a network
  * with a sigmoid output range; this one is a 4-layer 1-D convolution net) ----
  * Per series, per day: (x_t [w_t > 0], w_t) -> conv(2->64, k=9) -> ReLU -> conv(64->64) ->

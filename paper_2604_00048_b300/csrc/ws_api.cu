@@ -241,6 +241,11 @@ size_t tile_workspace_bytes(const ws_problem& P) {
   return kHeaderBytes + ck;
 }
 
+// GCV on sample times (ws_gcv.cu): the grid search with the rows of D formed from t.
+int gcv_plan_dates(const ws_problem& pb, int& grid, int& nch, size_t& ck_bytes);
+int launch_gcv_dates(const ws_problem& pb, const void* t, const void* x, const void* w, const float* grid_vals,
+                     int n_grid, float* lam_best, float* scores, void* ckpt, cudaStream_t st);
+
 // Posterior spread on sample times (ws_post.cu): the diagonal kernel with the rows of D
 // formed from t.
 int post_plan_dates(const ws_problem& pb, int& grid, int& nch, size_t& ck_bytes);
@@ -298,6 +303,12 @@ extern "C" size_t ws_workspace_size(const ws_problem* pb, uint32_t flags) {
     int grid = 0, nch = 0;
     size_t gck = 0;
     if (gcv_plan(*pb, grid, nch, gck) != WS_OK) return 0;
+    need = std::max(need, kHeaderBytes + round256(gck));
+  }
+  if ((flags & WS_GCV) && (flags & WS_DATES)) {
+    int grid = 0, nch = 0;
+    size_t gck = 0;
+    if (gcv_plan_dates(*pb, grid, nch, gck) != WS_OK) return 0;
     need = std::max(need, kHeaderBytes + round256(gck));
   }
   if (flags & WS_DATES) {
@@ -502,6 +513,41 @@ extern "C" int ws_gcv_smooth(const ws_problem* pb, const void* x, const void* w,
   rc = launch_gcv(P, x, w, lam_grid, n_grid, lam_best, scores, static_cast<char*>(workspace) + kHeaderBytes, st);
   if (rc != WS_OK) return rc;
   return ws_smooth_batch(&P, x, w, lam_best, z, nullptr, status, flags & WS_REFINE, workspace, ws_bytes, stream);
+}
+
+extern "C" int ws_gcv_smooth_dates(const ws_problem* pb, const void* t, const void* x, const void* w,
+                                   const float* lam_grid, int n_grid, void* z, float* lam_best, float* scores,
+                                   uint8_t* status, uint32_t flags, void* workspace, size_t ws_bytes, void* stream) {
+  clear_error();
+  int rc = validate_problem(pb);
+  if (rc != WS_OK) return rc;
+  if (flags & ~WS_REFINE) return set_error(WS_EINVAL, "unknown flags 0x%x", flags);
+  if (pb->dtype != WS_F32) return set_error(WS_EUNSUPPORTED, "GCV grid search: FP32 only");
+  if (pb->n_bands != 1) return set_error(WS_EUNSUPPORTED, "GCV grid search: one band");
+  if (lam_grid == nullptr || n_grid < 1 || n_grid > 16) return set_error(WS_EINVAL, "n_grid must be 1..16");
+  for (int g = 0; g < n_grid; ++g)
+    if (!(lam_grid[g] > 0.f) || !std::isfinite(lam_grid[g]))
+      return set_error(WS_EINVAL, "lam_grid[%d] must be finite and > 0", g);
+  ws_problem P = *pb;
+  P.lam_mode = WS_LAM_SCALAR;  // the final smooth takes lam_best per series
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (P.n_series == 0) return WS_OK;
+  if (!t || !x || !w || !z || !lam_best) return set_error(WS_EINVAL, "t, x, w, z and lam_best must be non-NULL");
+  if (P.T == 0) return ws_smooth_dates(&P, t, x, w, lam_best, z, status, 0, workspace, ws_bytes, stream);
+  size_t gck = 0;
+  int grid = 0, nch = 0;
+  rc = gcv_plan_dates(P, grid, nch, gck);
+  if (rc != WS_OK) return rc;
+  const size_t need_s = ws_workspace_size(&P, WS_DATES | (flags & WS_REFINE));
+  if (need_s == 0) return WS_ECUDA;
+  const size_t need = std::max(need_s, kHeaderBytes + round256(gck));
+  if (workspace == nullptr || (reinterpret_cast<uintptr_t>(workspace) & 255u) != 0)
+    return set_error(WS_EINVAL, "workspace must be non-NULL and 256-byte aligned");
+  if (ws_bytes < need) return set_error(WS_ENOMEM_WS, "workspace too small: %zu < %zu", ws_bytes, need);
+  rc = launch_gcv_dates(P, t, x, w, lam_grid, n_grid, lam_best, scores, static_cast<char*>(workspace) + kHeaderBytes,
+                        st);
+  if (rc != WS_OK) return rc;
+  return ws_smooth_dates(&P, t, x, w, lam_best, z, status, flags & WS_REFINE, workspace, ws_bytes, stream);
 }
 
 extern "C" int ws_smooth_batch(const ws_problem* pb, const void* x, const void* w, const void* lam, void* z,

@@ -36,6 +36,7 @@
 #include "ws_internal.h"
 #include "ws_ptx.cuh"
 #include "ws_sweep.cuh"
+#include "ws_dates.cuh"
 
 namespace ws {
 
@@ -52,14 +53,17 @@ struct GcvArgs {
   float* lam_best;  // [P]
   float* scores;    // [n_grid][P] or null
   float* ckpt;      // per CTA: nch * fields * 256
+  const float* t;   // sample times [T][P] (the uneven-spacing operator) or null (daily grid)
 };
 
-template <int D>
+// DT: the rows of D come from each series' sample times (staged like w).
+template <int D, bool DT>
 __global__ void __launch_bounds__(kGcvThreads, 2) k_gcv(const GcvArgs a) {
   using SW = Sweep<float, D, 1>;
   constexpr int kF = SW::kFields;
   __shared__ float sx[2][kGcvC][kGcvPix];
   __shared__ float sw[2][kGcvC + D][kGcvPix];
+  __shared__ float stt[2][DT ? kGcvC + D : 1][kGcvPix];
   const int tid = threadIdx.x, g = tid & (kGcvG - 1), pl = tid / kGcvG;
   const float lam = a.grid[g < a.n_grid ? g : 0];
   const int T = a.T, P = a.P, nch = a.nch;
@@ -71,19 +75,37 @@ __global__ void __launch_bounds__(kGcvThreads, 2) k_gcv(const GcvArgs a) {
     // stage chunk c: C x-rows and C + D w-rows of the CTA's 16 series (zero outside)
     auto issue = [&](int c, int st) {
       const int t0 = c * kGcvC;
-      for (int e = tid; e < (2 * kGcvC + D) * kGcvPix; e += kGcvThreads) {
+      constexpr int kRows = 2 * kGcvC + D + (DT ? kGcvC + D : 0);
+      for (int e = tid; e < kRows * kGcvPix; e += kGcvThreads) {
         const int row = e / kGcvPix, col = e % kGcvPix, pp = p0 + col;
         if (row < kGcvC) {
           const int t = t0 + row;
           const bool v = t < T && pp < P;
           cp_async_elem<4>(&sx[st][row][col], a.x + (v ? (size_t)t * P + pp : 0), v);
-        } else {
+        } else if (row < 2 * kGcvC + D) {
           const int t = t0 + row - kGcvC;
           const bool v = t < T && pp < P;
           cp_async_elem<4>(&sw[st][row - kGcvC][col], a.w + (v ? (size_t)t * P + pp : 0), v);
+        } else if constexpr (DT) {
+          const int t = t0 + row - 2 * kGcvC - D;
+          const bool v = t < T && pp < P;
+          cp_async_elem<4>(&stt[st][row - 2 * kGcvC - D][col], a.t + (v ? (size_t)t * P + pp : 0), v);
         }
       }
       cp_async_commit();
+    };
+    // rotation step of day i = c * C + k from the staged chunk (daily binomial rows, or the
+    // rows formed from the series' dates)
+    auto fstep = [&](SW& sv, int st, int k, int i, float wa, float (&rho)[D], float& invD) {
+      if constexpr (DT) {
+        float tw[D + 1], cf[D + 1];
+#pragma unroll
+        for (int j = 0; j <= D; ++j) tw[j] = stt[st][k + j][pl];
+        if (i < T - D) dates_coef<float, D>(tw, cf);
+        dates_factor_step(sv, i < T - D, lam, wa, cf, rho, invD);
+      } else {
+        sv.factor_step(i < T - D, lam, wa, rho, invD);
+      }
     };
 
     SW s;
@@ -106,11 +128,15 @@ __global__ void __launch_bounds__(kGcvThreads, 2) k_gcv(const GcvArgs a) {
         const int i = c * kGcvC + k;
         const float wi = sw[st][k][pl], wa = sw[st][k + D][pl], xi = sx[st][k][pl];
         bad |= !(wi >= 0.f) || !isfinite(wi);
+        if constexpr (DT) {
+          bad |= !isfinite(stt[st][k][pl]);
+          if (i + 1 < T) bad |= !(stt[st][k + 1][pl] > stt[st][k][pl]);
+        }
         npos += wi > 0.f;
         n += wi;
         float bv[1] = {wi > 0.f ? wi * xi : 0.f};
         float rho[D], yh[1], invD;
-        s.factor_step(i < T - D, lam, wa, rho, invD);
+        fstep(s, st, k, i, wa, rho, invD);
         s.subst_step(rho, invD, bv, yh);
       }
       __syncthreads();
@@ -145,7 +171,7 @@ __global__ void __launch_bounds__(kGcvThreads, 2) k_gcv(const GcvArgs a) {
           const float wi = sw[st][k][pl], wa = sw[st][k + D][pl], xi = sx[st][k][pl];
           float bv[1] = {wi > 0.f ? wi * xi : 0.f};
           float rho[D], yh[1], invD;
-          s.factor_step(i < T - D, lam, wa, rho, invD);
+          fstep(s, st, k, i, wa, rho, invD);
           s.subst_step(rho, invD, bv, yh);
           yk[k] = yh[0];
           ik[k] = invD;
@@ -228,27 +254,28 @@ __global__ void __launch_bounds__(kGcvThreads, 2) k_gcv(const GcvArgs a) {
   }
 }
 
-template <int D>
+template <int D, bool DT = false>
 static int gcv_grid_t(int n_groups, int& grid) {
   DeviceInfo di;
   int rc = device_info(di);
   if (rc != WS_OK) return rc;
   int occ = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_gcv<D>, kGcvThreads, 0) != cudaSuccess || occ < 1)
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_gcv<D, DT>, kGcvThreads, 0) != cudaSuccess || occ < 1)
     return set_error(WS_ECUDA, "gcv: occupancy query");
   grid = std::min(n_groups, di.sm_count * occ);
   if (grid < 1) grid = 1;
   return WS_OK;
 }
 
-int gcv_plan(const ws_problem& pb, int& grid, int& nch, size_t& ck_bytes) {
+template <bool DT>
+static int gcv_plan_t(const ws_problem& pb, int& grid, int& nch, size_t& ck_bytes) {
   const int n_groups = (int)((pb.n_series + kGcvPix - 1) / kGcvPix);
   int rc = WS_EINVAL;
   switch (pb.d) {
-    case 1: rc = gcv_grid_t<1>(n_groups, grid); break;
-    case 2: rc = gcv_grid_t<2>(n_groups, grid); break;
-    case 3: rc = gcv_grid_t<3>(n_groups, grid); break;
-    case 4: rc = gcv_grid_t<4>(n_groups, grid); break;
+    case 1: rc = gcv_grid_t<1, DT>(n_groups, grid); break;
+    case 2: rc = gcv_grid_t<2, DT>(n_groups, grid); break;
+    case 3: rc = gcv_grid_t<3, DT>(n_groups, grid); break;
+    case 4: rc = gcv_grid_t<4, DT>(n_groups, grid); break;
     default: return set_error(WS_EINVAL, "unsupported order d=%d", pb.d);
   }
   if (rc != WS_OK) return rc;
@@ -258,13 +285,29 @@ int gcv_plan(const ws_problem& pb, int& grid, int& nch, size_t& ck_bytes) {
   return WS_OK;
 }
 
+int gcv_plan(const ws_problem& pb, int& grid, int& nch, size_t& ck_bytes) {
+  return gcv_plan_t<false>(pb, grid, nch, ck_bytes);
+}
+int gcv_plan_dates(const ws_problem& pb, int& grid, int& nch, size_t& ck_bytes) {
+  return gcv_plan_t<true>(pb, grid, nch, ck_bytes);
+}
+
+int launch_gcv_dates(const ws_problem& pb, const void* t, const void* x, const void* w, const float* grid_vals,
+                     int n_grid, float* lam_best, float* scores, void* ckpt, cudaStream_t st);
+
 int launch_gcv(const ws_problem& pb, const void* x, const void* w, const float* grid_vals, int n_grid,
                float* lam_best, float* scores, void* ckpt, cudaStream_t st) {
+  return launch_gcv_dates(pb, nullptr, x, w, grid_vals, n_grid, lam_best, scores, ckpt, st);
+}
+
+int launch_gcv_dates(const ws_problem& pb, const void* t, const void* x, const void* w, const float* grid_vals,
+                     int n_grid, float* lam_best, float* scores, void* ckpt, cudaStream_t st) {
   GcvArgs a;
   memset(&a, 0, sizeof(a));
   int grid = 0, nch = 0;
   size_t ckb = 0;
-  int rc = gcv_plan(pb, grid, nch, ckb);
+  const bool dt = t != nullptr;
+  int rc = dt ? gcv_plan_t<true>(pb, grid, nch, ckb) : gcv_plan_t<false>(pb, grid, nch, ckb);
   if (rc != WS_OK) return rc;
   a.T = pb.T;
   a.P = (int)pb.n_series;
@@ -277,11 +320,21 @@ int launch_gcv(const ws_problem& pb, const void* x, const void* w, const float* 
   a.lam_best = lam_best;
   a.scores = scores;
   a.ckpt = static_cast<float*>(ckpt);
-  switch (pb.d) {
-    case 1: k_gcv<1><<<grid, kGcvThreads, 0, st>>>(a); break;
-    case 2: k_gcv<2><<<grid, kGcvThreads, 0, st>>>(a); break;
-    case 3: k_gcv<3><<<grid, kGcvThreads, 0, st>>>(a); break;
-    case 4: k_gcv<4><<<grid, kGcvThreads, 0, st>>>(a); break;
+  a.t = static_cast<const float*>(t);
+  if (dt) {
+    switch (pb.d) {
+      case 1: k_gcv<1, true><<<grid, kGcvThreads, 0, st>>>(a); break;
+      case 2: k_gcv<2, true><<<grid, kGcvThreads, 0, st>>>(a); break;
+      case 3: k_gcv<3, true><<<grid, kGcvThreads, 0, st>>>(a); break;
+      case 4: k_gcv<4, true><<<grid, kGcvThreads, 0, st>>>(a); break;
+    }
+  } else {
+    switch (pb.d) {
+      case 1: k_gcv<1, false><<<grid, kGcvThreads, 0, st>>>(a); break;
+      case 2: k_gcv<2, false><<<grid, kGcvThreads, 0, st>>>(a); break;
+      case 3: k_gcv<3, false><<<grid, kGcvThreads, 0, st>>>(a); break;
+      case 4: k_gcv<4, false><<<grid, kGcvThreads, 0, st>>>(a); break;
+    }
   }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return set_error(WS_ECUDA, "gcv kernel launch: %s", cudaGetErrorString(e));

@@ -66,6 +66,9 @@ _lib.ws_smooth_dates.restype = ctypes.c_int
 _lib.ws_smooth_dates.argtypes = [_PP, _vp, _vp, _vp, _vp, _vp, _vp, _u32, _vp, _sz, _vp]
 _lib.ws_smooth_dates_adjoint.restype = ctypes.c_int
 _lib.ws_smooth_dates_adjoint.argtypes = [_PP, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _u32, _vp, _vp, _sz, _vp]
+_lib.ws_gcv_smooth_dates.restype = ctypes.c_int
+_lib.ws_gcv_smooth_dates.argtypes = [_PP, _vp, _vp, _vp, ctypes.POINTER(ctypes.c_float), ctypes.c_int, _vp, _vp, _vp,
+                                     _vp, _u32, _vp, _sz, _vp]
 _lib.ws_posterior_dates.restype = ctypes.c_int
 _lib.ws_posterior_dates.argtypes = [_PP, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _sz, _vp]
 _lib.ws_weight_grad.restype = ctypes.c_int
@@ -239,10 +242,11 @@ GCV_GRID = [10.0 ** (i / 3.0) for i in range(16)]  # log10 lambda in {0, 1/3, ..
 
 
 def gcv_smooth(x: torch.Tensor, w: torch.Tensor, lam_grid=None, d: int = 2, *, refine: bool = False,
-               want_scores: bool = True, stream=None):
+               want_scores: bool = True, stream=None, t=None):
     """Per-series lambda by GCV over a grid of scalar values, then the smoothing at it.
 
     x: [T, 1, P] FP32, w: [T, P]. lam_grid: up to 16 positive values (default GCV_GRID).
+    t: optional [T, P] sample times (the uneven-spacing operator of smooth_dates).
     Returns (z, lam_best [P], scores [n_grid, P] or None, status [P])."""
     grid = [float(v) for v in (GCV_GRID if lam_grid is None else lam_grid)]
     lam_dummy = torch.empty(x.shape[2], dtype=x.dtype, device=x.device)
@@ -253,8 +257,15 @@ def gcv_smooth(x: torch.Tensor, w: torch.Tensor, lam_grid=None, d: int = 2, *, r
     lam_best = torch.empty(P, dtype=torch.float32, device=x.device)
     scores = torch.empty(len(grid), P, dtype=torch.float32, device=x.device) if want_scores else None
     status = torch.empty(P, dtype=torch.uint8, device=x.device)
-    ws = workspace(pb, x.device, GCV | flags)
+    ws = workspace(pb, x.device, GCV | flags | (DATES if t is not None else 0))
     arr = (ctypes.c_float * len(grid))(*grid)
+    if t is not None:
+        if tuple(t.shape) != (T, P) or t.dtype != x.dtype or not t.is_cuda or not t.is_contiguous():
+            raise ValueError("t must be a contiguous [T, P] CUDA tensor of x's dtype")
+        _check(_lib.ws_gcv_smooth_dates(ctypes.byref(pb), _ptr(t), _ptr(x), _ptr(w), arr, len(grid), _ptr(z),
+                                        _ptr(lam_best), _ptr(scores), _ptr(status), flags, _ptr(ws), ws.numel(),
+                                        _stream_ptr(stream)))
+        return z, lam_best, scores, status
     _check(_lib.ws_gcv_smooth(ctypes.byref(pb), _ptr(x), _ptr(w), arr, len(grid), _ptr(z), _ptr(lam_best),
                               _ptr(scores), _ptr(status), flags, _ptr(ws), ws.numel(), _stream_ptr(stream)))
     return z, lam_best, scores, status

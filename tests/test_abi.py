@@ -199,3 +199,19 @@ def test_posterior_dates_arguments_rejected_before_cuda(ws):
     assert L.ws_posterior_dates(ctypes.byref(pb), t, x, w, lam, z, x + 4, s2, sd, None, None, 0, None) == ws.WS_EINVAL
     pb0 = ws.make_problem(10, 2, 0, 2, ws.F32, ws.LAM_PER_DAY)
     assert L.ws_posterior_dates(ctypes.byref(pb0), *([None] * 9), None, 0, None) == ws.WS_OK
+
+
+def test_gcv_dates_arguments_rejected_before_cuda(ws):
+    """ws_gcv_smooth_dates: FP64 or several bands unsupported, a bad grid or NULL arrays
+    rejected, before any CUDA call."""
+    L = ws.lib()
+    arr = (ctypes.c_float * 2)(1.0, 10.0)
+    pb = ws.make_problem(10, 1, 8, 2, ws.F64, ws.LAM_SCALAR)
+    assert L.ws_gcv_smooth_dates(ctypes.byref(pb), None, None, None, arr, 2, *([None] * 4), 0, None, 0, None) == \
+        ws.WS_EUNSUPPORTED
+    pb = ws.make_problem(10, 1, 8, 2, ws.F32, ws.LAM_SCALAR)
+    assert L.ws_gcv_smooth_dates(ctypes.byref(pb), None, None, None, arr, 0, *([None] * 4), 0, None, 0, None) == \
+        ws.WS_EINVAL
+    assert L.ws_gcv_smooth_dates(ctypes.byref(pb), None, None, None, arr, 2, *([None] * 4), 0, None, 0, None) == \
+        ws.WS_EINVAL
+    assert "non-NULL" in ws.last_error()

@@ -98,3 +98,41 @@ def test_gcv_full_length_sampled(ws):
     x, w = _inputs(730, 4096, 1)
     ids = np.random.default_rng(5).choice(4096, 12, replace=False)
     _check(ws, x, w, 2, ws.GCV_GRID, ids)
+
+
+@pytest.mark.parametrize("d", [1, 2])
+def test_gcv_on_acquisition_dates(ws, d):
+    """ws_gcv_smooth_dates: the learned-lambda workload kept on each series' acquisition dates
+    (5-day revisit from a random phase; 146 dates of 730 days), 200 series: scores against the
+    dense GCV with the uneven-spacing operator, the choice optimal within 1e-3 of the oracle's
+    scores, the final (refined) smooth at the chosen lambda within 1e-4."""
+    base = synth.RECIPES["learned"].__dict__
+    out = synth.generate_dates_tile(synth.Recipe(**base), 200, device="cpu")
+    c = {k: v.double().numpy() for k, v in out.items()}
+    g = {k: v.to("cuda") for k, v in out.items()}
+    grid = ws.GCV_GRID
+    z, lam_best, scores, st = ws.gcv_smooth(g["x"], g["w"], grid, d, refine=True, t=g["t"])
+    torch.cuda.synchronize()
+    sc, lb, stc = scores.cpu().numpy(), lam_best.cpu().numpy(), st.cpu().numpy()
+    zc = z.cpu().double().numpy()[:, 0, :]
+    checked = 0
+    for p in range(0, 200, 3):
+        wp, xp, tp = c["w"][:, p], c["x"][:, 0, p], c["t"][:, p]
+        if not dense.is_pd(wp, float(grid[0]), d):
+            assert stc[p] == ws.SERIES_NOT_PD
+            continue
+        best, ref, _ = dense.gcv_one(xp, wp, grid, d, t=tp)
+        n = wp.sum()
+        trh = np.array([dense.hat_trace(wp, float(lv), d, tp) for lv in grid])
+        determined = 2 * trh / (n - trh) <= 100
+        rel = np.abs(sc[:, p] - ref) / ref
+        assert np.max(rel[determined], initial=0) <= 5e-3, (p, sc[:, p], ref)
+        if not determined.all():
+            continue
+        gi = int(np.argmin(sc[:, p]))
+        assert lb[p] == np.float32(grid[gi]) and ref[gi] <= ref.min() * (1 + 2e-3)
+        if gi == best:  # the oracle's own smooth at its own choice
+            zr = dense.smooth_one_dates(xp, wp, float(np.float32(grid[best])), d, tp)
+            assert np.max(np.abs(zc[:, p] - zr)) / max(np.max(np.abs(zr)), 1e-6) <= 1e-4
+            checked += 1
+    assert checked >= 20
