@@ -103,14 +103,16 @@ def test_gcv_full_length_sampled(ws):
 @pytest.mark.parametrize("d", [1, 2])
 def test_gcv_on_acquisition_dates(ws, d):
     """ws_gcv_smooth_dates: the learned-lambda workload kept on each series' acquisition dates
-    (5-day revisit from a random phase; 146 dates of 730 days), 200 series: scores against the
-    dense GCV with the uneven-spacing operator, the choice optimal within 1e-3 of the oracle's
+    (5-day revisit from a random phase; 146 dates of 730 days), 200 series, log10 lambda in
+    {2, 2 1/3, ..., 7}: scores against the dense GCV with the uneven-spacing operator, the choice optimal within 1e-3 of the oracle's
     scores, the final (refined) smooth at the chosen lambda within 1e-4."""
     base = synth.RECIPES["learned"].__dict__
     out = synth.generate_dates_tile(synth.Recipe(**base), 200, device="cpu")
     c = {k: v.double().numpy() for k, v in out.items()}
     g = {k: v.to("cuda") for k, v in out.items()}
-    grid = ws.GCV_GRID
+    # on 5-day spacing a divided-difference row weighs (1/5)^(2d) of a daily one: the grid is
+    # shifted two decades up so that its small end does not interpolate the observations
+    grid = [10.0 ** (2 + i / 3.0) for i in range(16)]
     z, lam_best, scores, st = ws.gcv_smooth(g["x"], g["w"], grid, d, refine=True, t=g["t"])
     torch.cuda.synchronize()
     sc, lb, stc = scores.cpu().numpy(), lam_best.cpu().numpy(), st.cpu().numpy()
