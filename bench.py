@@ -42,6 +42,8 @@ def parse_args():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--pixels", type=int, default=262144, help="series per rank (262144 = the full tile)")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--e2e-sub", type=int, default=8, help="sub-blocks of the end-to-end block")
+    ap.add_argument("--e2e-streams", type=int, default=3, help="streams the end-to-end sub-blocks rotate over")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-ragged", action="store_true")
     ap.add_argument("--no-gcv", action="store_true")
@@ -660,7 +662,7 @@ def run_ours(args):
     # of different sub-blocks overlap (PCIe is full duplex)
     e2e = None
     if not args.no_e2e:
-        Pe, nsub, nstr = min(P, 32768), 8, 3
+        Pe, nsub, nstr = min(P, 32768), args.e2e_sub, args.e2e_streams
         Ps = Pe // nsub
         host = []
         for k in range(nsub):

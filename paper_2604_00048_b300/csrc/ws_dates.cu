@@ -59,8 +59,12 @@ struct DatesArgs {
   F* ckpt;         // per CTA: nch * kFields * NP
 };
 
-// Shared memory of one stage, in rows of NP elements: x (C * NB), w (C + D), t (C + D), lambda (C).
-__host__ __device__ constexpr int dates_stage_rows(int NB, int D) { return kDatesC * NB + 2 * (kDatesC + D) + kDatesC; }
+// Shared memory of one stage, in rows of NP elements: x (C * NB), w (C + D), t (C + D), lambda
+// (C), and for the adjoint and the correction solve z (C * NB: the forward output or z0, staged
+// with the chunks of the backward pass).
+__host__ __device__ constexpr int dates_stage_rows(int NB, int D, bool z) {
+  return kDatesC * NB + 2 * (kDatesC + D) + kDatesC + (z ? kDatesC * NB : 0);
+}
 
 template <typename F, int D, int NB, int MODE>
 __global__ void __launch_bounds__(dates_np<F>(), sizeof(F) == 4 ? 4 : 1) k_dates(const DatesArgs<F> a) {
@@ -68,8 +72,9 @@ __global__ void __launch_bounds__(dates_np<F>(), sizeof(F) == 4 ? 4 : 1) k_dates
   constexpr int NP = dates_np<F>(), C = kDatesC;
   using SW = Sweep<F, D, NB>;
   constexpr int kF = SW::kFields;
-  constexpr int SR = dates_stage_rows(NB, D);
-  constexpr int rW = C * NB, rT = rW + C + D, rL = rT + C + D;
+  constexpr bool HZ = ADJ || RAW;
+  constexpr int SR = dates_stage_rows(NB, D, HZ);
+  constexpr int rW = C * NB, rT = rW + C + D, rL = rT + C + D, rZ = rL + C;
   extern __shared__ __align__(16) unsigned char dates_smem[];
   F* const sm = reinterpret_cast<F*>(dates_smem);
   const int tid = threadIdx.x;
@@ -83,7 +88,8 @@ __global__ void __launch_bounds__(dates_np<F>(), sizeof(F) == 4 ? 4 : 1) k_dates
     const size_t sBP = (size_t)a.B * P;
     const F* const xcol = a.x + (size_t)a.b0 * P + (act ? p : 0);  // this thread's column
     const size_t ocol = act ? (size_t)p : 0;
-    auto issue = [&](int c, int st) {
+    const F* const zcol = HZ ? a.zin + (size_t)a.b0 * P + (act ? p : 0) : nullptr;
+    auto issue = [&](int c, int st, bool withz) {
       const int t0 = c * C;
       const F* xr = xcol + (size_t)t0 * sBP;
       const F* lr = a.lam + (size_t)t0 * P + ocol;
@@ -103,6 +109,16 @@ __global__ void __launch_bounds__(dates_np<F>(), sizeof(F) == 4 ? 4 : 1) k_dates
         cp_async_elem<sizeof(F)>(row(st, rW + k), v ? wr + (size_t)k * P : a.w, v);
         cp_async_elem<sizeof(F)>(row(st, rT + k), v ? tr + (size_t)k * P : a.t, v);
       }
+      if (HZ && withz) {
+        const F* zr = zcol + (size_t)t0 * sBP;
+#pragma unroll
+        for (int k = 0; k < C; ++k) {
+          const bool v = act && t0 + k < T;
+#pragma unroll
+          for (int b = 0; b < NB; ++b)
+            cp_async_elem<sizeof(F)>(row(st, rZ + k * NB + b), v ? zr + (size_t)k * sBP + (size_t)b * P : a.zin, v);
+        }
+      }
       cp_async_commit();
     };
 
@@ -112,8 +128,8 @@ __global__ void __launch_bounds__(dates_np<F>(), sizeof(F) == 4 ? 4 : 1) k_dates
     int npos = 0;
     bool bad = false;
     const F lam_s = (a.lam_scalar && act) ? a.lam[p] : F(0);
-    issue(0, 0);
-    if (nch > 1) issue(1, 1);
+    issue(0, 0, false);
+    if (nch > 1) issue(1, 1, false);
     for (int c = 0; c < nch; ++c) {
       if (c + 1 < nch) cp_async_wait<1>(); else cp_async_wait<0>();
       const int st = c & 1;
@@ -146,7 +162,7 @@ __global__ void __launch_bounds__(dates_np<F>(), sizeof(F) == 4 ? 4 : 1) k_dates
         dates_factor_step(s, has_row, li, wa, cf, rho, invD);
         s.subst_step(rho, invD, bv, yh);
       }
-      if (c + 2 < nch) issue(c + 2, st);
+      if (c + 2 < nch) issue(c + 2, st, false);
     }
     const int dmin = D < T ? D : T;
     const uint8_t code = bad ? WS_SERIES_BADARG : (npos < dmin ? WS_SERIES_NOT_PD : WS_SERIES_OK);
@@ -172,6 +188,7 @@ __global__ void __launch_bounds__(dates_np<F>(), sizeof(F) == 4 ? 4 : 1) k_dates
       }
       s.load(ck + (size_t)c * kF * NP, NP);
       const int nd = min(C, T - c * C);
+      const bool zstaged = HZ && c < nch - 2;
       F rk[C][D];
 #pragma unroll
       for (int k = 0; k < C; ++k) {
@@ -221,7 +238,8 @@ __global__ void __launch_bounds__(dates_np<F>(), sizeof(F) == 4 ? 4 : 1) k_dates
             zc[b][0] = acc;
             F out = okser ? acc : F(0);
             if (ADJ) {
-              const F zv = act ? a.zin[((size_t)i * a.B + a.b0 + b) * P + p] : F(0);
+              // z staged with the chunk, except for the two chunks still resident from pass 1
+              const F zv = zstaged ? *row(st, rZ + k * NB + b) : (act ? a.zin[((size_t)i * a.B + a.b0 + b) * P + p] : F(0));
               F cg = out, cz = zv;
 #pragma unroll
               for (int q = 1; q <= D; ++q) {
@@ -234,7 +252,8 @@ __global__ void __launch_bounds__(dates_np<F>(), sizeof(F) == 4 ? 4 : 1) k_dates
               dl = fma(cg, cz, dl);
               out = wk * out;
             }
-            if (RAW && act) out += a.zin[((size_t)i * a.B + a.b0 + b) * P + p];  // z0 + correction
+            if (RAW && act)  // z0 + correction
+              out += zstaged ? *row(st, rZ + k * NB + b) : a.zin[((size_t)i * a.B + a.b0 + b) * P + p];
             nanacc = fma(out, F(0), nanacc);
             if (act) a.z[((size_t)i * a.B + a.b0 + b) * P + p] = out;
           }
@@ -250,7 +269,7 @@ __global__ void __launch_bounds__(dates_np<F>(), sizeof(F) == 4 ? 4 : 1) k_dates
           }
         }
       }
-      if (c >= 2) issue(c - 2, st);
+      if (c >= 2) issue(c - 2, st, true);
     }
     if (ADJ && a.glam != nullptr && a.lam_scalar && act) a.glam[p] = a.b0 == 0 ? glam_sum : a.glam[p] + glam_sum;
     if (act && a.status != nullptr) {
@@ -269,7 +288,7 @@ static int dates_cfg_t(int n_tiles, int& grid, size_t& smem) {
   int rc = device_info(di);
   if (rc != WS_OK) return rc;
   constexpr int NP = dates_np<F>();
-  smem = (size_t)2 * dates_stage_rows(NB, D) * NP * sizeof(F);
+  smem = (size_t)2 * dates_stage_rows(NB, D, MODE != 0) * NP * sizeof(F);
   auto kern = k_dates<F, D, NB, MODE>;
   if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
     return set_error(WS_ECUDA, "dates: shared memory attribute");
