@@ -42,7 +42,7 @@ def parse_args():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--pixels", type=int, default=262144, help="series per rank (262144 = the full tile)")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--e2e-sub", type=int, default=8, help="sub-blocks of the end-to-end block")
+    ap.add_argument("--e2e-sub", type=int, default=16, help="sub-blocks of the end-to-end block")
     ap.add_argument("--e2e-streams", type=int, default=3, help="streams the end-to-end sub-blocks rotate over")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-ragged", action="store_true")
