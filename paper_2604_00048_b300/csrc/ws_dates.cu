@@ -23,7 +23,12 @@
 // dL/dlambda_k = -sum_b (D g_b)_k (D z_b)_k [* lambda_k], with (D f)_k formed as nested
 // divided differences (level q at day k: (level q-1 at k+1 - level q-1 at k) * q / (t_{k+q}
 // - t_k), the recursive discrete derivative): on smooth sequences each subtraction is
-// exact, where the expanded weights would cancel digits in FP32. z is read with plain loads.
+// exact, where the expanded weights would cancel digits in FP32. z is staged with the
+// backward pass's chunks (plain loads for the two chunks still resident from pass 1).
+//
+// Correction solve (RAW, the refinement step): the same sweeps with the residual as an
+// unweighted right-hand side, the result added onto z0 (staged like z above) in place;
+// k_dates_resid forms the residual beforehand.
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
