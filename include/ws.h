@@ -415,6 +415,14 @@ void ws_plan_destroy(ws_plan* plan);
  * or WS_ECUDA. */
 int ws_sync_status(void* workspace, size_t ws_bytes, void* stream);
 
+/* Diagnostic of the bounded device-side waits: launches one CTA that waits on an mbarrier no
+ * thread ever arrives at, with the bounded wait of the staging pipelines; after the wait
+ * limit (about one second) it gives up, records the timeout in the workspace's error word
+ * (the first 256 bytes, as ws_smooth_batch's) and returns. A following ws_sync_status
+ * returns WS_ETIMEOUT and clears the word; the context stays usable. workspace: device,
+ * 256-byte aligned, at least 256 bytes. No counterpart in the paper. */
+int ws_selftest_wait(void* workspace, size_t ws_bytes, void* stream);
+
 /* Copies the text of the last error on the calling thread into buf (NUL-terminated,
  * truncated to n bytes). Returns the code of that error (WS_OK if none). */
 int ws_last_error(char* buf, size_t n);

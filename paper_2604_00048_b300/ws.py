@@ -80,6 +80,8 @@ _lib.ws_smooth_batch_noalloc.argtypes = [_PP, _vp, _vp, _vp, _vp, _vp, _vp, _u32
 NOALLOC_MAX_BYTES = 64 << 20
 _lib.ws_tune_set.restype = ctypes.c_int
 _lib.ws_tune_set.argtypes = [ctypes.c_int32, ctypes.c_int32]
+_lib.ws_selftest_wait.restype = ctypes.c_int
+_lib.ws_selftest_wait.argtypes = [_vp, _sz, _vp]
 _lib.ws_sync_status.restype = ctypes.c_int
 _lib.ws_sync_status.argtypes = [_vp, _sz, _vp]
 _lib.ws_last_error.restype = ctypes.c_int

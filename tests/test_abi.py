@@ -215,3 +215,10 @@ def test_gcv_dates_arguments_rejected_before_cuda(ws):
     assert L.ws_gcv_smooth_dates(ctypes.byref(pb), None, None, None, arr, 2, *([None] * 4), 0, None, 0, None) == \
         ws.WS_EINVAL
     assert "non-NULL" in ws.last_error()
+
+
+def test_selftest_wait_arguments_rejected_before_cuda(ws):
+    L = ws.lib()
+    assert L.ws_selftest_wait(None, 4096, None) == ws.WS_EINVAL
+    assert L.ws_selftest_wait(ctypes.c_void_p(1 << 40), 16, None) == ws.WS_EINVAL
+    assert L.ws_selftest_wait(ctypes.c_void_p((1 << 40) + 8), 4096, None) == ws.WS_EINVAL
