@@ -43,7 +43,7 @@ def test_homo_fp64_whole_workload(ws):
 
 def test_hetero_tile_full_size_sampled(ws):
     """The 512 x 512 x 3288-day x 10-band tile: smooth + refinement step + adjoint (log
-    lambda), the step bench.py times, checked on 24 sampled series against the banded
+    lambda), the step bench.py times, checked on 1024 sampled series against the banded
     oracle (z to 1e-4, gradients to 1e-3)."""
     rc = synth.RECIPES["hetero_tile"]
     P = 262144
@@ -55,7 +55,7 @@ def test_hetero_tile_full_size_sampled(ws):
     gz = torch.randn(x.shape, generator=torch.Generator(device="cuda").manual_seed(3), device="cuda")
     gx, glam, st2 = ws.smooth_adjoint(w, lam, z, gz, 2, log_lambda=True)
     ws.sync_status()
-    ids = np.sort(np.random.default_rng(8).choice(P, 24, replace=False))
+    ids = np.sort(np.random.default_rng(8).choice(P, 1024, replace=False))
     it = torch.as_tensor(ids, device="cuda")
     xs, ws_, ls = (t.index_select(-1, it).cpu().double().numpy() for t in (x, w, lam))
     zs, gzs = z.index_select(2, it).cpu().double().numpy(), gz.index_select(2, it).cpu().double().numpy()
@@ -71,7 +71,7 @@ def test_hetero_tile_full_size_sampled(ws):
 
 
 def test_gcv_full_size_sampled(ws):
-    """The learned-lambda evaluation set (262,144 x 730): the GCV choice on 8 sampled series
+    """The learned-lambda evaluation set (262,144 x 730): the GCV choice on 64 sampled series
     is optimal under the FP64 oracle's scores within 1e-3, and the final z matches."""
     base = synth.RECIPES["learned"]
     rc = synth.Recipe(**{**base.__dict__, "seed": base.seed + 1000})
@@ -79,7 +79,7 @@ def test_gcv_full_size_sampled(ws):
     out = synth.generate_tile(rc, P, device="cuda")
     z, lam_best, scores, st = ws.gcv_smooth(out["x"], out["w"], None, 2, refine=True)
     ws.sync_status()
-    ids = np.random.default_rng(4).choice(P, 8, replace=False)
+    ids = np.random.default_rng(4).choice(P, 64, replace=False)
     xs = out["x"][:, 0, :].cpu().double().numpy()
     wsn = out["w"].cpu().double().numpy()
     lb = lam_best.cpu().numpy()

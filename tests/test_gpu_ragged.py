@@ -151,15 +151,18 @@ def test_ragged_status_and_scalar_lambda(ws):
 
 def test_ragged_full_size_sampled(ws):
     """1,048,576 series, T ~ U{120..3288}, d in {1,2,3} in equal thirds, per-day
-    lambda = 10^U[0,5]: autotuned, graph-replayed, one refinement step; 64 sampled series
-    against the oracle."""
+    lambda = 10^U[0,5]: autotuned, graph-replayed, one refinement step; 1024 sampled series:
+    those of order 1 and 2 against the banded FP64 oracle, the first 64 of order 3 against
+    the 50-digit solve (FP64 is not a reference there)."""
     rc = synth.RECIPES["ragged"]
     out = synth.generate_ragged(rc, 1 << 20, device="cuda")
     plan = ws.RaggedPlan(out["offsets"], out["order"])
     z, st = plan.execute(out["x"], out["w"], out["lam"], autotune=True, graph=True, refine=True)
     ws.sync_status()
-    ids = np.random.default_rng(11).choice(1 << 20, 64, replace=False)
-    _check(out, z, st, ids, tol=1e-4, mp_orders=(3,))
+    ids = np.random.default_rng(11).choice(1 << 20, 1024, replace=False)
+    ords = out["order"].cpu().numpy()
+    _check(out, z, st, [i for i in ids if ords[i] < 3], tol=1e-4)
+    _check(out, z, st, [i for i in ids if ords[i] == 3][:64], tol=1e-4, mp_orders=(3,))
 
 
 def test_ragged_scalar_lambda_refined(ws):
