@@ -387,6 +387,26 @@ def dates_measure(dev, steps, P=262144):
     e1.record()
     torch.cuda.synchronize()
     ms_adj = e0.elapsed_time(e1) / steps
+    # the posterior spread and the GCV search (band 0) on the same dates
+    outs = (torch.empty(x.shape[0], P, device=dev), torch.empty(x.shape[1], P, device=dev), torch.empty_like(x),
+            torch.empty(P, dtype=torch.uint8, device=dev))
+    x0 = x[:, :1, :].contiguous()
+    ws.posterior(x, w, lam, z, rc.d, out=outs, t=t)
+    ws.gcv_smooth(x0, w, None, rc.d, refine=True, want_scores=False, t=t)
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(steps):
+        ws.posterior(x, w, lam, z, rc.d, out=outs, t=t)
+    e1.record()
+    torch.cuda.synchronize()
+    ms_post = e0.elapsed_time(e1) / steps
+    e0.record()
+    for _ in range(steps):
+        ws.gcv_smooth(x0, w, None, rc.d, refine=True, want_scores=False, t=t)
+    e1.record()
+    torch.cuda.synchronize()
+    ms_gcv = e0.elapsed_time(e1) / steps
+    del outs, x0
     Ta, B, _ = x.shape
     hbm, _ = peaks()
     byts = 4.0 * (2 * B + 3) * float(P) * Ta
@@ -396,6 +416,7 @@ def dates_measure(dev, steps, P=262144):
            "ms": ms, "series_per_s": P / (ms / 1e3), "achieved_gbs": byts / (ms / 1e3) / 1e9,
            "frac_of_measured_hbm": byts / (ms / 1e3) / 1e9 / hbm,
            "refined_ms": ms_ref, "adjoint_ms": ms_adj, "adjoint_achieved_gbs": byts_adj / (ms_adj / 1e3) / 1e9,
+           "posterior_ms": ms_post, "gcv_band0_ms": ms_gcv,
            "series_with_status": int((st != 0).sum().item())}
     del t, x, w, lam, z, st, gz, gx, glam
     torch.cuda.empty_cache()
