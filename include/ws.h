@@ -13,11 +13,15 @@
  * A scalar lambda gives the homoscedastic smoother of Eq. 2. Several spectral
  * bands share w and lambda and are solved as right-hand sides against one factor
  * (Section 2, "batched multivariate"). The reverse-mode derivatives of Eqs. 4-5
- * (Section 2.3) make the solve a differentiable layer.
+ * (Section 2.3) make the solve a differentiable layer. The *_dates entry points keep each
+ * series on its own unevenly spaced sample times instead of the daily grid (the difference
+ * operator for uneven spacing that Section 2 adopts); ws_posterior gives the credibility
+ * intervals of Fig. 4, ws_weight_grad the gradient in soft weights, ws_gcv_smooth a lambda
+ * per series, the ws_plan_* calls ragged batches and the ws_tcn_* calls the lambda network.
  *
  * Conventions shared by every entry point
- *   - Pointers named x, w, lam, z, factor, gz, gx, glam, status, workspace are
- *     DEVICE pointers owned by the caller. The library never allocates memory on
+ *   - Pointers named x, w, lam, t, z, factor, gz, gx, glam, gw, diag, sigma2, sd, status,
+ *     workspace are DEVICE pointers owned by the caller. The library never allocates memory on
  *     a call path; callers size `workspace` with ws_workspace_size().
  *   - `stream` is a cudaStream_t passed as void*. Every call only enqueues work
  *     on that stream and never synchronises it (except ws_sync_status).
