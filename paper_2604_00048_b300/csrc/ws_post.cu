@@ -20,9 +20,10 @@
 //     The d x d window of Sigma is carried in double-word arithmetic in FP32 (for large
 //     lambda, rho approaches the difference coefficients and each new entry is a d-th
 //     difference of a smooth sequence, which single precision loses digits on); rho and
-//     invD are FP32. One series per thread, 128 per CTA; each thread stages its own column
-//     of w and lambda (chunks of 8 days, two stages, LDGSTS), so no block barrier is
-//     needed. Pass 1 runs the factor forward and stores its state (the d(d+1)/2 partial
+//     invD are FP32. One series per thread, 128 per CTA (64 in FP64); each thread stages its
+//     own column of w and lambda (chunks of 8 days, two stages, LDGSTS), so no block barrier
+//     is needed. On sample times (ws_posterior_dates) it also stages its column of t and
+//     forms the rows of D per day (ws_dates.cuh). Pass 1 runs the factor forward and stores its state (the d(d+1)/2 partial
 //     row entries) per chunk; pass 2 goes back over the chunks, recomputes each chunk's
 //     rho and invD into registers from its checkpoint, and runs the recursion, writing
 //     diag[t][p] and summing tr H.
