@@ -217,6 +217,15 @@ def _check_tile(x, w, lam, d):
     return T, B, P, (LAM_SCALAR if lam.dim() == 1 else LAM_PER_DAY)
 
 
+def _check_out(t, shape, dtype, device, name):
+    """An array the caller passes for an output: the kernels write every element of exactly
+    `shape`, so it must have that shape, be contiguous and match the dtype and device."""
+    if t is None:
+        return
+    if tuple(t.shape) != tuple(shape) or not t.is_contiguous() or t.dtype != dtype or t.device != device:
+        raise ValueError(f"{name} must be a contiguous {tuple(shape)} {dtype} tensor on {device}")
+
+
 def smooth(x: torch.Tensor, w: torch.Tensor, lam: torch.Tensor, d: int = 2, *, z=None, status=None,
            factor=None, refine: bool = False, stream=None, workspace_buf=None):
     """z = (W + D^T Lambda D)^{-1} W x per series and band (Eq. 3; Eq. 2 for scalar lam).
@@ -224,6 +233,8 @@ def smooth(x: torch.Tensor, w: torch.Tensor, lam: torch.Tensor, d: int = 2, *, z
     refine: one step of iterative refinement with a double-word residual.
     Returns (z, status). `factor` (optional [T, d+1, P]) receives the factor."""
     T, B, P, lm = _check_tile(x, w, lam, d)
+    _check_out(z, x.shape, x.dtype, x.device, "z")
+    _check_out(status, (P,), torch.uint8, x.device, "status")
     pb = make_problem(T, B, P, d, _dtype_code(x), lm)
     flags = REFINE if refine else 0
     if z is None:
@@ -292,6 +303,10 @@ def posterior(x: torch.Tensor, w: torch.Tensor, lam: torch.Tensor, z: torch.Tens
     pb = make_problem(T, B, P, d, _dtype_code(x), lm)
     if out is not None:
         diag, sigma2, sd, status = out
+        _check_out(diag, (T, P), x.dtype, x.device, "diag")
+        _check_out(sigma2, (B, P), x.dtype, x.device, "sigma2")
+        _check_out(sd, x.shape, x.dtype, x.device, "sd")
+        _check_out(status, (P,), torch.uint8, x.device, "status")
     else:
         diag = torch.empty(T, P, dtype=x.dtype, device=x.device)
         sigma2 = torch.empty(B, P, dtype=x.dtype, device=x.device)
@@ -348,6 +363,10 @@ def smooth_adjoint(w: torch.Tensor, lam: torch.Tensor, z: torch.Tensor, gz: torc
     T, B, P, lm = _check_tile(gz, w, lam, d)
     if tuple(z.shape) != tuple(gz.shape) or not z.is_contiguous() or z.dtype != gz.dtype:
         raise ValueError("z must match gz")
+    _check_out(gx, gz.shape, gz.dtype, gz.device, "gx")
+    _check_out(glam, lam.shape, gz.dtype, gz.device, "glam")
+    _check_out(status, (P,), torch.uint8, gz.device, "status")
+    _check_out(factor, (T, d + 1, P), gz.dtype, gz.device, "factor")
     pb = make_problem(T, B, P, d, _dtype_code(gz), lm)
     if gx is None and want_gx:
         gx = torch.empty_like(gz)
@@ -377,6 +396,8 @@ def smooth_dates(t: torch.Tensor, x: torch.Tensor, w: torch.Tensor, lam: torch.T
     T, B, P, lm = _check_tile(x, w, lam, d)
     if tuple(t.shape) != (T, P) or t.dtype != x.dtype or not t.is_cuda or not t.is_contiguous():
         raise ValueError("t must be a contiguous [T, P] CUDA tensor of x's dtype")
+    _check_out(z, x.shape, x.dtype, x.device, "z")
+    _check_out(status, (P,), torch.uint8, x.device, "status")
     pb = make_problem(T, B, P, d, _dtype_code(x), lm)
     if z is None:
         z = torch.empty_like(x)
@@ -400,6 +421,9 @@ def smooth_dates_adjoint(t: torch.Tensor, w: torch.Tensor, lam: torch.Tensor, z:
         raise ValueError("z must match gz")
     if tuple(t.shape) != (T, P) or t.dtype != gz.dtype or not t.is_cuda or not t.is_contiguous():
         raise ValueError("t must be a contiguous [T, P] CUDA tensor of gz's dtype")
+    _check_out(gx, gz.shape, gz.dtype, gz.device, "gx")
+    _check_out(glam, lam.shape, gz.dtype, gz.device, "glam")
+    _check_out(status, (P,), torch.uint8, gz.device, "status")
     pb = make_problem(T, B, P, d, _dtype_code(gz), lm)
     if gx is None:
         gx = torch.empty_like(gz)
@@ -428,6 +452,8 @@ def smooth_adjoint_weights(x: torch.Tensor, w: torch.Tensor, lam: torch.Tensor, 
     T, B, P, lm = _check_tile(gz, w, lam, d)
     if tuple(x.shape) != tuple(gz.shape) or x.dtype != gz.dtype or not x.is_cuda or not x.is_contiguous():
         raise ValueError("x must match gz")
+    _check_out(gx, gz.shape, gz.dtype, gz.device, "gx")
+    _check_out(gw, w.shape, gz.dtype, gz.device, "gw")
     g = gx if gx is not None else torch.empty_like(gz)
     if gw is None:
         gw = torch.empty_like(w)
@@ -445,6 +471,13 @@ def factor(w: torch.Tensor, lam: torch.Tensor, d: int = 2, *, out=None, status=N
     if w.dim() != 2:
         raise ValueError("w must be [T, P]")
     T, P = w.shape
+    if lam.dim() == 2 and tuple(lam.shape) != (T, P) or lam.dim() == 1 and lam.shape[0] != P or lam.dim() > 2:
+        raise ValueError("lam must be [T, P] (per day) or [P] (scalar)")
+    for tt in (w, lam):
+        if not tt.is_cuda or not tt.is_contiguous() or tt.dtype != w.dtype or tt.device != w.device:
+            raise ValueError("w and lam must be contiguous CUDA tensors of one dtype and device")
+    _check_out(out, (T, d + 1, P), w.dtype, w.device, "out")
+    _check_out(status, (P,), torch.uint8, w.device, "status")
     lm = LAM_SCALAR if lam.dim() == 1 else LAM_PER_DAY
     pb = make_problem(T, 1, P, d, _dtype_code(w), lm)
     if out is None:
@@ -458,7 +491,16 @@ def factor(w: torch.Tensor, lam: torch.Tensor, d: int = 2, *, out=None, status=N
 
 def solve(fac: torch.Tensor, w: torch.Tensor, x: torch.Tensor, d: int = 2, *, z=None, stream=None):
     """z = Omega^{-1} W x with a stored factor."""
+    if x.dim() != 3:
+        raise ValueError("x must be [T, B, P]")
     T, B, P = x.shape
+    for tt, shp, name in ((fac, (T, d + 1, P), "fac"), (w, (T, P), "w")):
+        if tuple(tt.shape) != shp or not tt.is_cuda or not tt.is_contiguous() or tt.dtype != x.dtype or \
+                tt.device != x.device:
+            raise ValueError(f"{name} must be a contiguous {shp} CUDA tensor of x's dtype")
+    if not x.is_cuda or not x.is_contiguous():
+        raise ValueError("x must be a contiguous CUDA tensor")
+    _check_out(z, x.shape, x.dtype, x.device, "z")
     pb = make_problem(T, B, P, d, _dtype_code(x), LAM_PER_DAY)
     if z is None:
         z = torch.empty_like(x)

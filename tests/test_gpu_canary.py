@@ -153,3 +153,40 @@ def test_gcv_margins(ws, P, dates):
     torch.cuda.synchronize()
     for buf in (z, lb, sc, st, wsp):
         assert buf.margins_intact()
+
+
+def test_binding_rejects_wrong_output_arrays(ws):
+    """Output arrays a caller passes to the binding must have exactly the shape the kernels
+    write (and be contiguous, of the inputs' dtype, on their device): anything else is a
+    ValueError before any launch."""
+    rc, g, c = tile_inputs("layer", 64, T=30, B=2)
+    x, w, lam = g["x"], g["w"], g["lam"]
+    T, B, P = x.shape
+    short = torch.empty(T, B, P - 1, device="cuda")
+    with pytest.raises(ValueError):
+        ws.smooth(x, w, lam, 2, z=short)
+    with pytest.raises(ValueError):
+        ws.smooth(x, w, lam, 2, status=torch.empty(P + 1, dtype=torch.uint8, device="cuda"))
+    z, _ = ws.smooth(x, w, lam, 2)
+    gz = torch.randn_like(x)
+    with pytest.raises(ValueError):
+        ws.smooth_adjoint(w, lam, z, gz, 2, gx=short)
+    with pytest.raises(ValueError):
+        ws.smooth_adjoint(w, lam, z, gz, 2, glam=torch.empty(T - 1, P, device="cuda"))
+    with pytest.raises(ValueError):
+        ws.posterior(x, w, lam, z, 2, out=(torch.empty(T, P, device="cuda"), torch.empty(B, P, device="cuda"),
+                                           short, torch.empty(P, dtype=torch.uint8, device="cuda")))
+    with pytest.raises(ValueError):
+        ws.smooth_adjoint_weights(x, w, lam, z, gz, 2, gw=torch.empty(T, P, 2, device="cuda"))
+    with pytest.raises(ValueError):
+        ws.factor(w, lam, 2, out=torch.empty(T, 2, P, device="cuda"))
+    fac, _ = ws.factor(w, lam, 2)
+    with pytest.raises(ValueError):
+        ws.solve(fac[:, :2].contiguous(), w, x, 2)
+    with pytest.raises(ValueError):
+        ws.solve(fac, w, x, 2, z=x.transpose(0, 2))
+    t = torch.arange(T, dtype=torch.float32, device="cuda").view(T, 1).expand(T, P).contiguous()
+    with pytest.raises(ValueError):
+        ws.smooth_dates(t, x, w, lam, 2, z=short)
+    with pytest.raises(ValueError):
+        ws.smooth_dates_adjoint(t, w, lam, z, gz, 2, gx=short)
