@@ -77,3 +77,24 @@ def test_piecewise_noise_variance_recipe():
     rc = synth.RECIPES["learned"]
     out = synth.generate_tile(rc, 256, want_clean=True)
     assert out["x"].shape == (730, 1, 256)
+
+
+def test_dates_tile_is_the_daily_tile_on_acquisition_days():
+    """generate_dates_tile keeps each series on its revisit days: strictly increasing dates 5
+    days apart from the series' phase, every valid day of the daily tile among them with the
+    same observation, no valid day dropped, lambda the daily field there times the revisit."""
+    import torch
+
+    from paper_2604_00048_b300 import synth
+
+    rc = synth.Recipe(**{**synth.RECIPES["hetero_tile"].__dict__, "T": 200, "n_bands": 3})
+    out = synth.generate_dates_tile(rc, 70, device="cpu", block=32)
+    daily = synth.generate_tile(rc, 70, device="cpu")
+    t = out["t"].long()
+    Ta = (rc.T - rc.revisit) // rc.revisit + 1
+    assert out["x"].shape == (Ta, 3, 70) and t.shape == (Ta, 70)
+    assert torch.all(t[1:] - t[:-1] == rc.revisit) and torch.all(t[0] < rc.revisit) and torch.all(t[-1] < rc.T)
+    assert torch.equal(out["w"], torch.gather(daily["w"], 0, t))
+    assert torch.equal(out["x"], torch.gather(daily["x"], 0, t.view(Ta, 1, 70).expand(Ta, 3, 70)))
+    assert torch.equal(out["w"].sum(0), daily["w"].sum(0))
+    assert torch.allclose(out["lam"], torch.gather(daily["lam"], 0, t) * rc.revisit)
