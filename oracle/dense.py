@@ -79,24 +79,6 @@ def smooth_one_dates(x, w, lam, d: int, t) -> np.ndarray:
     return sla.solve_triangular(L.T, y, lower=False).reshape(x.shape)
 
 
-def smooth_tile_dates(x, w, lam, d: int, t):
-    """Tile layout (x [t, b, p], w [t, p], lam [t, p] or [p]) on sample times t shared by the
-    tile's series. Returns (z, ok) as smooth_tile."""
-    x = np.asarray(x, dtype=np.float64)
-    w = np.asarray(w, dtype=np.float64)
-    lam = np.asarray(lam, dtype=np.float64)
-    T, B, P = x.shape
-    z = np.zeros_like(x)
-    ok = np.ones(P, dtype=bool)
-    for p in range(P):
-        lp = lam[p] if lam.ndim == 1 else lam[:, p]
-        if not is_pd(w[:, p], lp, d):
-            ok[p] = False
-            continue
-        z[:, :, p] = smooth_one_dates(x[:, :, p], w[:, p], lp, d, t)
-    return z, ok
-
-
 def vjp_one_dates(w, lam, d: int, t, z, gz, per_day: bool = True):
     """Reverse-mode derivatives through z = Omega^{-1} W x with the uneven-spacing operator
     (Section 2.3 on sample times t): g = Omega^{-1} dL/dz, dL/dx = W g (Eq. 5, transposed),
