@@ -44,49 +44,94 @@ def omega_band(w, lam, d: int):
     return A
 
 
+def _ldl_band(A, d: int):
+    """Omega = L diag(piv) L^T for the upper band A of Omega (no pivoting); L unit lower with
+    L[t+r][t] stored as Lb[t+r][r]. Raises ValueError if a pivot is not positive."""
+    T = len(A)
+    Lb = [[mpmath.mpf(0) for _ in range(d + 1)] for _ in range(T)]
+    piv = [mpmath.mpf(0)] * T
+    for t in range(T):
+        s = A[t][0]
+        for j in range(1, d + 1):
+            if t - j >= 0:
+                s -= Lb[t][j] ** 2 * piv[t - j]
+        if not s > 0:
+            raise ValueError(f"Omega is not positive definite (pivot {t})")
+        piv[t] = s
+        for r in range(1, d + 1):
+            if t + r >= T:
+                break
+            s = A[t][r]
+            # Omega[t+r, t] = sum_j L[t+r, t-j] piv[t-j] L[t, t-j]
+            for j in range(1, d + 1 - r):
+                if t - j >= 0:
+                    s -= Lb[t + r][r + j] * Lb[t][j] * piv[t - j]
+            Lb[t + r][r] = s / piv[t]
+    return Lb, piv
+
+
+def _ldl_solve(Lb, piv, b, d: int):
+    """Omega^{-1} b from the banded LDL^T factor: forward, diagonal, back substitution."""
+    T = len(b)
+    y = [mpmath.mpf(0)] * T
+    for t in range(T):
+        s = b[t]
+        for j in range(1, d + 1):
+            if t - j >= 0:
+                s -= Lb[t][j] * y[t - j]
+        y[t] = s
+    z = [mpmath.mpf(0)] * T
+    for t in range(T - 1, -1, -1):
+        s = y[t] / piv[t]
+        for j in range(1, d + 1):
+            if t + j < T:
+                s -= Lb[t + j][j] * z[t + j]
+        z[t] = s
+    return z
+
+
 def smooth_mp(x, w, lam, d: int, dps: int = 50) -> np.ndarray:
     """z = Omega^{-1} W x for one series at `dps` digits, returned rounded to FP64.
     Raises ZeroDivisionError / ValueError if Omega is not positive definite."""
     with mpmath.workdps(dps):
         x = np.asarray(x, dtype=np.float64)
         w = np.asarray(w, dtype=np.float64)
-        T = x.shape[0]
-        A = omega_band(w, lam, d)
-        # Omega = L diag(piv) L^T, L unit lower with L[t+r][t] stored as Lb[t+r][r]
-        Lb = [[mpmath.mpf(0) for _ in range(d + 1)] for _ in range(T)]
-        piv = [mpmath.mpf(0)] * T
-        for t in range(T):
-            s = A[t][0]
-            for j in range(1, d + 1):
-                if t - j >= 0:
-                    s -= Lb[t][j] ** 2 * piv[t - j]
-            if not s > 0:
-                raise ValueError(f"Omega is not positive definite (pivot {t})")
-            piv[t] = s
-            for r in range(1, d + 1):
-                if t + r >= T:
-                    break
-                s = A[t][r]
-                # Omega[t+r, t] = sum_j L[t+r, t-j] piv[t-j] L[t, t-j]
-                for j in range(1, d + 1 - r):
-                    if t - j >= 0:
-                        s -= Lb[t + r][r + j] * Lb[t][j] * piv[t - j]
-                Lb[t + r][r] = s / piv[t]
-        y = [mpmath.mpf(0)] * T
-        for t in range(T):
-            s = mpmath.mpf(float(w[t])) * mpmath.mpf(float(x[t]))
-            for j in range(1, d + 1):
-                if t - j >= 0:
-                    s -= Lb[t][j] * y[t - j]
-            y[t] = s
-        z = [mpmath.mpf(0)] * T
-        for t in range(T - 1, -1, -1):
-            s = y[t] / piv[t]
-            for j in range(1, d + 1):
-                if t + j < T:
-                    s -= Lb[t + j][j] * z[t + j]
-            z[t] = s
-        return np.array([float(v) for v in z])
+        Lb, piv = _ldl_band(omega_band(w, lam, d), d)
+        b = [mpmath.mpf(float(wt)) * mpmath.mpf(float(xt)) for wt, xt in zip(w, x)]
+        return np.array([float(v) for v in _ldl_solve(Lb, piv, b, d)])
+
+
+def vjp_mp(w, lam, d: int, z, gz, dps: int = 50, per_day: bool = True):
+    """Reverse-mode derivatives of one series at `dps` digits (Section 2.3, Eqs. 4-5):
+    g_b = Omega^{-1} gz_b, dL/dx_b = W g_b, dL/dlambda_k = -sum_b (D g_b)_k (D z_b)_k for the
+    rows k < T-d (zeros after; their sum for a scalar lambda). z, gz: [T] or [T, B] FP64
+    values, converted exactly. Returns (gx, glam) rounded to FP64, shaped like the FP64
+    oracle's vjp_one. For series where FP64 cannot resolve D g: g carries a large component
+    along the polynomials D annihilates, and its FP64 rounding alone swamps D g."""
+    with mpmath.workdps(dps):
+        w = np.asarray(w, dtype=np.float64)
+        T = w.shape[0]
+        z2 = np.asarray(z, dtype=np.float64).reshape(T, -1)
+        g2 = np.asarray(gz, dtype=np.float64).reshape(T, -1)
+        c = _coeffs(d)
+        Lb, piv = _ldl_band(omega_band(w, lam, d), d)
+        gx = np.zeros_like(g2)
+        rows = [mpmath.mpf(0)] * max(T - d, 0)
+        for b in range(g2.shape[1]):
+            g = _ldl_solve(Lb, piv, [mpmath.mpf(float(v)) for v in g2[:, b]], d)
+            zz = [mpmath.mpf(float(v)) for v in z2[:, b]]
+            for t in range(T):
+                gx[t, b] = float(mpmath.mpf(float(w[t])) * g[t])
+            for k in range(T - d):
+                dg = sum(c[i] * g[k + i] for i in range(d + 1))
+                dz = sum(c[i] * zz[k + i] for i in range(d + 1))
+                rows[k] -= dg * dz
+        if per_day:
+            glam = np.zeros(T)
+            glam[: max(T - d, 0)] = [float(v) for v in rows]
+        else:
+            glam = np.array(float(sum(rows)))
+        return gx.reshape(np.shape(z)), glam
 
 
 def residual_mp(x, w, lam, d: int, z, dps: int = 50) -> float:

@@ -8,10 +8,11 @@ import pytest
 from oracle import banded, dense, multiprec
 
 
-def _exact_solve(x, w, lam, d):
-    """z = Omega^{-1} W x in exact rationals: Omega assembled entry by entry from its
-    definition W + D^T Lambda D (Eq. 3), Gauss-Jordan elimination with Fractions."""
-    T = len(x)
+def _exact_solve(x, w, lam, d, rhs=None):
+    """z = Omega^{-1} W x (or Omega^{-1} rhs) in exact rationals: Omega assembled entry by
+    entry from its definition W + D^T Lambda D (Eq. 3), Gauss-Jordan elimination with
+    Fractions."""
+    T = len(w)
     c = [Fraction(v) for v in dense.diff_coeffs(d)]
     lam = np.asarray(lam, dtype=np.float64)
     lr = [Fraction(float(lam))] * (T - d) if lam.ndim == 0 else [Fraction(float(v)) for v in lam[:T - d]]
@@ -22,7 +23,10 @@ def _exact_solve(x, w, lam, d):
         for i in range(d + 1):
             for j in range(d + 1):
                 M[k + i][k + j] += lr[k] * c[i] * c[j]
-    b = [Fraction(float(w[t])) * Fraction(float(x[t])) for t in range(T)]
+    if rhs is None:
+        b = [Fraction(float(w[t])) * Fraction(float(x[t])) for t in range(T)]
+    else:
+        b = [Fraction(float(v)) for v in rhs]
     for col in range(T):
         piv = next(r for r in range(col, T) if M[r][col] != 0)
         M[col], M[piv] = M[piv], M[col]
@@ -104,3 +108,56 @@ def test_fp64_is_not_a_reference_at_cond_1e13():
     assert np.max(np.abs(z50 - z70)) <= 1e-15 * sc
     assert np.max(np.abs(zb[:, 0, 0] - zd)) / sc > 1e-4
     assert max(np.max(np.abs(zb[:, 0, 0] - z50)), np.max(np.abs(zd - z50))) / sc > 1e-4
+
+
+@pytest.mark.parametrize("d", [1, 2, 3, 4])
+def test_vjp_mp_equals_exact_rational(d):
+    """Dyadic inputs, ill-conditioned lambda mix: the 50-digit VJP (g = Omega^{-1} gz,
+    W g, -(D g)_k (D z)_k summed over two bands) equals the one computed from the exact
+    rational solve, to the FP64 rounding of the returned values. The exact side solves by
+    Gauss-Jordan on the dense Omega and applies D as the matrix of dense.difference_matrix
+    (rows of binomial coefficients), so it shares neither the banded LDL^T nor the
+    coefficient loop of the oracle."""
+    rng = np.random.default_rng(200 + d)
+    T, B = 13, 2
+    w = (rng.random(T) < 0.4).astype(float)
+    w[0] = w[-1] = 1.0
+    w[T // 2] = 0.5
+    lam = 2.0 ** rng.integers(-4, 30, size=T).astype(float)
+    z = np.round(rng.normal(size=(T, B)) * 256) / 256
+    gz = np.round(rng.normal(size=(T, B)) * 256) / 256
+    Dm = dense.difference_matrix(T, d).astype(int)
+    rows = [Fraction(0)] * (T - d)
+    gx_exact = np.zeros((T, B), dtype=object)
+    for b in range(B):
+        g = _exact_solve(None, w, lam, d, rhs=gz[:, b])
+        for t in range(T):
+            gx_exact[t, b] = Fraction(float(w[t])) * g[t]
+        for k in range(T - d):
+            dg = sum(int(Dm[k, j]) * g[j] for j in range(T))
+            dz = sum(int(Dm[k, j]) * Fraction(float(z[j, b])) for j in range(T))
+            rows[k] -= dg * dz
+    gx, glam = multiprec.vjp_mp(w, lam, d, z, gz)
+    sx = max(abs(float(v)) for v in gx_exact.ravel())
+    assert max(abs(Fraction(float(a)) - b) for a, b in zip(gx.ravel(), gx_exact.ravel())) <= 2.3e-16 * sx
+    sl = max(abs(float(v)) for v in rows)
+    assert max(abs(Fraction(float(a)) - b) for a, b in zip(glam[:T - d], rows)) <= 2.3e-16 * sl
+    assert np.all(glam[T - d:] == 0)
+    _, gsum = multiprec.vjp_mp(w, lam, d, z, gz, per_day=False)
+    assert abs(Fraction(float(gsum)) - sum(rows)) <= 2.3e-16 * max(sl, abs(float(sum(rows)))) * (T - d)
+
+
+@pytest.mark.parametrize("d", [1, 2, 3])
+def test_vjp_mp_agrees_with_fp64_when_well_conditioned(d):
+    """Daily weights and lambda in [1, 100]: the 50-digit VJP equals the dense FP64 oracle's
+    (whose Eqs. 4-5 are pinned by finite differences and the dot-product identity)."""
+    rng = np.random.default_rng(30 + d)
+    T = 80
+    w = (rng.random(T) < 0.7).astype(float)
+    lam = 10.0 ** rng.uniform(0, 2, T)
+    z = rng.normal(size=(T, 3))
+    gz = rng.normal(size=(T, 3))
+    gxm, glm = multiprec.vjp_mp(w, lam, d, z, gz)
+    gxd, gld = dense.vjp_one(w, lam, d, z, gz)
+    assert np.max(np.abs(gxm - gxd)) <= 1e-11 * np.max(np.abs(gxd))
+    assert np.max(np.abs(glm - gld)) <= 1e-11 * np.max(np.abs(gld))
