@@ -350,10 +350,17 @@ int ws_tune_set(int32_t ctas_per_sm, int32_t chunk_days);
  * (WS_LAM_PER_DAY) or one value per series (WS_LAM_SCALAR). FP32.
  * A plan sorts the series by (order, length) into work items of 32 series (one per
  * lane of a warp); a persistent grid pulls items from an atomic counter, each warp
- * running the same two-sweep rotation solve as ws_smooth_batch. ws_plan_create reads
- * offsets and orders back to the host (it synchronises `stream`) and allocates the plan's
- * device tables and checkpoint area (freed by ws_plan_destroy); ws_plan_execute
- * allocates nothing. */
+ * running the same two-sweep rotation solve as ws_smooth_batch (Section 3.1: O(T_i d)
+ * storage per series).
+ * Set-up and call path: ws_plan_create is set-up. It reads offsets and orders back to the
+ * host (it synchronises `stream`), allocates the plan's device tables (item lists,
+ * length-class tables, two error/counter words) and creates the length classes' eight
+ * streams and events; ws_plan_destroy frees them. ws_plan_execute is the call path: it
+ * allocates no device memory and never synchronises (except the autotuner's first run,
+ * which times candidates with events). Its scratch (checkpoints, the length-class tiles
+ * and their tile-kernel workspaces, the refinement state) is the caller's `workspace`,
+ * sized by ws_plan_workspace_size for the same flags. Without WS_PLAN_AUTOTUNE and
+ * WS_PLAN_GRAPH an execute can itself be captured into the caller's CUDA graph. */
 typedef struct ws_ragged {
   int64_t n_series;            /* n >= 0 */
   const int64_t* offsets;      /* device, n + 1 entries, offsets[0] = 0, non-decreasing */
@@ -387,28 +394,43 @@ typedef struct ws_plan_stats {
 #define WS_PLAN_TILES 0x8u     /* ws_plan_execute: series of at least 64 days (one band) are
                                   solved as length-class tiles by the tile kernels: padded
                                   with zero weights to a multiple of 32 days, which leaves
-                                  the solution unchanged; the plan allocates four float
-                                  arrays of the padded size on first use */
+                                  the solution unchanged; the workspace holds four float
+                                  arrays of the padded size and eight tile workspaces */
 #define WS_PLAN_REFINE 0x4u    /* ws_plan_execute: iterative refinement (the paper
                                   fixes no precision): up to three FP32 steps, r = W x - Omega z
                                   with a double-word combination, z += Omega^{-1} r; a series
                                   leaves the steps once its correction is <= 3e-6 max|z| (the
                                   others are regrouped into fresh items for the next step);
-                                  series whose last correction is still > 3e-5 max|z| are
-                                  solved again in double-float arithmetic (hi + lo FP32 pairs,
-                                  about 48 bits). On first use the plan allocates N floats,
-                                  about 30 bytes per series and about 0.76 GB of checkpoints
-                                  at T = 3288. */
+                                  series whose first correction exceeds 1e-4 max|z| (FP32
+                                  too close to its conditioning limit for the corrections to
+                                  measure the error), and series whose last correction is
+                                  still > 3e-5 max|z| or more than half the step before it
+                                  (a slowly contracting step), are solved again in
+                                  double-float arithmetic (hi + lo FP32 pairs,
+                                  about 48 bits). The workspace holds N floats, about 30
+                                  bytes per series and about 0.76 GB of double-float
+                                  checkpoints at T = 3288. */
 
 int ws_plan_create(const ws_ragged* rg, ws_plan** out, void* stream);
 
+/* Bytes of device scratch ws_plan_execute needs with these flags (0 on error): the
+ * per-lane kernel's checkpoints (with WS_PLAN_AUTOTUNE before the autotuner has run, the
+ * largest candidate's), plus the length-class tiles with WS_PLAN_TILES, plus the
+ * refinement state with WS_PLAN_REFINE. Its contents need no initialisation. */
+size_t ws_plan_workspace_size(const ws_plan* plan, uint32_t flags);
+
 /* z = Omega^{-1} W x for every series of the plan (Eq. 3 with each series' own T_i and d).
- * status: optional per-series codes. flags: WS_PLAN_AUTOTUNE, WS_PLAN_GRAPH, WS_PLAN_REFINE. With
- * WS_PLAN_AUTOTUNE the first call times the candidates (running the solve several times
- * on these buffers) and keeps the fastest; with WS_PLAN_GRAPH the launch is captured once
- * and later calls update its arguments and replay it. */
+ * status: optional per-series codes. flags: WS_PLAN_AUTOTUNE, WS_PLAN_GRAPH, WS_PLAN_REFINE,
+ * WS_PLAN_TILES. workspace: device, 256-byte aligned, ws_bytes >=
+ * ws_plan_workspace_size(plan, flags), else WS_EINVAL / WS_ENOMEM_WS before any launch;
+ * it must stay allocated while the call runs (and while ws_plan_info may read the re-solve
+ * count of the last refined execute from it); calls that overlap in time need different
+ * workspaces. With WS_PLAN_AUTOTUNE the first call times the candidates (running the solve
+ * several times on these buffers) and keeps the fastest; with WS_PLAN_GRAPH the launch is
+ * captured once (again when the workspace or configuration changes) and later calls update
+ * its arguments and replay it. */
 int ws_plan_execute(ws_plan* plan, const void* x, const void* w, const void* lam, void* z, uint8_t* status,
-                    uint32_t flags, void* stream);
+                    uint32_t flags, void* workspace, size_t ws_bytes, void* stream);
 
 int ws_plan_info(const ws_plan* plan, ws_plan_stats* out);
 

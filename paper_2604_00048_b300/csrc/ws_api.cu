@@ -157,7 +157,7 @@ static int check_workspace(const ws_problem& pb, void* workspace, size_t ws_byte
 // One tile-kernel mode over every band group of the problem.
 static int run_tile(const ws_problem& P, int mode, const void* rhs, const void* w, const void* lam,
                     const void* zin, const void* g0, void* out, void* out2, void* factor, uint8_t* status,
-                    int accum, int adj_flags, void* workspace, cudaStream_t st) {
+                    int accum, int adj_flags, void* workspace, cudaStream_t st, void* df_base = nullptr) {
   // adj_flags (MODE_ADJ): bit 0 gradient in log lambda, bit 1 output g instead of W g
   // pointer contract of each mode (an inconsistent internal call is an error, never a fault)
   if (rhs == nullptr || w == nullptr || lam == nullptr) return set_error(WS_EINVAL, "tile: missing input");
@@ -221,6 +221,10 @@ static int run_tile(const ws_problem& P, int mode, const void* rhs, const void* 
     a.grad_loglam = adj_flags & 1;
     a.raw_g = (adj_flags >> 1) & 1;
     a.accum = accum;
+    if (df_base != nullptr) {
+      char* slots = nullptr;
+      adj_df_layout(P, df_base, &a.df_mark, &a.df_count, &a.df_list, &slots);
+    }
     rc = launch_tile(P, mode, nb, cfg, a, maps, st);
     if (rc != WS_OK) return rc;
     b0 += nb;
@@ -297,7 +301,8 @@ extern "C" size_t ws_workspace_size(const ws_problem* pb, uint32_t flags) {
   size_t ck = 0;
   if (pb->n_series == 0 || pb->T == 0) return kHeaderBytes;
   if (tile_ckpt_bytes(*pb, ck) != WS_OK) return 0;
-  const size_t extra = (flags & WS_REFINE_ADJOINT) ? 2 * resid_bytes(*pb) : ((flags & WS_REFINE) ? resid_bytes(*pb) : 0);
+  const size_t extra = (flags & WS_REFINE_ADJOINT) ? 2 * resid_bytes(*pb) + adj_df_bytes(*pb)
+                                                  : ((flags & WS_REFINE) ? resid_bytes(*pb) : 0);
   size_t need = kHeaderBytes + ck + extra;
   if (flags & WS_GCV) {  // the grid search's checkpoints, then the final smooth, reuse one region
     int grid = 0, nch = 0;
@@ -657,20 +662,34 @@ extern "C" int ws_solve_adjoint(const ws_problem* pb, const void* factor_or_null
   const bool refine = (flags & WS_REFINE_ADJOINT) != 0;
   const int loglam = ((flags & WS_GRAD_LOGLAM) ? 1 : 0) | ((flags & WS_ADJ_RAW_G) ? 2 : 0);
   size_t ck_bytes = 0;
-  rc = check_workspace(P, workspace, ws_bytes, refine ? 2 * resid_bytes(P) : 0, ck_bytes);
+  const size_t df_bytes = refine ? adj_df_bytes(P) : 0;
+  rc = check_workspace(P, workspace, ws_bytes, refine ? 2 * resid_bytes(P) + df_bytes : 0, ck_bytes);
   if (rc != WS_OK) return rc;
   if (!refine)
     return run_tile(P, MODE_ADJ, gz, w, lam, z, nullptr, gx, glam, nullptr, status, 0, loglam, workspace, st);
   // g0 = Omega^{-1} gz, r = gz - Omega g0 (double-word), then the adjoint pass solves
-  // Omega d = r and applies the epilogue to g = g0 + d.
+  // Omega d = r and applies the epilogue to g = g0 + d. FP32: that pass lists the series
+  // whose step did not settle, and those are solved again in double-float.
   char* base = static_cast<char*>(workspace) + kHeaderBytes + ck_bytes;
   void* g0 = base;
   void* r = base + resid_bytes(P);
+  void* df = df_bytes > 0 ? base + 2 * resid_bytes(P) : nullptr;
+  if (df != nullptr) {  // marks and the list count start at zero
+    unsigned *mark = nullptr, *count = nullptr;
+    int* list = nullptr;
+    char* slots = nullptr;
+    adj_df_layout(P, df, &mark, &count, &list, &slots);
+    if (cudaMemsetAsync(df, 0, reinterpret_cast<char*>(count) + sizeof(unsigned) - static_cast<char*>(df), st) !=
+        cudaSuccess)
+      return set_error(WS_ECUDA, "clearing the re-solve list failed");
+  }
   rc = run_tile(P, MODE_RAW, gz, w, lam, nullptr, nullptr, g0, nullptr, nullptr, nullptr, 0, 0, workspace, st);
   if (rc != WS_OK) return rc;
   rc = launch_residual(P, gz, w, lam, g0, r, 1, static_cast<unsigned*>(workspace), st);
   if (rc != WS_OK) return rc;
-  return run_tile(P, MODE_ADJ, r, w, lam, z, g0, gx, glam, nullptr, status, 1, loglam, workspace, st);
+  rc = run_tile(P, MODE_ADJ, r, w, lam, z, g0, gx, glam, nullptr, status, 1, loglam, workspace, st, df);
+  if (rc != WS_OK || df == nullptr || (gx == nullptr && glam == nullptr)) return rc;
+  return launch_adj_df(P, gz, w, lam, z, gx, glam, loglam, df, st);
 }
 
 extern "C" int ws_tune_set(int32_t ctas_per_sm, int32_t chunk_days) {

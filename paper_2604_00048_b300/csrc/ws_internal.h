@@ -73,6 +73,11 @@ struct TileArgs {
   int grad_loglam;
   int raw_g;              // ADJOINT: out receives g itself instead of W g
   int accum;              // RAW: out += solution (refinement correction)
+  // ADJOINT with accum (refined adjoint, FP32): series whose step did not settle are marked
+  // once (df_mark) and appended to df_list (df_count) for the double-float re-solve; NULL: off
+  unsigned* df_mark;
+  int* df_list;
+  unsigned* df_count;
 };
 
 struct DeviceInfo {
@@ -132,6 +137,13 @@ int launch_wgrad(const ws_problem& pb, const void* x, const void* w, const void*
 int launch_factored(int what, const ws_problem& pb, const void* fac_in, void* fac_out, const void* w,
                     const void* lam, const void* x, void* out, const void* z, const void* gs, void* gx, void* glam,
                     uint8_t* status, int weighted, int loglam, cudaStream_t st);
+// Double-float re-solve of the adjoint for the series the refined FP32 adjoint listed
+// (ws_adjdf.cu): scratch bytes, its layout, and the launch (overwrites gx and glam of the
+// listed series). adj_flags as run_tile's.
+size_t adj_df_bytes(const ws_problem& pb);
+void adj_df_layout(const ws_problem& pb, void* base, unsigned** mark, unsigned** count, int** list, char** slots);
+int launch_adj_df(const ws_problem& pb, const void* gz, const void* w, const void* lam, const void* z, void* gx,
+                  void* glam, int adj_flags, void* base, cudaStream_t st);
 // raw = 0: r = W x - Omega z0; raw = 1: r = x - Omega z0. err: the workspace's device
 // error word (set when a staging wait gives up).
 int launch_residual(const ws_problem& pb, const void* x, const void* w, const void* lam, const void* z0,

@@ -51,16 +51,17 @@ struct RaggedArgs {
   // refinement (plan-owned; NULL without WS_PLAN_REFINE)
   float* resid;           // r = W x - Omega z, same packing as x
   uint8_t* active;        // per item: 1 while some series of the item has not settled
-  uint8_t* conv;          // per series, after the last correction: bit 0 set when it was below
-                          // tau * max|z| (settled), bit 1 when below tau_drop * max|z| (done:
-                          // later steps leave the series out)
+  uint8_t* conv;          // per series, after the last correction: bit 0 settled, bit 1 done
+                          // (later steps leave the series out), bit 2 listed for the
+                          // double-float re-solve by the first step
   float* zmax;            // per series: max |z| of the unrefined solution
+  float* prevc;           // per series: max |correction| of the previous step (0 before the first)
   int32_t* list64;        // series re-solved in double-float
   int* count64;
   double* ck64;           // double-float checkpoints (8 bytes each), kFieldsMax * max_nch64 per thread
   const int8_t* d_of;     // per series order
   int max_nch64;
-  float tau, tau_drop;
+  float tau, tau_drop, tau_cond;
   const uint8_t* item_tiled;  // per item: 1 = its series are solved through the length-class tiles
 };
 
@@ -239,13 +240,27 @@ __device__ void ragged_item(const RaggedArgs& a, int item, float* sm, float* ck,
   }
   if (MODE == MODE_SMOOTH && live && a.zmax != nullptr) a.zmax[sid] = amax;
   if (MODE == MODE_RAW) {
-    // a series has settled when its correction is below tau * max|z| (NaN never settles);
-    // it is done, and leaves the later steps, below tau_drop * max|z|: a correction a little
-    // under tau can still leave an error several times tau when the step contracts slowly
+    // Settle test. The first correction measures the FP32 solve's own error: above
+    // tau_cond * max|z| the series is ill-conditioned for FP32 (eps32 * cond near 1), where
+    // the corrections can shrink quickly towards a point still far from the solution (the
+    // refinement's limit is set by the residual's rounding times cond(Omega)); such a series
+    // leaves the FP32 steps and is listed for the double-float re-solve at once.
+    // Otherwise a series has settled when its correction is below tau * max|z| (NaN never
+    // settles) and the step contracts: the correction at most half the previous one, so the
+    // error left (correction * ratio / (1 - ratio)) is below the correction; the first step
+    // has no ratio and needs tau_drop. A series is done, and leaves the later steps, below
+    // tau_drop * max|z|.
     const float zm = live ? a.zmax[sid] : 0.f;
-    const bool settled = !live || amax <= a.tau * zm;
-    const bool done = !live || amax <= a.tau_drop * zm;
-    if (live) a.conv[sid] = (settled ? 1 : 0) | (done ? 2 : 0);
+    const float prev = live ? a.prevc[sid] : 0.f;
+    const bool small = amax <= a.tau_drop * zm;
+    const bool suspect = live && prev == 0.f && amax > a.tau_cond * zm;
+    const bool done = !live || small || suspect;
+    const bool settled = !live || (!suspect && (small || (amax <= a.tau * zm && amax <= 0.5f * prev)));
+    if (live) {
+      a.prevc[sid] = amax;
+      a.conv[sid] = (settled ? 1 : 0) | (done ? 2 : 0) | (suspect ? 4 : 0);
+      if (suspect) a.list64[atomicAdd(a.count64, 1)] = sid;
+    }
     if (__all_sync(0xffffffffu, done) && lane == 0) a.active[item] = 0;
   }
   if (MODE == MODE_SMOOTH && live && a.status != nullptr) {
@@ -354,7 +369,7 @@ __global__ void __launch_bounds__(256) k_ragged_collect(const RaggedArgs a) {
   const int item = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   if (item >= a.n_items || !a.active[item]) return;
   const int sid = a.order[(size_t)item * 32 + lane];
-  const bool need = sid >= 0 && !(a.conv[sid] & 1);
+  const bool need = sid >= 0 && !(a.conv[sid] & 1) && !(a.conv[sid] & 4);  // bit 2: listed already
   const unsigned m = __ballot_sync(0xffffffffu, need);
   if (m == 0) return;
   int base = 0;
@@ -595,13 +610,17 @@ struct ws_plan {
   int32_t* d_item_t = nullptr;
   int* d_counter = nullptr;
   unsigned* d_err = nullptr;
+  // per-execute scratch: views into the caller's workspace (ws_plan_workspace_size), bound
+  // by each ws_plan_execute; the plan owns only its tables
   float* d_ckpt = nullptr;
-  size_t ckpt_bytes = 0;
-  // refinement state, allocated on the first execute with WS_PLAN_REFINE
+  void* ws_base = nullptr;     // workspace of the last execute
+  uint32_t ws_flags = 0;       // flags it was laid out for
+  // refinement state (WS_PLAN_REFINE)
   float* d_resid = nullptr;    // N floats (one band at a time)
   uint8_t* d_active = nullptr; // n_items
   uint8_t* d_conv = nullptr;   // n_series
   float* d_zmax = nullptr;     // n_series
+  float* d_prevc = nullptr;    // n_series
   int32_t* d_list64 = nullptr; // n_series
   int* d_count64 = nullptr;    // n_bands
   double* d_ck64 = nullptr;
@@ -632,6 +651,7 @@ struct ws_plan {
   cudaEvent_t tev[9] = {};         // fork + one join event per stream
   int graph_rc = 0, graph_warps = 0;
   bool graph_refine = false, graph_tiles = false;
+  void* graph_ws = nullptr;    // workspace the graph was captured with
 };
 
 static size_t ragged_smem(int RC, int warps, int max_d) {
@@ -667,6 +687,7 @@ static int ragged_grid(int RC, int warps, int items, int max_d, int* grid) {
 constexpr int kRefineSteps = 3;     // FP32 refinement steps before the double-float re-solve
 constexpr float kRefineTau = 3e-5f;  // settled: correction <= tau * max|z|
 constexpr float kRefineTauDrop = 3e-6f;  // done (left out of later steps): correction <= tau_drop * max|z|
+constexpr float kRefineTauCond = 1e-4f;  // first correction above tau_cond * max|z|: double-float at once
 constexpr int kHPBlocksPerSM = 4;    // double-float re-solve: 4 x 128 threads per SM (128 registers each)
 
 static void fill_refine_args(const ws_plan* pl, RaggedArgs& a) {
@@ -674,6 +695,7 @@ static void fill_refine_args(const ws_plan* pl, RaggedArgs& a) {
   a.active = pl->d_active;
   a.conv = pl->d_conv;
   a.zmax = pl->d_zmax;
+  a.prevc = pl->d_prevc;
   a.list64 = pl->d_list64;
   a.count64 = pl->d_count64 + a.band;
   a.ck64 = pl->d_ck64;
@@ -681,6 +703,7 @@ static void fill_refine_args(const ws_plan* pl, RaggedArgs& a) {
   a.max_nch64 = pl->max_nch64;
   a.tau = kRefineTau;
   a.tau_drop = kRefineTauDrop;
+  a.tau_cond = kRefineTauCond;
 }
 
 // The items a launch runs: the plan's own, or a regrouped set of a refinement step.
@@ -761,7 +784,10 @@ static int ragged_refine(ws_plan* pl, const void* x, const void* w, const void* 
   a.lam = (const float*)lam;
   a.z = (float*)z;
   fill_refine_args(pl, a);
-  if (cudaMemsetAsync(pl->d_active, 1, pl->n_items, st) != cudaSuccess) return set_error(WS_ECUDA, "ragged: memset");
+  if (cudaMemsetAsync(pl->d_active, 1, pl->n_items, st) != cudaSuccess ||
+      cudaMemsetAsync(pl->d_prevc, 0, sizeof(float) * pl->rg.n_series, st) != cudaSuccess ||
+      cudaMemsetAsync(a.count64, 0, sizeof(int), st) != cudaSuccess)
+    return set_error(WS_ECUDA, "ragged: memset");
   ItemSet cur{pl->d_order, pl->d_item_d, pl->d_item_t, pl->d_active, pl->n_items};
   const int4 reg = make_int4(pl->creg[0], pl->creg[1], pl->creg[2], pl->creg[3]);
   const int nci = pl->creg[4] / 32;
@@ -798,7 +824,6 @@ static int ragged_refine(ws_plan* pl, const void* x, const void* w, const void* 
   a.active = cur.active;
   a.n_items = cur.n_items;
   const int gi = (cur.n_items + 7) / 8;
-  if (cudaMemsetAsync(a.count64, 0, sizeof(int), st) != cudaSuccess) return set_error(WS_ECUDA, "ragged: memset");
   k_ragged_collect<<<gi, 256, 0, st>>>(a);
   k_ragged64<<<pl->grid64, 128, 0, st>>>(a);
   cudaError_t e = cudaGetLastError();
@@ -863,8 +888,8 @@ static int ragged_tiles(ws_plan* pl, const void* x, const void* w, const void* l
   return WS_OK;
 }
 
-static int tiles_alloc(ws_plan* pl) {
-  if (pl->d_tiles != nullptr || pl->classes.empty()) return WS_OK;
+// Size of one length class's tile-kernel workspace (the largest class's, 256-byte multiple).
+static int tile_ws_size(const ws_plan* pl, size_t* out) {
   size_t wsb = 0;
   for (const LenClass& c : pl->classes) {
     ws_problem P;
@@ -880,56 +905,109 @@ static int tiles_alloc(ws_plan* pl) {
     if (b == 0) return WS_ECUDA;
     wsb = std::max(wsb, b);
   }
-  wsb = (wsb + 255) & ~(size_t)255;
-  bool ok = cudaMalloc(&pl->d_tiles, 4 * pl->tile_elems * sizeof(float)) == cudaSuccess &&
-            cudaMalloc(&pl->d_tile_st, std::max<size_t>(1, pl->tile_st_bytes)) == cudaSuccess &&
-            cudaMalloc(&pl->d_tile_ws, wsb * kTileStreams) == cudaSuccess;
-  for (int k = 0; ok && k < kTileStreams; ++k)
-    ok = cudaStreamCreateWithFlags(&pl->tstream[k], cudaStreamNonBlocking) == cudaSuccess;
-  for (int k = 0; ok && k <= kTileStreams; ++k) ok = cudaEventCreateWithFlags(&pl->tev[k], cudaEventDisableTiming) == cudaSuccess;
-  if (!ok) return set_error(WS_ECUDA, "plan: length-class tile allocation (%zu elements)", pl->tile_elems);
-  cudaMemset(pl->d_tile_ws, 0, wsb * kTileStreams);  // the tile kernels' error words
-  pl->tile_ws_bytes = wsb;
+  *out = (wsb + 255) & ~(size_t)255;
   return WS_OK;
 }
 
-static int refine_alloc(ws_plan* pl) {
-  if (pl->d_resid != nullptr) return WS_OK;
-  const size_t n = (size_t)std::max<int64_t>(1, pl->rg.n_series), ni = (size_t)std::max(1, pl->n_items);
-  DeviceInfo di;
-  int rc = device_info(di);
+static size_t r256(size_t v) { return (v + 255) & ~(size_t)255; }
+
+// Checkpoint bytes of the per-lane kernel in configuration (RC, warps).
+static int ckpt_need(const ws_plan* pl, int RC, int warps, size_t* out) {
+  int grid = 0;
+  int rc = ragged_grid(RC, warps, pl->n_items, pl->max_d, &grid);
   if (rc != WS_OK) return rc;
-  pl->grid64 = di.sm_count * kHPBlocksPerSM;
-  const size_t ck = (size_t)pl->grid64 * 128 * std::max(1, pl->max_nch64) * kFieldsMax * sizeof(double);
-  const bool ok = cudaMalloc(&pl->d_resid, sizeof(float) * (size_t)std::max<int64_t>(1, pl->N)) == cudaSuccess &&
-                  cudaMalloc(&pl->d_active, ni) == cudaSuccess && cudaMalloc(&pl->d_conv, n) == cudaSuccess &&
-                  cudaMalloc(&pl->d_zmax, 4 * n) == cudaSuccess && cudaMalloc(&pl->d_list64, 4 * n) == cudaSuccess &&
-                  cudaMalloc(&pl->d_count64, sizeof(int) * pl->rg.n_bands) == cudaSuccess &&
-                  cudaMalloc(&pl->d_ck64, ck) == cudaSuccess;
-  const size_t cs = (size_t)std::max(32, pl->creg[4]), cni = cs / 32;
-  const bool okc = ok && cudaMalloc(&pl->d_corder, 2 * cs * 4) == cudaSuccess &&
-                   cudaMalloc(&pl->d_citem_d, 2 * cni) == cudaSuccess &&
-                   cudaMalloc(&pl->d_citem_t, 2 * cni * 4) == cudaSuccess &&
-                   cudaMalloc(&pl->d_cactive, 2 * cni) == cudaSuccess &&
-                   cudaMalloc(&pl->d_ccount, 2 * 4 * sizeof(int)) == cudaSuccess;
-  if (!okc) return set_error(WS_ECUDA, "plan: refinement allocation");
-  cudaMemset(pl->d_count64, 0, sizeof(int) * pl->rg.n_bands);
+  *out = (size_t)grid * warps * ((pl->max_t + RC - 1) / RC) * kFieldsMax * 32 * 4;
   return WS_OK;
+}
+
+static const int kCands[][2] = {{8, 8}, {8, 16}, {16, 4}, {16, 6}, {16, 8}, {16, 12}, {16, 16}, {32, 4}, {32, 8}};
+constexpr int kNCands = sizeof(kCands) / sizeof(kCands[0]);
+
+// Workspace layout of one execute: checkpoints (the largest candidate's when the autotuner
+// is still to run), then the length-class tiles, then the refinement state.
+struct PlanWs {
+  size_t ckpt = 0, tiles = 0, tile_st = 0, tile_ws = 0, refine = 0, total = 0;
+  size_t resid = 0, active = 0, conv = 0, zmax = 0, prevc = 0, list64 = 0, count64 = 0, ck64 = 0;
+  size_t corder = 0, citem_d = 0, citem_t = 0, cactive = 0, ccount = 0;
+};
+
+static int plan_ws(const ws_plan* pl, uint32_t flags, PlanWs* L) {
+  *L = PlanWs();
+  size_t off = 0;
+  size_t ck = 0;
+  int rc = ckpt_need(pl, pl->RC, pl->warps, &ck);
+  if (rc != WS_OK) return rc;
+  if ((flags & WS_PLAN_AUTOTUNE) && !pl->tuned)
+    for (int c = 0; c < kNCands; ++c) {
+      size_t q = 0;
+      rc = ckpt_need(pl, kCands[c][0], kCands[c][1], &q);
+      if (rc == WS_EUNSUPPORTED) continue;
+      if (rc != WS_OK) return rc;
+      ck = std::max(ck, q);
+    }
+  L->ckpt = off;
+  off += r256(ck);
+  const bool tiles = (flags & WS_PLAN_TILES) && pl->rg.n_bands == 1 && !pl->classes.empty();
+  if (tiles) {
+    L->tiles = off;
+    off += r256(4 * pl->tile_elems * sizeof(float));
+    L->tile_st = off;
+    off += r256(std::max<size_t>(1, pl->tile_st_bytes));
+    L->tile_ws = off;
+    off += pl->tile_ws_bytes * kTileStreams;
+  }
+  if (flags & WS_PLAN_REFINE) {
+    const size_t n = (size_t)std::max<int64_t>(1, pl->rg.n_series), ni = (size_t)std::max(1, pl->n_items);
+    const size_t cs = (size_t)std::max(32, pl->creg[4]), cni = cs / 32;
+    L->refine = off;
+    L->resid = off;   off += r256(sizeof(float) * (size_t)std::max<int64_t>(1, pl->N));
+    L->active = off;  off += r256(ni);
+    L->conv = off;    off += r256(n);
+    L->zmax = off;    off += r256(4 * n);
+    L->prevc = off;   off += r256(4 * n);
+    L->list64 = off;  off += r256(4 * n);
+    L->count64 = off; off += r256(sizeof(int) * pl->rg.n_bands);
+    L->ck64 = off;    off += r256((size_t)pl->grid64 * 128 * std::max(1, pl->max_nch64) * kFieldsMax * sizeof(double));
+    L->corder = off;  off += r256(2 * cs * 4);
+    L->citem_d = off; off += r256(2 * cni);
+    L->citem_t = off; off += r256(2 * cni * 4);
+    L->cactive = off; off += r256(2 * cni);
+    L->ccount = off;  off += r256(2 * 4 * sizeof(int));
+  }
+  L->total = std::max<size_t>(off, 256);
+  return WS_OK;
+}
+
+// Point the plan's scratch views into `ws` laid out for `flags`.
+static void bind_ws(ws_plan* pl, uint32_t flags, const PlanWs& L, void* ws) {
+  char* b = static_cast<char*>(ws);
+  pl->d_ckpt = reinterpret_cast<float*>(b + L.ckpt);
+  const bool tiles = (flags & WS_PLAN_TILES) && pl->rg.n_bands == 1 && !pl->classes.empty();
+  pl->d_tiles = tiles ? reinterpret_cast<float*>(b + L.tiles) : nullptr;
+  pl->d_tile_st = tiles ? reinterpret_cast<uint8_t*>(b + L.tile_st) : nullptr;
+  pl->d_tile_ws = tiles ? static_cast<void*>(b + L.tile_ws) : nullptr;
+  const bool refine = (flags & WS_PLAN_REFINE) != 0;
+  pl->d_resid = refine ? reinterpret_cast<float*>(b + L.resid) : nullptr;
+  pl->d_active = refine ? reinterpret_cast<uint8_t*>(b + L.active) : nullptr;
+  pl->d_conv = refine ? reinterpret_cast<uint8_t*>(b + L.conv) : nullptr;
+  pl->d_zmax = refine ? reinterpret_cast<float*>(b + L.zmax) : nullptr;
+  pl->d_prevc = refine ? reinterpret_cast<float*>(b + L.prevc) : nullptr;
+  pl->d_list64 = refine ? reinterpret_cast<int32_t*>(b + L.list64) : nullptr;
+  pl->d_count64 = refine ? reinterpret_cast<int*>(b + L.count64) : nullptr;
+  pl->d_ck64 = refine ? reinterpret_cast<double*>(b + L.ck64) : nullptr;
+  pl->d_corder = refine ? reinterpret_cast<int32_t*>(b + L.corder) : nullptr;
+  pl->d_citem_d = refine ? reinterpret_cast<int8_t*>(b + L.citem_d) : nullptr;
+  pl->d_citem_t = refine ? reinterpret_cast<int32_t*>(b + L.citem_t) : nullptr;
+  pl->d_cactive = refine ? reinterpret_cast<uint8_t*>(b + L.cactive) : nullptr;
+  pl->d_ccount = refine ? reinterpret_cast<int*>(b + L.ccount) : nullptr;
+  pl->ws_base = ws;
+  pl->ws_flags = flags;
 }
 
 static int ragged_config(ws_plan* pl, int RC, int warps) {
   pl->RC = RC;
   pl->warps = warps;
-  int rc = ragged_grid(RC, warps, pl->n_items, pl->max_d, &pl->grid);
-  if (rc != WS_OK) return rc;
-  const size_t need = (size_t)pl->grid * warps * ((pl->max_t + RC - 1) / RC) * kFieldsMax * 32 * 4;
-  if (need > pl->ckpt_bytes) {
-    if (pl->d_ckpt) cudaFree(pl->d_ckpt);
-    pl->d_ckpt = nullptr;
-    if (cudaMalloc(&pl->d_ckpt, need) != cudaSuccess) return set_error(WS_ECUDA, "ragged: checkpoint allocation");
-    pl->ckpt_bytes = need;
-  }
-  return WS_OK;
+  return ragged_grid(RC, warps, pl->n_items, pl->max_d, &pl->grid);
 }
 
 extern "C" int ws_plan_create(const ws_ragged* rg, ws_plan** out, void* stream) {
@@ -1069,6 +1147,20 @@ extern "C" int ws_plan_create(const ws_ragged* rg, ws_plan** out, void* stream) 
   }
   cudaMemset(pl->d_err, 0, 4);
   int rc = ragged_config(pl, 16, 8);
+  DeviceInfo di;
+  if (rc == WS_OK) rc = device_info(di);
+  if (rc == WS_OK) {
+    pl->grid64 = di.sm_count * kHPBlocksPerSM;
+    if (!pl->classes.empty()) {  // the length classes' streams and fork/join events
+      rc = tile_ws_size(pl, &pl->tile_ws_bytes);
+      bool ok = rc == WS_OK;
+      for (int k = 0; ok && k < kTileStreams; ++k)
+        ok = cudaStreamCreateWithFlags(&pl->tstream[k], cudaStreamNonBlocking) == cudaSuccess;
+      for (int k = 0; ok && k <= kTileStreams; ++k)
+        ok = cudaEventCreateWithFlags(&pl->tev[k], cudaEventDisableTiming) == cudaSuccess;
+      if (!ok && rc == WS_OK) rc = set_error(WS_ECUDA, "plan: length-class streams");
+    }
+  }
   if (rc != WS_OK) {
     ws_plan_destroy(pl);
     return rc;
@@ -1084,14 +1176,14 @@ static int ragged_tiles(ws_plan* pl, const void* x, const void* w, const void* l
 // fastest; with try_tiles, time the length-class tiles (short series per lane) against it.
 static int ragged_autotune(ws_plan* pl, const void* x, const void* w, const void* lam, void* z, bool try_tiles,
                            cudaStream_t st) {
-  const int cands[][2] = {{8, 8}, {8, 16}, {16, 4}, {16, 6}, {16, 8}, {16, 12}, {16, 16}, {32, 4}, {32, 8}};
-  constexpr int kCands = sizeof(cands) / sizeof(cands[0]);
+  const auto& cands = kCands;
+  constexpr int nc = kNCands;
   float best = 1e30f;
   int bi = -1;
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
-  for (int c = 0; c < kCands; ++c) {
+  for (int c = 0; c < nc; ++c) {
     int rc = ragged_config(pl, cands[c][0], cands[c][1]);
     if (rc == WS_EUNSUPPORTED) continue;  // more shared memory than a CTA may have
     if (rc != WS_OK) return rc;
@@ -1129,8 +1221,18 @@ static int ragged_autotune(ws_plan* pl, const void* x, const void* w, const void
   return WS_OK;
 }
 
+extern "C" size_t ws_plan_workspace_size(const ws_plan* pl, uint32_t flags) {
+  if (pl == nullptr) {
+    set_error(WS_EINVAL, "plan is NULL");
+    return 0;
+  }
+  PlanWs L;
+  if (plan_ws(pl, flags, &L) != WS_OK) return 0;
+  return L.total;
+}
+
 extern "C" int ws_plan_execute(ws_plan* pl, const void* x, const void* w, const void* lam, void* z, uint8_t* status,
-                               uint32_t flags, void* stream) {
+                               uint32_t flags, void* workspace, size_t ws_bytes, void* stream) {
   if (pl == nullptr) return set_error(WS_EINVAL, "plan is NULL");
   if (flags & ~(WS_PLAN_AUTOTUNE | WS_PLAN_GRAPH | WS_PLAN_REFINE | WS_PLAN_TILES))
     return set_error(WS_EINVAL, "unknown flags 0x%x", flags);
@@ -1138,8 +1240,12 @@ extern "C" int ws_plan_execute(ws_plan* pl, const void* x, const void* w, const 
   const bool tiles_req = (flags & WS_PLAN_TILES) != 0 && pl->rg.n_bands == 1 && !pl->classes.empty();
   if (pl->n_items == 0) return WS_OK;
   int rc;
-  if (refine && (rc = refine_alloc(pl)) != WS_OK) return rc;
-  if (tiles_req && (rc = tiles_alloc(pl)) != WS_OK) return rc;
+  PlanWs L;
+  if ((rc = plan_ws(pl, flags, &L)) != WS_OK) return rc;
+  if (workspace == nullptr || (reinterpret_cast<uintptr_t>(workspace) & 255u) != 0)
+    return set_error(WS_EINVAL, "workspace must be non-NULL and 256-byte aligned");
+  if (ws_bytes < L.total) return set_error(WS_ENOMEM_WS, "workspace too small: %zu < %zu", ws_bytes, L.total);
+  bind_ws(pl, flags, L, workspace);
   // with no days at all (every series empty) only the status codes are written
   if (pl->N > 0 && (!x || !w || !z)) return set_error(WS_EINVAL, "x, w and z must be non-NULL");
   if (!lam && (pl->N > 0 || pl->rg.lam_mode == WS_LAM_SCALAR)) return set_error(WS_EINVAL, "lam must be non-NULL");
@@ -1147,6 +1253,11 @@ extern "C" int ws_plan_execute(ws_plan* pl, const void* x, const void* w, const 
   if ((flags & WS_PLAN_AUTOTUNE) && !pl->tuned && (rc = ragged_autotune(pl, x, w, lam, z, tiles_req, st)) != WS_OK)
     return rc;
   const bool tiles = tiles_req && pl->tiles_win;
+  if (tiles)
+    for (int k = 0; k < kTileStreams; ++k)
+      if (cudaMemsetAsync(static_cast<char*>(pl->d_tile_ws) + (size_t)k * pl->tile_ws_bytes, 0, kHeaderBytes, st) !=
+          cudaSuccess)
+        return set_error(WS_ECUDA, "ragged: memset");
   if (!(flags & WS_PLAN_GRAPH) || pl->rg.n_bands > 1) {
     for (int b = 0; b < pl->rg.n_bands; ++b) {
       if (tiles && refine && cudaMemsetAsync(pl->d_zmax, 0, sizeof(float) * pl->rg.n_series, st) != cudaSuccess)
@@ -1158,8 +1269,10 @@ extern "C" int ws_plan_execute(ws_plan* pl, const void* x, const void* w, const 
     return WS_OK;
   }
   // CUDA graph: captured once per configuration, kernel arguments updated on each replay
+  // (re-captured when the configuration or the workspace changes: the length classes' tile
+  // kernels take tensor maps of workspace arrays)
   if (pl->exec == nullptr || pl->graph_rc != pl->RC || pl->graph_warps != pl->warps || pl->graph_refine != refine ||
-      pl->graph_tiles != tiles) {
+      pl->graph_tiles != tiles || pl->graph_ws != workspace) {
     if (pl->exec) cudaGraphExecDestroy(pl->exec);
     if (pl->graph) cudaGraphDestroy(pl->graph);
     pl->exec = nullptr;
@@ -1189,6 +1302,7 @@ extern "C" int ws_plan_execute(ws_plan* pl, const void* x, const void* w, const 
     pl->graph_warps = pl->warps;
     pl->graph_refine = refine;
     pl->graph_tiles = tiles;
+    pl->graph_ws = workspace;
     size_t nn = 0;
     cudaGraphGetNodes(g, nullptr, &nn);
     std::vector<cudaGraphNode_t> nodes(nn);
@@ -1201,8 +1315,8 @@ extern "C" int ws_plan_execute(ws_plan* pl, const void* x, const void* w, const 
     }
   } else {
     // new buffers: the ragged kernels take RaggedArgs first (only its user buffers change; the
-    // other parameters are kept); the tile kernels of the length classes read plan-owned
-    // arrays only and are left as captured
+    // other parameters are kept); the tile kernels of the length classes read workspace
+    // arrays only (the same workspace) and are left as captured
     for (auto nd : pl->knodes) {
       cudaKernelNodeParams kp;
       if (cudaGraphKernelNodeGetParams(nd, &kp) != cudaSuccess) return set_error(WS_ECUDA, "graph params");
@@ -1258,28 +1372,12 @@ extern "C" void ws_plan_destroy(ws_plan* pl) {
   cudaFree(pl->d_item_t);
   cudaFree(pl->d_class_sid);
   cudaFree(pl->d_item_tiled);
-  cudaFree(pl->d_tiles);
-  cudaFree(pl->d_tile_st);
-  cudaFree(pl->d_tile_ws);
   for (int k = 0; k < kTileStreams; ++k)
     if (pl->tstream[k]) cudaStreamDestroy(pl->tstream[k]);
   for (int k = 0; k <= kTileStreams; ++k)
     if (pl->tev[k]) cudaEventDestroy(pl->tev[k]);
   cudaFree(pl->d_counter);
   cudaFree(pl->d_err);
-  cudaFree(pl->d_ckpt);
-  cudaFree(pl->d_resid);
-  cudaFree(pl->d_active);
-  cudaFree(pl->d_conv);
-  cudaFree(pl->d_corder);
-  cudaFree(pl->d_citem_d);
-  cudaFree(pl->d_citem_t);
-  cudaFree(pl->d_cactive);
-  cudaFree(pl->d_ccount);
-  cudaFree(pl->d_zmax);
-  cudaFree(pl->d_list64);
-  cudaFree(pl->d_count64);
-  cudaFree(pl->d_ck64);
   cudaFree(pl->d_dof);
   delete pl;
 }

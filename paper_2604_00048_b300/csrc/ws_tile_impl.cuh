@@ -295,6 +295,9 @@ __global__ void __launch_bounds__(kNP* S, S > 1 ? 2 : 4) k_tile(const __grid_con
     }
     F glam_sum = F(0);  // ADJ with scalar lambda
     F nanacc = F(0);    // becomes NaN if any output is not finite
+    // ADJ with accumulation (refinement correction): largest |correction|, |g| and |D^d g|
+    // of this thread's bands, for the settle test of the double-float re-solve
+    F dmx = F(0), gmx = F(0), dgmx = F(0);
     for (int c = a.nch - 1; c >= 0; --c) {
       const int st = c & 1;
       if (c < a.nch - 2) {
@@ -380,6 +383,10 @@ __global__ void __launch_bounds__(kNP* S, S > 1 ? 2 : 4) k_tile(const __grid_con
               F pg = gn[j], pz = zt[j][0];   // level q-1 at day t+1 (q = 1: the values)
               zt[j][0] = zv;
               gn[j] = out;
+              if (a.accum) {
+                dmx = fmax(dmx, fabs(acc));
+                gmx = fmax(gmx, fabs(out));
+              }
 #pragma unroll
               for (int q = 1; q <= D; ++q) {
                 const F ng = pg - cg, nz = pz - cz;  // Delta^q at day t
@@ -393,6 +400,7 @@ __global__ void __launch_bounds__(kNP* S, S > 1 ? 2 : 4) k_tile(const __grid_con
                 cz = nz;
               }
               dl = fma(cg, cz, dl);
+              if (a.accum && i < T - D) dgmx = fmax(dgmx, fabs(cg));
               if (!a.raw_g) out = wk * out;
             }
             nanacc = fma(out, F(0), nanacc);
@@ -444,11 +452,24 @@ __global__ void __launch_bounds__(kNP* S, S > 1 ? 2 : 4) k_tile(const __grid_con
     }
     // per-series status; the band halves combine their non-finite flags
     bool nonfin = !(nanacc == F(0));
-    if (S > 1) {
-      if (h == 1) nflag[pl] = nonfin ? 1u : 0u;
-      __syncthreads();
-      if (h == 0) nonfin = nonfin || nflag[pl] != 0u;
+    // settle test of the refined adjoint: the error left after the step, |delta|^2 / |g|
+    // (the step squares a contracting relative error) plus g's own rounding, differenced
+    // d times (at most 2^d), against 1e-4 of |D^d g|
+    bool unsettled = false;
+    if (MODE == MODE_ADJ && a.df_list != nullptr && gmx > F(0)) {
+      const F e1 = dmx * (dmx / gmx) + F(1.2e-7) * gmx;
+      unsettled = F(1 << D) * e1 > F(1e-4) * dgmx;
     }
+    if (S > 1) {
+      if (h == 1) nflag[pl] = (nonfin ? 1u : 0u) | (unsettled ? 2u : 0u);
+      __syncthreads();
+      if (h == 0) {
+        nonfin = nonfin || (nflag[pl] & 1u) != 0u;
+        unsettled = unsettled || (nflag[pl] & 2u) != 0u;
+      }
+    }
+    if (MODE == MODE_ADJ && unsettled && okser && act && h == 0 && atomicExch(a.df_mark + p, 1u) == 0u)
+      a.df_list[atomicAdd(a.df_count, 1u)] = p;
     if (MODE == MODE_ADJ && gout2 != nullptr && a.lam_scalar && act && h == 0)
       gout2[p] = a.b0 == 0 ? glam_sum : gout2[p] + glam_sum;
     if (act && a.status != nullptr && h == 0) {

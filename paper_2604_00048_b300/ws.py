@@ -106,7 +106,10 @@ PLAN_AUTOTUNE, PLAN_GRAPH, PLAN_REFINE, PLAN_TILES = 0x1, 0x2, 0x4, 0x8
 _lib.ws_plan_create.restype = ctypes.c_int
 _lib.ws_plan_create.argtypes = [ctypes.POINTER(Ragged), ctypes.POINTER(ctypes.c_void_p), ctypes.c_void_p]
 _lib.ws_plan_execute.restype = ctypes.c_int
-_lib.ws_plan_execute.argtypes = [ctypes.c_void_p] + [ctypes.c_void_p] * 5 + [ctypes.c_uint32, ctypes.c_void_p]
+_lib.ws_plan_execute.argtypes = [ctypes.c_void_p] + [ctypes.c_void_p] * 5 + [ctypes.c_uint32, ctypes.c_void_p,
+                                                                               _sz, ctypes.c_void_p]
+_lib.ws_plan_workspace_size.restype = _sz
+_lib.ws_plan_workspace_size.argtypes = [ctypes.c_void_p, ctypes.c_uint32]
 _lib.ws_plan_info.restype = ctypes.c_int
 _lib.ws_plan_info.argtypes = [ctypes.c_void_p, ctypes.POINTER(PlanStats)]
 _lib.ws_plan_destroy.restype = None
@@ -543,17 +546,45 @@ class RaggedPlan:
         h = ctypes.c_void_p()
         _check(_lib.ws_plan_create(ctypes.byref(self._rg), ctypes.byref(h), _stream_ptr(stream)))
         self._h = h
+        self._ws = None
+
+    @staticmethod
+    def _flags(autotune=False, graph=False, refine=False, tiles=False) -> int:
+        return ((PLAN_AUTOTUNE if autotune else 0) | (PLAN_GRAPH if graph else 0) | (PLAN_REFINE if refine else 0)
+                | (PLAN_TILES if tiles else 0))
+
+    def workspace_size(self, autotune=False, graph=False, refine=False, tiles=False) -> int:
+        need = int(_lib.ws_plan_workspace_size(self._h, self._flags(autotune, graph, refine, tiles)))
+        if need == 0:
+            raise WSError(WS_EINVAL, last_error())
+        return need
 
     def execute(self, x, w, lam, z=None, status=None, autotune: bool = False, graph: bool = False,
-                refine: bool = False, tiles: bool = False, stream=None):
+                refine: bool = False, tiles: bool = False, stream=None, workspace_buf=None):
+        """workspace_buf: a uint8 CUDA tensor of at least workspace_size(...) bytes the caller
+        owns (e.g. to capture the call into its own CUDA graph); else the plan keeps one,
+        grown on demand (the library itself never allocates on this call)."""
         if z is None:
             z = torch.empty_like(x)
         if status is None:
             status = torch.empty(self.n, dtype=torch.uint8, device=x.device)
-        flags = ((PLAN_AUTOTUNE if autotune else 0) | (PLAN_GRAPH if graph else 0) | (PLAN_REFINE if refine else 0)
-                 | (PLAN_TILES if tiles else 0))
+        flags = self._flags(autotune, graph, refine, tiles)
+        need = int(_lib.ws_plan_workspace_size(self._h, flags))
+        if need == 0:
+            raise WSError(WS_EINVAL, last_error())
+        if workspace_buf is not None:
+            if workspace_buf.numel() < need or workspace_buf.dtype != torch.uint8 or not workspace_buf.is_cuda:
+                raise ValueError(f"workspace needs {need} bytes (uint8, CUDA)")
+            wsb = workspace_buf
+        else:
+            if self._ws is None or self._ws.numel() < need:
+                if self._ws is not None:
+                    torch.cuda.synchronize(x.device)  # earlier calls may still use the old scratch
+                self._ws = None
+                self._ws = torch.empty(need, dtype=torch.uint8, device=x.device)
+            wsb = self._ws
         _check(_lib.ws_plan_execute(self._h, _ptr(x), _ptr(w), _ptr(lam), _ptr(z), _ptr(status), flags,
-                                    _stream_ptr(stream)))
+                                    _ptr(wsb), wsb.numel(), _stream_ptr(stream)))
         return z, status
 
     def info(self) -> dict:

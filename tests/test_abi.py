@@ -107,7 +107,8 @@ def test_noalloc_and_plan_argument_checks(ws):
     assert lib.ws_plan_create(ctypes.byref(rg), ctypes.byref(h), None) == ws.WS_EINVAL  # offsets NULL
     rg64 = ws.Ragged(4, 256, None, 2, 1, ws.F64, ws.LAM_PER_DAY)  # rejected before the offsets are read
     assert lib.ws_plan_create(ctypes.byref(rg64), ctypes.byref(h), None) == ws.WS_EUNSUPPORTED
-    assert lib.ws_plan_execute(None, None, None, None, None, None, 0, None) == ws.WS_EINVAL
+    assert lib.ws_plan_execute(None, None, None, None, None, None, 0, None, 0, None) == ws.WS_EINVAL
+    assert lib.ws_plan_workspace_size(None, 0) == 0
     assert lib.ws_plan_info(None, None) == ws.WS_EINVAL
 
 

@@ -203,3 +203,38 @@ def test_ragged_tiles_sparse_refined(ws):
     z, st = plan.execute(out["x"], out["w"], out["lam"], refine=True, graph=True, tiles=True)
     ws.sync_status()
     _check(out, z, st, range(400), tol=1e-4, mp_orders=(3,))
+
+
+def test_ragged_execute_captured_in_callers_graph(ws):
+    """The call path allocates nothing and never synchronises: ws_plan_execute with
+    WS_PLAN_TILES | WS_PLAN_REFINE on a caller-owned workspace is captured into the caller's
+    CUDA graph (torch's capture, which rejects allocation and synchronising calls), and a
+    replay reproduces the eager result exactly (each series' arithmetic does not depend on
+    which item or launch order runs it)."""
+    rc = synth.RECIPES["ragged"]
+    out = synth.generate_ragged(rc, 700, device="cuda", t_range=(40, 900))
+    plan = ws.RaggedPlan(out["offsets"], out["order"])
+    need = plan.workspace_size(refine=True, tiles=True)
+    assert need > 0 and need >= plan.workspace_size(tiles=True) and need >= plan.workspace_size(refine=True)
+    wsb = torch.zeros(need, dtype=torch.uint8, device="cuda")
+    z0, st0 = plan.execute(out["x"], out["w"], out["lam"], refine=True, tiles=True, workspace_buf=wsb)
+    torch.cuda.synchronize()
+    z = torch.full_like(out["x"], float("nan"))
+    st = torch.full_like(st0, 255)
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(s):
+        # thread-local capture: this thread's allocating or synchronising calls fail it
+        with torch.cuda.graph(g, stream=s, capture_error_mode="thread_local"):
+            plan.execute(out["x"], out["w"], out["lam"], z=z, status=st, refine=True, tiles=True,
+                         workspace_buf=wsb, stream=s)
+    g.replay()
+    torch.cuda.synchronize()
+    assert torch.equal(z, z0) and torch.equal(st, st0)
+    _check(out, z, st, range(700), tol=1e-4, mp_orders=(3,))
+    # a workspace one byte short is rejected before any launch
+    flags = ws.PLAN_REFINE | ws.PLAN_TILES
+    rc = ws.lib().ws_plan_execute(plan._h, out["x"].data_ptr(), out["w"].data_ptr(), out["lam"].data_ptr(),
+                                  z.data_ptr(), st.data_ptr(), flags, wsb.data_ptr(), need - 1, None)
+    assert rc == ws.WS_ENOMEM_WS
