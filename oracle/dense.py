@@ -251,6 +251,23 @@ def vjp_tile(w, lam, d: int, z, gz, log_lambda: bool = False):
     return gx, glam
 
 
+def masked_mse(z, target, mask, scale: float):
+    """The training loss of Section 4.3 (mean squared error of z against held-out
+    observations), as a weighted sum: per series p, L_p = scale/2 * sum_{t,b} m_tp (z_tbp -
+    target_tbp)^2 with day weights m (1 on held-out days, 0 elsewhere; None: all ones), and
+    its gradient dL/dz = scale * m * (z - target). With scale = 2 / (number of held-out
+    entries) the sum of L_p over the series is their mean squared error. Days with m = 0
+    contribute nothing whatever the target holds there. Returns (L [P], gz [T, B, P])."""
+    z = np.asarray(z, dtype=np.float64)
+    target = np.asarray(target, dtype=np.float64)
+    T, B, P = z.shape
+    m = np.ones((T, P)) if mask is None else np.asarray(mask, dtype=np.float64)
+    e = np.where(m[:, None, :] > 0, z - np.nan_to_num(target), 0.0)
+    gz = scale * m[:, None, :] * e
+    loss = 0.5 * scale * np.sum(m[:, None, :] * e * e, axis=(0, 1))
+    return loss, gz
+
+
 def hat_trace(w, lam, d: int, t=None) -> float:
     """tr H with H = Omega^{-1} W: sum_t w_t (Omega^{-1})_tt, from the dense inverse (t: sample
     times for the uneven-spacing operator, None for the daily grid)."""

@@ -481,3 +481,29 @@ def test_dates_hat_trace_limits_and_gcv(rng, d):
     a = dense.gcv_one(x, w, grid, d)
     b = dense.gcv_one(x, w, grid, d, t=np.arange(T, dtype=float))
     assert a[0] == b[0] and np.allclose(a[1], b[1], rtol=1e-9)
+
+
+def test_masked_mse_is_the_held_out_mean_and_its_gradient():
+    """Section 4.3's loss: with scale = 2 / n_held the summed loss equals the mean squared
+    error over the held-out entries (computed by boolean indexing), masked days are inert
+    even where the target is NaN, and gz matches central differences of the loss."""
+    rng = np.random.default_rng(11)
+    T, B, P = 17, 3, 5
+    z = rng.normal(size=(T, B, P))
+    tgt = rng.normal(size=(T, B, P))
+    m = (rng.random((T, P)) < 0.3).astype(float)
+    tgt[:, :, :][np.broadcast_to(m[:, None, :] == 0, tgt.shape)] = np.nan
+    sel = np.broadcast_to(m[:, None, :] > 0, z.shape)
+    n_held = int(sel.sum())
+    loss, gz = dense.masked_mse(z, tgt, m, 2.0 / n_held)
+    assert abs(loss.sum() - np.mean((z[sel] - tgt[sel]) ** 2)) <= 1e-14
+    assert np.all(np.isfinite(gz)) and np.all(gz[~sel] == 0)
+    h = 1e-6
+    for (t, b, p) in [(0, 0, 0), (3, 1, 2), (16, 2, 4), (8, 0, 1)]:
+        zp, zm = z.copy(), z.copy()
+        zp[t, b, p] += h
+        zm[t, b, p] -= h
+        fd = (dense.masked_mse(zp, tgt, m, 0.7)[0].sum() - dense.masked_mse(zm, tgt, m, 0.7)[0].sum()) / (2 * h)
+        assert abs(fd - dense.masked_mse(z, tgt, m, 0.7)[1][t, b, p]) <= 1e-8
+    l1, g1 = dense.masked_mse(z, np.nan_to_num(tgt), None, 0.5)
+    assert np.allclose(g1, 0.5 * (z - np.nan_to_num(tgt))) and l1.shape == (P,)
