@@ -336,12 +336,36 @@ int ws_solve_adjoint(const ws_problem* pb, const void* factor_or_null, const voi
                      uint32_t flags, uint8_t* status, void* workspace, size_t ws_bytes,
                      void* stream);
 
+/* The adjoint of Section 4.3's training loss with the loss fused into its sweeps: the
+ * masked mean squared error of the smooth z against held-out targets,
+ *   L_p = scale/2 * sum_{t,b} m_tp (z_tbp - target_tbp)^2,
+ * whose gradient gz = scale * m * (z - target) is formed per day inside the kernel (never
+ * stored), then Eqs. 4-5 as ws_solve_adjoint (recomputed factor): gx = W Omega^{-1} gz,
+ * glam_k = -sum_b (D g_b)_k (D z_b)_k (times lambda_k with WS_GRAD_LOGLAM). With
+ * scale = 2 / (number of held-out entries) the sum of L over the series is their mean.
+ * target: [T][B][P] like x (read only where m > 0, so NaN elsewhere is harmless); mask:
+ * [T][P] non-negative day weights shared by the bands (1 on held-out days), or NULL for all
+ * ones; z: the forward output. loss: optional [P] output (L_p), gx / glam optional as in
+ * ws_solve_adjoint. flags: WS_GRAD_LOGLAM, WS_ADJ_RAW_G. workspace: ws_workspace_size(pb, 0).
+ * Outputs must not overlap the inputs or each other (WS_EINVAL). status as ws_solve_adjoint. */
+int ws_solve_adjoint_mse(const ws_problem* pb, const void* w, const void* lam, const void* z,
+                         const void* target, const void* mask, double scale, void* gx, void* glam,
+                         void* loss, uint32_t flags, uint8_t* status, void* workspace, size_t ws_bytes,
+                         void* stream);
+
 /* Tuning knobs of the tile kernels, process-wide (0 = automatic): the number of CTAs
  * (128 pixels each) to fit on one SM, 1..8, which sets the shared memory per CTA, and
  * an upper bound on the days per staged chunk, 1..255. The chunk is the largest that
  * fits; registers may allow fewer CTAs than requested. ws_workspace_size() reflects the
  * current setting. Returns WS_EINVAL for out-of-range values. */
 int ws_tune_set(int32_t ctas_per_sm, int32_t chunk_days);
+
+/* Tuning of the tile kernels (no counterpart in the paper): pixel series per CTA, 0
+ * (automatic), 128 or 64 (FP32 only; FP64 always uses 128). 64-pixel CTAs give each
+ * pixel twice the shared memory at the same CTAs per SM, so chunks twice as deep and half
+ * the checkpoint traffic; ws_tune_set's ctas_per_sm then counts 64-pixel CTAs.
+ * ws_workspace_size() reflects the current setting. Returns WS_EINVAL for other values. */
+int ws_tune_pixels_per_cta(int32_t pixels);
 
 /* ---------------------------------------------------------------------------------
  * Ragged batches: series of different lengths (and orders) packed back to back.

@@ -120,14 +120,16 @@ static int extra_planes_mode(int mode, int d) { return mode == MODE_ADJ ? d : ex
 
 static size_t round256(size_t v) { return (v + 255) & ~(size_t)255; }
 
-// Checkpoint bytes of the tile kernels over all band groups and modes.
+// Checkpoint bytes of the tile kernels over all band groups and modes (the adjoint with
+// and without the fused MSE loss, whose extra staged rows may shorten its chunks).
 static int tile_ckpt_bytes(const ws_problem& pb, size_t& bytes) {
   bytes = 0;
-  for (int mode : {MODE_SMOOTH, MODE_RAW, MODE_ADJ}) {
+  const int modes[4] = {MODE_SMOOTH, MODE_RAW, MODE_ADJ, MODE_ADJ + 8};  // + 8: with the MSE loss
+  for (int mode : modes) {
     for (int b0 = 0; b0 < pb.n_bands;) {
       const int nb = group_size(pb, pb.n_bands - b0);
       TileCfg cfg;
-      int rc = plan_tile(pb, mode, nb, cfg);
+      int rc = plan_tile(pb, mode & 7, nb, cfg, mode >> 3);
       if (rc != WS_OK) return rc;
       const size_t need = (size_t)cfg.grid * cfg.nch * cfg.fields * cfg.NP * elem_size(pb);
       if (need > bytes) bytes = need;
@@ -154,10 +156,18 @@ static int check_workspace(const ws_problem& pb, void* workspace, size_t ws_byte
   return WS_OK;
 }
 
+// The masked-MSE loss fused into the adjoint (rhs is then the target).
+struct AdjMse {
+  const void* mask;  // [T][P] or NULL
+  double scale;
+  void* loss;        // [P] or NULL
+};
+
 // One tile-kernel mode over every band group of the problem.
 static int run_tile(const ws_problem& P, int mode, const void* rhs, const void* w, const void* lam,
                     const void* zin, const void* g0, void* out, void* out2, void* factor, uint8_t* status,
-                    int accum, int adj_flags, void* workspace, cudaStream_t st, void* df_base = nullptr) {
+                    int accum, int adj_flags, void* workspace, cudaStream_t st, void* df_base = nullptr,
+                    const AdjMse* mse = nullptr) {
   // adj_flags (MODE_ADJ): bit 0 gradient in log lambda, bit 1 output g instead of W g
   // pointer contract of each mode (an inconsistent internal call is an error, never a fault)
   if (rhs == nullptr || w == nullptr || lam == nullptr) return set_error(WS_EINVAL, "tile: missing input");
@@ -169,29 +179,31 @@ static int run_tile(const ws_problem& P, int mode, const void* rhs, const void* 
   const bool per_day = P.lam_mode == WS_LAM_PER_DAY;
   // the array staged into the Z region in pass 2: z (adjoint) or z0 = out (accumulating RAW)
   const void* zin_stage = mode == MODE_ADJ ? zin : ((mode == MODE_RAW && accum) ? out : nullptr);
+  const bool has_m = mse != nullptr && mse->mask != nullptr;
   const bool tma_ok = ((size_t)P.n_series * es) % 16 == 0 && aligned16(rhs) && aligned16(w) &&
                       (out == nullptr || aligned16(out)) && (!per_day || aligned16(lam)) &&
-                      (zin_stage == nullptr || aligned16(zin_stage));
+                      (zin_stage == nullptr || aligned16(zin_stage)) && (!has_m || aligned16(mse->mask));
   for (int b0 = 0; b0 < P.n_bands;) {
     const int nb = group_size(P, P.n_bands - b0);
     TileCfg cfg;
-    int rc = plan_tile(P, mode, nb, cfg);
+    int rc = plan_tile(P, mode, nb, cfg, mse != nullptr ? 1 : 0);
     if (rc != WS_OK) return rc;
-    CUtensorMap maps[5];
+    CUtensorMap maps[6];
     memset(maps, 0, sizeof(maps));
     bool tma = tma_ok;
     if (tma) {
       const uint64_t Pn = (uint64_t)P.n_series, B = (uint64_t)P.n_bands, T = (uint64_t)P.T;
       const uint64_t dx[3] = {Pn, B, T}, sx[2] = {Pn * es, B * Pn * es};
-      const uint32_t bx[3] = {(uint32_t)kNP, (uint32_t)nb, (uint32_t)cfg.C};
+      const uint32_t bx[3] = {(uint32_t)cfg.NP, (uint32_t)nb, (uint32_t)cfg.C};
       const uint64_t d2[2] = {Pn, T}, s2[1] = {Pn * es};
-      const uint32_t bw[2] = {(uint32_t)kNP, (uint32_t)(cfg.C + P.d)};
-      const uint32_t bl[2] = {(uint32_t)kNP, (uint32_t)cfg.C};
+      const uint32_t bw[2] = {(uint32_t)cfg.NP, (uint32_t)(cfg.C + P.d)};
+      const uint32_t bl[2] = {(uint32_t)cfg.NP, (uint32_t)cfg.C};
       tma = make_tmap(&maps[0], P.dtype, 3, rhs, dx, sx, bx) == WS_OK &&
             make_tmap(&maps[1], P.dtype, 2, w, d2, s2, bw) == WS_OK &&
             (!per_day || make_tmap(&maps[2], P.dtype, 2, lam, d2, s2, bl) == WS_OK) &&
             (out == nullptr || make_tmap(&maps[3], P.dtype, 3, out, dx, sx, bx) == WS_OK) &&
-            (zin_stage == nullptr || make_tmap(&maps[4], P.dtype, 3, zin_stage, dx, sx, bx) == WS_OK);
+            (zin_stage == nullptr || make_tmap(&maps[4], P.dtype, 3, zin_stage, dx, sx, bx) == WS_OK) &&
+            (!has_m || make_tmap(&maps[5], P.dtype, 2, mse->mask, d2, s2, bl) == WS_OK);
     }
     TileArgs a;
     memset(&a, 0, sizeof(a));
@@ -200,7 +212,7 @@ static int run_tile(const ws_problem& P, int mode, const void* rhs, const void* 
     a.B = P.n_bands;
     a.b0 = b0;
     a.C = cfg.C;
-    a.NP = kNP;
+    a.NP = cfg.NP;
     a.nch = cfg.nch;
     a.n_tiles = cfg.n_tiles;
     a.lam_scalar = per_day ? 0 : 1;
@@ -224,6 +236,12 @@ static int run_tile(const ws_problem& P, int mode, const void* rhs, const void* 
     if (df_base != nullptr) {
       char* slots = nullptr;
       adj_df_layout(P, df_base, &a.df_mark, &a.df_count, &a.df_list, &slots);
+    }
+    if (mse != nullptr) {
+      a.mse = 1;
+      a.mask = mse->mask;
+      a.mse_scale = mse->scale;
+      a.loss = mse->loss;
     }
     rc = launch_tile(P, mode, nb, cfg, a, maps, st);
     if (rc != WS_OK) return rc;
@@ -690,6 +708,58 @@ extern "C" int ws_solve_adjoint(const ws_problem* pb, const void* factor_or_null
   rc = run_tile(P, MODE_ADJ, r, w, lam, z, g0, gx, glam, nullptr, status, 1, loglam, workspace, st, df);
   if (rc != WS_OK || df == nullptr || (gx == nullptr && glam == nullptr)) return rc;
   return launch_adj_df(P, gz, w, lam, z, gx, glam, loglam, df, st);
+}
+
+extern "C" int ws_solve_adjoint_mse(const ws_problem* pb, const void* w, const void* lam, const void* z,
+                                    const void* target, const void* mask, double scale, void* gx, void* glam,
+                                    void* loss, uint32_t flags, uint8_t* status, void* workspace, size_t ws_bytes,
+                                    void* stream) {
+  clear_error();
+  int rc = validate_problem(pb);
+  if (rc != WS_OK) return rc;
+  if (flags & ~(WS_GRAD_LOGLAM | WS_ADJ_RAW_G)) return set_error(WS_EINVAL, "unknown flags 0x%x", flags);
+  if (!std::isfinite(scale)) return set_error(WS_EINVAL, "scale must be finite");
+  const ws_problem& P = *pb;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (P.n_series == 0) return WS_OK;
+  const int es = elem_size(P);
+  const size_t np = (size_t)P.n_series;
+  if (P.T == 0) {
+    if ((status != nullptr && cudaMemsetAsync(status, 0, np, st) != cudaSuccess) ||
+        (loss != nullptr && cudaMemsetAsync(loss, 0, np * es, st) != cudaSuccess) ||
+        (glam != nullptr && P.lam_mode == WS_LAM_SCALAR && cudaMemsetAsync(glam, 0, np * es, st) != cudaSuccess))
+      return set_error(WS_ECUDA, "memset failed");
+    return WS_OK;
+  }
+  if (!w || !lam || !z || !target) return set_error(WS_EINVAL, "w, lam, z and target must be non-NULL");
+  const size_t nx = (size_t)P.T * P.n_bands * np * es, nd = (size_t)P.T * np * es;
+  const size_t nl = P.lam_mode == WS_LAM_SCALAR ? np * es : nd;
+  const void* ins[5] = {w, lam, z, target, mask};
+  const size_t nin[5] = {nd, nl, nx, nx, nd};
+  for (int i = 0; i < 5; ++i) {
+    if (ins[i] == nullptr) continue;
+    if ((gx != nullptr && overlaps(gx, nx, ins[i], nin[i])) || (glam != nullptr && overlaps(glam, nl, ins[i], nin[i])) ||
+        (loss != nullptr && overlaps(loss, np * es, ins[i], nin[i])))
+      return set_error(WS_EINVAL, "gx, glam and loss must not overlap the inputs");
+  }
+  if ((gx != nullptr && glam != nullptr && overlaps(gx, nx, glam, nl)) ||
+      (loss != nullptr && ((gx != nullptr && overlaps(loss, np * es, gx, nx)) ||
+                           (glam != nullptr && overlaps(loss, np * es, glam, nl)))))
+    return set_error(WS_EINVAL, "gx, glam and loss must not overlap each other");
+  size_t ck_bytes = 0;
+  rc = check_workspace(P, workspace, ws_bytes, 0, ck_bytes);
+  if (rc != WS_OK) return rc;
+  const int adj = ((flags & WS_GRAD_LOGLAM) ? 1 : 0) | ((flags & WS_ADJ_RAW_G) ? 2 : 0);
+  const AdjMse m{mask, scale, loss};
+  return run_tile(P, MODE_ADJ, target, w, lam, z, nullptr, gx, glam, nullptr, status, 0, adj, workspace, st, nullptr,
+                  &m);
+}
+
+extern "C" int ws_tune_pixels_per_cta(int32_t pixels) {
+  clear_error();
+  if (pixels != 0 && pixels != 64 && pixels != 128) return set_error(WS_EINVAL, "pixels per CTA must be 0, 64 or 128");
+  g_tune_np = pixels;
+  return WS_OK;
 }
 
 extern "C" int ws_tune_set(int32_t ctas_per_sm, int32_t chunk_days) {

@@ -11,7 +11,7 @@ namespace ws {
 
 constexpr int kNbMax = 10;
 enum { MODE_SMOOTH = 0, MODE_RAW = 1, MODE_ADJ = 2 };
-constexpr int kNP = 128;  // pixels per CTA of the tile kernels
+constexpr int kNP = 128;  // pixels per CTA of the tile kernels (64 is the other instantiation, FP32)
 
 // Threads per pixel of a band group: two (each owning half the bands) for 6, 8, 10 bands.
 __host__ __device__ inline int band_split(int nb, bool fp64) { return (!fp64 && nb >= 6 && nb % 2 == 0) ? 2 : 1; }
@@ -22,18 +22,20 @@ __host__ __device__ inline int tile_extra_planes(int mode, int D, int S) {
 }
 // checkpoint words per pixel per chunk: factor state + forward-substitution state
 __host__ __device__ inline int tile_ckpt_fields(int NB, int D) { return D * (D + 1) + NB * D; }
-__host__ __device__ inline size_t tile_stage_rows(int mode, int C, int NB, int D, int S) {
-  return (size_t)C * NB + C + D + C + (size_t)tile_extra_planes(mode, D, S) * C + tile_ckpt_fields(NB, D);
+// stage: X (C*NB), Z (C*NB, RAW/ADJ), W (C+d), L (C), E (extra planes * C), M (C, ADJ with
+// the fused MSE loss: the day weights)
+__host__ __device__ inline size_t tile_stage_rows(int mode, int C, int NB, int D, int S, int mse = 0) {
+  const size_t xz = (size_t)C * NB * ((mode == MODE_RAW || mode == MODE_ADJ) ? 2 : 1);
+  return xz + C + D + C + (size_t)tile_extra_planes(mode, D, S) * C + (mse ? (size_t)C : 0);
 }
-__host__ __device__ inline size_t tile_smem_rows(int mode, int C, int NB, int D, int S) {
-  size_t rows = 2 * tile_stage_rows(mode, C, NB, D, S);
-  if (mode == MODE_RAW || mode == MODE_ADJ) rows += (size_t)C * NB;
+__host__ __device__ inline size_t tile_smem_rows(int mode, int C, int NB, int D, int S, int mse = 0) {
+  size_t rows = 2 * tile_stage_rows(mode, C, NB, D, S, mse);
   if (mode == MODE_ADJ) rows += (size_t)S * C;
   return rows;
 }
-// rows + 3 mbarriers (64 bytes reserved) + kNP status words
-__host__ __device__ inline size_t tile_smem_bytes(int mode, int C, int NB, int D, int S, int es) {
-  return tile_smem_rows(mode, C, NB, D, S) * kNP * es + 64 + kNP * 4;
+// rows of NP elements + 3 mbarriers (64 bytes reserved) + NP status words
+__host__ __device__ inline size_t tile_smem_bytes(int mode, int C, int NB, int D, int S, int es, int NP, int mse = 0) {
+  return tile_smem_rows(mode, C, NB, D, S, mse) * NP * es + 64 + NP * 4;
 }         // bands per launch; more bands run as band groups
 constexpr size_t kHeaderBytes = 256;  // device error word + reserved
 
@@ -78,6 +80,11 @@ struct TileArgs {
   unsigned* df_mark;
   int* df_list;
   unsigned* df_count;
+  // ADJ with the masked-MSE loss fused in (x is then the target): gz = mse_scale * m * (z - x)
+  int mse;
+  const void* mask;       // [T][P] day weights m, or NULL (all ones)
+  double mse_scale;
+  void* loss;             // [P] scale/2 * sum m (z - x)^2 (accumulated over band groups), or NULL
 };
 
 struct DeviceInfo {
@@ -116,15 +123,15 @@ int launch_dates(const ws_problem& pb, bool adj, const void* t, const void* x, c
                  void* out, const void* zin, void* glam, int loglam, uint8_t* status, void* ckpt, cudaStream_t st);
 
 // Launchers (return WS_OK or an error code, errors recorded via set_error).
-extern int g_tune_ctas, g_tune_chunk;  // ws_tune_set() overrides (0 = automatic)
-int plan_tile(const ws_problem& pb, int mode, int nb, TileCfg& cfg);
+extern int g_tune_ctas, g_tune_chunk, g_tune_np;  // ws_tune_set() overrides (0 = automatic)
+int plan_tile(const ws_problem& pb, int mode, int nb, TileCfg& cfg, int mse = 0);
 int launch_tile(const ws_problem& pb, int mode, int nb, const TileCfg& cfg, const TileArgs& a,
                 const CUtensorMap* maps, cudaStream_t st);
-const void* tile_kernel_ptr(const ws_problem& pb, int mode, int nb);
-const void* tile_kernel_ptr_d1(const ws_problem& pb, int mode, int nb);
-const void* tile_kernel_ptr_d2(const ws_problem& pb, int mode, int nb);
-const void* tile_kernel_ptr_d3(const ws_problem& pb, int mode, int nb);
-const void* tile_kernel_ptr_d4(const ws_problem& pb, int mode, int nb);
+const void* tile_kernel_ptr(const ws_problem& pb, int mode, int nb, int np);
+const void* tile_kernel_ptr_d1(const ws_problem& pb, int mode, int nb, int np);
+const void* tile_kernel_ptr_d2(const ws_problem& pb, int mode, int nb, int np);
+const void* tile_kernel_ptr_d3(const ws_problem& pb, int mode, int nb, int np);
+const void* tile_kernel_ptr_d4(const ws_problem& pb, int mode, int nb, int np);
 int launch_tile_d1(const ws_problem&, int, int, const TileCfg&, const TileArgs&, const CUtensorMap*, cudaStream_t);
 int launch_tile_d2(const ws_problem&, int, int, const TileCfg&, const TileArgs&, const CUtensorMap*, cudaStream_t);
 int launch_tile_d3(const ws_problem&, int, int, const TileCfg&, const TileArgs&, const CUtensorMap*, cudaStream_t);

@@ -35,49 +35,56 @@ namespace ws {
 // ----------------------------------------------------------------------------------
 // host side
 
-int g_tune_ctas = 0, g_tune_chunk = 0;
+int g_tune_ctas = 0, g_tune_chunk = 0, g_tune_np = 0;
 
-// Largest chunk (days) whose shared memory fits `ctas` CTAs on one SM.
-static long chunk_for(const ws_problem& pb, int mode, int nb, int S, int ctas, const DeviceInfo& di) {
+// Largest chunk (days) whose shared memory fits `ctas` CTAs of `np` pixels on one SM.
+static long chunk_for(const ws_problem& pb, int mode, int nb, int S, int ctas, int np, const DeviceInfo& di,
+                      int mse) {
   const int es = pb.dtype == WS_F64 ? 8 : 4;
   const int D = pb.d;
   long per_cta = (long)di.smem_per_sm / ctas - 1024;
   if (per_cta > di.smem_optin) per_cta = di.smem_optin;
-  const long rows = (per_cta - 64 - kNP * 4) / ((long)kNP * es);
-  const long fixed = (long)tile_smem_rows(mode, 0, nb, D, S);         // rows independent of C
-  const long coef = (long)tile_smem_rows(mode, 1, nb, D, S) - fixed;  // rows per day of chunk
+  const long rows = (per_cta - 64 - np * 4) / ((long)np * es);
+  const long fixed = (long)tile_smem_rows(mode, 0, nb, D, S, mse);         // rows independent of C
+  const long coef = (long)tile_smem_rows(mode, 1, nb, D, S, mse) - fixed;  // rows per day of chunk
   return (rows - fixed) / coef;
 }
 
-int plan_tile(const ws_problem& pb, int mode, int nb, TileCfg& cfg) {
+int plan_tile(const ws_problem& pb, int mode, int nb, TileCfg& cfg, int mse) {
   DeviceInfo di;
   int rc = device_info(di);
   if (rc != WS_OK) return rc;
   const int es = pb.dtype == WS_F64 ? 8 : 4;
   const int D = pb.d, T = pb.T;
   const int S = band_split(nb, pb.dtype == WS_F64);
-  cfg.NP = kNP;
+  // pixels per CTA: 128, or 64 (FP32) for deeper chunks at the same CTAs per SM. The
+  // adjoint defaults to 64: on the 10-band tile (d = 2, 3288 days) four 64-pixel CTAs per
+  // SM took 36.7 ms against 38.2 ms for two 128-pixel ones at the same chunk depth (one
+  // CTA's barrier stalls then idle fewer warps); smooth and correction solve measured the same
+  // either way (22.6-22.7 ms, 46.5-47.6 ms) and keep 128.
+  const bool np64 = g_tune_np == 64 || (g_tune_np == 0 && mode == MODE_ADJ);
+  const int np = (pb.dtype == WS_F32 && np64) ? 64 : 128;
+  cfg.NP = np;
   cfg.S = S;
   cfg.stages = 2;
   // Aim at 16 resident warps per SM (latency of the sequential recurrence), but keep
   // chunks of at least 5 days (checkpoint traffic grows as 1/C); 4 for the correction and
-  // adjoint modes, whose per-day work is larger: on the 10-band tile their two CTAs per SM at
-  // 4 days beat one CTA at 12 days by 22% (adjoint) and 7% (correction solve).
-  int ctas = g_tune_ctas > 0 ? g_tune_ctas : (S > 1 ? 2 : 4);
+  // adjoint modes, whose per-day work is larger.
+  int ctas = g_tune_ctas > 0 ? g_tune_ctas : (S > 1 ? 2 : 4) * (128 / np);
   const long min_chunk = (mode == MODE_RAW || mode == MODE_ADJ) ? 4 : 5;
   long C = 0;
   for (; ctas >= 1; --ctas) {
-    C = chunk_for(pb, mode, nb, S, ctas, di);
+    C = chunk_for(pb, mode, nb, S, ctas, np, di, mse);
     if (C >= min_chunk || ctas == 1 || g_tune_ctas > 0) break;
   }
   // registers may allow fewer CTAs than shared memory: then give the chunk the room
-  const void* kern = tile_kernel_ptr(pb, mode, nb);
+  const void* kern = tile_kernel_ptr(pb, mode, nb, np);
   if (kern == nullptr) return set_error(WS_EUNSUPPORTED, "no tile kernel for %d bands", nb);
   auto fit = [&](long Cc, int* occ) -> int {
-    const size_t smem = tile_smem_bytes(mode, (int)Cc, nb, D, S, es);
+    const size_t smem = tile_smem_bytes(mode, (int)Cc, nb, D, S, es, np, mse);
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return set_error(WS_ECUDA, "cudaFuncSetAttribute: %s", cudaGetErrorString(e));
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, kern, kNP * S, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, kern, np * S, smem);
     if (e != cudaSuccess) return set_error(WS_ECUDA, "occupancy query: %s", cudaGetErrorString(e));
     return WS_OK;
   };
@@ -92,27 +99,27 @@ int plan_tile(const ws_problem& pb, int mode, int nb, TileCfg& cfg) {
   int occ = 0;
   if ((rc = fit(C, &occ)) != WS_OK) return rc;
   if (occ >= 1 && occ < ctas && g_tune_chunk == 0) {
-    C = clampC(chunk_for(pb, mode, nb, S, occ, di));
+    C = clampC(chunk_for(pb, mode, nb, S, occ, np, di, mse));
     if ((rc = fit(C, &occ)) != WS_OK) return rc;
   }
   if (occ < 1) return set_error(WS_EUNSUPPORTED, "tile kernel does not fit on an SM (chunk %ld)", C);
   cfg.C = (int)C;
   cfg.nch = T > 0 ? (T + cfg.C - 1) / cfg.C : 0;
-  cfg.n_tiles = (int)((pb.n_series + kNP - 1) / kNP);
-  cfg.stage_elems = tile_stage_rows(mode, cfg.C, nb, D, S) * kNP;
-  cfg.smem_bytes = tile_smem_bytes(mode, cfg.C, nb, D, S, es);
+  cfg.n_tiles = (int)((pb.n_series + np - 1) / np);
+  cfg.stage_elems = tile_stage_rows(mode, cfg.C, nb, D, S, mse) * np;
+  cfg.smem_bytes = tile_smem_bytes(mode, cfg.C, nb, D, S, es, np, mse);
   const long cap = (long)di.sm_count * occ;
   cfg.grid = (int)(cfg.n_tiles < cap ? cfg.n_tiles : cap);
   cfg.fields = D * (D + 1) + nb * D;
   return WS_OK;
 }
 
-const void* tile_kernel_ptr(const ws_problem& pb, int mode, int nb) {
+const void* tile_kernel_ptr(const ws_problem& pb, int mode, int nb, int np) {
   switch (pb.d) {
-    case 1: return tile_kernel_ptr_d1(pb, mode, nb);
-    case 2: return tile_kernel_ptr_d2(pb, mode, nb);
-    case 3: return tile_kernel_ptr_d3(pb, mode, nb);
-    case 4: return tile_kernel_ptr_d4(pb, mode, nb);
+    case 1: return tile_kernel_ptr_d1(pb, mode, nb, np);
+    case 2: return tile_kernel_ptr_d2(pb, mode, nb, np);
+    case 3: return tile_kernel_ptr_d3(pb, mode, nb, np);
+    case 4: return tile_kernel_ptr_d4(pb, mode, nb, np);
   }
   return nullptr;
 }

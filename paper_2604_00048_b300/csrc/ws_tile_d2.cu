@@ -7,7 +7,7 @@ int launch_tile_d2(const ws_problem& pb, int mode, int nb, const TileCfg& cfg, c
                     const CUtensorMap* maps, cudaStream_t st) {
   return dispatch_tile_d<2>(pb, mode, nb, cfg, a, maps, st);
 }
-const void* tile_kernel_ptr_d2(const ws_problem& pb, int mode, int nb) {
-  return tile_kernel_ptr_t<2>(pb, mode, nb);
+const void* tile_kernel_ptr_d2(const ws_problem& pb, int mode, int nb, int np) {
+  return tile_kernel_ptr_t<2>(pb, mode, nb, np);
 }
 }  // namespace ws

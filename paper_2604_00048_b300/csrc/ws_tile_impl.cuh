@@ -1,8 +1,10 @@
-// Tile-layout banded-solve kernel: kNP = 128 pixel series per CTA, one series per
+// Tile-layout banded-solve kernel: NP (128 or 64) pixel series per CTA, one series per
 // thread for up to 5 bands; for 6, 8 or 10 bands two threads share a pixel (S = 2),
 // each owning NBT = NB / S bands and both running the (cheap, per-pixel) rotation
 // factor, which halves the registers per thread and doubles the warps that hide the
-// latency of the sequential time recurrence.
+// latency of the sequential time recurrence. 64-pixel CTAs give each pixel twice the
+// shared memory of 128-pixel ones at the same CTAs per SM: chunks twice as deep, half the
+// checkpoint traffic.
 //
 //   MODE_SMOOTH: z = Omega^{-1} W x                       (Eq. 3; Eq. 2 for scalar lambda)
 //   MODE_RAW:    out = [z0 +] Omega^{-1} x                (correction solve of the iterative
@@ -18,26 +20,27 @@
 //     rotation factor + forward substitution (ws_sweep.cuh) and stores its state at every
 //     chunk boundary to a checkpoint area in global memory.
 //   pass 2 (backward in time): for each chunk, last to first, the state is reloaded from
-//     its checkpoint and the chunk is recomputed from the staged inputs, writing yhat and
-//     rho in place; back substitution then runs over the chunk in reverse, writing the
-//     output in place over yhat, and TMA stores the output box. The last two chunks of
-//     pass 1 are still resident and are reused. RAW/ADJ also need a per-day array in
-//     pass 2 (z0 or the forward output z): a single-buffered Z region loaded by TMA at the
-//     start of the chunk's recompute and waited for before its back substitution.
+//     its checkpoint (loaded into registers one chunk ahead) and the chunk is recomputed
+//     from the staged inputs, writing yhat and rho in place; back substitution then runs
+//     over the chunk in reverse, writing the output in place over yhat, and TMA stores the
+//     output box. The last two chunks of pass 1 are still resident and are reused. RAW
+//     with accumulation and ADJ also need a per-day array in pass 2 (z0 or the forward
+//     output z): it is staged with the chunk's inputs, two chunks ahead like them (the two
+//     chunks resident from pass 1 get theirs when pass 1 ends).
 // Inputs are read twice and the output written once, plus d(d+1) + B*d checkpoint words
 // per pixel per chunk, instead of spilling the factor and y for every day.
 //
-// Shared memory (rows of kNP elements):
+// Shared memory (rows of NP elements):
 //   stage s (s = 0, 1):
 //     X [C*NB rows]  right-hand sides, band-minor (pass 2: yhat, then the output)
+//     Z [C*NB rows]  RAW/ADJ: z0 or z of the chunk in pass 2
 //     W [C+d rows]   w       (SMOOTH/RAW with S = 1, pass 2: rho_2 over the first C rows)
 //     L [C rows]     lambda  (SMOOTH/RAW with S = 1, pass 2: rho_1)
 //     E [extra rows] SMOOTH/RAW with S = 1: rho_3..rho_d ((d-2)*C rows); otherwise
 //                    rho_1..rho_d (d*C rows): ADJ keeps w and lambda for its epilogue, and
 //                    with S = 2 the other band half still reads them
-//   Z [C*NB rows]    RAW/ADJ: z0 or z of the chunk in pass 2
 //   G [S*C rows]     ADJ: per-thread partial sums of (D g)(D z) before the band-split combine
-//   then 3 mbarriers and kNP status words.
+//   then 3 mbarriers and NP status words.
 // When TMA cannot describe the arrays (row pitch not a multiple of 16 bytes, base not
 // 16-byte aligned) every thread copies its own columns with LDGSTS instead and stores its
 // outputs with plain coalesced stores; the arithmetic is the same.
@@ -52,34 +55,42 @@
 
 namespace ws {
 
-template <typename F, int D, int NBT, int S, int MODE>
-__global__ void __launch_bounds__(kNP* S, S > 1 ? 2 : 4) k_tile(const __grid_constant__ CUtensorMap tm_x,
-                                                 const __grid_constant__ CUtensorMap tm_w,
-                                                 const __grid_constant__ CUtensorMap tm_l,
-                                                 const __grid_constant__ CUtensorMap tm_o,
-                                                 const __grid_constant__ CUtensorMap tm_z, const TileArgs a) {
+template <typename F, int D, int NBT, int S, int MODE, int NP>
+__global__ void __launch_bounds__(NP* S, (S > 1 ? 2 : 4) * (128 / NP))
+    k_tile(const __grid_constant__ CUtensorMap tm_x, const __grid_constant__ CUtensorMap tm_w,
+           const __grid_constant__ CUtensorMap tm_l, const __grid_constant__ CUtensorMap tm_o,
+           const __grid_constant__ CUtensorMap tm_z, const __grid_constant__ CUtensorMap tm_m,
+           const TileArgs a) {
   constexpr int NB = NBT * S;
   constexpr int EXTRA = MODE == MODE_ADJ || S > 1 ? D : (D > 2 ? D - 2 : 0);
   constexpr bool HAS_Z = MODE == MODE_RAW || MODE == MODE_ADJ;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   using SW = Sweep<F, D, NBT>;
   const int tid = threadIdx.x;
-  const int pl = tid % kNP;  // pixel lane within the tile
-  const int h = tid / kNP;   // band half (S = 2) or 0
+  const int pl = tid % NP;  // pixel lane within the tile
+  const int h = tid / NP;   // band half (S = 2) or 0
   const int C = a.C, T = a.T;
   constexpr int kFF = SW::kFactorFields;
   constexpr int kFields = kFF + NB * D;
-  const size_t stage_rows = (size_t)C * NB + C + D + C + (size_t)EXTRA * C + kFields;
+  constexpr int kYT = NBT * D;  // this thread's forward-substitution words in a checkpoint
+  // ADJ with the masked-MSE loss fused in: x is the target, the right-hand side
+  // gz = scale * m_t * (z - target) is formed per day from the staged z, target and m
+  const bool mse = MODE == MODE_ADJ && a.mse;
+  const bool has_m = mse && a.mask != nullptr;
+  const F mscale = static_cast<F>(a.mse_scale);
+  const size_t stage_rows = tile_stage_rows(MODE, C, NB, D, S, mse ? 1 : 0);
   F* const smem = reinterpret_cast<F*>(smem_raw);
-  F* const zbuf = smem + 2 * stage_rows * kNP;                  // Z region
-  F* const gbuf = zbuf + (HAS_Z ? (size_t)C * NB * kNP : 0);     // G region
-  const size_t rows_total = tile_smem_rows(MODE, C, NB, D, S);
-  uint64_t* bar = reinterpret_cast<uint64_t*>(smem + rows_total * kNP);
+  F* const gbuf = smem + 2 * stage_rows * NP;  // G region (ADJ)
+  const size_t rows_total = tile_smem_rows(MODE, C, NB, D, S, mse ? 1 : 0);
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem + rows_total * NP);
   unsigned* nflag = reinterpret_cast<unsigned*>(bar + 4);
-  const int rowW = NB * C, rowL = rowW + C + D, rowE = rowL + C, rowK = rowE + EXTRA * C;
-  const uint32_t tx_bytes = static_cast<uint32_t>((NB * C + C + D + (a.lam_scalar ? 0 : C)) * kNP * sizeof(F));
-  const uint32_t tz_bytes = static_cast<uint32_t>(NB * C * kNP * sizeof(F));
-  const uint32_t tk_bytes = static_cast<uint32_t>(kFields * kNP * sizeof(F));
+  const int rowZ = NB * C;                                   // HAS_Z: pass 2's z / z0 of the chunk
+  const int rowW = NB * C * (HAS_Z ? 2 : 1), rowL = rowW + C + D, rowE = rowL + C;
+  const int rowM = rowE + EXTRA * C;  // ADJ with the MSE loss: day weights m of the chunk
+  const uint32_t tx_bytes = static_cast<uint32_t>((NB * C + C + D + (a.lam_scalar ? 0 : C)) * NP * sizeof(F));
+  const uint32_t tz_bytes = static_cast<uint32_t>(NB * C * NP * sizeof(F));
+  const uint32_t tm_bytes = static_cast<uint32_t>(has_m ? C * NP * sizeof(F) : 0);
+  const F* gm = static_cast<const F*>(a.mask);
   const F* gx_in = static_cast<const F*>(a.x);
   const F* gw = static_cast<const F*>(a.w);
   const F* gl = static_cast<const F*>(a.lam);
@@ -89,8 +100,8 @@ __global__ void __launch_bounds__(kNP* S, S > 1 ? 2 : 4) k_tile(const __grid_con
   F* gout2 = static_cast<F*>(a.out2);
   F* gf = static_cast<F*>(a.factor);
   const bool want_out = gout != nullptr;
-  const bool want_z = HAS_Z && gzin != nullptr;  // RAW without accumulation reads no Z
-  auto stage = [&](int st) -> F* { return smem + (size_t)st * stage_rows * kNP; };
+  const bool want_z = HAS_Z && gzin != nullptr;  // RAW without accumulation reads no z
+  auto stage = [&](int st) -> F* { return smem + (size_t)st * stage_rows * NP; };
   auto rho_row = [&](int j, int k) -> int {  // j = 1..D
     if (MODE == MODE_ADJ || S > 1) return rowE + (j - 1) * C + k;
     if (j == 1) return rowL + k;
@@ -107,23 +118,46 @@ __global__ void __launch_bounds__(kNP* S, S > 1 ? 2 : 4) k_tile(const __grid_con
       if (!a.lam_scalar) prefetch_tmap(&tm_l);
       if (want_out) prefetch_tmap(&tm_o);
       if (want_z) prefetch_tmap(&tm_z);
+      if (has_m) prefetch_tmap(&tm_m);
     }
   }
   __syncthreads();
   uint32_t phase = 0u;    // bit i: parity of the next completion of barrier i
   uint32_t pending = 0u;  // bit i: a load on barrier i has not been waited for
 
+  // z of chunk c (pass 2) into stage st: TMA on barrier `b`, or LDGSTS (own columns).
+  auto copy_z = [&](int c, int st, int p0, uint64_t* b) {
+    F* Sz = stage(st) + (size_t)rowZ * NP;
+    if (a.tma) {
+      if (tid == 0) tma_load_3d(Sz, &tm_z, b, p0, a.b0, c * C);
+    } else {
+      const int p = p0 + pl;
+      const bool act = p < a.P;
+      for (int k = 0; k < C; ++k) {
+        const int t = c * C + k;
+        const bool v = act && t < T;
+#pragma unroll
+        for (int j = 0; j < NBT; ++j) {
+          const int b2 = h * NBT + j;
+          cp_async_elem<sizeof(F)>(Sz + (size_t)(k * NB + b2) * NP + pl,
+                                   v ? gzin + ((size_t)t * a.B + a.b0 + b2) * a.P + p : gzin, v);
+        }
+      }
+    }
+  };
+
   // Stage load of chunk c: every thread calls it (TMA: thread 0 issues; LDGSTS: each
-  // thread copies its own columns). ckg: the chunk's checkpoint to prefetch (pass 2, TMA).
-  auto issue = [&](int c, int st, int p0, const F* ckg) {
+  // thread copies its own columns). with_z: pass 2 of RAW/ADJ also stages z of the chunk.
+  auto issue = [&](int c, int st, int p0, bool with_z) {
     F* Sg = stage(st);
     if (a.tma) {
       if (tid == 0) {
-        mbar_arrive_expect_tx(&bar[st], tx_bytes + (ckg != nullptr ? tk_bytes : 0u));
-        if (ckg != nullptr) bulk_load_1d(Sg + (size_t)rowK * kNP, ckg, tk_bytes, &bar[st]);
+        mbar_arrive_expect_tx(&bar[st], tx_bytes + (with_z ? tz_bytes : 0u) + tm_bytes);
         tma_load_3d(Sg, &tm_x, &bar[st], p0, a.b0, c * C);
-        tma_load_2d(Sg + (size_t)rowW * kNP, &tm_w, &bar[st], p0, c * C);
-        if (!a.lam_scalar) tma_load_2d(Sg + (size_t)rowL * kNP, &tm_l, &bar[st], p0, c * C);
+        tma_load_2d(Sg + (size_t)rowW * NP, &tm_w, &bar[st], p0, c * C);
+        if (!a.lam_scalar) tma_load_2d(Sg + (size_t)rowL * NP, &tm_l, &bar[st], p0, c * C);
+        if (with_z) copy_z(c, st, p0, &bar[st]);
+        if (has_m) tma_load_2d(Sg + (size_t)rowM * NP, &tm_m, &bar[st], p0, c * C);
       }
     } else {
       const int p = p0 + pl;
@@ -134,49 +168,27 @@ __global__ void __launch_bounds__(kNP* S, S > 1 ? 2 : 4) k_tile(const __grid_con
 #pragma unroll
         for (int j = 0; j < NBT; ++j) {
           const int b = h * NBT + j;
-          cp_async_elem<sizeof(F)>(Sg + (size_t)(k * NB + b) * kNP + pl,
+          cp_async_elem<sizeof(F)>(Sg + (size_t)(k * NB + b) * NP + pl,
                                    v ? gx_in + ((size_t)t * a.B + a.b0 + b) * a.P + p : gx_in, v);
         }
         if (h == 0 && !a.lam_scalar)
-          cp_async_elem<sizeof(F)>(Sg + (size_t)(rowL + k) * kNP + pl, v ? gl + (size_t)t * a.P + p : gl, v);
+          cp_async_elem<sizeof(F)>(Sg + (size_t)(rowL + k) * NP + pl, v ? gl + (size_t)t * a.P + p : gl, v);
+        if (h == 0 && has_m)
+          cp_async_elem<sizeof(F)>(Sg + (size_t)(rowM + k) * NP + pl, v ? gm + (size_t)t * a.P + p : gm, v);
       }
       if (h == 0)
         for (int k = 0; k < C + D; ++k) {
           const int t = c * C + k;
           const bool v = act && t < T;
-          cp_async_elem<sizeof(F)>(Sg + (size_t)(rowW + k) * kNP + pl, v ? gw + (size_t)t * a.P + p : gw, v);
+          cp_async_elem<sizeof(F)>(Sg + (size_t)(rowW + k) * NP + pl, v ? gw + (size_t)t * a.P + p : gw, v);
         }
+      if (with_z) copy_z(c, st, p0, nullptr);
       cp_async_commit();
     }
     pending |= 1u << st;
   };
 
-  auto issue_z = [&](int c, int p0) {
-    if (a.tma) {
-      if (tid == 0) {
-        mbar_arrive_expect_tx(&bar[2], tz_bytes);
-        tma_load_3d(zbuf, &tm_z, &bar[2], p0, a.b0, c * C);
-      }
-    } else {
-      const int p = p0 + pl;
-      const bool act = p < a.P;
-      for (int k = 0; k < C; ++k) {
-        const int t = c * C + k;
-        const bool v = act && t < T;
-#pragma unroll
-        for (int j = 0; j < NBT; ++j) {
-          const int b = h * NBT + j;
-          cp_async_elem<sizeof(F)>(zbuf + (size_t)(k * NB + b) * kNP + pl,
-                                   v ? gzin + ((size_t)t * a.B + a.b0 + b) * a.P + p : gzin, v);
-        }
-      }
-      cp_async_commit();
-    }
-    pending |= 4u;
-  };
-
-  // Wait for barrier i. LDGSTS path: `newer` groups were committed after the awaited one
-  // (waiting for the Z group drains every group, which is correct and only costs overlap).
+  // Wait for barrier i. LDGSTS path: `newer` groups were committed after the awaited one.
   // TMA path: thread 0 alone polls the barrier (the others wait at the block barrier
   // that always follows, which orders the copied data for them).
   auto wait_bar = [&](int i, int newer) -> bool {
@@ -209,20 +221,22 @@ __global__ void __launch_bounds__(kNP* S, S > 1 ? 2 : 4) k_tile(const __grid_con
   };
 
   for (int tile = blockIdx.x; tile < a.n_tiles; tile += gridDim.x) {
-    const int p0 = tile * kNP;
+    const int p0 = tile * NP;
     const int p = p0 + pl;
     const bool act = p < a.P;
-    F* ck = static_cast<F*>(a.ckpt) + (size_t)blockIdx.x * a.nch * kFields * kNP + pl;  // this thread's column
+    // checkpoints: field f of chunk c of this CTA's tile at ck[(c * kFields + f) * NP]
+    F* ck = static_cast<F*>(a.ckpt) + (size_t)blockIdx.x * a.nch * kFields * NP + pl;
 
     // ---------------- pass 1: forward sweep, checkpoints ----------------
-    issue(0, 0, p0, nullptr);
-    if (a.nch > 1) issue(1, 1, p0, nullptr);
+    issue(0, 0, p0, mse);
+    if (a.nch > 1) issue(1, 1, p0, mse);
     SW s;
     s.reset();
     int npos = 0;
     bool bad = false;
     F lam_s = F(0);
     if (a.lam_scalar && act) lam_s = gl[p];
+    F lsum = F(0);  // MSE loss: sum of m (z - target)^2 over this thread's bands
     for (int c = 0; c < a.nch; ++c) {
       const int st = c & 1;
       const bool ok = wait_bar(st, c + 1 < a.nch ? 1 : 0);
@@ -234,36 +248,60 @@ __global__ void __launch_bounds__(kNP* S, S > 1 ? 2 : 4) k_tile(const __grid_con
       if (c == 0) {
 #pragma unroll
         for (int m = 0; m < D; ++m)
-          if (m < T) s.init_weight(m, Sg[(size_t)(rowW + m) * kNP + pl]);
+          if (m < T) s.init_weight(m, Sg[(size_t)(rowW + m) * NP + pl]);
       }
-      F* ckc = ck + (size_t)c * kFields * kNP;
-      if (h == 0) s.save_factor(ckc, kNP);
-      s.save_y(ckc + (size_t)(kFF + h * NBT * D) * kNP, kNP);
+      F* ckc = ck + (size_t)c * kFields * NP;
+      if (h == 0) s.save_factor(ckc, NP);
+      s.save_y(ckc + (size_t)(kFF + h * kYT) * NP, NP);
       const int nd = min(C, T - c * C);
-      const F* Sx = Sg + (size_t)h * NBT * kNP + pl;
-      const F* Sw = Sg + (size_t)rowW * kNP + pl;
-      const F* Sl = Sg + (size_t)rowL * kNP + pl;
-      for (int k = 0; k < nd; ++k, Sx += NB * kNP, Sw += kNP, Sl += kNP) {
+      const F* Sx = Sg + (size_t)h * NBT * NP + pl;
+      const F* Sw = Sg + (size_t)rowW * NP + pl;
+      const F* Sl = Sg + (size_t)rowL * NP + pl;
+      for (int k = 0; k < nd; ++k, Sx += NB * NP, Sw += NP, Sl += NP) {
         const int i = c * C + k;
         const F wi = Sw[0];
-        const F wa = Sw[D * kNP];
+        const F wa = Sw[D * NP];
         const F li = a.lam_scalar ? lam_s : Sl[0];
         const bool has_row = i < T - D;
         bad |= !(wi >= F(0)) || !finite_(wi);
         npos += wi > F(0);
         if (has_row) bad |= !(li > F(0)) || !finite_(li);
         F bv[NBT], rho[D], yh[NBT], invD;
+        const F mk = has_m ? Sg[(size_t)(rowM + k) * NP + pl] : F(1);
 #pragma unroll
         for (int j = 0; j < NBT; ++j) {
-          const F xv = Sx[j * kNP];
+          const F xv = Sx[j * NP];
           bv[j] = MODE == MODE_SMOOTH ? (wi > F(0) ? wi * xv : F(0)) : xv;
+          if (mse) {  // gz = scale m (z - target); masked days are inert whatever the target
+            const F e = mk > F(0) ? Sx[(size_t)rowZ * NP + j * NP] - xv : F(0);
+            bv[j] = mscale * mk * e;
+            lsum = fma(mk * e, e, lsum);
+          }
         }
         s.factor_step(has_row, li, wa, rho, invD);
         s.subst_step(rho, invD, bv, yh);
       }
-      if (c + 2 >= a.nch) fence_proxy_async_global();  // checkpoints are read back by bulk copies
       __syncthreads();
-      if (c + 2 < a.nch) issue(c + 2, st, p0, nullptr);
+      if (c + 2 < a.nch) issue(c + 2, st, p0, mse);
+    }
+
+    // The last two chunks of pass 1 stay resident for pass 2: stage their z now (one
+    // barrier for both), waited for before the first back substitution.
+    if (want_z && !mse) {  // (with the MSE loss pass 1 staged z already)
+      if (a.tma) {
+        if (tid == 0) {
+          mbar_arrive_expect_tx(&bar[2], tz_bytes * (a.nch > 1 ? 2u : 1u));
+          copy_z(a.nch - 1, (a.nch - 1) & 1, p0, &bar[2]);
+          if (a.nch > 1) copy_z(a.nch - 2, (a.nch - 2) & 1, p0, &bar[2]);
+        }
+        pending |= 4u;
+      } else {
+        copy_z(a.nch - 1, (a.nch - 1) & 1, p0, nullptr);
+        if (a.nch > 1) copy_z(a.nch - 2, (a.nch - 2) & 1, p0, nullptr);
+        cp_async_commit();
+        cp_async_wait<0>();
+        __syncthreads();
+      }
     }
 
     // ---------------- pass 2: backward sweep, chunk recompute ----------------
@@ -298,6 +336,16 @@ __global__ void __launch_bounds__(kNP* S, S > 1 ? 2 : 4) k_tile(const __grid_con
     // ADJ with accumulation (refinement correction): largest |correction|, |g| and |D^d g|
     // of this thread's bands, for the settle test of the double-float re-solve
     F dmx = F(0), gmx = F(0), dgmx = F(0);
+    // the next chunk's checkpoint (factor state + this thread's substitution state), loaded
+    // into registers one chunk ahead so that its latency hides behind a chunk of work
+    F pf[kFF + kYT];
+    {
+      const F* ckc = ck + (size_t)(a.nch - 1) * kFields * NP;
+#pragma unroll
+      for (int f = 0; f < kFF; ++f) pf[f] = ckc[(size_t)f * NP];
+#pragma unroll
+      for (int f = 0; f < kYT; ++f) pf[kFF + f] = ckc[(size_t)(kFF + h * kYT + f) * NP];
+    }
     for (int c = a.nch - 1; c >= 0; --c) {
       const int st = c & 1;
       if (c < a.nch - 2) {
@@ -307,37 +355,42 @@ __global__ void __launch_bounds__(kNP* S, S > 1 ? 2 : 4) k_tile(const __grid_con
           return;
         }
       }
-      if (want_z) issue_z(c, p0);
       F* Sg = stage(st);
-      // the chunk's checkpoint: prefetched into the stage by the bulk copy, except for the
-      // two chunks still resident from pass 1 (and on the LDGSTS path)
-      const F* ckc = (a.tma && c < a.nch - 2) ? Sg + (size_t)rowK * kNP + pl : ck + (size_t)c * kFields * kNP;
-      s.load_factor(ckc, kNP);
-      s.load_y(ckc + (size_t)(kFF + h * NBT * D) * kNP, kNP);
+      s.load_factor(pf, 1);
+      s.load_y(pf + kFF, 1);
+      if (c > 0) {
+        const F* ckc = ck + (size_t)(c - 1) * kFields * NP;
+#pragma unroll
+        for (int f = 0; f < kFF; ++f) pf[f] = ckc[(size_t)f * NP];
+#pragma unroll
+        for (int f = 0; f < kYT; ++f) pf[kFF + f] = ckc[(size_t)(kFF + h * kYT + f) * NP];
+      }
       const int nd = min(C, T - c * C);
       {
-        F* Sx = Sg + (size_t)h * NBT * kNP + pl;
-        const F* Sw = Sg + (size_t)rowW * kNP + pl;
-        const F* Sl = Sg + (size_t)rowL * kNP + pl;
-        for (int k = 0; k < nd; ++k, Sx += NB * kNP, Sw += kNP, Sl += kNP) {
+        F* Sx = Sg + (size_t)h * NBT * NP + pl;
+        const F* Sw = Sg + (size_t)rowW * NP + pl;
+        const F* Sl = Sg + (size_t)rowL * NP + pl;
+        for (int k = 0; k < nd; ++k, Sx += NB * NP, Sw += NP, Sl += NP) {
           const int i = c * C + k;
           const F wi = Sw[0];
-          const F wa = Sw[D * kNP];
+          const F wa = Sw[D * NP];
           const F li = a.lam_scalar ? lam_s : Sl[0];
           const bool has_row = i < T - D;
           F bv[NBT], rho[D], yh[NBT], invD;
+          const F mk = has_m ? Sg[(size_t)(rowM + k) * NP + pl] : F(1);
 #pragma unroll
           for (int j = 0; j < NBT; ++j) {
-            const F xv = Sx[j * kNP];
+            const F xv = Sx[j * NP];
             bv[j] = MODE == MODE_SMOOTH ? (wi > F(0) ? wi * xv : F(0)) : xv;
+            if (mse) bv[j] = mscale * mk * (mk > F(0) ? Sx[(size_t)rowZ * NP + j * NP] - xv : F(0));
           }
           s.factor_step(has_row, li, wa, rho, invD);
           s.subst_step(rho, invD, bv, yh);
 #pragma unroll
-          for (int j = 0; j < NBT; ++j) Sx[j * kNP] = yh[j];
+          for (int j = 0; j < NBT; ++j) Sx[j * NP] = yh[j];
           if (h == 0) {
 #pragma unroll
-            for (int j = 1; j <= D; ++j) Sg[(size_t)rho_row(j, k) * kNP + pl] = rho[j - 1];
+            for (int j = 1; j <= D; ++j) Sg[(size_t)rho_row(j, k) * NP + pl] = rho[j - 1];
             if (MODE == MODE_SMOOTH && gf != nullptr && a.write_status && act) {
               gf[((size_t)i * (D + 1)) * a.P + p] = okser ? invD : F(0);
 #pragma unroll
@@ -346,37 +399,38 @@ __global__ void __launch_bounds__(kNP* S, S > 1 ? 2 : 4) k_tile(const __grid_con
           }
         }
       }
-      if (S > 1) __syncthreads();  // rho rows written by the h = 0 threads; w/lambda reads done
-      if (want_z) {
+      if (want_z && !mse && c == a.nch - 1 && a.tma) {  // z of the two chunks resident from pass 1
         const bool ok = wait_bar(2, 0);
         if (__syncthreads_or(!ok)) {
           abort_all();
           return;
         }
+      } else if (S > 1) {
+        __syncthreads();  // rho rows written by the h = 0 threads; w/lambda reads done
       }
       {
-        F* Sx = Sg + (size_t)((nd - 1) * NB + h * NBT) * kNP + pl;
-        const F* Sz = zbuf + (size_t)((nd - 1) * NB + h * NBT) * kNP + pl;
-        for (int k = nd - 1; k >= 0; --k, Sx -= NB * kNP, Sz -= NB * kNP) {
+        F* Sx = Sg + (size_t)((nd - 1) * NB + h * NBT) * NP + pl;
+        const F* Sz = Sg + (size_t)(rowZ + (nd - 1) * NB + h * NBT) * NP + pl;
+        for (int k = nd - 1; k >= 0; --k, Sx -= NB * NP, Sz -= NB * NP) {
           const int i = c * C + k;
           F rho[D];
 #pragma unroll
-          for (int j = 1; j <= D; ++j) rho[j - 1] = Sg[(size_t)rho_row(j, k) * kNP + pl];
+          for (int j = 1; j <= D; ++j) rho[j - 1] = Sg[(size_t)rho_row(j, k) * NP + pl];
           F wk = F(0);
-          if (MODE == MODE_ADJ) wk = Sg[(size_t)(rowW + k) * kNP + pl];
+          if (MODE == MODE_ADJ) wk = Sg[(size_t)(rowW + k) * NP + pl];
           F dl = F(0);
 #pragma unroll
           for (int j = 0; j < NBT; ++j) {
-            F acc = Sx[j * kNP];
+            F acc = Sx[j * NP];
 #pragma unroll
             for (int q = 1; q <= D; ++q) acc = fma(-rho[q - 1], zc[j][q - 1], acc);
 #pragma unroll
             for (int q = D - 1; q > 0; --q) zc[j][q] = zc[j][q - 1];
             zc[j][0] = acc;
             F out = okser ? acc : F(0);
-            if (MODE == MODE_RAW && want_z) out += Sz[j * kNP];  // z0 + correction
+            if (MODE == MODE_RAW && want_z) out += Sz[j * NP];  // z0 + correction
             if (MODE == MODE_ADJ) {
-              const F zv = Sz[j * kNP];
+              const F zv = Sz[j * NP];
               if (a.accum && okser && act)  // g = g0 + correction
                 out += gg0[((size_t)i * a.B + a.b0 + h * NBT + j) * a.P + p];
               F cg = out, cz = zv;           // level q at day t
@@ -404,21 +458,21 @@ __global__ void __launch_bounds__(kNP* S, S > 1 ? 2 : 4) k_tile(const __grid_con
               if (!a.raw_g) out = wk * out;
             }
             nanacc = fma(out, F(0), nanacc);
-            Sx[j * kNP] = out;
+            Sx[j * NP] = out;
           }
-          if (MODE == MODE_ADJ) gbuf[(size_t)(h * C + k) * kNP + pl] = i < T - D ? dl : F(0);
+          if (MODE == MODE_ADJ) gbuf[(size_t)(h * C + k) * NP + pl] = i < T - D ? dl : F(0);
         }
       }
       if (a.tma) fence_proxy_async_smem();
       __syncthreads();
       if (MODE == MODE_ADJ && gout2 != nullptr && h == 0) {
-        const F* Sl = Sg + (size_t)rowL * kNP + pl;
+        const F* Sl = Sg + (size_t)rowL * NP + pl;
         for (int k = 0; k < nd; ++k) {
-          F dl = gbuf[(size_t)k * kNP + pl];
+          F dl = gbuf[(size_t)k * NP + pl];
 #pragma unroll
-          for (int q = 1; q < S; ++q) dl += gbuf[(size_t)(q * C + k) * kNP + pl];
+          for (int q = 1; q < S; ++q) dl += gbuf[(size_t)(q * C + k) * NP + pl];
           F gl_t = okser ? -dl : F(0);
-          if (a.grad_loglam) gl_t *= a.lam_scalar ? lam_s : Sl[(size_t)k * kNP];
+          if (a.grad_loglam) gl_t *= a.lam_scalar ? lam_s : Sl[(size_t)k * NP];
           if (a.lam_scalar) {
             glam_sum += gl_t;
           } else if (act) {
@@ -432,7 +486,7 @@ __global__ void __launch_bounds__(kNP* S, S > 1 ? 2 : 4) k_tile(const __grid_con
 #pragma unroll
           for (int j = 0; j < NBT; ++j) {
             const int b = h * NBT + j;
-            gout[((size_t)(c * C + k) * a.B + a.b0 + b) * a.P + p] = Sg[(size_t)(k * NB + b) * kNP + pl];
+            gout[((size_t)(c * C + k) * a.B + a.b0 + b) * a.P + p] = Sg[(size_t)(k * NB + b) * NP + pl];
           }
       if (MODE == MODE_ADJ || !a.tma) __syncthreads();  // stage reads done before it is refilled
       if (a.tma) {
@@ -443,11 +497,12 @@ __global__ void __launch_bounds__(kNP* S, S > 1 ? 2 : 4) k_tile(const __grid_con
           }
           if (c >= 2) {
             bulk_wait_read_all();
-            issue(c - 2, st, p0, static_cast<const F*>(a.ckpt) + ((size_t)blockIdx.x * a.nch + (c - 2)) * kFields * kNP);
+            issue(c - 2, st, p0, want_z);
           }
         }
+        if (c >= 2) pending |= 1u << st;
       } else if (c >= 2) {
-        issue(c - 2, st, p0, nullptr);
+        issue(c - 2, st, p0, want_z);
       }
     }
     // per-series status; the band halves combine their non-finite flags
@@ -461,12 +516,21 @@ __global__ void __launch_bounds__(kNP* S, S > 1 ? 2 : 4) k_tile(const __grid_con
       unsettled = F(1 << D) * e1 > F(1e-4) * dgmx;
     }
     if (S > 1) {
-      if (h == 1) nflag[pl] = (nonfin ? 1u : 0u) | (unsettled ? 2u : 0u);
+      if (h == 1) {
+        nflag[pl] = (nonfin ? 1u : 0u) | (unsettled ? 2u : 0u);
+        if (mse) gbuf[pl] = lsum;  // (the G region is free once the last chunk is done)
+      }
       __syncthreads();
       if (h == 0) {
         nonfin = nonfin || (nflag[pl] & 1u) != 0u;
         unsettled = unsettled || (nflag[pl] & 2u) != 0u;
+        if (mse) lsum += gbuf[pl];
       }
+    }
+    if (mse && a.loss != nullptr && act && h == 0) {
+      F* lp = static_cast<F*>(a.loss) + p;
+      const F v = F(0.5) * mscale * lsum;
+      *lp = a.b0 == 0 ? v : *lp + v;
     }
     if (MODE == MODE_ADJ && unsettled && okser && act && h == 0 && atomicExch(a.df_mark + p, 1u) == 0u)
       a.df_list[atomicAdd(a.df_count, 1u)] = p;
@@ -484,78 +548,99 @@ __global__ void __launch_bounds__(kNP* S, S > 1 ? 2 : 4) k_tile(const __grid_con
   if (a.tma && tid == 0) bulk_wait_all();
 }
 
-template <typename F, int D, int NBT, int S, int MODE>
+template <typename F, int D, int NBT, int S, int MODE, int NP>
 int launch_tile_one(const TileCfg& cfg, const TileArgs& a, const CUtensorMap* maps, cudaStream_t st) {
-  auto kern = k_tile<F, D, NBT, S, MODE>;
+  auto kern = k_tile<F, D, NBT, S, MODE, NP>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cfg.smem_bytes);
   if (e != cudaSuccess) return set_error(WS_ECUDA, "cudaFuncSetAttribute: %s", cudaGetErrorString(e));
-  kern<<<cfg.grid, kNP * S, cfg.smem_bytes, st>>>(maps[0], maps[1], maps[2], maps[3], maps[4], a);
+  kern<<<cfg.grid, NP * S, cfg.smem_bytes, st>>>(maps[0], maps[1], maps[2], maps[3], maps[4], maps[5], a);
   e = cudaGetLastError();
   if (e != cudaSuccess) return set_error(WS_ECUDA, "tile kernel launch: %s", cudaGetErrorString(e));
   return WS_OK;
 }
 
-template <typename F, int D, int MODE>
-int dispatch_tile_nb(int nb, const TileCfg& cfg, const TileArgs& a, const CUtensorMap* maps, cudaStream_t st) {
-  if (sizeof(F) == 8) {
-    if (nb == 2 && D == 2) return launch_tile_one<F, D, 2, 1, MODE>(cfg, a, maps, st);
-    if (nb == 1) return launch_tile_one<F, D, 1, 1, MODE>(cfg, a, maps, st);
-    return set_error(WS_EUNSUPPORTED, "FP64 band group of %d bands not instantiated", nb);
-  }
+// Kernel of a band group: FP32 groups of 1..10 bands (6, 8, 10 with two threads per pixel)
+// at 128 or 64 pixels per CTA; FP64 groups of 1 band (2 for d = 2) at 128 pixels.
+template <typename F, int D, int MODE, int NP>
+const void* kernel_ptr_np(int nb) {
+  if constexpr (sizeof(F) == 8) {
+    if constexpr (NP != 128) {
+      return nullptr;
+    } else {
+      if (nb == 2 && D == 2) return (const void*)k_tile<F, D, 2, 1, MODE, NP>;
+      if (nb == 1) return (const void*)k_tile<F, D, 1, 1, MODE, NP>;
+      return nullptr;
+    }
+  } else {
   switch (nb) {
-    case 1: return launch_tile_one<F, D, 1, 1, MODE>(cfg, a, maps, st);
-    case 2: return launch_tile_one<F, D, 2, 1, MODE>(cfg, a, maps, st);
-    case 4: return launch_tile_one<F, D, 4, 1, MODE>(cfg, a, maps, st);
+    case 1: return (const void*)k_tile<F, D, 1, 1, MODE, NP>;
+    case 2: return (const void*)k_tile<F, D, 2, 1, MODE, NP>;
+    case 4: return (const void*)k_tile<F, D, 4, 1, MODE, NP>;
 #ifndef WS_FAST_BUILD
-    case 3: return launch_tile_one<F, D, 3, 1, MODE>(cfg, a, maps, st);
-    case 5: return launch_tile_one<F, D, 5, 1, MODE>(cfg, a, maps, st);
-    case 6: return launch_tile_one<F, D, 3, 2, MODE>(cfg, a, maps, st);
-    case 7: return launch_tile_one<F, D, 7, 1, MODE>(cfg, a, maps, st);
-    case 8: return launch_tile_one<F, D, 4, 2, MODE>(cfg, a, maps, st);
-    case 9: return launch_tile_one<F, D, 9, 1, MODE>(cfg, a, maps, st);
-    case 10: return launch_tile_one<F, D, 5, 2, MODE>(cfg, a, maps, st);
-#endif
-    default: return set_error(WS_EUNSUPPORTED, "band group of %d bands not instantiated", nb);
-  }
-}
-
-template <typename F, int D, int MODE>
-const void* kernel_ptr_nb(int nb) {
-  if (sizeof(F) == 8) {
-    if (nb == 2 && D == 2) return (const void*)k_tile<F, D, 2, 1, MODE>;
-    if (nb == 1) return (const void*)k_tile<F, D, 1, 1, MODE>;
-    return nullptr;
-  }
-  switch (nb) {
-    case 1: return (const void*)k_tile<F, D, 1, 1, MODE>;
-    case 2: return (const void*)k_tile<F, D, 2, 1, MODE>;
-    case 4: return (const void*)k_tile<F, D, 4, 1, MODE>;
-#ifndef WS_FAST_BUILD
-    case 3: return (const void*)k_tile<F, D, 3, 1, MODE>;
-    case 5: return (const void*)k_tile<F, D, 5, 1, MODE>;
-    case 6: return (const void*)k_tile<F, D, 3, 2, MODE>;
-    case 7: return (const void*)k_tile<F, D, 7, 1, MODE>;
-    case 8: return (const void*)k_tile<F, D, 4, 2, MODE>;
-    case 9: return (const void*)k_tile<F, D, 9, 1, MODE>;
-    case 10: return (const void*)k_tile<F, D, 5, 2, MODE>;
+    case 3: return (const void*)k_tile<F, D, 3, 1, MODE, NP>;
+    case 5: return (const void*)k_tile<F, D, 5, 1, MODE, NP>;
+    case 6: return (const void*)k_tile<F, D, 3, 2, MODE, NP>;
+    case 7: return (const void*)k_tile<F, D, 7, 1, MODE, NP>;
+    case 8: return (const void*)k_tile<F, D, 4, 2, MODE, NP>;
+    case 9: return (const void*)k_tile<F, D, 9, 1, MODE, NP>;
+    case 10: return (const void*)k_tile<F, D, 5, 2, MODE, NP>;
 #endif
   }
   return nullptr;
+  }
+}
+
+template <typename F, int D, int MODE, int NP>
+int dispatch_tile_np(int nb, const TileCfg& cfg, const TileArgs& a, const CUtensorMap* maps, cudaStream_t st) {
+  if constexpr (sizeof(F) == 8) {
+    if constexpr (NP == 128) {
+      if (nb == 2 && D == 2) return launch_tile_one<F, D, 2, 1, MODE, NP>(cfg, a, maps, st);
+      if (nb == 1) return launch_tile_one<F, D, 1, 1, MODE, NP>(cfg, a, maps, st);
+    }
+    return set_error(WS_EUNSUPPORTED, "FP64 band group of %d bands at %d pixels per CTA not instantiated", nb, NP);
+  } else {
+  switch (nb) {
+    case 1: return launch_tile_one<F, D, 1, 1, MODE, NP>(cfg, a, maps, st);
+    case 2: return launch_tile_one<F, D, 2, 1, MODE, NP>(cfg, a, maps, st);
+    case 4: return launch_tile_one<F, D, 4, 1, MODE, NP>(cfg, a, maps, st);
+#ifndef WS_FAST_BUILD
+    case 3: return launch_tile_one<F, D, 3, 1, MODE, NP>(cfg, a, maps, st);
+    case 5: return launch_tile_one<F, D, 5, 1, MODE, NP>(cfg, a, maps, st);
+    case 6: return launch_tile_one<F, D, 3, 2, MODE, NP>(cfg, a, maps, st);
+    case 7: return launch_tile_one<F, D, 7, 1, MODE, NP>(cfg, a, maps, st);
+    case 8: return launch_tile_one<F, D, 4, 2, MODE, NP>(cfg, a, maps, st);
+    case 9: return launch_tile_one<F, D, 9, 1, MODE, NP>(cfg, a, maps, st);
+    case 10: return launch_tile_one<F, D, 5, 2, MODE, NP>(cfg, a, maps, st);
+#endif
+    default: return set_error(WS_EUNSUPPORTED, "band group of %d bands not instantiated", nb);
+  }
+  }
+}
+
+template <typename F, int D, int MODE>
+const void* kernel_ptr_nb(int nb, int np) {
+  return np == 64 ? kernel_ptr_np<F, D, MODE, 64>(nb) : kernel_ptr_np<F, D, MODE, 128>(nb);
+}
+
+template <typename F, int D, int MODE>
+int dispatch_tile_nb(int nb, const TileCfg& cfg, const TileArgs& a, const CUtensorMap* maps, cudaStream_t st) {
+  return cfg.NP == 64 ? dispatch_tile_np<F, D, MODE, 64>(nb, cfg, a, maps, st)
+                      : dispatch_tile_np<F, D, MODE, 128>(nb, cfg, a, maps, st);
 }
 
 template <int D>
-const void* tile_kernel_ptr_t(const ws_problem& pb, int mode, int nb) {
+const void* tile_kernel_ptr_t(const ws_problem& pb, int mode, int nb, int np) {
   if (pb.dtype == WS_F32) {
     switch (mode) {
-      case MODE_SMOOTH: return kernel_ptr_nb<float, D, MODE_SMOOTH>(nb);
-      case MODE_RAW: return kernel_ptr_nb<float, D, MODE_RAW>(nb);
-      case MODE_ADJ: return kernel_ptr_nb<float, D, MODE_ADJ>(nb);
+      case MODE_SMOOTH: return kernel_ptr_nb<float, D, MODE_SMOOTH>(nb, np);
+      case MODE_RAW: return kernel_ptr_nb<float, D, MODE_RAW>(nb, np);
+      case MODE_ADJ: return kernel_ptr_nb<float, D, MODE_ADJ>(nb, np);
     }
   } else {
     switch (mode) {
-      case MODE_SMOOTH: return kernel_ptr_nb<double, D, MODE_SMOOTH>(nb);
-      case MODE_RAW: return kernel_ptr_nb<double, D, MODE_RAW>(nb);
-      case MODE_ADJ: return kernel_ptr_nb<double, D, MODE_ADJ>(nb);
+      case MODE_SMOOTH: return kernel_ptr_nb<double, D, MODE_SMOOTH>(nb, np);
+      case MODE_RAW: return kernel_ptr_nb<double, D, MODE_RAW>(nb, np);
+      case MODE_ADJ: return kernel_ptr_nb<double, D, MODE_ADJ>(nb, np);
     }
   }
   return nullptr;

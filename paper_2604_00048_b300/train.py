@@ -3,8 +3,8 @@
 Training step (all arithmetic in the library's kernels; this module only sequences calls):
     lambda, log lambda = g_theta(x, w)                          ws_tcn_forward (training)
     z = (W + D^T Lambda D)^{-1} W x                             ws_smooth_batch
-    L = mean_t,s (z - clean)^2,  dL/dz                          ws_mse_grad
-    dL/dlog lambda                                              ws_solve_adjoint (Eqs. 4-5)
+    L = mean_t,s (z - clean)^2, dL/dz, dL/dlog lambda          ws_solve_adjoint_mse (the loss
+                                                                fused into the adjoint, Eqs. 4-5)
     dL/dtheta                                                   ws_tcn_backward
     theta <- Adam(theta, dL/dtheta)                             ws_adam_step, ws_tcn_pack
 The clean signal is known because the series are synthetic (the paper trains on masked
@@ -60,15 +60,16 @@ def batch(rc: synth.Recipe, first: int, n: int, device="cuda"):
 
 
 def train_step(net: "ws.Tcn", x, w, clean, lr: float, d: int = 2):
-    """One Adam step on one batch; returns the batch loss (mean squared error to clean)."""
+    """One Adam step on one batch; returns the batch loss (mean squared error to clean, as
+    a one-element tensor). The loss and its gradient are formed inside the adjoint's sweeps
+    (ws_solve_adjoint_mse): dL/dz is never written to memory."""
     lam, _ = net.forward(x[:, 0, :], w, training=True, want_loglam=False)
     z, _ = ws.smooth(x, w, lam, d)
-    loss = torch.zeros(1, device=x.device)
-    gz = ws.mse_grad(z[:, 0, :].contiguous(), clean, 2.0 / clean.numel(), loss)
-    _, glam, _ = ws.smooth_adjoint(w, lam, z, gz[:, None, :].contiguous(), d, want_gx=False, log_lambda=True)
+    _, glam, loss, _ = ws.smooth_adjoint_mse(w, lam, z, clean[:, None, :], d, scale=2.0 / clean.numel(),
+                                             want_gx=False, log_lambda=True)
     net.backward(glam)
     net.step(lr)
-    return loss
+    return loss.sum().reshape(1)
 
 
 def learned_smooth(net: "ws.Tcn", x, w, d: int = 2, refine: bool = False):

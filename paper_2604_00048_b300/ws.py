@@ -80,6 +80,11 @@ _lib.ws_smooth_batch_noalloc.argtypes = [_PP, _vp, _vp, _vp, _vp, _vp, _vp, _u32
 NOALLOC_MAX_BYTES = 64 << 20
 _lib.ws_tune_set.restype = ctypes.c_int
 _lib.ws_tune_set.argtypes = [ctypes.c_int32, ctypes.c_int32]
+_lib.ws_solve_adjoint_mse.restype = ctypes.c_int
+_lib.ws_solve_adjoint_mse.argtypes = [ctypes.POINTER(Problem)] + [ctypes.c_void_p] * 5 + [ctypes.c_double] + \
+    [ctypes.c_void_p] * 3 + [ctypes.c_uint32, ctypes.c_void_p, ctypes.c_void_p, _sz, ctypes.c_void_p]
+_lib.ws_tune_pixels_per_cta.restype = ctypes.c_int
+_lib.ws_tune_pixels_per_cta.argtypes = [ctypes.c_int32]
 _lib.ws_selftest_wait.restype = ctypes.c_int
 _lib.ws_selftest_wait.argtypes = [_vp, _sz, _vp]
 _lib.ws_sync_status.restype = ctypes.c_int
@@ -387,6 +392,37 @@ def smooth_adjoint(w: torch.Tensor, lam: torch.Tensor, z: torch.Tensor, gz: torc
     return gx, glam, status
 
 
+
+def smooth_adjoint_mse(w: torch.Tensor, lam: torch.Tensor, z: torch.Tensor, target: torch.Tensor, d: int = 2, *,
+                       mask=None, scale: float = 1.0, gx=None, glam=None, loss=None, want_gx: bool = True,
+                       want_glam: bool = True, want_loss: bool = True, log_lambda: bool = False, status=None,
+                       stream=None, workspace_buf=None):
+    """Adjoint of the masked MSE loss L_p = scale/2 sum m (z - target)^2 with the loss gradient
+    formed inside the kernel (Section 4.3; Eqs. 4-5): returns (gx, glam, loss [P], status)."""
+    T, B, P, lm = _check_tile(target, w, lam, d)
+    if tuple(z.shape) != tuple(target.shape) or not z.is_contiguous() or z.dtype != target.dtype:
+        raise ValueError("z must match target")
+    _check_out(mask, (T, P), target.dtype, target.device, "mask")
+    _check_out(gx, target.shape, target.dtype, target.device, "gx")
+    _check_out(glam, lam.shape, target.dtype, target.device, "glam")
+    _check_out(loss, (P,), target.dtype, target.device, "loss")
+    _check_out(status, (P,), torch.uint8, target.device, "status")
+    pb = make_problem(T, B, P, d, _dtype_code(target), lm)
+    if gx is None and want_gx:
+        gx = torch.empty_like(target)
+    if glam is None and want_glam:
+        glam = torch.empty_like(lam)
+    if loss is None and want_loss:
+        loss = torch.empty(P, dtype=target.dtype, device=target.device)
+    if status is None:
+        status = torch.empty(P, dtype=torch.uint8, device=target.device)
+    ws = workspace(pb, target.device, 0, workspace_buf)
+    flags = GRAD_LOGLAM if log_lambda else 0
+    _check(_lib.ws_solve_adjoint_mse(ctypes.byref(pb), _ptr(w), _ptr(lam), _ptr(z), _ptr(target), _ptr(mask),
+                                     float(scale), _ptr(gx), _ptr(glam), _ptr(loss), flags, _ptr(status), _ptr(ws),
+                                     ws.numel(), _stream_ptr(stream)))
+    return gx, glam, loss, status
+
 DATES = 0x40
 
 
@@ -511,9 +547,11 @@ def solve(fac: torch.Tensor, w: torch.Tensor, x: torch.Tensor, d: int = 2, *, z=
     return z
 
 
-def tune_set(ctas_per_sm: int = 0, chunk_days: int = 0):
-    """Process-wide tile tuning knobs (0 = automatic): CTAs per SM and a chunk-size cap."""
+def tune_set(ctas_per_sm: int = 0, chunk_days: int = 0, pixels_per_cta: int = 0):
+    """Process-wide tile tuning knobs (0 = automatic): CTAs per SM, a chunk-size cap and
+    the pixel series per CTA (64 or 128)."""
     _check(_lib.ws_tune_set(int(ctas_per_sm), int(chunk_days)))
+    _check(_lib.ws_tune_pixels_per_cta(int(pixels_per_cta)))
 
 
 def sync_status(device=None, stream=None):
