@@ -51,9 +51,10 @@ def parse_args():
     ap.add_argument("--no-posterior", action="store_true")
     ap.add_argument("--no-wgrad", action="store_true")
     ap.add_argument("--no-dates", action="store_true")
+    ap.add_argument("--no-partitioned", action="store_true")
     ap.add_argument("--tcn-ckpt", default=None, help="trained lambda network (else one epoch is trained first)")
     ap.add_argument("--train-epochs", type=float, default=1.0, help="epochs of lambda-network training before timing")
-    ap.add_argument("--only", choices=["gcv", "learned", "ragged", "posterior", "dates"], default=None,
+    ap.add_argument("--only", choices=["gcv", "learned", "ragged", "posterior", "dates", "partitioned"], default=None,
                     help="run one secondary measurement alone (profiling) and print it")
     ap.add_argument("--series", type=int, default=None, help="series of the --only measurement")
     ap.add_argument("--days", type=int, default=None, help="days of the --only posterior measurement (profiling)")
@@ -467,6 +468,49 @@ def posterior_measure(dev, steps, x=None, w=None, lam=None, z=None, P=262144, T=
     return res
 
 
+def partitioned_measure(dev, steps, P=64):
+    """Few long series: P series of the heteroscedastic tile (3288 days, 10 bands, d = 2)
+    smoothed by the partitioned parallel-in-time solve (double-float, no refinement step
+    needed) against the one-series-per-thread tile path with its refinement step (the
+    FP32 path's accuracy contract at lambda up to 1e5); both timed with CUDA events."""
+    import torch
+
+    from paper_2604_00048_b300 import synth, ws
+
+    rc = synth.RECIPES["hetero_tile"]
+    out = synth.generate_tile(rc, P, device=dev)
+    x, w, lam = out["x"], out["w"], out["lam"]
+    z = torch.empty_like(x)
+    st = torch.empty(P, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.Stream(device=dev)
+
+    def timed(fn):
+        with torch.cuda.stream(stream):
+            for _ in range(3):
+                fn()
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(max(5, steps)):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            with torch.cuda.stream(stream):
+                fn()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        return statistics.median(ts), min(ts)
+
+    ms_p, best_p = timed(lambda: ws.smooth_partitioned(x, w, lam, rc.d, z=z, status=st, stream=stream))
+    zp = z.clone()
+    ms_t, best_t = timed(lambda: ws.smooth(x, w, lam, rc.d, z=z, status=st, refine=True, stream=stream))
+    ws.sync_status(dev, stream)
+    rel = float(((zp - z).abs().amax(dim=0) / z.abs().amax(dim=0).clamp_min(1e-6)).max())
+    return {"workload": f"partitioned: {P} series x {rc.T} days x {rc.n_bands} bands, d={rc.d}, FP32 in/out",
+            "partitioned_ms": ms_p, "partitioned_best_ms": best_p, "tile_refined_ms": ms_t,
+            "tile_refined_best_ms": best_t, "speedup_vs_tile": ms_t / ms_p,
+            "max_rel_diff_vs_tile": rel, "series_with_status": int((st != 0).sum().item())}
+
+
 def learned_measure(dev, steps, ckpt=None, train_epochs=1.0, P=262144):
     """Learned lambda vs the GCV grid on the evaluation set (262,144 new series x 730 days,
     d = 2, one band): the lambda network is trained first on the project's kernels (one
@@ -577,6 +621,8 @@ def run_only(args):
         res = posterior_measure(dev, steps, P=args.series or 262144, T=args.days)
     elif args.only == "learned":
         res = learned_measure(dev, steps, args.tcn_ckpt, args.train_epochs, args.series or 262144)
+    elif args.only == "partitioned":
+        res = partitioned_measure(dev, steps, args.series or 64)
     else:
         res = ragged_measure(dev, steps, args.series or (1 << 20))
     print(json.dumps({"only": args.only, **res}), flush=True)
@@ -765,6 +811,7 @@ def run_ours(args):
     dates = None if args.no_dates else dates_measure(dev, max(3, args.steps))
     gcv = None if args.no_gcv else gcv_measure(dev, max(3, args.steps))
     learned = None if args.no_learned else learned_measure(dev, max(3, args.steps), args.tcn_ckpt, args.train_epochs)
+    partitioned = None if args.no_partitioned else partitioned_measure(dev, max(5, args.steps))
     line = {"metric": METRIC, "value": value, "unit": "series/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
@@ -773,7 +820,7 @@ def run_ours(args):
             "fwd_unrefined_series_per_s": P * world / (fwd_ms / 1e3),
             "smooth_ms": fwd_ms, "refine_ms": ref_ms, "adjoint_ms": bwd_ms,
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "ragged": ragged, "gcv": gcv, "learned": learned,
-            "posterior": posterior, "weight_grad": wgrad, "dates": dates,
+            "posterior": posterior, "weight_grad": wgrad, "dates": dates, "partitioned": partitioned,
             "gpu_launches": launches_per_step * args.steps, "clocks": ck,
             "series_with_status": bad}
     if rank == 0:

@@ -84,6 +84,7 @@ extern "C" {
 #define WS_REFINE_ADJOINT 0x4u /* ws_solve_adjoint: one step of iterative refinement of g */
 #define WS_POSTERIOR 0x10u     /* ws_workspace_size: size for ws_posterior */
 #define WS_DATES 0x40u         /* ws_workspace_size: size for ws_smooth_dates */
+#define WS_PARTITIONED 0x80u   /* ws_workspace_size: size for ws_smooth_partitioned */
 #define WS_ADJ_RAW_G 0x20u     /* ws_solve_adjoint: gx receives g = Omega^{-1} gz itself (not W g),
                                   the input of ws_weight_grad */
 
@@ -335,6 +336,24 @@ int ws_solve_adjoint(const ws_problem* pb, const void* factor_or_null, const voi
                      const void* lam, const void* z, const void* gz, void* gx, void* glam,
                      uint32_t flags, uint8_t* status, void* workspace, size_t ws_bytes,
                      void* stream);
+
+/* z = Omega^{-1} W x (Eq. 3) by a partitioned parallel-in-time solve, for few long series
+ * (Section 2.3's cost argument: with one series per thread, a handful of series keep a
+ * handful of threads busy). Each series' days are cut into domains of 16, 32 or 64 days
+ * (the largest that still gives the GPU about 9,500 threads; one domain if T <= 64); the
+ * last d days of each domain but the last are a separator. One thread per (series,
+ * domain) factors its interior band (LDL^T of Omega assembled from w and lambda) and forms
+ * its Schur-complement pieces; one thread per series factors the separators'
+ * block-tridiagonal Schur complement and one per (series, band) solves it; one per
+ * (series, domain) then finishes its interior. Arithmetic: double-float (hi + lo FP32
+ * pairs, about 48 bits) for FP32 data, FP64 for FP64 data, so no refinement step is
+ * needed. Same layout, arguments, status codes and zero-filled outputs as ws_smooth_batch
+ * (flags: none). workspace: ws_workspace_size(pb, WS_PARTITIONED) bytes, 256-byte aligned
+ * (else WS_EINVAL / WS_ENOMEM_WS before any launch); contents need no initialisation.
+ * Per series it moves a few hundred bytes of scratch per day, so it suits up to a few
+ * thousand series; beyond that ws_smooth_batch is faster. */
+int ws_smooth_partitioned(const ws_problem* pb, const void* x, const void* w, const void* lam, void* z,
+                          uint8_t* status, void* workspace, size_t ws_bytes, void* stream);
 
 /* The adjoint of Section 4.3's training loss with the loss fused into its sweeps: the
  * masked mean squared error of the smooth z against held-out targets,

@@ -341,6 +341,7 @@ extern "C" size_t ws_workspace_size(const ws_problem* pb, uint32_t flags) {
     dck = std::max(dck, dck2);
     need = std::max(need, kHeaderBytes + round256(dck) + ((flags & WS_REFINE) ? resid_bytes(*pb) : 0));
   }
+  if (flags & WS_PARTITIONED) need = std::max(need, kHeaderBytes + part_workspace_bytes(*pb));
   if (flags & WS_POSTERIOR) {
     size_t pck = 0;
     if (post_bytes(*pb, pck) != WS_OK) return 0;
@@ -753,6 +754,32 @@ extern "C" int ws_solve_adjoint_mse(const ws_problem* pb, const void* w, const v
   const AdjMse m{mask, scale, loss};
   return run_tile(P, MODE_ADJ, target, w, lam, z, nullptr, gx, glam, nullptr, status, 0, adj, workspace, st, nullptr,
                   &m);
+}
+
+extern "C" int ws_smooth_partitioned(const ws_problem* pb, const void* x, const void* w, const void* lam, void* z,
+                                     uint8_t* status, void* workspace, size_t ws_bytes, void* stream) {
+  clear_error();
+  int rc = validate_problem(pb);
+  if (rc != WS_OK) return rc;
+  const ws_problem& P = *pb;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (P.n_series == 0) return WS_OK;
+  if (P.T == 0) {
+    if (status != nullptr && cudaMemsetAsync(status, 0, (size_t)P.n_series, st) != cudaSuccess)
+      return set_error(WS_ECUDA, "status memset failed");
+    return WS_OK;
+  }
+  if (!x || !w || !lam || !z) return set_error(WS_EINVAL, "x, w, lam and z must be non-NULL");
+  const int es = elem_size(P);
+  const size_t nx = (size_t)P.T * P.n_bands * P.n_series * es, nd = (size_t)P.T * P.n_series * es;
+  const size_t nl = P.lam_mode == WS_LAM_SCALAR ? (size_t)P.n_series * es : nd;
+  if (overlaps(z, nx, x, nx) || overlaps(z, nx, w, nd) || overlaps(z, nx, lam, nl))
+    return set_error(WS_EINVAL, "z must not overlap the inputs");
+  const size_t need = kHeaderBytes + part_workspace_bytes(P);
+  if (workspace == nullptr || (reinterpret_cast<uintptr_t>(workspace) & 255u) != 0)
+    return set_error(WS_EINVAL, "workspace must be non-NULL and 256-byte aligned");
+  if (ws_bytes < need) return set_error(WS_ENOMEM_WS, "workspace too small: %zu < %zu", ws_bytes, need);
+  return launch_partitioned(P, x, w, lam, z, status, static_cast<char*>(workspace) + kHeaderBytes, st);
 }
 
 extern "C" int ws_tune_pixels_per_cta(int32_t pixels) {

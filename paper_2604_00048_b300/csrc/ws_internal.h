@@ -151,6 +151,10 @@ size_t adj_df_bytes(const ws_problem& pb);
 void adj_df_layout(const ws_problem& pb, void* base, unsigned** mark, unsigned** count, int** list, char** slots);
 int launch_adj_df(const ws_problem& pb, const void* gz, const void* w, const void* lam, const void* z, void* gx,
                   void* glam, int adj_flags, void* base, cudaStream_t st);
+// Partitioned parallel-in-time solve (ws_part.cu): scratch bytes and launch.
+size_t part_workspace_bytes(const ws_problem& pb);
+int launch_partitioned(const ws_problem& pb, const void* x, const void* w, const void* lam, void* z, uint8_t* status,
+                       void* scratch, cudaStream_t st);
 // raw = 0: r = W x - Omega z0; raw = 1: r = x - Omega z0. err: the workspace's device
 // error word (set when a staging wait gives up).
 int launch_residual(const ws_problem& pb, const void* x, const void* w, const void* lam, const void* z0,

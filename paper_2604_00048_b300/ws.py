@@ -83,6 +83,8 @@ _lib.ws_tune_set.argtypes = [ctypes.c_int32, ctypes.c_int32]
 _lib.ws_solve_adjoint_mse.restype = ctypes.c_int
 _lib.ws_solve_adjoint_mse.argtypes = [ctypes.POINTER(Problem)] + [ctypes.c_void_p] * 5 + [ctypes.c_double] + \
     [ctypes.c_void_p] * 3 + [ctypes.c_uint32, ctypes.c_void_p, ctypes.c_void_p, _sz, ctypes.c_void_p]
+_lib.ws_smooth_partitioned.restype = ctypes.c_int
+_lib.ws_smooth_partitioned.argtypes = [ctypes.POINTER(Problem)] + [ctypes.c_void_p] * 6 + [_sz, ctypes.c_void_p]
 _lib.ws_tune_pixels_per_cta.restype = ctypes.c_int
 _lib.ws_tune_pixels_per_cta.argtypes = [ctypes.c_int32]
 _lib.ws_selftest_wait.restype = ctypes.c_int
@@ -358,6 +360,27 @@ def refine(x: torch.Tensor, w: torch.Tensor, lam: torch.Tensor, z: torch.Tensor,
     _check(_lib.ws_refine(ctypes.byref(pb), _ptr(x), _ptr(w), _ptr(lam), _ptr(z), _ptr(ws), ws.numel(),
                           _stream_ptr(stream)))
     return z
+
+
+PARTITIONED = 0x80
+
+
+def smooth_partitioned(x: torch.Tensor, w: torch.Tensor, lam: torch.Tensor, d: int = 2, *, z=None, status=None,
+                       stream=None, workspace_buf=None):
+    """z = Omega^{-1} W x by the partitioned parallel-in-time solve (few long series):
+    returns (z, status), tile layout as smooth()."""
+    T, B, P, lm = _check_tile(x, w, lam, d)
+    _check_out(z, x.shape, x.dtype, x.device, "z")
+    _check_out(status, (P,), torch.uint8, x.device, "status")
+    pb = make_problem(T, B, P, d, _dtype_code(x), lm)
+    if z is None:
+        z = torch.empty_like(x)
+    if status is None:
+        status = torch.empty(P, dtype=torch.uint8, device=x.device)
+    ws = workspace(pb, x.device, PARTITIONED, workspace_buf)
+    _check(_lib.ws_smooth_partitioned(ctypes.byref(pb), _ptr(x), _ptr(w), _ptr(lam), _ptr(z), _ptr(status),
+                                      _ptr(ws), ws.numel(), _stream_ptr(stream)))
+    return z, status
 
 
 def smooth_adjoint(w: torch.Tensor, lam: torch.Tensor, z: torch.Tensor, gz: torch.Tensor, d: int = 2, *,
