@@ -178,6 +178,46 @@ def max_over_ranks(ms: float, device) -> float:
     return float(tt.item())
 
 
+def pinned_copy_gbs(dev, nbytes=1 << 30, reps=5):
+    """Plain pinned host <-> device copy bandwidth (GB/s): host-to-device alone,
+    device-to-host alone, and both directions at once on two streams (the link's
+    full-duplex rate), best of `reps`: the denominator of the end-to-end copies."""
+    import torch
+
+    h1 = torch.empty(nbytes, dtype=torch.uint8).pin_memory()
+    h2 = torch.empty(nbytes, dtype=torch.uint8).pin_memory()
+    d1 = torch.empty(nbytes, dtype=torch.uint8, device=dev)
+    d2 = torch.empty(nbytes, dtype=torch.uint8, device=dev)
+    s1, s2 = torch.cuda.Stream(device=dev), torch.cuda.Stream(device=dev)
+
+    def best(fn):
+        ts = []
+        for _ in range(reps):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            fn()
+            torch.cuda.synchronize()
+            ts.append(time.perf_counter() - t0)
+        return min(ts)
+
+    def h2d():
+        with torch.cuda.stream(s1):
+            d1.copy_(h1, non_blocking=True)
+
+    def d2h():
+        with torch.cuda.stream(s2):
+            h2.copy_(d2, non_blocking=True)
+
+    def both():
+        h2d()
+        d2h()
+
+    t_h, t_d, t_b = best(h2d), best(d2h), best(both)
+    del h1, h2, d1, d2
+    return {"h2d_gbs": nbytes / t_h / 1e9, "d2h_gbs": nbytes / t_d / 1e9, "bidirectional_gbs": 2 * nbytes / t_b / 1e9,
+            "bytes": nbytes}
+
+
 def aggregate_rate(per_rank: int, world: int, steps: int, ms: float) -> float:
     """Whole-job throughput: the series of all ranks over the slowest rank's time."""
     return per_rank * world * steps / (ms / 1e3)
@@ -190,30 +230,43 @@ def dist_env():
     return rank, world, local
 
 
+NOMINAL_HBM_GBS = 7700.0  # B300 HBM3e nominal bandwidth (context beside the measured peak)
+CPU_SAMPLE = 512  # series of the oracle's timed sample, the same in both arms
+
+
+def cpu_oracle_runs(x, w, lam, gz, d, runs, warmup=1, with_bwd=True):
+    """Banded FP64 oracle (Algorithm 1, OpenMP over pixels) on one contiguous sample of
+    series (tile layout [T][B][n], the same arrays in both arms of the bench): `warmup`
+    untimed runs, then `runs` timed runs of smooth (+ adjoint). Returns the run times (s)."""
+    from oracle import banded
+
+    times = []
+    for i in range(warmup + runs):
+        t0 = time.perf_counter()
+        z, _ = banded.smooth_tile(x, w, lam, d)
+        if with_bwd:
+            banded.vjp_tile(w, lam, d, z, gz, log_lambda=True)
+        if i >= warmup:
+            times.append(time.perf_counter() - t0)
+    return times
+
+
 def cpu_oracle_rate(x, w, lam, gz, d, target_s, with_bwd=True):
-    """Banded FP64 oracle (Algorithm 1, OpenMP over pixels) on a bounded pixel sample:
-    returns (series/s, cores, sample description)."""
+    """The oracle's rate on the first CPU_SAMPLE series (contiguous copies), repeated until
+    about target_s seconds of timed work: returns (series/s, cores, sample description)."""
     import numpy as np
 
     from oracle import banded
 
     cores = banded.max_threads()
-    P = x.shape[2]
-    n = min(P, 64)
-    t0 = time.perf_counter()
-    z, _ = banded.smooth_tile(x[:, :, :n], w[:, :n], lam[:, :n], d)
-    if with_bwd:
-        banded.vjp_tile(w[:, :n], lam[:, :n], d, z, gz[:, :, :n], log_lambda=True)
-    dt = time.perf_counter() - t0
-    n2 = int(min(P, max(n, n * target_s / max(dt, 1e-3))))
-    if n2 > n:
-        t0 = time.perf_counter()
-        z, _ = banded.smooth_tile(x[:, :, :n2], w[:, :n2], lam[:, :n2], d)
-        if with_bwd:
-            banded.vjp_tile(w[:, :n2], lam[:, :n2], d, z, gz[:, :, :n2], log_lambda=True)
-        dt = time.perf_counter() - t0
-        n = n2
-    return n / dt, cores, f"{n} of the tile's series (all {x.shape[0]} days, {x.shape[1]} bands), FP64"
+    n = min(x.shape[2], CPU_SAMPLE)
+    xs, wsn, ls, gs = (np.ascontiguousarray(a[..., :n]) for a in (x, w, lam, gz))
+    t1 = cpu_oracle_runs(xs, wsn, ls, gs, d, 1, warmup=1, with_bwd=with_bwd)[0]
+    runs = int(max(1, min(20, target_s / max(t1, 1e-3))))
+    times = cpu_oracle_runs(xs, wsn, ls, gs, d, runs, warmup=0, with_bwd=with_bwd)
+    return n * len(times) / sum(times), cores, (
+        f"{n} of the tile's series (all {x.shape[0]} days, {x.shape[1]} bands, contiguous), FP64, "
+        f"{len(times)} timed runs after one warm-up")
 
 
 def ragged_measure(dev, steps, n=1 << 20):
@@ -575,19 +628,13 @@ def run_reference(args):
     from paper_2604_00048_b300 import synth
 
     rc = synth.RECIPES["hetero_tile"]
-    n = 512
+    n = CPU_SAMPLE
     inp = synth.generate_tile(rc, n, device="cpu", dtype=torch.float32)
-    x, w, lam = (inp[k].double().numpy() for k in ("x", "w", "lam"))
+    x, w, lam = (np.ascontiguousarray(inp[k].double().numpy()) for k in ("x", "w", "lam"))
     gz = np.random.default_rng(7).normal(size=x.shape)
     from oracle import banded
 
-    times = []
-    for i in range(args.warmup + args.steps):
-        t0 = time.perf_counter()
-        z, _ = banded.smooth_tile(x, w, lam, rc.d)
-        banded.vjp_tile(w, lam, rc.d, z, gz, log_lambda=True)
-        if i >= args.warmup:
-            times.append(time.perf_counter() - t0)
+    times = cpu_oracle_runs(x, w, lam, gz, rc.d, args.steps, warmup=args.warmup)
     dt = sum(times)
     val = n * len(times) / dt
     cores = banded.max_threads()
@@ -701,6 +748,7 @@ def run_ours(args):
     ms = t_start.elapsed_time(t_end)
     ws.sync_status(dev, stream)
     ms = max_over_ranks(ms, dev)
+    step_ms = [e[0].elapsed_time(e[3]) for e in ev]
     fwd_ms = statistics.median([e[0].elapsed_time(e[1]) for e in ev])
     ref_ms = statistics.median([e[1].elapsed_time(e[2]) for e in ev])
     bwd_ms = statistics.median([e[2].elapsed_time(e[3]) for e in ev]) if has_bwd else 0.0
@@ -721,7 +769,8 @@ def run_ours(args):
     roof = {"bound": "hbm", "kernel": kname, "achieved": achieved, "peak": hbm, "unit": "GB/s",
             "frac": achieved / hbm, "peak_kind": f"{peak_kind} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)"
             if peak_kind == "measured" else "fallback", "traffic": traffic,
-            "algorithmic_bytes_per_launch": kbytes, "kernel_ms": kms}
+            "algorithmic_bytes_per_launch": kbytes, "kernel_ms": kms,
+            "peak_nominal": NOMINAL_HBM_GBS, "frac_nominal": achieved / NOMINAL_HBM_GBS}
 
     # end to end through the C-ABI with host buffers (pinned), on a block of the tile: the
     # block is streamed as sub-blocks of series over three streams (each with its own device
@@ -777,15 +826,19 @@ def run_ours(args):
         dt = time.perf_counter() - t0
         h2d = sum(hb[n].numel() * 4 for hb in host for n in ("x", "w", "l") + (("g",) if has_bwd else ()))
         d2h = sum(hb[n].numel() * 4 for hb in host for n in ("z",) + (("gx", "gl") if has_bwd else ()))
+        link = pinned_copy_gbs(dev)
+        moved = (h2d + d2h) * ke / dt / 1e9
         e2e = {"value": Pe * world * ke / dt, "unit": "series/s", "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": d2h, "series_per_step": Pe,
                "note": "pinned host buffers, copies + C-ABI calls + sync inside the timed region, "
-                       f"{Pe}-series block of the tile in {nsub} sub-blocks over {nstr} streams"}
+                       f"{Pe}-series block of the tile in {nsub} sub-blocks over {nstr} streams",
+               "host_link": {**link, "e2e_copy_gbs": moved,
+                             "frac_of_bidirectional_copy": moved / link["bidirectional_gbs"]}}
         del host, devb
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
-        ns = 2048
+        ns = CPU_SAMPLE
         xs = x[:, :, :ns].double().cpu().numpy()
         wsn = w[:, :ns].double().cpu().numpy()
         ls = lam[:, :ns].double().cpu().numpy()
@@ -819,6 +872,7 @@ def run_ours(args):
             "fwd_series_per_s": P * world / ((fwd_ms + ref_ms) / 1e3),
             "fwd_unrefined_series_per_s": P * world / (fwd_ms / 1e3),
             "smooth_ms": fwd_ms, "refine_ms": ref_ms, "adjoint_ms": bwd_ms,
+            "step_ms_median": statistics.median(step_ms), "step_ms_best": min(step_ms),
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "ragged": ragged, "gcv": gcv, "learned": learned,
             "posterior": posterior, "weight_grad": wgrad, "dates": dates, "partitioned": partitioned,
             "gpu_launches": launches_per_step * args.steps, "clocks": ck,
