@@ -96,3 +96,32 @@ def test_adjoint_mse_equals_unfused_path(ws):
     assert _glam_err(glam.cpu().numpy()[:, ok], glam2.cpu().numpy()[:, ok]) <= 1e-5
     ref = 0.5 * scale * (mask[:, None, :] * (z - g["x"]) ** 2).sum(dim=(0, 1))
     assert torch.allclose(loss, ref, rtol=1e-5, atol=1e-12)
+
+
+def test_adjoint_mse_layer_workload_full_size_sampled(ws):
+    """The differentiable-layer workload at full size (65,536 series x 1095 days x 4 bands,
+    20% of the valid days held out) in the launch configuration of a training step: the GPU
+    smooth's z, the fused adjoint on all series, and 64 sampled series (first and last
+    included) against the oracle's masked_mse + VJP at that z (1e-3)."""
+    ws.tune_set(0, 0, 0)
+    from paper_2604_00048_b300 import synth
+    rc = synth.RECIPES["layer"]
+    P = 65536
+    out = synth.generate_tile(rc, P, device="cuda")
+    x, w, lam, hold = out["x"], out["w"], out["lam"], out["holdout"]
+    z, _ = ws.smooth(x, w, lam, rc.d, refine=True)
+    mask = hold.to(torch.float32)
+    scale = 2.0 / float(mask.sum() * rc.n_bands)
+    gx, glam, loss, st = ws.smooth_adjoint_mse(w, lam, z, x, rc.d, mask=mask, scale=scale, log_lambda=True)
+    ws.sync_status()
+    idx = np.sort(np.concatenate([[0, P - 1], np.random.default_rng(9).choice(np.arange(1, P - 1), 62, replace=False)]))
+    zs = z[:, :, idx].cpu().double().numpy()
+    xs, ws_, ls = x[:, :, idx].cpu().double().numpy(), w[:, idx].cpu().double().numpy(), lam[:, idx].cpu().double().numpy()
+    ms = mask[:, idx].cpu().double().numpy()
+    lr, gzr = dense.masked_mse(zs, xs, ms, scale)
+    gxr, glr = dense.vjp_tile(ws_, ls, rc.d, zs, gzr, log_lambda=True)
+    ok = st[idx].cpu().numpy() == 0
+    assert ok.all()
+    assert rel_err_per_series(gx[:, :, idx].cpu().numpy(), gxr) <= 1e-3
+    assert _glam_err(glam[:, idx].cpu().numpy(), glr) <= 1e-3
+    assert np.max(np.abs(loss[idx].cpu().numpy() - lr) / np.maximum(np.abs(lr), 1e-30)) <= 1e-5

@@ -90,3 +90,24 @@ def test_partitioned_status_codes(ws):
     assert np.all(z.cpu().numpy()[:, :, bad] == 0)
     zr, ok = dense.smooth_tile(c["x"][:, :, [0, 4, 5]], c["w"][:, [0, 4, 5]], c["lam"][:, [0, 4, 5]], 2)
     assert rel_err_per_series(z.cpu().numpy()[:, :, [0, 4, 5]], zr) <= 1e-4
+
+
+def test_partitioned_1024_series_sampled(ws):
+    """1,024 series of the 10-band tile at T = 3288 (the top of the few-series regime): 32
+    sampled series against the banded FP64 oracle (1e-4) and agreement with the tile path
+    with its refinement step on all series."""
+    from paper_2604_00048_b300 import synth
+    rc = synth.RECIPES["hetero_tile"]
+    P = 1024
+    out = synth.generate_tile(rc, P, device="cuda")
+    z, st = ws.smooth_partitioned(out["x"], out["w"], out["lam"], 2)
+    zt, stt = ws.smooth(out["x"], out["w"], out["lam"], 2, refine=True)
+    ws.sync_status()
+    assert torch.equal(st, stt) and int((st != 0).sum()) == 0
+    rel = ((z - zt).abs().amax(dim=0) / zt.abs().amax(dim=0).clamp_min(1e-6)).max().item()
+    assert rel <= 1e-4
+    idx = np.random.default_rng(4).choice(P, 32, replace=False)
+    c = {k: out[k][..., idx].cpu().double().numpy() for k in ("x", "w", "lam")}
+    zb, stb = banded.smooth_tile(c["x"], c["w"], c["lam"], 2)
+    assert np.all(stb == 0)
+    assert rel_err_per_series(z[:, :, idx].cpu().numpy(), zb) <= 1e-4
