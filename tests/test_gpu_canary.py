@@ -190,3 +190,58 @@ def test_binding_rejects_wrong_output_arrays(ws):
         ws.smooth_dates(t, x, w, lam, 2, z=short)
     with pytest.raises(ValueError):
         ws.smooth_dates_adjoint(t, w, lam, z, gz, 2, gx=short)
+
+
+@pytest.mark.parametrize("P", [300, 301])
+@pytest.mark.parametrize("d", [1, 3])
+@pytest.mark.parametrize("B", [3, 10])
+def test_adjoint_mse_margins(ws, P, d, B):
+    """The adjoint with the fused masked-MSE loss: gx, glam, the per-series loss, status
+    and the workspace."""
+    rc, g, c = tile_inputs("layer", P, T=37, B=B, revisit=1, p_valid=0.6)
+    x, w, lam = g["x"], g["w"], g["lam"]
+    T = x.shape[0]
+    z, _ = ws.smooth(x, w, lam, d)
+    pb = ws.make_problem(T, B, P, d, ws.F32, ws.LAM_PER_DAY)
+    wsp = _workspace(ws, pb, 0)
+    mask = (torch.rand(T, P, device="cuda") < 0.3).float()
+    gx, gl = Padded(x.shape, torch.float32), Padded(lam.shape, torch.float32)
+    ls, st = Padded((P,), torch.float32), Padded((P,), torch.uint8)
+    ws.smooth_adjoint_mse(w, lam, z, x, d, mask=mask, scale=0.01, gx=gx.t, glam=gl.t, loss=ls.t, status=st.t,
+                          log_lambda=True, workspace_buf=wsp.t)
+    ws.sync_status()
+    for buf in (gx, gl, ls, st, wsp):
+        assert buf.margins_intact()
+
+
+@pytest.mark.parametrize("P", [5, 301])
+@pytest.mark.parametrize("d", [1, 2, 3, 4])
+@pytest.mark.parametrize("T", [37, 150])
+def test_partitioned_margins(ws, P, d, T):
+    """The partitioned solve: z, status and the workspace, with one domain (T = 37) and
+    several with a short last one (T = 150)."""
+    rc, g, c = tile_inputs("layer", P, T=T, B=3, revisit=1, p_valid=0.6)
+    x, w, lam = g["x"], g["w"], g["lam"]
+    pb = ws.make_problem(T, 3, P, d, ws.F32, ws.LAM_PER_DAY)
+    wsp = _workspace(ws, pb, ws.PARTITIONED)
+    z, st = Padded(x.shape, torch.float32), Padded((P,), torch.uint8)
+    ws.smooth_partitioned(x, w, lam, d, z=z.t, status=st.t, workspace_buf=wsp.t)
+    ws.sync_status()
+    for buf in (z, st, wsp):
+        assert buf.margins_intact()
+
+
+@pytest.mark.parametrize("tiles", [False, True])
+def test_ragged_margins(ws, tiles):
+    """The ragged plan's execute on caller scratch: z, status and the workspace, with the
+    refinement step (and the length-class tiles)."""
+    rc = synth.RECIPES["ragged"]
+    out = synth.generate_ragged(rc, 333, device="cuda", t_range=(1, 300))
+    plan = ws.RaggedPlan(out["offsets"], out["order"])
+    need = plan.workspace_size(refine=True, tiles=tiles)
+    wsp = Padded((need,), torch.uint8, zero=True)
+    z, st = Padded(out["x"].shape, torch.float32), Padded((333,), torch.uint8)
+    plan.execute(out["x"], out["w"], out["lam"], z=z.t, status=st.t, refine=True, tiles=tiles, workspace_buf=wsp.t)
+    ws.sync_status()
+    for buf in (z, st, wsp):
+        assert buf.margins_intact()
