@@ -52,9 +52,12 @@ def parse_args():
     ap.add_argument("--no-wgrad", action="store_true")
     ap.add_argument("--no-dates", action="store_true")
     ap.add_argument("--no-partitioned", action="store_true")
+    ap.add_argument("--no-layer", action="store_true")
+    ap.add_argument("--no-homo", action="store_true")
     ap.add_argument("--tcn-ckpt", default=None, help="trained lambda network (else one epoch is trained first)")
     ap.add_argument("--train-epochs", type=float, default=1.0, help="epochs of lambda-network training before timing")
-    ap.add_argument("--only", choices=["gcv", "learned", "ragged", "posterior", "dates", "partitioned"], default=None,
+    ap.add_argument("--only", choices=["gcv", "learned", "ragged", "posterior", "dates", "partitioned", "layer", "homo"],
+                    default=None,
                     help="run one secondary measurement alone (profiling) and print it")
     ap.add_argument("--series", type=int, default=None, help="series of the --only measurement")
     ap.add_argument("--days", type=int, default=None, help="days of the --only posterior measurement (profiling)")
@@ -521,6 +524,120 @@ def posterior_measure(dev, steps, x=None, w=None, lam=None, z=None, P=262144, T=
     return res
 
 
+def homo_measure(dev, steps, P=4096):
+    """The plain homoscedastic smoother in FP64 (4,096 series x 365 days, one band, scalar
+    lambda): a launch-bound size, timed as replays of a CUDA graph holding the C-ABI call."""
+    import torch
+
+    from paper_2604_00048_b300 import synth, ws
+
+    rc = synth.RECIPES["homo_fp64"]
+    out = synth.generate_tile(rc, P, device=dev, dtype=torch.float64)
+    x, w, lam = out["x"], out["w"], out["lam"]
+    z = torch.empty_like(x)
+    st = torch.empty(P, dtype=torch.uint8, device=dev)
+    pb = ws.make_problem(rc.T, 1, P, rc.d, ws.F64, ws.LAM_SCALAR)
+    wsb = torch.zeros(ws.workspace_size(pb, 0), dtype=torch.uint8, device=dev)
+    s = torch.cuda.Stream(device=dev)
+    s.wait_stream(torch.cuda.current_stream(dev))
+    with torch.cuda.stream(s):
+        for _ in range(3):
+            ws.smooth(x, w, lam, rc.d, z=z, status=st, workspace_buf=wsb, stream=s)
+    torch.cuda.synchronize()
+    reps = max(50, 10 * steps)
+
+    def graph_ms(call):
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.stream(s):
+            with torch.cuda.graph(g, stream=s, capture_error_mode="thread_local"):
+                call()
+        for _ in range(5):
+            g.replay()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            g.replay()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    ms = graph_ms(lambda: ws.smooth(x, w, lam, rc.d, z=z, status=st, workspace_buf=wsb, stream=s))
+    bad = int((st != 0).sum().item())
+    wsp = torch.zeros(ws.workspace_size(pb, ws.PARTITIONED), dtype=torch.uint8, device=dev)
+    zp = torch.empty_like(x)
+    with torch.cuda.stream(s):
+        ws.smooth_partitioned(x, w, lam, rc.d, z=zp, status=st, workspace_buf=wsp, stream=s)
+    torch.cuda.synchronize()
+    ms_p = graph_ms(lambda: ws.smooth_partitioned(x, w, lam, rc.d, z=zp, status=st, workspace_buf=wsp, stream=s))
+    rel = float(((zp - z).abs().amax(dim=0) / z.abs().amax(dim=0).clamp_min(1e-12)).max())
+    return {"workload": f"homo_fp64: {P} series x {rc.T} days, d={rc.d}, 1 band, FP64, scalar lambda",
+            "ms": ms, "series_per_s": P / (ms / 1e3), "replays": reps, "series_with_status": bad,
+            "partitioned_ms": ms_p, "partitioned_series_per_s": P / (ms_p / 1e3),
+            "partitioned_max_rel_diff": rel,
+            "note": "CUDA-graph replays of one C-ABI call (tile path: one series per thread, 32 CTAs)"}
+
+
+def layer_measure(dev, steps, P=65536):
+    """The differentiable layer (65,536 series x 1095 days x 4 bands, d = 2, FP32; loss = the
+    mean squared error of z against the 20% held-out valid observations): forward + backward
+    through the autograd layer in recompute and store-factor modes (gradients to x and
+    log lambda; the loss in PyTorch), and the C-ABI path with the loss fused into the adjoint
+    (ws_smooth_batch with refinement + ws_solve_adjoint_mse)."""
+    import torch
+
+    from paper_2604_00048_b300 import autograd, synth, ws
+
+    rc = synth.RECIPES["layer"]
+    out = synth.generate_tile(rc, P, device=dev)
+    x, w, lam, mask = out["x"], out["w"], out["lam"], out["holdout"].to(torch.float32)
+    del out
+    scale = 2.0 / float(mask.sum() * rc.n_bands)
+    loglam = lam.log()
+
+    def autograd_step(store):
+        xg = x.clone().requires_grad_(True)
+        ll = loglam.clone().requires_grad_(True)
+        z, _ = autograd.whittaker_smooth(xg, w, ll.exp(), rc.d, refine=True, store_factor=store)
+        loss = 0.5 * scale * (mask[:, None, :] * (z - x) ** 2).sum()
+        loss.backward()
+        return xg.grad, ll.grad
+
+    z = torch.empty_like(x)
+    st = torch.empty(P, dtype=torch.uint8, device=dev)
+    gx, glam, lossp = torch.empty_like(x), torch.empty_like(lam), torch.empty(P, device=dev)
+
+    def fused_step():
+        ws.smooth(x, w, lam, rc.d, z=z, status=st, refine=True)
+        ws.smooth_adjoint_mse(w, lam, z, x, rc.d, mask=mask, scale=scale, gx=gx, glam=glam, loss=lossp,
+                              log_lambda=True)
+
+    def timed(fn):
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(max(5, steps)):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            fn()
+            e1.record()
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        return statistics.median(ts)
+
+    ms_re = timed(lambda: autograd_step(False))
+    ms_st = timed(lambda: autograd_step(True))
+    ms_fu = timed(fused_step)
+    ws.sync_status(dev)
+    return {"workload": f"layer: {P} series x {rc.T} days x {rc.n_bands} bands, d={rc.d}, FP32, held-out MSE loss, "
+                        "gradients to x and log lambda",
+            "autograd_recompute_ms": ms_re, "autograd_store_factor_ms": ms_st,
+            "fused_loss_cabi_ms": ms_fu, "series_per_s_fused": P / (ms_fu / 1e3),
+            "stored_factor_bytes": (rc.d + 1) * rc.T * P * 4,
+            "note": "autograd rows include PyTorch's loss and exp ops; the fused row is two C-ABI calls"}
+
+
 def partitioned_measure(dev, steps, P=64):
     """Few long series: P series of the heteroscedastic tile (3288 days, 10 bands, d = 2)
     smoothed by the partitioned parallel-in-time solve (double-float, no refinement step
@@ -670,6 +787,10 @@ def run_only(args):
         res = learned_measure(dev, steps, args.tcn_ckpt, args.train_epochs, args.series or 262144)
     elif args.only == "partitioned":
         res = partitioned_measure(dev, steps, args.series or 64)
+    elif args.only == "layer":
+        res = layer_measure(dev, steps, args.series or 65536)
+    elif args.only == "homo":
+        res = homo_measure(dev, steps, args.series or 4096)
     else:
         res = ragged_measure(dev, steps, args.series or (1 << 20))
     print(json.dumps({"only": args.only, **res}), flush=True)
@@ -865,6 +986,8 @@ def run_ours(args):
     gcv = None if args.no_gcv else gcv_measure(dev, max(3, args.steps))
     learned = None if args.no_learned else learned_measure(dev, max(3, args.steps), args.tcn_ckpt, args.train_epochs)
     partitioned = None if args.no_partitioned else partitioned_measure(dev, max(5, args.steps))
+    layer = None if args.no_layer else layer_measure(dev, max(5, args.steps))
+    homo = None if args.no_homo else homo_measure(dev, max(5, args.steps))
     line = {"metric": METRIC, "value": value, "unit": "series/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
@@ -875,6 +998,7 @@ def run_ours(args):
             "step_ms_median": statistics.median(step_ms), "step_ms_best": min(step_ms),
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "ragged": ragged, "gcv": gcv, "learned": learned,
             "posterior": posterior, "weight_grad": wgrad, "dates": dates, "partitioned": partitioned,
+            "layer": layer, "homo_fp64": homo,
             "gpu_launches": launches_per_step * args.steps, "clocks": ck,
             "series_with_status": bad}
     if rank == 0:

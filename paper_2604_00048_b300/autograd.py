@@ -3,8 +3,10 @@
 Forward: the CUDA smooth (with one refinement step by default). Backward: the CUDA adjoint
 (Eqs. 4-5): dL/dx = W Omega^{-1} dL/dz and dL/dlambda_k = -sum_b (D g_b)_k (D z_b)_k.
 `store_factor=True` keeps the factor of Omega from the forward pass ((d+1) words per
-pixel-day) and reuses it in the backward pass; the default recomputes it from (w, lambda),
-which saves that memory. The weights w get a gradient when they require one (soft
+pixel-day) and reuses it in the backward pass, which saves the backward pass's rotation
+arithmetic (not time: its kernels stream one series per thread without staging and measured
+slower than the recompute on the three-year 4-band layer workload); the default recomputes
+the factor from (w, lambda), which also saves that memory. The weights w get a gradient when they require one (soft
 weights of Eq. 1: dL/dw_t = sum_b g_tb (x_tb - z_tb), x taken as 0 on days with w_t = 0;
 x is then kept for the backward pass). For a log-lambda
 parametrisation pass lam = loglam.exp(): autograd applies the chain rule outside the layer.
