@@ -284,8 +284,9 @@ int launch_dates_refine(const ws_problem& pb, const void* t, const void* x, cons
 
 using namespace ws;
 
-// Adjoint with a stored factor: g = Omega^{-1} gz into the refinement region of the
-// workspace, then the gx / glam epilogue. (status is left untouched: ws_factor set it.)
+// Adjoint with a stored factor: one kernel per band group, whose forward sweep writes yhat
+// into the refinement region of the workspace and whose backward sweep forms g with gx and
+// glam. (status is left untouched: ws_factor set it.)
 static int ws_adjoint_factored(const ws_problem* pb, const void* factor, const void* w, const void* lam, const void* z,
                                const void* gz, void* gx, void* glam, uint32_t flags, uint8_t* status,
                                void* workspace, size_t ws_bytes, void* stream) {
@@ -297,9 +298,7 @@ static int ws_adjoint_factored(const ws_problem* pb, const void* factor, const v
   if (rc != WS_OK) return rc;
   void* gs = static_cast<char*>(workspace) + kHeaderBytes + ck_bytes;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  rc = launch_factored(1, P, factor, nullptr, w, lam, gz, gs, nullptr, nullptr, nullptr, nullptr, nullptr, 0, 0, st);
-  if (rc != WS_OK) return rc;
-  return launch_factored(2, P, factor, nullptr, w, lam, nullptr, nullptr, z, gs, gx, glam, nullptr, 0,
+  return launch_factored(2, P, factor, nullptr, w, lam, gz, nullptr, z, gs, gx, glam, nullptr, 0,
                          ((flags & WS_GRAD_LOGLAM) ? 1 : 0) | ((flags & WS_ADJ_RAW_G) ? 2 : 0), st);
 }
 
