@@ -351,7 +351,13 @@ int ws_solve_adjoint(const ws_problem* pb, const void* factor_or_null, const voi
  * (flags: none). workspace: ws_workspace_size(pb, WS_PARTITIONED) bytes, 256-byte aligned
  * (else WS_EINVAL / WS_ENOMEM_WS before any launch); contents need no initialisation.
  * Per series it moves a few hundred bytes of scratch per day, so it suits up to a few
- * thousand series; beyond that ws_smooth_batch is faster. */
+ * thousand series; beyond that ws_smooth_batch is faster. Accuracy: elimination on Omega
+ * (not the rotation factor of ws_smooth_batch) has an error of order eps * cond(Omega)
+ * (eps about 3.6e-15 in double-float), against eps * sqrt(cond(Omega)) for the rotations:
+ * within 1e-4 up to cond(Omega) of about 1e10 (the heteroscedastic and homoscedastic
+ * workloads); for worse-conditioned series (d = 3 with unsmoothed lambda up to 1e5 and
+ * sparse weights reaches 1e13) use ws_smooth_batch with WS_REFINE or the ragged plan's
+ * refinement, whose double-float re-solve uses the rotations. */
 int ws_smooth_partitioned(const ws_problem* pb, const void* x, const void* w, const void* lam, void* z,
                           uint8_t* status, void* workspace, size_t ws_bytes, void* stream);
 
