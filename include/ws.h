@@ -403,7 +403,7 @@ int ws_tune_pixels_per_cta(int32_t pixels);
  * storage per series).
  * Set-up and call path: ws_plan_create is set-up. It reads offsets and orders back to the
  * host (it synchronises `stream`), allocates the plan's device tables (item lists,
- * length-class tables, two error/counter words) and creates the length classes' eight
+ * length-class tables, two error/counter words) and creates the length classes' 32
  * streams and events; ws_plan_destroy frees them. ws_plan_execute is the call path: it
  * allocates no device memory and never synchronises (except the autotuner's first run,
  * which times candidates with events). Its scratch (checkpoints, the length-class tiles
@@ -444,7 +444,7 @@ typedef struct ws_plan_stats {
                                   solved as length-class tiles by the tile kernels: padded
                                   with zero weights to a multiple of 32 days, which leaves
                                   the solution unchanged; the workspace holds four float
-                                  arrays of the padded size and eight tile workspaces */
+                                  arrays of the padded size and 32 tile workspaces */
 #define WS_PLAN_REFINE 0x4u    /* ws_plan_execute: iterative refinement (the paper
                                   fixes no precision): up to three FP32 steps, r = W x - Omega z
                                   with a double-word combination, z += Omega^{-1} r; a series
