@@ -17,14 +17,16 @@
 // bits, since B300's FP64 rate is a small fraction of its FP32 rate; FP64 for FP64 data):
 //   k_part_block   one thread per (series, domain): LDL^T of the interior band (assembled
 //                  from w and lambda, Eq. 3), solves with the 2d coupling columns E_L =
-//                  Omega_{I_j, S_(j-1)} and E_R = Omega_{I_j, S_j} and with the B right-hand
-//                  sides, and writes the Schur pieces E^T Omega_II^{-1} E and E^T Omega_II^{-1} b
-//                  (only the first and last d rows of E are nonzero) and the interior factor;
+//                  Omega_{I_j, S_(j-1)} and E_R = Omega_{I_j, S_j}, and writes the Schur pieces
+//                  E^T Omega_II^{-1} E (only the first and last d rows of E are nonzero) and
+//                  the interior factor;
+//   k_part_rhs     one thread per (series, domain, band): E^T Omega_II^{-1} b with the stored
+//                  factor;
 //   k_part_reduce  one thread per series: status codes, then block LDL^T of S;
 //   k_part_rsolve  one thread per (series, band): block forward / back substitution on S,
 //                  z on the separator days;
-//   k_part_finish  one thread per (series, domain): z_I = Omega_II^{-1} (b_I - E_L z_S(j-1) -
-//                  E_R z_S(j)) with the stored factor; non-finite outputs flagged.
+//   k_part_finish  one thread per (series, domain, band): z_I = Omega_II^{-1} (b_I -
+//                  E_L z_S(j-1) - E_R z_S(j)) with the stored factor; non-finite outputs flagged.
 // Scratch lives in the caller's workspace; slot-major layouts ([field][slot], slot =
 // domain * P + series) keep a warp's accesses contiguous.
 #include <cuda_runtime.h>
@@ -165,6 +167,29 @@ __device__ __forceinline__ void band_solve(const H* Lf, int n, H* y) {
   }
 }
 
+// The coupling columns of a domain's interior: E_L[i][c] = Omega[s-D+c][s+i] for the
+// first D rows, E_R[i][c] = Omega[s+n-D+i][e+c] for the last D rows.
+template <typename F, typename H, int D>
+__device__ __forceinline__ void coupling(const PartArgs& a, int p, int s, int e, int n, bool has_l, bool has_r,
+                                         H (&EL)[D][D], H (&ER)[D][D]) {
+#pragma unroll
+  for (int i = 0; i < D; ++i)
+#pragma unroll
+    for (int c = 0; c < D; ++c) {
+      EL[i][c] = h_of<H>(0.f);
+      ER[i][c] = h_of<H>(0.f);
+      if (has_l && i < n) {
+        const int u = s - D + c, t = s + i;
+        if (t - u <= D) EL[i][c] = omega_entry<F, H, D>(a, p, u, t - u);
+      }
+      const int ii = n - D + i;
+      if (has_r && ii >= 0) {
+        const int t = s + ii, u = e + c;
+        if (u - t <= D) ER[i][c] = omega_entry<F, H, D>(a, p, t, u - t);
+      }
+    }
+}
+
 template <typename F, typename H, int D>
 __global__ void __launch_bounds__(kPartThreads) k_part_block(const PartArgs a) {
   const int slot = blockIdx.x * blockDim.x + threadIdx.x;
@@ -232,22 +257,7 @@ __global__ void __launch_bounds__(kPartThreads) k_part_block(const PartArgs a) {
   // Omega[s+i][e+c] (nonzero for n-1-i <= D-1-c); spikes V = Omega_II^{-1} E
   H y[kPartMaxM];
   H EL[D][D], ER[D][D];  // EL[i][c] for the first D rows, ER[i][c] for local row n-D+i
-#pragma unroll
-  for (int i = 0; i < D; ++i)
-#pragma unroll
-    for (int c = 0; c < D; ++c) {
-      EL[i][c] = h_of<H>(0.f);
-      ER[i][c] = h_of<H>(0.f);
-      if (has_l && i < n) {
-        const int u = s - D + c, t = s + i;
-        if (t - u <= D) EL[i][c] = omega_entry<F, H, D>(a, p, u, t - u);
-      }
-      const int ii = n - D + i;
-      if (has_r && ii >= 0) {
-        const int t = s + ii, u = e + c;
-        if (u - t <= D) ER[i][c] = omega_entry<F, H, D>(a, p, t, u - t);
-      }
-    }
+  coupling<F, H, D>(a, p, s, e, n, has_l, has_r, EL, ER);
   double* gl = static_cast<double*>(a.gl);
   double* gr = static_cast<double*>(a.gr);
   double* gc = static_cast<double*>(a.gc);
@@ -292,28 +302,48 @@ __global__ void __launch_bounds__(kPartThreads) k_part_block(const PartArgs a) {
       }
     }
   }
-  // right-hand sides: hl = E_L^T Omega_II^{-1} b, hr = b_(S_j) - E_R^T Omega_II^{-1} b
+}
+
+// One thread per (series, domain, band): y = Omega_II^{-1} b with the stored interior factor,
+// then hl = E_L^T y and hr = b_(S_j) - E_R^T y.
+template <typename F, typename H, int D>
+__global__ void __launch_bounds__(kPartThreads) k_part_rhs(const PartArgs a) {
+  const int NS = a.K * a.P;
+  const int id = blockIdx.x * blockDim.x + threadIdx.x;
+  if (id >= NS * a.B) return;
+  const int slot = id % NS, b = id / NS;
+  const int p = slot % a.P, j = slot / a.P;
+  int s, e;
+  bool has_l, has_r;
+  domain(a, j, D, s, e, has_l, has_r);
+  const int n = e - s;
+  const H* fac = static_cast<const H*>(a.fac);
+  H Lf[kPartMaxM * (D + 1)];
+  for (int i = 0; i < n; ++i)
+#pragma unroll
+    for (int q = 0; q <= D; ++q) Lf[i * (D + 1) + q] = fac[(size_t)(i * (D + 1) + q) * NS + slot];
+  H EL[D][D], ER[D][D];
+  coupling<F, H, D>(a, p, s, e, n, has_l, has_r, EL, ER);
+  H y[kPartMaxM];
+  for (int i = 0; i < n; ++i) y[i] = rhs_b<F, H>(a, p, s + i, b);
+  band_solve<H, D>(Lf, n, y);
   double* hl = static_cast<double*>(a.hl);
   double* hr = static_cast<double*>(a.hr);
-  for (int b = 0; b < a.B; ++b) {
-    for (int i = 0; i < n; ++i) y[i] = rhs_b<F, H>(a, p, s + i, b);
-    band_solve<H, D>(Lf, n, y);
 #pragma unroll
-    for (int c = 0; c < D; ++c) {
-      if (has_l) {
-        H acc = h_of<H>(0.f);
+  for (int c = 0; c < D; ++c) {
+    if (has_l) {
+      H acc = h_of<H>(0.f);
 #pragma unroll
-        for (int i = 0; i < D; ++i)
-          if (i < n) acc = acc + EL[i][c] * y[i];
-        hl[(size_t)(c * a.B + b) * NS + slot] = h_d(acc);
-      }
-      if (has_r) {
-        H acc = h_of<H>(0.f);
+      for (int i = 0; i < D; ++i)
+        if (i < n) acc = acc + EL[i][c] * y[i];
+      hl[(size_t)(c * a.B + b) * NS + slot] = h_d(acc);
+    }
+    if (has_r) {
+      H acc = h_of<H>(0.f);
 #pragma unroll
-        for (int i = 0; i < D; ++i)
-          if (n - D + i >= 0) acc = acc + ER[i][c] * y[n - D + i];
-        hr[(size_t)(c * a.B + b) * NS + slot] = h_d(rhs_b<F, H>(a, p, e + c, b) - acc);
-      }
+      for (int i = 0; i < D; ++i)
+        if (n - D + i >= 0) acc = acc + ER[i][c] * y[n - D + i];
+      hr[(size_t)(c * a.B + b) * NS + slot] = h_d(rhs_b<F, H>(a, p, e + c, b) - acc);
     }
   }
 }
@@ -560,12 +590,13 @@ __global__ void __launch_bounds__(kPartThreads) k_part_rsolve(const PartArgs a) 
   }
 }
 
-// One thread per (series, domain): interior z with the separators' z known.
+// One thread per (series, domain, band): interior z with the separators' z known.
 template <typename F, typename H, int D>
 __global__ void __launch_bounds__(kPartThreads) k_part_finish(const PartArgs a) {
-  const int slot = blockIdx.x * blockDim.x + threadIdx.x;
   const int NS = a.K * a.P;
-  if (slot >= NS) return;
+  const int id = blockIdx.x * blockDim.x + threadIdx.x;
+  if (id >= NS * a.B) return;
+  const int slot = id % NS, b = id / NS;
   const int p = slot % a.P, j = slot / a.P;
   int s, e;
   bool has_l, has_r;
@@ -574,8 +605,7 @@ __global__ void __launch_bounds__(kPartThreads) k_part_finish(const PartArgs a) 
   const bool ok = a.code[p] == WS_SERIES_OK;
   F* z = static_cast<F*>(a.z);
   if (!ok) {
-    for (int b = 0; b < a.B; ++b)
-      for (int i = 0; i < n; ++i) z[((size_t)(s + i) * a.B + b) * a.P + p] = F(0);
+    for (int i = 0; i < n; ++i) z[((size_t)(s + i) * a.B + b) * a.P + p] = F(0);
     return;
   }
   const H* fac = static_cast<const H*>(a.fac);
@@ -585,43 +615,26 @@ __global__ void __launch_bounds__(kPartThreads) k_part_finish(const PartArgs a) 
 #pragma unroll
     for (int q = 0; q <= D; ++q) Lf[i * (D + 1) + q] = fac[(size_t)(i * (D + 1) + q) * NS + slot];
   H EL[D][D], ER[D][D];
-#pragma unroll
-  for (int i = 0; i < D; ++i)
-#pragma unroll
-    for (int c = 0; c < D; ++c) {
-      EL[i][c] = h_of<H>(0.f);
-      ER[i][c] = h_of<H>(0.f);
-      if (has_l && i < n) {
-        const int u = s - D + c, t = s + i;
-        if (t - u <= D) EL[i][c] = omega_entry<F, H, D>(a, p, u, t - u);
-      }
-      const int ii = n - D + i;
-      if (has_r && ii >= 0) {
-        const int t = s + ii, u = e + c;
-        if (u - t <= D) ER[i][c] = omega_entry<F, H, D>(a, p, t, u - t);
-      }
-    }
+  coupling<F, H, D>(a, p, s, e, n, has_l, has_r, EL, ER);
   H y[kPartMaxM];
+  for (int i = 0; i < n; ++i) y[i] = rhs_b<F, H>(a, p, s + i, b);
+  // b_I - E_L z_S(j-1) - E_R z_S(j): E_L touches the first D rows, E_R the last D
+#pragma unroll
+  for (int c = 0; c < D; ++c) {
+    const H zl = has_l ? h_ofd<H>(zs[((size_t)((j - 1) * D + c) * a.B + b) * a.P + p]) : h_of<H>(0.f);
+    const H zr = has_r ? h_ofd<H>(zs[((size_t)(j * D + c) * a.B + b) * a.P + p]) : h_of<H>(0.f);
+#pragma unroll
+    for (int i = 0; i < D; ++i) {
+      if (has_l && i < n) y[i] = y[i] - EL[i][c] * zl;
+      if (has_r && n - D + i >= 0) y[n - D + i] = y[n - D + i] - ER[i][c] * zr;
+    }
+  }
+  band_solve<H, D>(Lf, n, y);
   bool nonfin = false;
-  for (int b = 0; b < a.B; ++b) {
-    for (int i = 0; i < n; ++i) y[i] = rhs_b<F, H>(a, p, s + i, b);
-    // b_I - E_L z_S(j-1) - E_R z_S(j): E_L touches the first D rows, E_R the last D
-#pragma unroll
-    for (int c = 0; c < D; ++c) {
-      const H zl = has_l ? h_ofd<H>(zs[((size_t)((j - 1) * D + c) * a.B + b) * a.P + p]) : h_of<H>(0.f);
-      const H zr = has_r ? h_ofd<H>(zs[((size_t)(j * D + c) * a.B + b) * a.P + p]) : h_of<H>(0.f);
-#pragma unroll
-      for (int i = 0; i < D; ++i) {
-        if (has_l && i < n) y[i] = y[i] - EL[i][c] * zl;
-        if (has_r && n - D + i >= 0) y[n - D + i] = y[n - D + i] - ER[i][c] * zr;
-      }
-    }
-    band_solve<H, D>(Lf, n, y);
-    for (int i = 0; i < n; ++i) {
-      const F out = (F)h_d(y[i]);
-      nonfin |= !isfinite((double)out);
-      z[((size_t)(s + i) * a.B + b) * a.P + p] = out;
-    }
+  for (int i = 0; i < n; ++i) {
+    const F out = (F)h_d(y[i]);
+    nonfin |= !isfinite((double)out);
+    z[((size_t)(s + i) * a.B + b) * a.P + p] = out;
   }
   if (nonfin) atomicOr(a.flags + p, 2u);
 }
@@ -689,10 +702,12 @@ template <typename F, typename H, int D>
 static int part_launch_t(const PartArgs& a, cudaStream_t st) {
   const int NS = a.K * a.P;
   const int gb = (NS + kPartThreads - 1) / kPartThreads;
+  const int gbb = (NS * a.B + kPartThreads - 1) / kPartThreads;
   k_part_block<F, H, D><<<gb, kPartThreads, 0, st>>>(a);
+  k_part_rhs<F, H, D><<<gbb, kPartThreads, 0, st>>>(a);
   k_part_reduce<D><<<(a.P + kPartThreads - 1) / kPartThreads, kPartThreads, 0, st>>>(a);
   k_part_rsolve<F, D><<<(a.P * a.B + kPartThreads - 1) / kPartThreads, kPartThreads, 0, st>>>(a);
-  k_part_finish<F, H, D><<<gb, kPartThreads, 0, st>>>(a);
+  k_part_finish<F, H, D><<<gbb, kPartThreads, 0, st>>>(a);
   k_part_status<<<(a.P + kPartThreads - 1) / kPartThreads, kPartThreads, 0, st>>>(a);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return set_error(WS_ECUDA, "partitioned solve launch: %s", cudaGetErrorString(e));
