@@ -392,6 +392,14 @@ int ws_tune_set(int32_t ctas_per_sm, int32_t chunk_days);
  * ws_workspace_size() reflects the current setting. Returns WS_EINVAL for other values. */
 int ws_tune_pixels_per_cta(int32_t pixels);
 
+/* Tuning of the tile kernels (no counterpart in the paper): chunks per checkpoint of the
+ * forward sweep, 0 (automatic: 2), 1 or 2. With 2 the backward sweep recomputes both
+ * chunks resident in the two-stage ring from one checkpoint, halving the checkpoint words
+ * written and read; with 1 every chunk has its own checkpoint and the next chunk's input
+ * loads while the current one is computed. Results are identical. Returns WS_EINVAL for
+ * other values. */
+int ws_tune_checkpoint_group(int32_t chunks);
+
 /* ---------------------------------------------------------------------------------
  * Ragged batches: series of different lengths (and orders) packed back to back.
  * Band b of series i occupies x[b*N + offsets[i] + t], t < T_i = offsets[i+1] - offsets[i],

@@ -214,6 +214,7 @@ static int run_tile(const ws_problem& P, int mode, const void* rhs, const void* 
     a.C = cfg.C;
     a.NP = cfg.NP;
     a.nch = cfg.nch;
+    a.ck_group = cfg.ck_group;
     a.n_tiles = cfg.n_tiles;
     a.lam_scalar = per_day ? 0 : 1;
     a.tma = tma ? 1 : 0;
@@ -785,6 +786,13 @@ extern "C" int ws_tune_pixels_per_cta(int32_t pixels) {
   clear_error();
   if (pixels != 0 && pixels != 64 && pixels != 128) return set_error(WS_EINVAL, "pixels per CTA must be 0, 64 or 128");
   g_tune_np = pixels;
+  return WS_OK;
+}
+
+extern "C" int ws_tune_checkpoint_group(int32_t chunks) {
+  clear_error();
+  if (chunks < 0 || chunks > 2) return set_error(WS_EINVAL, "chunks per checkpoint must be 0, 1 or 2");
+  g_tune_ckgroup = chunks;
   return WS_OK;
 }
 

@@ -52,12 +52,14 @@ struct TileCfg {
   size_t smem_bytes = 0;
   bool tma = false;
   int fields = 0;      // checkpoint words per pixel per chunk
+  int ck_group = 2;    // chunks per checkpoint (1 or 2)
 };
 
 // Arguments of the tile kernels (plain pointers + sizes).
 struct TileArgs {
   int T, P, B, b0;
   int C, NP, nch, n_tiles;
+  int ck_group;           // chunks per checkpoint: 1, or 2 (both ring stages recomputed together)
   int lam_scalar, tma;
   int write_status;       // this launch owns the status codes (first band group)
   const void* x;          // SMOOTH: x; ADJOINT: gz
@@ -123,7 +125,7 @@ int launch_dates(const ws_problem& pb, bool adj, const void* t, const void* x, c
                  void* out, const void* zin, void* glam, int loglam, uint8_t* status, void* ckpt, cudaStream_t st);
 
 // Launchers (return WS_OK or an error code, errors recorded via set_error).
-extern int g_tune_ctas, g_tune_chunk, g_tune_np;  // ws_tune_set() overrides (0 = automatic)
+extern int g_tune_ctas, g_tune_chunk, g_tune_np, g_tune_ckgroup;  // ws_tune_* overrides (0 = automatic)
 int plan_tile(const ws_problem& pb, int mode, int nb, TileCfg& cfg, int mse = 0);
 int launch_tile(const ws_problem& pb, int mode, int nb, const TileCfg& cfg, const TileArgs& a,
                 const CUtensorMap* maps, cudaStream_t st);

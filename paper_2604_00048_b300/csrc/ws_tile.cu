@@ -35,7 +35,7 @@ namespace ws {
 // ----------------------------------------------------------------------------------
 // host side
 
-int g_tune_ctas = 0, g_tune_chunk = 0, g_tune_np = 0;
+int g_tune_ctas = 0, g_tune_chunk = 0, g_tune_np = 0, g_tune_ckgroup = 0;
 
 // Largest chunk (days) whose shared memory fits `ctas` CTAs of `np` pixels on one SM.
 static long chunk_for(const ws_problem& pb, int mode, int nb, int S, int ctas, int np, const DeviceInfo& di,
@@ -111,6 +111,9 @@ int plan_tile(const ws_problem& pb, int mode, int nb, TileCfg& cfg, int mse) {
   const long cap = (long)di.sm_count * occ;
   cfg.grid = (int)(cfg.n_tiles < cap ? cfg.n_tiles : cap);
   cfg.fields = D * (D + 1) + nb * D;
+  // Checkpoints every second chunk: pass 2 recomputes both resident chunks of the ring from
+  // one checkpoint, halving the checkpoint words written and read.
+  cfg.ck_group = g_tune_ckgroup > 0 ? g_tune_ckgroup : 2;
   return WS_OK;
 }
 

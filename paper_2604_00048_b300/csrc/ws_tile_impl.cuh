@@ -49,9 +49,19 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 #include "ws_internal.h"
 #include "ws_ptx.cuh"
 #include "ws_sweep.cuh"
+
+// Unroll factor of the per-day loops (the rotating per-day state then needs no copies
+// between iterations).
+#ifndef WS_TILE_UNROLL
+#define WS_TILE_UNROLL 2
+#endif
+#define WS_PRAGMA_(x) _Pragma(#x)
+#define WS_UNROLL_N(n) WS_PRAGMA_(unroll n)
 
 namespace ws {
 
@@ -78,7 +88,7 @@ __global__ void __launch_bounds__(NP* S, (S > 1 ? 2 : 4) * (128 / NP))
   const bool mse = MODE == MODE_ADJ && a.mse;
   const bool has_m = mse && a.mask != nullptr;
   const F mscale = static_cast<F>(a.mse_scale);
-  const size_t stage_rows = tile_stage_rows(MODE, C, NB, D, S, mse ? 1 : 0);
+  const int stage_rows = (int)tile_stage_rows(MODE, C, NB, D, S, mse ? 1 : 0);
   F* const smem = reinterpret_cast<F*>(smem_raw);
   F* const gbuf = smem + 2 * stage_rows * NP;  // G region (ADJ)
   const size_t rows_total = tile_smem_rows(MODE, C, NB, D, S, mse ? 1 : 0);
@@ -101,7 +111,20 @@ __global__ void __launch_bounds__(NP* S, (S > 1 ? 2 : 4) * (128 / NP))
   F* gf = static_cast<F*>(a.factor);
   const bool want_out = gout != nullptr;
   const bool want_z = HAS_Z && gzin != nullptr;  // RAW without accumulation reads no z
-  auto stage = [&](int st) -> F* { return smem + (size_t)st * stage_rows * NP; };
+  auto stage = [&](int st) -> F* { return smem + st * stage_rows * NP; };
+  // chunks per checkpoint (1 or 2) and the ring stage of chunk q in pass 2. Pass 1 puts
+  // chunk q in stage q & 1. With G = 2, pass 2 handles chunks in groups {2m, 2m + 1}; the
+  // next group's earlier chunk goes into the stage freed first (the later chunk's, back-
+  // substituted first), so the roles of the two stages alternate from group to group,
+  // counted from the last complete group (a last chunk alone keeps stage 0).
+  const int G = a.ck_group == 2 ? 2 : 1;
+  auto pstage = [&](int q) -> int {
+    if (G == 1) return q & 1;
+    if ((a.nch & 1) && q == a.nch - 1) return 0;
+    const int mlf = ((a.nch - 1) >> 1) - (a.nch & 1);
+    const int es = (mlf - (q >> 1)) & 1;
+    return (q & 1) ? es ^ 1 : es;
+  };
   auto rho_row = [&](int j, int k) -> int {  // j = 1..D
     if (MODE == MODE_ADJ || S > 1) return rowE + (j - 1) * C + k;
     if (j == 1) return rowL + k;
@@ -127,7 +150,7 @@ __global__ void __launch_bounds__(NP* S, (S > 1 ? 2 : 4) * (128 / NP))
 
   // z of chunk c (pass 2) into stage st: TMA on barrier `b`, or LDGSTS (own columns).
   auto copy_z = [&](int c, int st, int p0, uint64_t* b) {
-    F* Sz = stage(st) + (size_t)rowZ * NP;
+    F* Sz = stage(st) + rowZ * NP;
     if (a.tma) {
       if (tid == 0) tma_load_3d(Sz, &tm_z, b, p0, a.b0, c * C);
     } else {
@@ -139,7 +162,7 @@ __global__ void __launch_bounds__(NP* S, (S > 1 ? 2 : 4) * (128 / NP))
 #pragma unroll
         for (int j = 0; j < NBT; ++j) {
           const int b2 = h * NBT + j;
-          cp_async_elem<sizeof(F)>(Sz + (size_t)(k * NB + b2) * NP + pl,
+          cp_async_elem<sizeof(F)>(Sz + (k * NB + b2) * NP + pl,
                                    v ? gzin + ((size_t)t * a.B + a.b0 + b2) * a.P + p : gzin, v);
         }
       }
@@ -154,10 +177,10 @@ __global__ void __launch_bounds__(NP* S, (S > 1 ? 2 : 4) * (128 / NP))
       if (tid == 0) {
         mbar_arrive_expect_tx(&bar[st], tx_bytes + (with_z ? tz_bytes : 0u) + tm_bytes);
         tma_load_3d(Sg, &tm_x, &bar[st], p0, a.b0, c * C);
-        tma_load_2d(Sg + (size_t)rowW * NP, &tm_w, &bar[st], p0, c * C);
-        if (!a.lam_scalar) tma_load_2d(Sg + (size_t)rowL * NP, &tm_l, &bar[st], p0, c * C);
+        tma_load_2d(Sg + rowW * NP, &tm_w, &bar[st], p0, c * C);
+        if (!a.lam_scalar) tma_load_2d(Sg + rowL * NP, &tm_l, &bar[st], p0, c * C);
         if (with_z) copy_z(c, st, p0, &bar[st]);
-        if (has_m) tma_load_2d(Sg + (size_t)rowM * NP, &tm_m, &bar[st], p0, c * C);
+        if (has_m) tma_load_2d(Sg + rowM * NP, &tm_m, &bar[st], p0, c * C);
       }
     } else {
       const int p = p0 + pl;
@@ -168,7 +191,7 @@ __global__ void __launch_bounds__(NP* S, (S > 1 ? 2 : 4) * (128 / NP))
 #pragma unroll
         for (int j = 0; j < NBT; ++j) {
           const int b = h * NBT + j;
-          cp_async_elem<sizeof(F)>(Sg + (size_t)(k * NB + b) * NP + pl,
+          cp_async_elem<sizeof(F)>(Sg + (k * NB + b) * NP + pl,
                                    v ? gx_in + ((size_t)t * a.B + a.b0 + b) * a.P + p : gx_in, v);
         }
         if (h == 0 && !a.lam_scalar)
@@ -224,7 +247,7 @@ __global__ void __launch_bounds__(NP* S, (S > 1 ? 2 : 4) * (128 / NP))
     const int p0 = tile * NP;
     const int p = p0 + pl;
     const bool act = p < a.P;
-    // checkpoints: field f of chunk c of this CTA's tile at ck[(c * kFields + f) * NP]
+    // checkpoints: field f of checkpoint j (chunk j * G) of this CTA's tile at ck[(j * kFields + f) * NP]
     F* ck = static_cast<F*>(a.ckpt) + (size_t)blockIdx.x * a.nch * kFields * NP + pl;
 
     // ---------------- pass 1: forward sweep, checkpoints ----------------
@@ -248,15 +271,18 @@ __global__ void __launch_bounds__(NP* S, (S > 1 ? 2 : 4) * (128 / NP))
       if (c == 0) {
 #pragma unroll
         for (int m = 0; m < D; ++m)
-          if (m < T) s.init_weight(m, Sg[(size_t)(rowW + m) * NP + pl]);
+          if (m < T) s.init_weight(m, Sg[(rowW + m) * NP + pl]);
       }
-      F* ckc = ck + (size_t)c * kFields * NP;
-      if (h == 0) s.save_factor(ckc, NP);
-      s.save_y(ckc + (size_t)(kFF + h * kYT) * NP, NP);
+      if (G == 1 || (c & 1) == 0) {  // the checkpoint of chunk c (groups of G chunks)
+        F* ckc = ck + (size_t)(c >> (G - 1)) * kFields * NP;
+        if (h == 0) s.save_factor(ckc, NP);
+        s.save_y(ckc + (size_t)(kFF + h * kYT) * NP, NP);
+      }
       const int nd = min(C, T - c * C);
-      const F* Sx = Sg + (size_t)h * NBT * NP + pl;
-      const F* Sw = Sg + (size_t)rowW * NP + pl;
-      const F* Sl = Sg + (size_t)rowL * NP + pl;
+      const F* Sx = Sg + h * NBT * NP + pl;
+      const F* Sw = Sg + rowW * NP + pl;
+      const F* Sl = Sg + rowL * NP + pl;
+WS_UNROLL_N(WS_TILE_UNROLL)
       for (int k = 0; k < nd; ++k, Sx += NB * NP, Sw += NP, Sl += NP) {
         const int i = c * C + k;
         const F wi = Sw[0];
@@ -267,13 +293,13 @@ __global__ void __launch_bounds__(NP* S, (S > 1 ? 2 : 4) * (128 / NP))
         npos += wi > F(0);
         if (has_row) bad |= !(li > F(0)) || !finite_(li);
         F bv[NBT], rho[D], yh[NBT], invD;
-        const F mk = has_m ? Sg[(size_t)(rowM + k) * NP + pl] : F(1);
+        const F mk = has_m ? Sg[(rowM + k) * NP + pl] : F(1);
 #pragma unroll
         for (int j = 0; j < NBT; ++j) {
           const F xv = Sx[j * NP];
           bv[j] = MODE == MODE_SMOOTH ? (wi > F(0) ? wi * xv : F(0)) : xv;
           if (mse) {  // gz = scale m (z - target); masked days are inert whatever the target
-            const F e = mk > F(0) ? Sx[(size_t)rowZ * NP + j * NP] - xv : F(0);
+            const F e = mk > F(0) ? Sx[rowZ * NP + j * NP] - xv : F(0);
             bv[j] = mscale * mk * e;
             lsum = fma(mk * e, e, lsum);
           }
@@ -340,84 +366,112 @@ __global__ void __launch_bounds__(NP* S, (S > 1 ? 2 : 4) * (128 / NP))
     // into registers one chunk ahead so that its latency hides behind a chunk of work
     F pf[kFF + kYT];
     {
-      const F* ckc = ck + (size_t)(a.nch - 1) * kFields * NP;
+      const F* ckc = ck + (size_t)((a.nch - 1) >> (G - 1)) * kFields * NP;
 #pragma unroll
       for (int f = 0; f < kFF; ++f) pf[f] = ckc[(size_t)f * NP];
 #pragma unroll
       for (int f = 0; f < kYT; ++f) pf[kFF + f] = ckc[(size_t)(kFF + h * kYT + f) * NP];
     }
     for (int c = a.nch - 1; c >= 0; --c) {
-      const int st = c & 1;
-      if (c < a.nch - 2) {
-        const bool ok = wait_bar(st, c >= 1 ? 1 : 0);
-        if (__syncthreads_or(!ok)) {
-          abort_all();
-          return;
-        }
-      }
+      const int st = pstage(c);
+      // G = 2: the later chunk of a group (or a last chunk alone) leads: it recomputes the
+      // whole group from the group's checkpoint; the earlier chunk then back-substitutes
+      // from what the lead left in its stage.
+      const int c0 = G == 2 ? (c & ~1) : c;
+      const bool lead = G == 1 || (c & 1) || c == a.nch - 1;
       F* Sg = stage(st);
-      s.load_factor(pf, 1);
-      s.load_y(pf + kFF, 1);
-      if (c > 0) {
-        const F* ckc = ck + (size_t)(c - 1) * kFields * NP;
-#pragma unroll
-        for (int f = 0; f < kFF; ++f) pf[f] = ckc[(size_t)f * NP];
-#pragma unroll
-        for (int f = 0; f < kYT; ++f) pf[kFF + f] = ckc[(size_t)(kFF + h * kYT + f) * NP];
-      }
-      const int nd = min(C, T - c * C);
-      {
-        F* Sx = Sg + (size_t)h * NBT * NP + pl;
-        const F* Sw = Sg + (size_t)rowW * NP + pl;
-        const F* Sl = Sg + (size_t)rowL * NP + pl;
-        for (int k = 0; k < nd; ++k, Sx += NB * NP, Sw += NP, Sl += NP) {
-          const int i = c * C + k;
-          const F wi = Sw[0];
-          const F wa = Sw[D * NP];
-          const F li = a.lam_scalar ? lam_s : Sl[0];
-          const bool has_row = i < T - D;
-          F bv[NBT], rho[D], yh[NBT], invD;
-          const F mk = has_m ? Sg[(size_t)(rowM + k) * NP + pl] : F(1);
-#pragma unroll
-          for (int j = 0; j < NBT; ++j) {
-            const F xv = Sx[j * NP];
-            bv[j] = MODE == MODE_SMOOTH ? (wi > F(0) ? wi * xv : F(0)) : xv;
-            if (mse) bv[j] = mscale * mk * (mk > F(0) ? Sx[(size_t)rowZ * NP + j * NP] - xv : F(0));
+      if (lead) {
+        if (G == 1) {
+          if (c < a.nch - 2) {
+            const bool ok = wait_bar(st, c >= 1 ? 1 : 0);
+            if (__syncthreads_or(!ok)) {
+              abort_all();
+              return;
+            }
           }
-          s.factor_step(has_row, li, wa, rho, invD);
-          s.subst_step(rho, invD, bv, yh);
+        }
+        s.load_factor(pf, 1);
+        s.load_y(pf + kFF, 1);
+        if (c0 > 0) {
+          const F* ckc = ck + (size_t)((c0 - 1) >> (G - 1)) * kFields * NP;
 #pragma unroll
-          for (int j = 0; j < NBT; ++j) Sx[j * NP] = yh[j];
-          if (h == 0) {
+          for (int f = 0; f < kFF; ++f) pf[f] = ckc[(size_t)f * NP];
 #pragma unroll
-            for (int j = 1; j <= D; ++j) Sg[(size_t)rho_row(j, k) * NP + pl] = rho[j - 1];
-            if (MODE == MODE_SMOOTH && gf != nullptr && a.write_status && act) {
-              gf[((size_t)i * (D + 1)) * a.P + p] = okser ? invD : F(0);
+          for (int f = 0; f < kYT; ++f) pf[kFF + f] = ckc[(size_t)(kFF + h * kYT + f) * NP];
+        }
+        for (int q = c0; q <= c; ++q) {
+          // G = 2: wait for each chunk of the group just before recomputing it (the later
+          // chunk, loaded last, lands while the earlier one is recomputed)
+          const int sq = pstage(q);
+          if (G == 2 && ((pending >> sq) & 1u)) {
+            const bool later_pending = q < c && ((pending >> pstage(c)) & 1u);
+            const bool ok = wait_bar(sq, later_pending ? 1 : 0);
+            if (__syncthreads_or(!ok)) {
+              abort_all();
+              return;
+            }
+          }
+          F* Sq = stage(sq);
+          const int ndq = min(C, T - q * C);
+          F* Sx = Sq + h * NBT * NP + pl;
+          const F* Sw = Sq + rowW * NP + pl;
+          const F* Sl = Sq + rowL * NP + pl;
+WS_UNROLL_N(WS_TILE_UNROLL)
+          for (int k = 0; k < ndq; ++k, Sx += NB * NP, Sw += NP, Sl += NP) {
+            const int i = q * C + k;
+            const F wi = Sw[0];
+            const F wa = Sw[D * NP];
+            const F li = a.lam_scalar ? lam_s : Sl[0];
+            const bool has_row = i < T - D;
+            F bv[NBT], rho[D], yh[NBT], invD;
+            const F mk = has_m ? Sq[(rowM + k) * NP + pl] : F(1);
 #pragma unroll
-              for (int j = 1; j <= D; ++j) gf[((size_t)i * (D + 1) + j) * a.P + p] = okser ? rho[j - 1] : F(0);
+            for (int j = 0; j < NBT; ++j) {
+              const F xv = Sx[j * NP];
+              bv[j] = MODE == MODE_SMOOTH ? (wi > F(0) ? wi * xv : F(0)) : xv;
+              if (mse) bv[j] = mscale * mk * (mk > F(0) ? Sx[rowZ * NP + j * NP] - xv : F(0));
+            }
+            s.factor_step(has_row, li, wa, rho, invD);
+            s.subst_step(rho, invD, bv, yh);
+#pragma unroll
+            for (int j = 0; j < NBT; ++j) Sx[j * NP] = yh[j];
+            if (h == 0) {
+#pragma unroll
+              for (int j = 1; j <= D; ++j) Sq[rho_row(j, k) * NP + pl] = rho[j - 1];
+              if (MODE == MODE_SMOOTH && gf != nullptr && a.write_status && act) {
+                gf[((size_t)i * (D + 1)) * a.P + p] = okser ? invD : F(0);
+#pragma unroll
+                for (int j = 1; j <= D; ++j) gf[((size_t)i * (D + 1) + j) * a.P + p] = okser ? rho[j - 1] : F(0);
+              }
             }
           }
         }
       }
+      const int nd = min(C, T - c * C);
       if (want_z && !mse && c == a.nch - 1 && a.tma) {  // z of the two chunks resident from pass 1
         const bool ok = wait_bar(2, 0);
         if (__syncthreads_or(!ok)) {
           abort_all();
           return;
         }
-      } else if (S > 1) {
+      } else if (S > 1 && lead) {
         __syncthreads();  // rho rows written by the h = 0 threads; w/lambda reads done
       }
-      {
-        F* Sx = Sg + (size_t)((nd - 1) * NB + h * NBT) * NP + pl;
-        const F* Sz = Sg + (size_t)(rowZ + (nd - 1) * NB + h * NBT) * NP + pl;
+      // back substitution over the chunk; ACC (ADJ with accumulation onto g0, the refined
+      // adjoint) is a compile-time branch so that the plain adjoint carries none of its
+      // loads and settle statistics
+      auto bsub = [&](auto acc_tag) {
+        constexpr bool ACC = MODE == MODE_ADJ && decltype(acc_tag)::value;
+        F* Sx = Sg + ((nd - 1) * NB + h * NBT) * NP + pl;
+        const F* Sz = Sg + (rowZ + (nd - 1) * NB + h * NBT) * NP + pl;
+WS_UNROLL_N(WS_TILE_UNROLL)
         for (int k = nd - 1; k >= 0; --k, Sx -= NB * NP, Sz -= NB * NP) {
           const int i = c * C + k;
           F rho[D];
 #pragma unroll
-          for (int j = 1; j <= D; ++j) rho[j - 1] = Sg[(size_t)rho_row(j, k) * NP + pl];
+          for (int j = 1; j <= D; ++j) rho[j - 1] = Sg[rho_row(j, k) * NP + pl];
           F wk = F(0);
-          if (MODE == MODE_ADJ) wk = Sg[(size_t)(rowW + k) * NP + pl];
+          if (MODE == MODE_ADJ) wk = Sg[(rowW + k) * NP + pl];
           F dl = F(0);
 #pragma unroll
           for (int j = 0; j < NBT; ++j) {
@@ -431,13 +485,13 @@ __global__ void __launch_bounds__(NP* S, (S > 1 ? 2 : 4) * (128 / NP))
             if (MODE == MODE_RAW && want_z) out += Sz[j * NP];  // z0 + correction
             if (MODE == MODE_ADJ) {
               const F zv = Sz[j * NP];
-              if (a.accum && okser && act)  // g = g0 + correction
+              if (ACC && okser && act)  // g = g0 + correction
                 out += gg0[((size_t)i * a.B + a.b0 + h * NBT + j) * a.P + p];
               F cg = out, cz = zv;           // level q at day t
               F pg = gn[j], pz = zt[j][0];   // level q-1 at day t+1 (q = 1: the values)
               zt[j][0] = zv;
               gn[j] = out;
-              if (a.accum) {
+              if (ACC) {
                 dmx = fmax(dmx, fabs(acc));
                 gmx = fmax(gmx, fabs(out));
               }
@@ -454,30 +508,38 @@ __global__ void __launch_bounds__(NP* S, (S > 1 ? 2 : 4) * (128 / NP))
                 cz = nz;
               }
               dl = fma(cg, cz, dl);
-              if (a.accum && i < T - D) dgmx = fmax(dgmx, fabs(cg));
+              if (ACC && i < T - D) dgmx = fmax(dgmx, fabs(cg));
               if (!a.raw_g) out = wk * out;
             }
             nanacc = fma(out, F(0), nanacc);
             Sx[j * NP] = out;
           }
-          if (MODE == MODE_ADJ) gbuf[(size_t)(h * C + k) * NP + pl] = i < T - D ? dl : F(0);
+          if (MODE == MODE_ADJ) gbuf[(h * C + k) * NP + pl] = i < T - D ? dl : F(0);
         }
-      }
+      };
+      if (MODE == MODE_ADJ && a.accum)
+        bsub(std::true_type{});
+      else
+        bsub(std::false_type{});
       if (a.tma) fence_proxy_async_smem();
       __syncthreads();
       if (MODE == MODE_ADJ && gout2 != nullptr && h == 0) {
-        const F* Sl = Sg + (size_t)rowL * NP + pl;
-        for (int k = 0; k < nd; ++k) {
-          F dl = gbuf[(size_t)k * NP + pl];
+        const F* Sl = Sg + rowL * NP + pl;
+        F* dst = gout2 + (size_t)(c * C) * a.P + p;
+        const bool first_group = a.b0 == 0;  // later band groups add onto the first's sums
+        for (int k = 0; k < nd; ++k, dst += a.P) {
+          F dl = gbuf[k * NP + pl];
 #pragma unroll
-          for (int q = 1; q < S; ++q) dl += gbuf[(size_t)(q * C + k) * NP + pl];
+          for (int q = 1; q < S; ++q) dl += gbuf[(q * C + k) * NP + pl];
           F gl_t = okser ? -dl : F(0);
-          if (a.grad_loglam) gl_t *= a.lam_scalar ? lam_s : Sl[(size_t)k * NP];
+          if (a.grad_loglam) gl_t *= a.lam_scalar ? lam_s : Sl[k * NP];
           if (a.lam_scalar) {
             glam_sum += gl_t;
           } else if (act) {
-            F* dst = gout2 + (size_t)(c * C + k) * a.P + p;
-            *dst = a.b0 == 0 ? gl_t : *dst + gl_t;
+            if (first_group)
+              *dst = gl_t;
+            else
+              *dst += gl_t;
           }
         }
       }
@@ -489,20 +551,23 @@ __global__ void __launch_bounds__(NP* S, (S > 1 ? 2 : 4) * (128 / NP))
             gout[((size_t)(c * C + k) * a.B + a.b0 + b) * a.P + p] = Sg[(size_t)(k * NB + b) * NP + pl];
           }
       if (MODE == MODE_ADJ || !a.tma) __syncthreads();  // stage reads done before it is refilled
+      // refill the stage just freed: G = 1, chunk c - 2; G = 2, the next group's earlier
+      // chunk after a lead (it is recomputed first), its later chunk after the earlier one
+      const int nxt = G == 1 ? c - 2 : (lead ? ((c & 1) ? c - 3 : c - 2) : c - 1);
       if (a.tma) {
         if (tid == 0) {
           if (want_out) {
             tma_store_3d(&tm_o, Sg, p0, a.b0, c * C);
             bulk_commit();
           }
-          if (c >= 2) {
+          if (nxt >= 0) {
             bulk_wait_read_all();
-            issue(c - 2, st, p0, want_z);
+            issue(nxt, st, p0, want_z);
           }
         }
-        if (c >= 2) pending |= 1u << st;
-      } else if (c >= 2) {
-        issue(c - 2, st, p0, want_z);
+        if (nxt >= 0) pending |= 1u << st;
+      } else if (nxt >= 0) {
+        issue(nxt, st, p0, want_z);
       }
     }
     // per-series status; the band halves combine their non-finite flags

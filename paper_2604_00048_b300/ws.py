@@ -87,6 +87,8 @@ _lib.ws_smooth_partitioned.restype = ctypes.c_int
 _lib.ws_smooth_partitioned.argtypes = [ctypes.POINTER(Problem)] + [ctypes.c_void_p] * 6 + [_sz, ctypes.c_void_p]
 _lib.ws_tune_pixels_per_cta.restype = ctypes.c_int
 _lib.ws_tune_pixels_per_cta.argtypes = [ctypes.c_int32]
+_lib.ws_tune_checkpoint_group.restype = ctypes.c_int
+_lib.ws_tune_checkpoint_group.argtypes = [ctypes.c_int32]
 _lib.ws_selftest_wait.restype = ctypes.c_int
 _lib.ws_selftest_wait.argtypes = [_vp, _sz, _vp]
 _lib.ws_sync_status.restype = ctypes.c_int
@@ -570,11 +572,12 @@ def solve(fac: torch.Tensor, w: torch.Tensor, x: torch.Tensor, d: int = 2, *, z=
     return z
 
 
-def tune_set(ctas_per_sm: int = 0, chunk_days: int = 0, pixels_per_cta: int = 0):
-    """Process-wide tile tuning knobs (0 = automatic): CTAs per SM, a chunk-size cap and
-    the pixel series per CTA (64 or 128)."""
+def tune_set(ctas_per_sm: int = 0, chunk_days: int = 0, pixels_per_cta: int = 0, checkpoint_group: int = 0):
+    """Process-wide tile tuning knobs (0 = automatic): CTAs per SM, a chunk-size cap, the
+    pixel series per CTA (64 or 128) and the chunks per checkpoint (1 or 2)."""
     _check(_lib.ws_tune_set(int(ctas_per_sm), int(chunk_days)))
     _check(_lib.ws_tune_pixels_per_cta(int(pixels_per_cta)))
+    _check(_lib.ws_tune_checkpoint_group(int(checkpoint_group)))
 
 
 def sync_status(device=None, stream=None):

@@ -52,6 +52,9 @@ def test_null_pointers_and_flags_rejected(ws):
     assert ws.lib().ws_tune_set(2, 300) == ws.WS_EINVAL
     assert ws.lib().ws_tune_set(-1, 0) == ws.WS_EINVAL
     assert ws.lib().ws_tune_set(0, 0) == ws.WS_OK
+    assert ws.lib().ws_tune_checkpoint_group(3) == ws.WS_EINVAL
+    assert ws.lib().ws_tune_checkpoint_group(-1) == ws.WS_EINVAL
+    assert ws.lib().ws_tune_checkpoint_group(0) == ws.WS_OK
 
 
 def test_empty_problem_is_a_no_op(ws):
