@@ -282,31 +282,39 @@ __global__ void __launch_bounds__(NP* S, (S > 1 ? 2 : 4) * (128 / NP))
       const F* Sx = Sg + h * NBT * NP + pl;
       const F* Sw = Sg + rowW * NP + pl;
       const F* Sl = Sg + rowL * NP + pl;
+      // the day loop; MSE (ADJ with the loss fused in) is a compile-time branch
+      auto p1days = [&](auto mse_tag) {
+        constexpr bool MSE = MODE == MODE_ADJ && decltype(mse_tag)::value;
 WS_UNROLL_N(WS_TILE_UNROLL)
-      for (int k = 0; k < nd; ++k, Sx += NB * NP, Sw += NP, Sl += NP) {
-        const int i = c * C + k;
-        const F wi = Sw[0];
-        const F wa = Sw[D * NP];
-        const F li = a.lam_scalar ? lam_s : Sl[0];
-        const bool has_row = i < T - D;
-        bad |= !(wi >= F(0)) || !finite_(wi);
-        npos += wi > F(0);
-        if (has_row) bad |= !(li > F(0)) || !finite_(li);
-        F bv[NBT], rho[D], yh[NBT], invD;
-        const F mk = has_m ? Sg[(rowM + k) * NP + pl] : F(1);
+        for (int k = 0; k < nd; ++k, Sx += NB * NP, Sw += NP, Sl += NP) {
+          const int i = c * C + k;
+          const F wi = Sw[0];
+          const F wa = Sw[D * NP];
+          const F li = a.lam_scalar ? lam_s : Sl[0];
+          const bool has_row = i < T - D;
+          bad |= !(wi >= F(0)) || !finite_(wi);
+          npos += wi > F(0);
+          if (has_row) bad |= !(li > F(0)) || !finite_(li);
+          F bv[NBT], rho[D], yh[NBT], invD;
+          const F mk = MSE && has_m ? Sg[(rowM + k) * NP + pl] : F(1);
 #pragma unroll
-        for (int j = 0; j < NBT; ++j) {
-          const F xv = Sx[j * NP];
-          bv[j] = MODE == MODE_SMOOTH ? (wi > F(0) ? wi * xv : F(0)) : xv;
-          if (mse) {  // gz = scale m (z - target); masked days are inert whatever the target
-            const F e = mk > F(0) ? Sx[rowZ * NP + j * NP] - xv : F(0);
-            bv[j] = mscale * mk * e;
-            lsum = fma(mk * e, e, lsum);
+          for (int j = 0; j < NBT; ++j) {
+            const F xv = Sx[j * NP];
+            bv[j] = MODE == MODE_SMOOTH ? (wi > F(0) ? wi * xv : F(0)) : xv;
+            if (MSE) {  // gz = scale m (z - target); masked days are inert whatever the target
+              const F e = mk > F(0) ? Sx[rowZ * NP + j * NP] - xv : F(0);
+              bv[j] = mscale * mk * e;
+              lsum = fma(mk * e, e, lsum);
+            }
           }
+          s.factor_step(has_row, li, wa, rho, invD);
+          s.subst_step(rho, invD, bv, yh);
         }
-        s.factor_step(has_row, li, wa, rho, invD);
-        s.subst_step(rho, invD, bv, yh);
-      }
+      };
+      if (mse)
+        p1days(std::true_type{});
+      else
+        p1days(std::false_type{});
       __syncthreads();
       if (c + 2 < a.nch) issue(c + 2, st, p0, mse);
     }
@@ -416,35 +424,44 @@ WS_UNROLL_N(WS_TILE_UNROLL)
           F* Sx = Sq + h * NBT * NP + pl;
           const F* Sw = Sq + rowW * NP + pl;
           const F* Sl = Sq + rowL * NP + pl;
+          // the day loop; MSE (ADJ) and the factor output (SMOOTH) are compile-time branches
+          auto p2days = [&](auto xtra_tag) {
+            constexpr bool MSE = MODE == MODE_ADJ && decltype(xtra_tag)::value;
+            constexpr bool FAC = MODE == MODE_SMOOTH && decltype(xtra_tag)::value;
 WS_UNROLL_N(WS_TILE_UNROLL)
-          for (int k = 0; k < ndq; ++k, Sx += NB * NP, Sw += NP, Sl += NP) {
-            const int i = q * C + k;
-            const F wi = Sw[0];
-            const F wa = Sw[D * NP];
-            const F li = a.lam_scalar ? lam_s : Sl[0];
-            const bool has_row = i < T - D;
-            F bv[NBT], rho[D], yh[NBT], invD;
-            const F mk = has_m ? Sq[(rowM + k) * NP + pl] : F(1);
+            for (int k = 0; k < ndq; ++k, Sx += NB * NP, Sw += NP, Sl += NP) {
+              const int i = q * C + k;
+              const F wi = Sw[0];
+              const F wa = Sw[D * NP];
+              const F li = a.lam_scalar ? lam_s : Sl[0];
+              const bool has_row = i < T - D;
+              F bv[NBT], rho[D], yh[NBT], invD;
+              const F mk = MSE && has_m ? Sq[(rowM + k) * NP + pl] : F(1);
 #pragma unroll
-            for (int j = 0; j < NBT; ++j) {
-              const F xv = Sx[j * NP];
-              bv[j] = MODE == MODE_SMOOTH ? (wi > F(0) ? wi * xv : F(0)) : xv;
-              if (mse) bv[j] = mscale * mk * (mk > F(0) ? Sx[rowZ * NP + j * NP] - xv : F(0));
-            }
-            s.factor_step(has_row, li, wa, rho, invD);
-            s.subst_step(rho, invD, bv, yh);
+              for (int j = 0; j < NBT; ++j) {
+                const F xv = Sx[j * NP];
+                bv[j] = MODE == MODE_SMOOTH ? (wi > F(0) ? wi * xv : F(0)) : xv;
+                if (MSE) bv[j] = mscale * mk * (mk > F(0) ? Sx[rowZ * NP + j * NP] - xv : F(0));
+              }
+              s.factor_step(has_row, li, wa, rho, invD);
+              s.subst_step(rho, invD, bv, yh);
 #pragma unroll
-            for (int j = 0; j < NBT; ++j) Sx[j * NP] = yh[j];
-            if (h == 0) {
+              for (int j = 0; j < NBT; ++j) Sx[j * NP] = yh[j];
+              if (h == 0) {
 #pragma unroll
-              for (int j = 1; j <= D; ++j) Sq[rho_row(j, k) * NP + pl] = rho[j - 1];
-              if (MODE == MODE_SMOOTH && gf != nullptr && a.write_status && act) {
-                gf[((size_t)i * (D + 1)) * a.P + p] = okser ? invD : F(0);
+                for (int j = 1; j <= D; ++j) Sq[rho_row(j, k) * NP + pl] = rho[j - 1];
+                if (FAC && act) {
+                  gf[((size_t)i * (D + 1)) * a.P + p] = okser ? invD : F(0);
 #pragma unroll
-                for (int j = 1; j <= D; ++j) gf[((size_t)i * (D + 1) + j) * a.P + p] = okser ? rho[j - 1] : F(0);
+                  for (int j = 1; j <= D; ++j) gf[((size_t)i * (D + 1) + j) * a.P + p] = okser ? rho[j - 1] : F(0);
+                }
               }
             }
-          }
+          };
+          if (MODE == MODE_ADJ ? mse : (MODE == MODE_SMOOTH && gf != nullptr && a.write_status))
+            p2days(std::true_type{});
+          else
+            p2days(std::false_type{});
         }
       }
       const int nd = min(C, T - c * C);
