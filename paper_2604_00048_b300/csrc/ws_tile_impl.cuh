@@ -49,6 +49,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <limits>
 #include <type_traits>
 
 #include "ws_internal.h"
@@ -83,6 +84,7 @@ __global__ void __launch_bounds__(NP* S, (S > 1 ? 2 : 4) * (128 / NP))
   constexpr int kFF = SW::kFactorFields;
   constexpr int kFields = kFF + NB * D;
   constexpr int kYT = NBT * D;  // this thread's forward-substitution words in a checkpoint
+  constexpr F kFMax = std::numeric_limits<F>::max();
   // ADJ with the masked-MSE loss fused in: x is the target, the right-hand side
   // gz = scale * m_t * (z - target) is formed per day from the staged z, target and m
   const bool mse = MODE == MODE_ADJ && a.mse;
@@ -292,9 +294,9 @@ WS_UNROLL_N(WS_TILE_UNROLL)
           const F wa = Sw[D * NP];
           const F li = a.lam_scalar ? lam_s : Sl[0];
           const bool has_row = i < T - D;
-          bad |= !(wi >= F(0)) || !finite_(wi);
+          bad |= !(wi >= F(0) && wi <= kFMax);  // negative, NaN or infinite
           npos += wi > F(0);
-          if (has_row) bad |= !(li > F(0)) || !finite_(li);
+          if (has_row) bad |= !(li > F(0) && li <= kFMax);
           F bv[NBT], rho[D], yh[NBT], invD;
           const F mk = MSE && has_m ? Sg[(rowM + k) * NP + pl] : F(1);
 #pragma unroll
@@ -528,7 +530,10 @@ WS_UNROLL_N(WS_TILE_UNROLL)
               if (ACC && i < T - D) dgmx = fmax(dgmx, fabs(cg));
               if (!a.raw_g) out = wk * out;
             }
-            nanacc = fma(out, F(0), nanacc);
+            // a non-finite g or z reaches every earlier day through the back substitution,
+            // so the plain solves test day 0 once at the end; outputs that add a stored
+            // array (z0, g0) are tested day by day
+            if (ACC || MODE == MODE_RAW) nanacc = fma(out, F(0), nanacc);
             Sx[j * NP] = out;
           }
           if (MODE == MODE_ADJ) gbuf[(h * C + k) * NP + pl] = i < T - D ? dl : F(0);
@@ -588,6 +593,10 @@ WS_UNROLL_N(WS_TILE_UNROLL)
       }
     }
     // per-series status; the band halves combine their non-finite flags
+    if (MODE == MODE_SMOOTH || (MODE == MODE_ADJ && !a.accum)) {
+#pragma unroll
+      for (int j = 0; j < NBT; ++j) nanacc = fma(zc[j][0], F(0), nanacc);
+    }
     bool nonfin = !(nanacc == F(0));
     // settle test of the refined adjoint: the error left after the step, |delta|^2 / |g|
     // (the step squares a contracting relative error) plus g's own rounding, differenced

@@ -186,3 +186,28 @@ def test_adjoint_sparse_resolve_band_groups_and_outputs(ws, d):
     assert rel_err_per_series(gx2.cpu().numpy()[:, :, ok], graw[:, :, ok]) <= 1e-3
     assert _glam_err(glam.cpu().numpy()[:, ok], glr[:, ok]) <= 1e-3
     assert torch.equal(glam, glam3)
+
+
+@pytest.mark.parametrize("refine", [False, True])
+def test_adjoint_nonfinite_status(ws, refine):
+    """A NaN in gz on the first, a middle or the last day (or an infinite one) makes the
+    series' gradients non-finite: status WS_SERIES_NONFINITE; the other series stay OK.
+    (Sixty days in chunks of 8, two threads per pixel.)"""
+    ws.tune_set(0, 8)
+    T, P, d = 60, 70, 2
+    rc, g, c = tile_inputs("layer", P, T=T, B=10, revisit=1, p_valid=1.0)
+    zr, ok = dense.smooth_tile(c["x"], c["w"], c["lam"], d)
+    assert ok.all()
+    z = torch.as_tensor(zr, dtype=torch.float32, device="cuda")
+    gz = torch.randn(g["x"].shape, generator=torch.Generator().manual_seed(3)).to("cuda")
+    gz[0, 0, 3] = float("nan")
+    gz[29, 7, 10] = float("nan")
+    gz[T - 1, 9, 40] = float("nan")
+    gz[T - 1, 2, 41] = float("inf")
+    gx, glam, st = ws.smooth_adjoint(g["w"], g["lam"], z, gz, d, refine=refine)
+    ws.sync_status()
+    ws.tune_set(0, 0)
+    st = st.cpu().numpy()
+    bad = [3, 10, 40, 41]
+    assert np.all(st[bad] == ws.SERIES_NONFINITE)
+    assert np.all(np.delete(st, bad) == 0)
