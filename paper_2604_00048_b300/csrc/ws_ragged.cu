@@ -58,9 +58,9 @@ struct RaggedArgs {
   float* prevc;           // per series: max |correction| of the previous step (0 before the first)
   int32_t* list64;        // series re-solved in double-float
   int* count64;
-  double* ck64;           // double-float checkpoints (8 bytes each), kFieldsMax * max_nch64 per thread
+  double* ck64;           // double-float re-solve: per thread, (yhat, rho_1..rho_d) of every day
+                          // (8 bytes each), interleaved across the kernel's threads
   const int8_t* d_of;     // per series order
-  int max_nch64;
   float tau, tau_drop, tau_cond;
   const uint8_t* item_tiled;  // per item: 1 = its series are solved through the length-class tiles
 };
@@ -429,20 +429,20 @@ __global__ void __launch_bounds__(256) k_ragged_regroup(const int64_t* __restric
   }
 }
 
-// High-precision re-solve of one listed series by one thread: the same two-pass recurrence
-// in double-float (HP = dwf, about 48 bits) instead of FP32, inputs read directly from
-// global memory (a small share of the batch goes this way), checkpoints every kRC64 days in
-// the thread's global slot, the chunk's recomputed (yhat, rho) in local arrays. Overwrites
-// z of the series.
-constexpr int kRC64 = 64;
+// High-precision re-solve of one listed series by one thread: the rotation factor, forward
+// and back substitution in double-float (HP = dwf, about 48 bits) instead of FP32, inputs
+// read directly from global memory (a small share of the batch goes this way). The forward
+// sweep stores each day's (yhat, rho_1..rho_d) in the thread's workspace column (word f of
+// day i at st[(i * (1 + d) + f) * nt], nt = threads of the launch, so a warp's stores of one
+// day are contiguous); the backward sweep reads them back four days ahead of their use
+// instead of recomputing the factor. Overwrites z of the series.
 using HP = dwf;
-static_assert(sizeof(HP) == sizeof(double), "checkpoint slots hold 8-byte values");
+static_assert(sizeof(HP) == sizeof(double), "the per-day store holds 8-byte values");
 
 template <int D>
-__device__ void ragged64_series(const RaggedArgs& a, int sid, HP* ck) {
+__device__ void ragged64_series(const RaggedArgs& a, int sid, HP* st, size_t nt) {
   using SW = Sweep<HP, D, 1>;
-  constexpr int kFF = SW::kFactorFields;
-  constexpr int kF = kFF + D;
+  constexpr int kSF = 1 + D;  // words per day: yhat, rho_1..rho_D
   const int64_t os = a.off[sid];
   const int T = (int)(a.off[sid + 1] - os);
   const float* xs = a.x + (size_t)a.band * a.N + os;
@@ -455,61 +455,69 @@ __device__ void ragged64_series(const RaggedArgs& a, int sid, HP* ck) {
   SW s;
   s.reset();
   for (int m = 0; m < D && m < T; ++m) s.init_weight(m, w_at(m));
-  const int nch = (T + kRC64 - 1) / kRC64;
-  for (int c = 0; c < nch; ++c) {
-    s.save_factor(ck + (size_t)c * kF, 1);
-    s.save_y(ck + (size_t)c * kF + kFF, 1);
-    const int i1 = min(T, (c + 1) * kRC64);
-    for (int i = c * kRC64; i < i1; ++i) {
-      const HP wi = w_at(i);
-      HP bv[1] = {wi > zero ? wi * HP(xs[i]) : zero};
-      HP rho[D], yh[1], invD;
-      s.factor_step(i < T - D, i < T - D ? lam_at(i) : zero, w_at(i + D), rho, invD);
-      s.subst_step(rho, invD, bv, yh);
-    }
+  for (int i = 0; i < T; ++i) {
+    const HP wi = w_at(i);
+    HP bv[1] = {wi > zero ? wi * HP(xs[i]) : zero};
+    HP rho[D], yh[1], invD;
+    s.factor_step(i < T - D, i < T - D ? lam_at(i) : zero, w_at(i + D), rho, invD);
+    s.subst_step(rho, invD, bv, yh);
+    HP* e = st + (size_t)i * kSF * nt;
+    e[0] = yh[0];
+#pragma unroll
+    for (int j = 0; j < D; ++j) e[(size_t)(j + 1) * nt] = rho[j];
   }
+  // back substitution, z_i = yhat_i - sum_j rho_{i,j} z_{i+j}; four register sets hold the
+  // words of the next four days, each reloaded four days ahead of its use
   HP zc[D];
 #pragma unroll
   for (int j = 0; j < D; ++j) zc[j] = zero;
-  HP yk[kRC64], rk[kRC64][D];
-  for (int c = nch - 1; c >= 0; --c) {
-    s.load_factor(ck + (size_t)c * kF, 1);
-    s.load_y(ck + (size_t)c * kF + kFF, 1);
-    const int i0 = c * kRC64, nd = min(kRC64, T - i0);
-    for (int k = 0; k < nd; ++k) {
-      const int i = i0 + k;
-      const HP wi = w_at(i);
-      HP bv[1] = {wi > zero ? wi * HP(xs[i]) : zero};
-      HP rho[D], yh[1], invD;
-      s.factor_step(i < T - D, i < T - D ? lam_at(i) : zero, w_at(i + D), rho, invD);
-      s.subst_step(rho, invD, bv, yh);
-      yk[k] = yh[0];
+  auto load = [&](int i, HP (&v)[kSF]) {
+    const HP* e = st + (size_t)i * kSF * nt;
 #pragma unroll
-      for (int j = 0; j < D; ++j) rk[k][j] = rho[j];
-    }
-    for (int k = nd - 1; k >= 0; --k) {
-      HP acc = yk[k];
+    for (int f = 0; f < kSF; ++f) v[f] = e[(size_t)f * nt];
+  };
+  auto step = [&](int i, const HP (&v)[kSF]) {
+    HP acc = v[0];
 #pragma unroll
-      for (int j = 1; j <= D; ++j) acc = fma(-rk[k][j - 1], zc[j - 1], acc);
+    for (int j = 1; j <= D; ++j) acc = fma(-v[j], zc[j - 1], acc);
 #pragma unroll
-      for (int j = D - 1; j > 0; --j) zc[j] = zc[j - 1];
-      zc[0] = acc;
-      zs[i0 + k] = acc.to_float();
-    }
+    for (int j = D - 1; j > 0; --j) zc[j] = zc[j - 1];
+    zc[0] = acc;
+    zs[i] = acc.to_float();
+  };
+  HP b0[kSF], b1[kSF], b2[kSF], b3[kSF];
+  int i = T - 1;
+  if (i >= 0) load(i, b0);
+  if (i >= 1) load(i - 1, b1);
+  if (i >= 2) load(i - 2, b2);
+  if (i >= 3) load(i - 3, b3);
+  for (; i >= 3; i -= 4) {
+    step(i, b0);
+    if (i >= 4) load(i - 4, b0);
+    step(i - 1, b1);
+    if (i >= 5) load(i - 5, b1);
+    step(i - 2, b2);
+    if (i >= 6) load(i - 6, b2);
+    step(i - 3, b3);
+    if (i >= 7) load(i - 7, b3);
   }
+  if (i >= 0) step(i, b0);
+  if (i >= 1) step(i - 1, b1);
+  if (i >= 2) step(i - 2, b2);
 }
 
 __global__ void __launch_bounds__(128) k_ragged64(const RaggedArgs a) {
   const int gt = blockIdx.x * blockDim.x + threadIdx.x;
-  HP* ck = reinterpret_cast<HP*>(a.ck64) + (size_t)gt * a.max_nch64 * kFieldsMax;
+  const size_t nt = (size_t)gridDim.x * blockDim.x;
+  HP* st = reinterpret_cast<HP*>(a.ck64) + gt;
   const int n = *a.count64;
-  for (int j = gt; j < n; j += gridDim.x * blockDim.x) {
+  for (int j = gt; j < n; j += (int)nt) {
     const int sid = a.list64[j];
     const int d = a.d_of[sid];
-    if (d == 1) ragged64_series<1>(a, sid, ck);
-    else if (d == 2) ragged64_series<2>(a, sid, ck);
-    else if (d == 3) ragged64_series<3>(a, sid, ck);
-    else ragged64_series<4>(a, sid, ck);
+    if (d == 1) ragged64_series<1>(a, sid, st, nt);
+    else if (d == 2) ragged64_series<2>(a, sid, st, nt);
+    else if (d == 3) ragged64_series<3>(a, sid, st, nt);
+    else ragged64_series<4>(a, sid, st, nt);
   }
 }
 
@@ -625,7 +633,7 @@ struct ws_plan {
   int* d_count64 = nullptr;    // n_bands
   double* d_ck64 = nullptr;
   int8_t* d_dof = nullptr;     // n_series
-  int max_nch64 = 0, grid64 = 0;
+  int max_t64 = 0, sf64 = 1, grid64 = 0;  // longest series, words per day (1 + largest d)
   // regrouped items of refinement steps 2.. (two sets, written alternately)
   int creg[5] = {0, 0, 0, 0, 0};  // first slot of each order's region; creg[4] = all slots
   int32_t* d_corder = nullptr;     // 2 x creg[4]
@@ -700,7 +708,6 @@ static void fill_refine_args(const ws_plan* pl, RaggedArgs& a) {
   a.count64 = pl->d_count64 + a.band;
   a.ck64 = pl->d_ck64;
   a.d_of = pl->d_dof;
-  a.max_nch64 = pl->max_nch64;
   a.tau = kRefineTau;
   a.tau_drop = kRefineTauDrop;
   a.tau_cond = kRefineTauCond;
@@ -967,7 +974,7 @@ static int plan_ws(const ws_plan* pl, uint32_t flags, PlanWs* L) {
     L->prevc = off;   off += r256(4 * n);
     L->list64 = off;  off += r256(4 * n);
     L->count64 = off; off += r256(sizeof(int) * pl->rg.n_bands);
-    L->ck64 = off;    off += r256((size_t)pl->grid64 * 128 * std::max(1, pl->max_nch64) * kFieldsMax * sizeof(double));
+    L->ck64 = off;    off += r256((size_t)pl->grid64 * 128 * std::max(1, pl->max_t64) * pl->sf64 * sizeof(double));
     L->corder = off;  off += r256(2 * cs * 4);
     L->citem_d = off; off += r256(2 * cni);
     L->citem_t = off; off += r256(2 * cni * 4);
@@ -1083,7 +1090,10 @@ extern "C" int ws_plan_create(const ws_ragged* rg, ws_plan** out, void* stream) 
     cudaMemcpy(pl->d_item_t, itt.data(), itt.size() * 4, cudaMemcpyHostToDevice);
     cudaMemcpy(pl->d_dof, dd.data(), n, cudaMemcpyHostToDevice);
   }
-  for (const Item& it : items) pl->max_nch64 = std::max(pl->max_nch64, (int)((it.tmax + kRC64 - 1) / kRC64));
+  for (const Item& it : items) {
+    pl->max_t64 = std::max(pl->max_t64, (int)it.tmax);
+    pl->sf64 = std::max(pl->sf64, 1 + it.d);
+  }
   {
     int nd[4] = {0, 0, 0, 0};
     for (int i = 0; i < n; ++i) ++nd[dd[i] - 1];
