@@ -379,7 +379,7 @@ int ws_solve_adjoint_mse(const ws_problem* pb, const void* w, const void* lam, c
                          void* stream);
 
 /* Tuning knobs of the tile kernels, process-wide (0 = automatic): the number of CTAs
- * (128 pixels each) to fit on one SM, 1..8, which sets the shared memory per CTA, and
+ * (of the pixels per CTA in force) to fit on one SM, 1..32, which sets the shared memory per CTA, and
  * an upper bound on the days per staged chunk, 1..255. The chunk is the largest that
  * fits; registers may allow fewer CTAs than requested. ws_workspace_size() reflects the
  * current setting. Returns WS_EINVAL for out-of-range values. */

@@ -258,6 +258,16 @@ int tile_smooth(const ws_problem& P, const void* x, const void* w, const void* l
   return run_tile(P, MODE_SMOOTH, x, w, lam, nullptr, nullptr, z, nullptr, nullptr, status, 0, 0, workspace, st);
 }
 
+// One refinement step of a tile problem's solution z in place (the ragged plan's length
+// classes): r = W x - Omega z (double-word residual) into r, then z += Omega^{-1} r.
+// Workspace as tile_smooth's.
+int tile_refine(const ws_problem& P, const void* x, const void* w, const void* lam, void* z, void* r,
+                void* workspace, cudaStream_t st) {
+  int rc = launch_residual(P, x, w, lam, z, r, 0, static_cast<unsigned*>(workspace), st);
+  if (rc != WS_OK) return rc;
+  return run_tile(P, MODE_RAW, r, w, lam, nullptr, nullptr, z, nullptr, nullptr, nullptr, 1, 0, workspace, st);
+}
+
 size_t tile_workspace_bytes(const ws_problem& P) {
   size_t ck = 0;
   if (tile_ckpt_bytes(P, ck) != WS_OK) return 0;
@@ -798,7 +808,7 @@ extern "C" int ws_tune_checkpoint_group(int32_t chunks) {
 
 extern "C" int ws_tune_set(int32_t ctas_per_sm, int32_t chunk_days) {
   clear_error();
-  if (ctas_per_sm < 0 || ctas_per_sm > 8) return set_error(WS_EINVAL, "ctas_per_sm must be 0..8");
+  if (ctas_per_sm < 0 || ctas_per_sm > 32) return set_error(WS_EINVAL, "ctas_per_sm must be 0..32");
   if (chunk_days < 0 || chunk_days > 255) return set_error(WS_EINVAL, "chunk_days must be 0..255");
   g_tune_ctas = ctas_per_sm;
   g_tune_chunk = chunk_days;

@@ -105,6 +105,8 @@ int make_tmap(CUtensorMap* map, int dtype, int rank, const void* base, const uin
 // One smoothing tile launch sequence (ws_api.cu), used by the ragged plan's length classes.
 int tile_smooth(const ws_problem& P, const void* x, const void* w, const void* lam, void* z, uint8_t* status,
                 void* workspace, cudaStream_t st);
+int tile_refine(const ws_problem& P, const void* x, const void* w, const void* lam, void* z, void* r,
+                void* workspace, cudaStream_t st);
 size_t tile_workspace_bytes(const ws_problem& P);
 
 // GCV grid search (ws_gcv.cu): persistent grid, chunks and checkpoint bytes; launch.

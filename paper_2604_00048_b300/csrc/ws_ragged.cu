@@ -92,7 +92,7 @@ __device__ void ragged_item(const RaggedArgs& a, int item, float* sm, float* ck,
   const int T = live ? (int)(a.off[sid + 1] - off) : 0;
   const int nch = (a.item_t[item] + RC - 1) / RC;
   if (MODE == MODE_RAW && !a.active[item]) return;  // every series of the item has settled
-  if (MODE == MODE_SMOOTH && a.item_tiled != nullptr && a.item_tiled[item]) return;  // solved as tiles
+  if (a.item_tiled != nullptr && a.item_tiled[item]) return;  // solved (or refined) as tiles
   const float* xb = MODE == MODE_RAW ? a.resid : a.x + (size_t)a.band * a.N;
   float* zb = a.z + (size_t)a.band * a.N;
   auto stg = [&](int st) -> float* { return sm + (size_t)st * L::rows * kPitch; };
@@ -353,6 +353,7 @@ __global__ void __launch_bounds__(256) k_ragged_resid(const RaggedArgs a) {
   const int lane = threadIdx.x & 31;
   const int item = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   if (item >= a.n_items || !a.active[item]) return;
+  if (a.item_tiled != nullptr && a.item_tiled[item]) return;  // refined as tiles
   switch (a.item_d[item]) {
     case 1: ragged_resid_item<1>(a, item, lane); break;
     case 2: ragged_resid_item<2>(a, item, lane); break;
@@ -598,6 +599,74 @@ __global__ void __launch_bounds__(256) k_scatter(const RaggedArgs a, const int32
   }
 }
 
+// After the length classes' tile refinement step: z of the tile back into the packed
+// series, and per series the largest |correction| over its days (against the z it
+// replaces), for the step's settle test. NaN corrections order above every finite value
+// (the integer max of the bit patterns keeps them).
+__global__ void __launch_bounds__(256) k_scatter_refine(const RaggedArgs a, const int32_t* __restrict__ sids,
+                                                        int Pc, int Tc, const float* __restrict__ tz,
+                                                        float* __restrict__ tcorr) {
+  __shared__ float sz[32][33];
+  const int p0 = blockIdx.x * 32, t0 = blockIdx.y * 32, lx = threadIdx.x, ly = threadIdx.y;
+  for (int j = ly; j < 32; j += 8) {
+    const int t = t0 + j, p = p0 + lx;
+    sz[lx][j] = (t < Tc && p < Pc) ? tz[(size_t)t * Pc + p] : 0.f;
+  }
+  __syncthreads();
+  // a warp handles four series (rows j = ly + 8q) of 32 days: every load is issued before the
+  // first store (the stores could alias them for the compiler)
+  const int t = t0 + lx;
+  int sid[4];
+  int64_t os[4];
+  bool in[4];
+  float old[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int p = p0 + ly + 8 * q;
+    sid[q] = p < Pc ? sids[p] : -1;
+  }
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    os[q] = sid[q] >= 0 ? a.off[sid[q]] : 0;
+    in[q] = sid[q] >= 0 && t < (int)(a.off[sid[q] + 1] - os[q]);
+  }
+#pragma unroll
+  for (int q = 0; q < 4; ++q) old[q] = in[q] ? a.z[os[q] + t] : 0.f;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    if (sid[q] < 0) continue;  // uniform over the warp (one series per row)
+    int m = 0;
+    if (in[q]) {
+      const float v = sz[ly + 8 * q][lx];
+      m = __float_as_int(fabsf(v - old[q]));
+      a.z[os[q] + t] = v;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if (lx == 0) atomicMax(reinterpret_cast<int*>(tcorr) + sid[q], m);
+  }
+}
+
+// Settle test of the tile refinement step, per series of the length classes: the first step's
+// test of the per-lane correction kernel (no previous correction): listed for the
+// double-float re-solve above tau_cond * max|z|, settled and done below tau_drop * max|z|,
+// otherwise left to the next FP32 step.
+__global__ void __launch_bounds__(256) k_tile_settle(const RaggedArgs a, const int32_t* __restrict__ sids, int n,
+                                                     const float* __restrict__ tcorr) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int sid = sids[i];
+  if (sid < 0) return;
+  const float zm = a.zmax[sid], amax = tcorr[sid];
+  const bool small = amax <= a.tau_drop * zm;
+  const bool suspect = amax > a.tau_cond * zm;
+  const bool done = small || suspect;
+  const bool settled = !suspect && small;
+  a.prevc[sid] = amax;
+  a.conv[sid] = (settled ? 1 : 0) | (done ? 2 : 0) | (suspect ? 4 : 0);
+  if (suspect) a.list64[atomicAdd(a.count64, 1)] = sid;
+}
+
 }  // namespace ws
 
 using namespace ws;
@@ -628,6 +697,7 @@ struct ws_plan {
   uint8_t* d_active = nullptr; // n_items
   uint8_t* d_conv = nullptr;   // n_series
   float* d_zmax = nullptr;     // n_series
+  float* d_tcorr = nullptr;    // n_series: max |correction| of the length classes' tile refinement step
   float* d_prevc = nullptr;    // n_series
   int32_t* d_list64 = nullptr; // n_series
   int* d_count64 = nullptr;    // n_bands
@@ -650,6 +720,7 @@ struct ws_plan {
   // length-class tiles (WS_PLAN_TILES)
   std::vector<LenClass> classes;
   int32_t* d_class_sid = nullptr;
+  int n_class_sid = 0;         // entries of d_class_sid (-1: padding columns)
   uint8_t* d_item_tiled = nullptr;
   size_t tile_elems = 0, tile_ws_bytes = 0, tile_st_bytes = 0;
   float* d_tiles = nullptr;        // 4 * tile_elems floats: x, w, lambda, z
@@ -727,7 +798,7 @@ static int ragged_launch(ws_plan* pl, const void* x, const void* w, const void* 
                          bool tiles = false, const ItemSet* items = nullptr) {
   RaggedArgs a;
   memset(&a, 0, sizeof(a));
-  a.item_tiled = (tiles && mode == MODE_SMOOTH) ? pl->d_item_tiled : nullptr;
+  a.item_tiled = tiles ? pl->d_item_tiled : nullptr;
   a.off = pl->rg.offsets;
   a.order = pl->d_order;
   a.item_d = pl->d_item_d;
@@ -773,9 +844,11 @@ static int ragged_launch(ws_plan* pl, const void* x, const void* w, const void* 
 // Refinement of a ragged solution z in place. Up to kRefineSteps FP32 steps
 // (r = W x - Omega z with a double-word combination, z += Omega^{-1} r); an item drops out
 // once all its series have settled. Series still unsettled after the last step are listed
-// and solved again from scratch in double-float arithmetic.
+// and solved again from scratch in double-float arithmetic. tile_step: the length classes'
+// series had their first step on the class tiles (ragged_tiles); their settle test runs
+// here and the first per-lane step leaves their items out.
 static int ragged_refine(ws_plan* pl, const void* x, const void* w, const void* lam, void* z, int band,
-                         cudaStream_t st) {
+                         cudaStream_t st, bool tile_step = false) {
   RaggedArgs a;
   memset(&a, 0, sizeof(a));
   a.off = pl->rg.offsets;
@@ -795,6 +868,11 @@ static int ragged_refine(ws_plan* pl, const void* x, const void* w, const void* 
       cudaMemsetAsync(pl->d_prevc, 0, sizeof(float) * pl->rg.n_series, st) != cudaSuccess ||
       cudaMemsetAsync(a.count64, 0, sizeof(int), st) != cudaSuccess)
     return set_error(WS_ECUDA, "ragged: memset");
+  if (tile_step && pl->n_class_sid > 0) {
+    k_tile_settle<<<(pl->n_class_sid + 255) / 256, 256, 0, st>>>(a, pl->d_class_sid, pl->n_class_sid, pl->d_tcorr);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return set_error(WS_ECUDA, "ragged tile settle launch: %s", cudaGetErrorString(e));
+  }
   ItemSet cur{pl->d_order, pl->d_item_d, pl->d_item_t, pl->d_active, pl->n_items};
   const int4 reg = make_int4(pl->creg[0], pl->creg[1], pl->creg[2], pl->creg[3]);
   const int nci = pl->creg[4] / 32;
@@ -804,11 +882,13 @@ static int ragged_refine(ws_plan* pl, const void* x, const void* w, const void* 
     a.item_t = cur.item_t;
     a.active = cur.active;
     a.n_items = cur.n_items;
+    const bool skip_tiled = tile_step && k == 0;  // the plan's own items: d_item_tiled applies
+    a.item_tiled = skip_tiled ? pl->d_item_tiled : nullptr;
     const int gi = (cur.n_items + 7) / 8;
     k_ragged_resid<<<gi, 256, 0, st>>>(a);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return set_error(WS_ECUDA, "ragged residual launch: %s", cudaGetErrorString(e));
-    int rc = ragged_launch(pl, x, w, lam, z, nullptr, band, st, MODE_RAW, true, false, &cur);
+    int rc = ragged_launch(pl, x, w, lam, z, nullptr, band, st, MODE_RAW, true, skip_tiled, &cur);
     if (rc != WS_OK) return rc;
     if (k + 1 == kRefineSteps || nci == 0) continue;
     // the next step runs the still unsettled series only, regrouped
@@ -830,6 +910,7 @@ static int ragged_refine(ws_plan* pl, const void* x, const void* w, const void* 
   a.item_t = cur.item_t;
   a.active = cur.active;
   a.n_items = cur.n_items;
+  a.item_tiled = nullptr;
   const int gi = (cur.n_items + 7) / 8;
   k_ragged_collect<<<gi, 256, 0, st>>>(a);
   k_ragged64<<<pl->grid64, 128, 0, st>>>(a);
@@ -857,6 +938,7 @@ static int ragged_tiles(ws_plan* pl, const void* x, const void* w, const void* l
   float* tw = tx + pl->tile_elems;
   float* tl = tw + pl->tile_elems;
   float* tz = tl + pl->tile_elems;
+  float* tr = refine ? tz + pl->tile_elems : nullptr;  // residual of the refinement step
   size_t stoff = 0;
   // fork: the class streams wait for the work queued before on st (also under capture)
   if (cudaEventRecord(pl->tev[0], st) != cudaSuccess) return set_error(WS_ECUDA, "ragged tiles: fork");
@@ -882,6 +964,11 @@ static int ragged_tiles(ws_plan* pl, const void* x, const void* w, const void* l
     int rc = tile_smooth(P, tx + c.base, tw + c.base, tl + c.base, tz + c.base, pl->d_tile_st + stoff, wsk, cs);
     if (rc != WS_OK) return rc;
     k_scatter<<<grd, blk, 0, cs>>>(a, sids, c.Pc, c.Tc, tz + c.base, pl->d_tile_st + stoff);
+    if (refine) {  // the first refinement step on the tile, then z and the correction sizes back
+      rc = tile_refine(P, tx + c.base, tw + c.base, tl + c.base, tz + c.base, tr + c.base, wsk, cs);
+      if (rc != WS_OK) return rc;
+      k_scatter_refine<<<grd, blk, 0, cs>>>(a, sids, c.Pc, c.Tc, tz + c.base, pl->d_tcorr);
+    }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return set_error(WS_ECUDA, "ragged tiles launch: %s", cudaGetErrorString(e));
     stoff += (size_t)c.Pc;
@@ -934,7 +1021,7 @@ constexpr int kNCands = sizeof(kCands) / sizeof(kCands[0]);
 // is still to run), then the length-class tiles, then the refinement state.
 struct PlanWs {
   size_t ckpt = 0, tiles = 0, tile_st = 0, tile_ws = 0, refine = 0, total = 0;
-  size_t resid = 0, active = 0, conv = 0, zmax = 0, prevc = 0, list64 = 0, count64 = 0, ck64 = 0;
+  size_t resid = 0, active = 0, conv = 0, zmax = 0, tcorr = 0, prevc = 0, list64 = 0, count64 = 0, ck64 = 0;
   size_t corder = 0, citem_d = 0, citem_t = 0, cactive = 0, ccount = 0;
 };
 
@@ -956,8 +1043,8 @@ static int plan_ws(const ws_plan* pl, uint32_t flags, PlanWs* L) {
   off += r256(ck);
   const bool tiles = (flags & WS_PLAN_TILES) && pl->rg.n_bands == 1 && !pl->classes.empty();
   if (tiles) {
-    L->tiles = off;
-    off += r256(4 * pl->tile_elems * sizeof(float));
+    L->tiles = off;  // x, w, lambda, z (+ r of the refinement step) of every class
+    off += r256(((flags & WS_PLAN_REFINE) ? 5 : 4) * pl->tile_elems * sizeof(float));
     L->tile_st = off;
     off += r256(std::max<size_t>(1, pl->tile_st_bytes));
     L->tile_ws = off;
@@ -971,6 +1058,7 @@ static int plan_ws(const ws_plan* pl, uint32_t flags, PlanWs* L) {
     L->active = off;  off += r256(ni);
     L->conv = off;    off += r256(n);
     L->zmax = off;    off += r256(4 * n);
+    L->tcorr = off;   off += r256(4 * n);
     L->prevc = off;   off += r256(4 * n);
     L->list64 = off;  off += r256(4 * n);
     L->count64 = off; off += r256(sizeof(int) * pl->rg.n_bands);
@@ -998,6 +1086,7 @@ static void bind_ws(ws_plan* pl, uint32_t flags, const PlanWs& L, void* ws) {
   pl->d_active = refine ? reinterpret_cast<uint8_t*>(b + L.active) : nullptr;
   pl->d_conv = refine ? reinterpret_cast<uint8_t*>(b + L.conv) : nullptr;
   pl->d_zmax = refine ? reinterpret_cast<float*>(b + L.zmax) : nullptr;
+  pl->d_tcorr = refine ? reinterpret_cast<float*>(b + L.tcorr) : nullptr;
   pl->d_prevc = refine ? reinterpret_cast<float*>(b + L.prevc) : nullptr;
   pl->d_list64 = refine ? reinterpret_cast<int32_t*>(b + L.list64) : nullptr;
   pl->d_count64 = refine ? reinterpret_cast<int*>(b + L.count64) : nullptr;
@@ -1144,6 +1233,7 @@ extern "C" int ws_plan_create(const ws_ragged* rg, ws_plan** out, void* stream) 
     }
     pl->tile_elems = base;
     pl->tile_st_bytes = st;
+    pl->n_class_sid = (int)csid.size();
     if (!csid.empty()) {
       bool ok = cudaMalloc(&pl->d_class_sid, csid.size() * 4) == cudaSuccess &&
                 cudaMalloc(&pl->d_item_tiled, pl->n_items) == cudaSuccess;
@@ -1270,11 +1360,12 @@ extern "C" int ws_plan_execute(ws_plan* pl, const void* x, const void* w, const 
         return set_error(WS_ECUDA, "ragged: memset");
   if (!(flags & WS_PLAN_GRAPH) || pl->rg.n_bands > 1) {
     for (int b = 0; b < pl->rg.n_bands; ++b) {
-      if (tiles && refine && cudaMemsetAsync(pl->d_zmax, 0, sizeof(float) * pl->rg.n_series, st) != cudaSuccess)
+      if (tiles && refine && (cudaMemsetAsync(pl->d_zmax, 0, sizeof(float) * pl->rg.n_series, st) != cudaSuccess ||
+                              cudaMemsetAsync(pl->d_tcorr, 0, sizeof(float) * pl->rg.n_series, st) != cudaSuccess))
         return set_error(WS_ECUDA, "ragged: memset");
       if ((rc = ragged_launch(pl, x, w, lam, z, status, b, st, MODE_SMOOTH, refine, tiles)) != WS_OK) return rc;
       if (tiles && (rc = ragged_tiles(pl, x, w, lam, z, status, refine, st)) != WS_OK) return rc;
-      if (refine && (rc = ragged_refine(pl, x, w, lam, z, b, st)) != WS_OK) return rc;
+      if (refine && (rc = ragged_refine(pl, x, w, lam, z, b, st, tiles)) != WS_OK) return rc;
     }
     return WS_OK;
   }
@@ -1293,12 +1384,13 @@ extern "C" int ws_plan_execute(ws_plan* pl, const void* x, const void* w, const 
       cudaStreamDestroy(cs);
       return set_error(WS_ECUDA, "graph capture");
     }
-    if (tiles && refine && cudaMemsetAsync(pl->d_zmax, 0, sizeof(float) * pl->rg.n_series, cs) != cudaSuccess)
+    if (tiles && refine && (cudaMemsetAsync(pl->d_zmax, 0, sizeof(float) * pl->rg.n_series, cs) != cudaSuccess ||
+                            cudaMemsetAsync(pl->d_tcorr, 0, sizeof(float) * pl->rg.n_series, cs) != cudaSuccess))
       rc = set_error(WS_ECUDA, "ragged: memset");
     else
       rc = ragged_launch(pl, x, w, lam, z, status, 0, cs, MODE_SMOOTH, refine, tiles);
     if (rc == WS_OK && tiles) rc = ragged_tiles(pl, x, w, lam, z, status, refine, cs);
-    if (rc == WS_OK && refine) rc = ragged_refine(pl, x, w, lam, z, 0, cs);
+    if (rc == WS_OK && refine) rc = ragged_refine(pl, x, w, lam, z, 0, cs, tiles);
     cudaGraph_t g = nullptr;
     cudaError_t e = cudaStreamEndCapture(cs, &g);
     cudaStreamDestroy(cs);

@@ -48,7 +48,7 @@ def test_null_pointers_and_flags_rejected(ws):
     assert rc == ws.WS_EINVAL and "non-NULL" in ws.last_error()
     rc = ws.lib().ws_smooth_batch(ctypes.byref(pb), None, None, None, None, None, None, 0x80, None, 0, None)
     assert rc == ws.WS_EINVAL and "flags" in ws.last_error()
-    assert ws.lib().ws_tune_set(9, 0) == ws.WS_EINVAL
+    assert ws.lib().ws_tune_set(33, 0) == ws.WS_EINVAL
     assert ws.lib().ws_tune_set(2, 300) == ws.WS_EINVAL
     assert ws.lib().ws_tune_set(-1, 0) == ws.WS_EINVAL
     assert ws.lib().ws_tune_set(0, 0) == ws.WS_OK
