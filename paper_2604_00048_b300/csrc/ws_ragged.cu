@@ -66,6 +66,7 @@ struct RaggedArgs {
 };
 
 constexpr int kFieldsMax = 4 * 5 + 4;  // d(d+1) + d for d <= 4, one band
+constexpr int kHPBlocksPerSM = 5;    // double-float re-solve: 5 x 128 threads per SM (at most 102 registers each)
 
 template <int RC>
 struct RaggedSmem {
@@ -507,7 +508,7 @@ __device__ void ragged64_series(const RaggedArgs& a, int sid, HP* st, size_t nt)
   if (i >= 2) step(i - 2, b2);
 }
 
-__global__ void __launch_bounds__(128) k_ragged64(const RaggedArgs a) {
+__global__ void __launch_bounds__(128, kHPBlocksPerSM) k_ragged64(const RaggedArgs a) {
   const int gt = blockIdx.x * blockDim.x + threadIdx.x;
   const size_t nt = (size_t)gridDim.x * blockDim.x;
   HP* st = reinterpret_cast<HP*>(a.ck64) + gt;
@@ -767,7 +768,6 @@ constexpr int kRefineSteps = 3;     // FP32 refinement steps before the double-f
 constexpr float kRefineTau = 3e-5f;  // settled: correction <= tau * max|z|
 constexpr float kRefineTauDrop = 3e-6f;  // done (left out of later steps): correction <= tau_drop * max|z|
 constexpr float kRefineTauCond = 1e-4f;  // first correction above tau_cond * max|z|: double-float at once
-constexpr int kHPBlocksPerSM = 4;    // double-float re-solve: 4 x 128 threads per SM (128 registers each)
 
 static void fill_refine_args(const ws_plan* pl, RaggedArgs& a) {
   a.resid = pl->d_resid;
