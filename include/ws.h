@@ -465,8 +465,11 @@ typedef struct ws_plan_stats {
                                   (a slowly contracting step), are solved again in
                                   double-float arithmetic (hi + lo FP32 pairs,
                                   about 48 bits). The workspace holds N floats, about 30
-                                  bytes per series and about 0.76 GB of double-float
-                                  checkpoints at T = 3288. */
+                                  bytes per series, (1 + largest d) x 8 bytes per day of the
+                                  longest series for each thread of the re-solve (5 x 128 per SM)
+                                  (9.97 GB at T = 3288, d <= 3), and with WS_PLAN_TILES a
+                                  fifth tile array (the residual of the length classes' first
+                                  step, which runs on their tiles). */
 
 int ws_plan_create(const ws_ragged* rg, ws_plan** out, void* stream);
 
