@@ -45,6 +45,8 @@ def parse_args():
     ap.add_argument("--e2e-sub", type=int, default=16, help="sub-blocks of the end-to-end block")
     ap.add_argument("--e2e-streams", type=int, default=3, help="streams the end-to-end sub-blocks rotate over")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--ragged-no-autotune", action="store_true",
+                    help="ragged: keep the default configuration with the length-class tiles (profiling)")
     ap.add_argument("--no-ragged", action="store_true")
     ap.add_argument("--no-gcv", action="store_true")
     ap.add_argument("--no-learned", action="store_true")
@@ -272,7 +274,7 @@ def cpu_oracle_rate(x, w, lam, gz, d, target_s, with_bwd=True):
         f"{len(times)} timed runs after one warm-up")
 
 
-def ragged_measure(dev, steps, n=1 << 20):
+def ragged_measure(dev, steps, n=1 << 20, autotune=True):
     """The ragged batch: 1,048,576 series, T ~ U{120..3288}, d in {1,2,3}, one band, FP32,
     one persistent launch replayed from a CUDA graph with the autotuned configuration."""
     import torch
@@ -286,7 +288,7 @@ def ragged_measure(dev, steps, n=1 << 20):
     plan = ws.RaggedPlan(out["offsets"], out["order"])
     z = torch.empty_like(x)
     st = torch.empty(n, dtype=torch.uint8, device=dev)
-    plan.execute(x, w, lam, z=z, status=st, autotune=True, graph=True, tiles=True)  # tiles kept only if faster
+    plan.execute(x, w, lam, z=z, status=st, autotune=autotune, graph=True, tiles=True)  # tiles kept only if faster
 
     def timed(refine, tiles=True):
         for _ in range(2):
@@ -792,7 +794,7 @@ def run_only(args):
     elif args.only == "homo":
         res = homo_measure(dev, steps, args.series or 4096)
     else:
-        res = ragged_measure(dev, steps, args.series or (1 << 20))
+        res = ragged_measure(dev, steps, args.series or (1 << 20), autotune=not args.ragged_no_autotune)
     print(json.dumps({"only": args.only, **res}), flush=True)
 
 
