@@ -545,11 +545,15 @@ WS_UNROLL_N(WS_TILE_UNROLL)
         bsub(std::false_type{});
       if (a.tma) fence_proxy_async_smem();
       __syncthreads();
-      if (MODE == MODE_ADJ && gout2 != nullptr && h == 0) {
+      // dL/dlambda of the chunk's days: per-day lambda splits the days over the band halves
+      // (day k by half k mod S, so neither waits for the other at the next barrier); scalar
+      // lambda sums over all days in half 0
+      if (MODE == MODE_ADJ && gout2 != nullptr && (!a.lam_scalar || h == 0)) {
+        const int k0 = a.lam_scalar ? 0 : h, ks = a.lam_scalar ? 1 : S;
         const F* Sl = Sg + rowL * NP + pl;
-        F* dst = gout2 + (size_t)(c * C) * a.P + p;
+        F* dst = gout2 + (size_t)(c * C + k0) * a.P + p;
         const bool first_group = a.b0 == 0;  // later band groups add onto the first's sums
-        for (int k = 0; k < nd; ++k, dst += a.P) {
+        for (int k = k0; k < nd; k += ks, dst += (size_t)ks * a.P) {
           F dl = gbuf[k * NP + pl];
 #pragma unroll
           for (int q = 1; q < S; ++q) dl += gbuf[(q * C + k) * NP + pl];
