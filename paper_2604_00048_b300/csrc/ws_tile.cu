@@ -57,11 +57,14 @@ int plan_tile(const ws_problem& pb, int mode, int nb, TileCfg& cfg, int mse) {
   const int es = pb.dtype == WS_F64 ? 8 : 4;
   const int D = pb.d, T = pb.T;
   const int S = band_split(nb, pb.dtype == WS_F64);
-  // pixels per CTA: 128, or 64 (FP32) for deeper chunks at the same CTAs per SM. FP32
-  // defaults to 64: on the 10-band tile (d = 2, 3288 days) four 64-pixel CTAs per SM took
-  // 31.1 / 20.6 / 44.7 ms (adjoint / smooth / smooth's refinement step) against 31.6 / 21.2 /
-  // 45.2 ms for two 128-pixel ones (one CTA's barrier waits then idle fewer warps).
-  const bool np64 = g_tune_np != 128;
+  // pixels per CTA: 128, or 64 (FP32) for deeper chunks at the same CTAs per SM. FP32 band
+  // groups of two or more bands default to 64: on the 10-band tile (d = 2, 3288 days) four
+  // 64-pixel CTAs per SM took 31.1 / 20.6 / 44.7 ms (adjoint / smooth / smooth's refinement
+  // step) against 31.6 / 21.2 / 45.2 ms for two 128-pixel ones (one CTA's barrier waits then
+  // idle fewer warps); the 4-band layer workload (smooth + fused-loss adjoint) 4.1 against
+  // 4.8 ms. One band keeps 128: the ragged plan's one-band length classes, 28.2 against
+  // 29.2 ms (refined execute 169.5 against 173.6 ms).
+  const bool np64 = g_tune_np == 64 || (g_tune_np == 0 && nb > 1);
   const int np = (pb.dtype == WS_F32 && np64) ? 64 : 128;
   cfg.NP = np;
   cfg.S = S;

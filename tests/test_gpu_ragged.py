@@ -149,15 +149,18 @@ def test_ragged_status_and_scalar_lambda(ws):
     _check(out2, z, st, ids, lam_scalar=True)
 
 
-def test_ragged_full_size_sampled(ws):
+@pytest.mark.parametrize("tiles", [False, True])
+def test_ragged_full_size_sampled(ws, tiles):
     """1,048,576 series, T ~ U{120..3288}, d in {1,2,3} in equal thirds, per-day
-    lambda = 10^U[0,5]: autotuned, graph-replayed, one refinement step; 1024 sampled series:
-    those of order 1 and 2 against the banded FP64 oracle, the first 64 of order 3 against
-    the 50-digit solve (FP64 is not a reference there)."""
+    lambda = 10^U[0,5]: autotuned, graph-replayed, refined (FP32 steps, double-float
+    re-solve); with tiles the series of 64 days or more are solved and take their first
+    refinement step on the length-class tiles (the configuration the bench times). 1024
+    sampled series: those of order 1 and 2 against the banded FP64 oracle, the first 64 of
+    order 3 against the 50-digit solve (FP64 is not a reference there)."""
     rc = synth.RECIPES["ragged"]
     out = synth.generate_ragged(rc, 1 << 20, device="cuda")
     plan = ws.RaggedPlan(out["offsets"], out["order"])
-    z, st = plan.execute(out["x"], out["w"], out["lam"], autotune=True, graph=True, refine=True)
+    z, st = plan.execute(out["x"], out["w"], out["lam"], autotune=not tiles, graph=True, refine=True, tiles=tiles)
     ws.sync_status()
     ids = np.random.default_rng(11).choice(1 << 20, 1024, replace=False)
     ords = out["order"].cpu().numpy()
