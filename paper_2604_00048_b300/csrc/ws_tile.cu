@@ -7,14 +7,15 @@
 //     rotation of day i needs w_{i+d}) and lambda are staged in shared memory by TMA
 //     (cp.async.bulk.tensor, two stages, mbarrier completion). Each thread runs the
 //     rotation factor + forward substitution (ws_sweep.cuh) and stores its state at
-//     every chunk boundary to a checkpoint area in global memory.
-//   pass 2 (backward in time): for each chunk, last to first, the state is reloaded
-//     from its checkpoint and the chunk is recomputed from the staged inputs,
-//     writing yhat and rho in place over x, w and lambda; back substitution then
-//     runs over the chunk in reverse, writing z in place over yhat, and TMA stores
-//     the z box. The last two chunks of pass 1 are still resident and are reused.
+//     the start of every group of chunks (two by default) to a checkpoint area in global
+//     memory.
+//   pass 2 (backward in time): group by group, last to first, the state is reloaded
+//     from its checkpoint and the group's chunks (both resident) are recomputed from the
+//     staged inputs, writing yhat and rho in place; back substitution then runs over
+//     each chunk in reverse, writing z in place over yhat, and TMA stores the z box. The
+//     last two chunks of pass 1 are still resident and are reused.
 // Inputs are read twice and z written once (plus d(d+1)+B*d checkpoint words per
-// pixel per chunk), instead of spilling the factor and y for every day.
+// pixel per group of chunks), instead of spilling the factor and y for every day.
 //
 // Shared-memory stage (rows of NP elements):
 //   X [C*NB rows]  x[t][b] (pass 2: yhat, then z)

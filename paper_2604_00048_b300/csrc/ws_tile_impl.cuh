@@ -17,18 +17,19 @@
 //   pass 1 (forward in time): chunks of C days of the right-hand sides, w (C+d days: the
 //     rotation of day i needs w_{i+d}) and lambda are staged in shared memory by TMA
 //     (cp.async.bulk.tensor, two stages, mbarrier completion). Each thread runs the
-//     rotation factor + forward substitution (ws_sweep.cuh) and stores its state at every
-//     chunk boundary to a checkpoint area in global memory.
-//   pass 2 (backward in time): for each chunk, last to first, the state is reloaded from
-//     its checkpoint (loaded into registers one chunk ahead) and the chunk is recomputed
-//     from the staged inputs, writing yhat and rho in place; back substitution then runs
-//     over the chunk in reverse, writing the output in place over yhat, and TMA stores the
-//     output box. The last two chunks of pass 1 are still resident and are reused. RAW
-//     with accumulation and ADJ also need a per-day array in pass 2 (z0 or the forward
-//     output z): it is staged with the chunk's inputs, two chunks ahead like them (the two
-//     chunks resident from pass 1 get theirs when pass 1 ends).
+//     rotation factor + forward substitution (ws_sweep.cuh) and stores its state at the
+//     start of every group of G chunks (G = 2 by default) to a checkpoint area in global
+//     memory.
+//   pass 2 (backward in time): group by group, last to first, the state is reloaded from
+//     the group's checkpoint (loaded into registers one group ahead) and the group's chunks,
+//     both resident in the two stages, are recomputed from the staged inputs, writing yhat
+//     and rho in place; back substitution then runs over each chunk in reverse, writing the
+//     output in place over yhat, and TMA stores the output box. The last two chunks of pass
+//     1 are still resident and are reused. RAW with accumulation and ADJ also need a per-day
+//     array in pass 2 (z0 or the forward output z): it is staged with the chunk's inputs (the
+//     two chunks resident from pass 1 get theirs when pass 1 ends).
 // Inputs are read twice and the output written once, plus d(d+1) + B*d checkpoint words
-// per pixel per chunk, instead of spilling the factor and y for every day.
+// per pixel per group of chunks, instead of spilling the factor and y for every day.
 //
 // Shared memory (rows of NP elements):
 //   stage s (s = 0, 1):
