@@ -124,10 +124,11 @@ __global__ void __launch_bounds__(kGcvThreads, 2) k_gcv(const GcvArgs a) {
           if (m < T) s.init_weight(m, sw[0][m][pl]);
       s.save(ck + (size_t)c * kF * kGcvThreads, kGcvThreads);
       const int nd = min(kGcvC, T - c * kGcvC);
+#pragma unroll 2
       for (int k = 0; k < nd; ++k) {
         const int i = c * kGcvC + k;
         const float wi = sw[st][k][pl], wa = sw[st][k + D][pl], xi = sx[st][k][pl];
-        bad |= !(wi >= 0.f) || !isfinite(wi);
+        bad |= !(wi >= 0.f && wi <= 3.4028235e38f);  // negative, NaN or infinite
         if constexpr (DT) {
           bad |= !isfinite(stt[st][k][pl]);
           if (i + 1 < T) bad |= !(stt[st][k + 1][pl] > stt[st][k][pl]);
