@@ -134,6 +134,7 @@ __global__ void __launch_bounds__(post_np<F>(), sizeof(F) == 4 ? (D <= 2 ? (DT ?
           for (int q = m; q < D; ++q) ckc[(size_t)(f++) * kPostNP] = s.pr[m][q];
       }
       const int nd = min(kPostC, T - c * kPostC);
+#pragma unroll 2
       for (int k = 0; k < nd; ++k) {
         const int i = c * kPostC + k;
         const F wi = sw[st][k][tid], wa = sw[st][k + D][tid];
