@@ -46,7 +46,7 @@ __device__ __forceinline__ void dates_factor_step(Sweep<F, D, NB>& s, bool has_r
 #pragma unroll
     for (int m = 0; m < D; ++m) {
       const F a = s.pr[m][m], b = v[m];
-      const F h = fma(a, a, b * b);
+      const F h = fma_pos(a, a, b * b);
       const F ir = h > F(0) ? rsqrt_(h) : F(0);
       const F cs = h > F(0) ? a * ir : F(1);
       const F sn = b * ir;
@@ -61,7 +61,7 @@ __device__ __forceinline__ void dates_factor_step(Sweep<F, D, NB>& s, bool has_r
       s.pr[m][D] = sn * v[D];
       v[D] = cs * v[D];
     }
-    const F hn = fma(v[D], v[D], w_ahead > F(0) ? w_ahead : F(0));
+    const F hn = fma_pos(v[D], v[D], w_ahead > F(0) ? w_ahead : F(0));
     nd = hn > F(0) ? hn * rsqrt_(hn) : F(0);
   } else {
 #pragma unroll

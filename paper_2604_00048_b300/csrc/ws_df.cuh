@@ -103,6 +103,17 @@ __device__ __forceinline__ dwf fma(dwf a, dwf b, dwf c) { return a * b + c; }
 __device__ __forceinline__ float fma(float a, float b, float c) { return fmaf(a, b, c); }
 __device__ __forceinline__ double fma(double a, double b, double c) { return ::fma(a, b, c); }
 
+// a * b + c with a * b >= 0 and c >= 0 (sums of squares): the same-sign ("sloppy") double-word
+// addition, one TwoSum and one FastTwoSum, whose relative error stays about 2u^2 when the
+// terms cannot cancel (Joldes, Muller and Popescu, 2017).
+__device__ __forceinline__ dwf fma_pos(dwf a, dwf b, dwf c) {
+  const dwf p = a * b;
+  DW<float> s = two_sum(p.hi, c.hi);
+  s.lo += p.lo + c.lo;
+  const DW<float> v = fast_two_sum(s.hi, s.lo);
+  return {v.hi, v.lo};
+}
+
 // 1/sqrt(x) for x > 0: r0 from the hardware reciprocal square root (one MUFU op, relative
 // error below 2^-22.9), then one Newton step in double-float, r = r0 + r0 (1 - x r0^2) / 2,
 // which squares the relative error (about 1.5 * 2^-45.8, at the level of the double-float

@@ -48,6 +48,10 @@ __device__ __forceinline__ float rsqrt_(float v) {
 __device__ __forceinline__ double rsqrt_(double v) { return rsqrt(v); }
 __device__ __forceinline__ float sqrt_(float v) { return sqrtf(v); }
 __device__ __forceinline__ double sqrt_(double v) { return sqrt(v); }
+// a * b + c where both terms are known non-negative (sums of squares in the rotations); the
+// double-float overload (ws_df.cuh) uses the cheaper same-sign addition there
+__device__ __forceinline__ float fma_pos(float a, float b, float c) { return fmaf(a, b, c); }
+__device__ __forceinline__ double fma_pos(double a, double b, double c) { return ::fma(a, b, c); }
 __device__ __forceinline__ bool finite_(float v) { return isfinite(v); }
 __device__ __forceinline__ bool finite_(double v) { return isfinite(v); }
 
@@ -98,7 +102,7 @@ struct Sweep {
 #pragma unroll
       for (int m = 0; m < D; ++m) {
         const F a = pr[m][m], b = v[m];
-        const F h = fma(a, a, b * b);
+        const F h = fma_pos(a, a, b * b);
         const F ir = h > F(0) ? rsqrt_(h) : F(0);
         const F cs = h > F(0) ? a * ir : F(1);
         const F sn = b * ir;
@@ -113,7 +117,7 @@ struct Sweep {
         pr[m][D] = sn * v[D];
         v[D] = cs * v[D];
       }
-      const F hn = fma(v[D], v[D], w_ahead > F(0) ? w_ahead : F(0));
+      const F hn = fma_pos(v[D], v[D], w_ahead > F(0) ? w_ahead : F(0));
       nd = hn > F(0) ? hn * rsqrt_(hn) : F(0);
     } else {
 #pragma unroll
