@@ -251,6 +251,7 @@ __device__ void ragged_item(const RaggedArgs& a, int item, float* sm, float* ck,
     // error left (correction * ratio / (1 - ratio)) is below the correction; the first step
     // has no ratio and needs tau_drop. A series is done, and leaves the later steps, below
     // tau_drop * max|z|.
+    if (!(nanacc == 0.f)) amax = __int_as_float(0x7fc00000);  // a non-finite correction (fmaxf drops NaN)
     const float zm = live ? a.zmax[sid] : 0.f;
     const float prev = live ? a.prevc[sid] : 0.f;
     const bool small = amax <= a.tau_drop * zm;

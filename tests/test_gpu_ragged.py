@@ -150,6 +150,29 @@ def test_ragged_status_and_scalar_lambda(ws):
 
 
 @pytest.mark.parametrize("tiles", [False, True])
+def test_ragged_nonfinite_refined(ws, tiles):
+    """A NaN observation on a weighted day: with refinement the series keeps its non-finite
+    status (its corrections never settle and it goes on to the double-float re-solve, which
+    meets the same NaN), and every other series still matches the oracle (lengths 64..300:
+    with tiles they go through the length classes and their tile refinement step)."""
+    rc = synth.Recipe(**{**synth.RECIPES["ragged"].__dict__, "p_valid": 1.0, "revisit": 1, "lam_log10": (0.0, 3.0)})
+    out = synth.generate_ragged(rc, 200, device="cuda", t_range=(64, 300), orders=(1, 2, 3))
+    off = out["offsets"].cpu().numpy()
+    x = out["x"].clone()
+    x[int(off[7]) + 10] = float("nan")
+    out2 = dict(out)
+    out2["x"] = x
+    plan = ws.RaggedPlan(out["offsets"], out["order"])
+    z, st = plan.execute(x, out["w"], out["lam"], refine=True, tiles=tiles)
+    ws.sync_status()
+    stc = st.cpu().numpy()
+    assert stc[7] == ws.SERIES_NONFINITE
+    ids = [i for i in range(200) if i != 7]
+    assert np.all(stc[ids] == 0)
+    _check(out2, z, st, ids, tol=1e-4)
+
+
+@pytest.mark.parametrize("tiles", [False, True])
 def test_ragged_full_size_sampled(ws, tiles):
     """1,048,576 series, T ~ U{120..3288}, d in {1,2,3} in equal thirds, per-day
     lambda = 10^U[0,5]: autotuned, graph-replayed, refined (FP32 steps, double-float
