@@ -275,7 +275,7 @@ __device__ void ragged_item(const RaggedArgs& a, int item, float* sm, float* ck,
 }
 
 template <int RC, int MODE>
-__global__ void __launch_bounds__(512) k_ragged(const RaggedArgs a) {
+__global__ void __launch_bounds__(512, 1) k_ragged(const RaggedArgs a) {
   extern __shared__ __align__(16) float rsm[];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   float* sm = rsm + (size_t)wid * a.warp_rows * kPitch;
